@@ -1,0 +1,321 @@
+"""Seeded synthetic inputs for the OS-MPM hot path.
+
+This module builds particle sets, background grids, Dirichlet rules and
+coupling parameters for the paper's numerical examples (Sec. 4) and for the
+small unit cases the tests use.  It is the one module that both the CUDA path
+and the FP64 CPU oracle read, so it holds none of the method's arithmetic:
+no shape functions, no transfers, no constitutive law, no solver.  Everything
+here is geometry (which lattice points lie in which region), bookkeeping
+(particle volume and mass from the cell size and density) and seeded random
+perturbations.
+
+Particle sampling follows one fixed rule (used everywhere): a regular lattice
+of ``ppc_1d**d`` points per grid cell at offsets ``(q + 1/2) / ppc_1d`` of the
+cell, kept when the point lies inside the material region (half-open boxes,
+``r < R`` for disks).  Creation order is cells with x fastest (then y, then z)
+and, inside a cell, sub-points with x fastest; that order is the stable
+particle id.  ``V0 = dx**d / ppc``, ``m = rho * V0``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import itertools
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+BIG = 1.0e30  # stands for an unbounded side of a Dirichlet box
+
+FLAG_BOUNDARY = 1  # bit 0: particle belongs to the boundary layer P_alpha^partial (Sec. 3.2.1)
+
+
+@dataclass
+class Grid:
+    dim: int
+    origin: Tuple[float, ...]
+    dx: float
+    res: Tuple[int, ...]
+
+    @property
+    def n_nodes(self) -> int:
+        return int(np.prod(self.res))
+
+
+@dataclass
+class Dirichlet:
+    """Prescribed grid-node velocity on the nodes whose position lies in the
+    closed box [lo, hi].  ``kind`` 0: uniform velocity ``vel`` on the
+    components in ``comp_mask`` (bit c = component c).  ``kind`` 1: rigid
+    rotation about the axis through ``center`` along ``axis`` (3D; in 2D the
+    axis is z) by ``omega`` radians per unit time, all components."""
+
+    lo: Tuple[float, ...]
+    hi: Tuple[float, ...]
+    comp_mask: int = 0b111
+    vel: Tuple[float, ...] = (0.0, 0.0, 0.0)
+    kind: int = 0
+    center: Tuple[float, ...] = (0.0, 0.0, 0.0)
+    axis: Tuple[float, ...] = (0.0, 0.0, 1.0)
+    omega: float = 0.0
+
+
+@dataclass
+class Particles:
+    x: np.ndarray      # (N, d) float64
+    v: np.ndarray      # (N, d)
+    B: np.ndarray      # (N, d, d) APIC affine matrix
+    F: np.ndarray      # (N, d, d) deformation gradient
+    vol0: np.ndarray   # (N,)
+    mass: np.ndarray   # (N,)
+    E: np.ndarray      # (N,) Young's modulus
+    nu: np.ndarray     # (N,) Poisson's ratio
+    flags: np.ndarray  # (N,) uint8
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    def copy(self) -> "Particles":
+        return Particles(*(np.array(getattr(self, f.name), copy=True)
+                           for f in dataclasses.fields(self)))
+
+
+@dataclass
+class DomainSpec:
+    name: str
+    grid: Grid
+    particles: Particles
+    gravity: Tuple[float, ...]
+    dirichlet: List[Dirichlet] = field(default_factory=list)
+    newton_tol: float = 1e-8      # on max |delta x_hat| / dt  (m/s)
+    newton_max: int = 100
+    cg_rtol: float = 1e-6
+    cg_max: int = 20000
+    ls_max: int = 40
+
+
+@dataclass
+class SchwarzSpec:
+    M: int                # sub-cycling ratio dT / dt (Sec. 3.1)
+    k_max: int = 50       # Schwarz iteration cap (Alg. 1)
+    eps_conv: float = 1e-5   # Sec. 4: tolerance of the interface residuals
+    tau_B: float = 0.0    # boundary-node mass threshold on the coarse grid
+    tau_S: float = 0.0    # same on the fine grid
+    eps_tol: float = 0.0  # projection regulariser (Eq. spatial_projection)
+
+
+# ----------------------------------------------------------------------------
+# lattice sampling
+# ----------------------------------------------------------------------------
+
+def sample_lattice(origin: Sequence[float], dx: float,
+                   cell_lo: Sequence[int], cell_hi: Sequence[int],
+                   ppc_1d: int,
+                   inside: Callable[[np.ndarray], np.ndarray]) -> np.ndarray:
+    """Lattice points of cells ``cell_lo <= c < cell_hi`` (per axis) of the
+    grid with ``origin`` and ``dx``; returns the kept points (K, d) in creation
+    order."""
+    d = len(origin)
+    origin = np.asarray(origin, dtype=np.float64)
+    # cells, x fastest
+    axes_c = [np.arange(cell_lo[a], cell_hi[a]) for a in range(d)]
+    cells = np.stack(np.meshgrid(*axes_c[::-1], indexing="ij")[::-1], axis=-1).reshape(-1, d)
+    q = np.arange(ppc_1d)
+    subs = np.stack(np.meshgrid(*([q] * d), indexing="ij")[::-1], axis=-1).reshape(-1, d)
+    off = (subs + 0.5) / ppc_1d
+    pts = (cells[:, None, :] + off[None, :, :]).reshape(-1, d)
+    x = origin[None, :] + pts * dx
+    keep = inside(x)
+    return np.ascontiguousarray(x[keep])
+
+
+def make_particles(x: np.ndarray, dx: float, ppc_1d: int, rho: float,
+                   E: np.ndarray, nu: np.ndarray,
+                   flags: Optional[np.ndarray] = None,
+                   F0: Optional[np.ndarray] = None) -> Particles:
+    n, d = x.shape
+    vol = dx ** d / ppc_1d ** d
+    F = np.broadcast_to(np.eye(d), (n, d, d)).copy() if F0 is None else np.array(F0, dtype=np.float64)
+    return Particles(
+        x=np.array(x, dtype=np.float64),
+        v=np.zeros((n, d)),
+        B=np.zeros((n, d, d)),
+        F=F,
+        vol0=np.full(n, vol),
+        mass=np.full(n, rho * vol),
+        E=np.broadcast_to(np.asarray(E, dtype=np.float64), (n,)).copy(),
+        nu=np.broadcast_to(np.asarray(nu, dtype=np.float64), (n,)).copy(),
+        flags=np.zeros(n, np.uint8) if flags is None else flags.astype(np.uint8),
+    )
+
+
+def _box(lo, hi):
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    return lambda x: np.all((x >= lo) & (x < hi), axis=1)
+
+
+def _r2(x, c):
+    c = np.asarray(c, dtype=np.float64)
+    return np.sum((x - c[None, :]) ** 2, axis=1)
+
+
+# ----------------------------------------------------------------------------
+# configurations
+# ----------------------------------------------------------------------------
+
+def cantilever(dx: float = 0.0125, ppc_1d: int = 2, L: float = 1.0, H: float = 0.1,
+               E: float = 1e6, nu: float = 0.3, rho: float = 1000.0,
+               g: float = -9.81, origin=(-0.1, -1.0), res=(112, 96),
+               newton_tol: float = 1e-8) -> DomainSpec:
+    """2D cantilever beam [0,L]x[0,H] clamped at x=0 under gravity (Sec. 4.1
+    geometry; single domain).  The clamp fixes every grid node with x_i <= 0."""
+    nc = (int(round(L / dx)), int(round(H / dx)))
+    x = sample_lattice((0.0, 0.0), dx, (0, 0), nc, ppc_1d, _box((0.0, 0.0), (L, H)))
+    p = make_particles(x, dx, ppc_1d, rho, E, nu)
+    grid = Grid(2, tuple(origin), dx, tuple(res))
+    clamp = Dirichlet(lo=(-BIG, -BIG), hi=(0.5 * dx, BIG), comp_mask=0b11)
+    return DomainSpec("cantilever", grid, p, (0.0, g), [clamp], newton_tol=newton_tol)
+
+
+def eb_gravity(gamma: float, L=1.0, H=0.1, E=1e6, nu=0.3, rho=1000.0) -> float:
+    """Gravity that gives gravito-bending number ``gamma`` for a plane-strain
+    beam of height H and unit width: Gamma = rho g H L^3 / D,
+    D = E H^3 / (12 (1 - nu^2))  (Sec. 4.1)."""
+    D = E * H ** 3 / (12.0 * (1.0 - nu ** 2))
+    return gamma * D / (rho * H * L ** 3)
+
+
+def inclusion(dx_S: float = 0.005, M: int = 2, dx_B: float = 0.05,
+              r_inc: float = 0.05, E_inc: float = 1e8, E: float = 1e6, nu: float = 0.3,
+              rho: float = 1000.0, dT: float = 0.01, top_disp: float = 1e-3,
+              r_hole: float = 0.1, r_fine: float = 0.15, ppc_1d: int = 2,
+              newton_tol: float = 1e-8, cg_rtol: float = 1e-6):
+    """2D elastic inclusion for OS-MPM (Sec. 4.3 geometry with a displaced top
+    edge).  Coarse: matrix [0.1,0.9]^2 minus the disk r < r_hole on the grid
+    [0,1]^2 at dx_B.  Fine: disk r < r_fine on the grid [0.3,0.7]^2 at dx_S,
+    with the stiff inclusion r < r_inc.  Returns (coarse, fine, schwarz, dT)."""
+    c = (0.5, 0.5)
+    # coarse domain
+    nB = int(round(1.0 / dx_B)) + 1
+    gB = Grid(2, (0.0, 0.0), dx_B, (nB, nB))
+    lo_c = int(round(0.1 / dx_B))
+    hi_c = int(round(0.9 / dx_B))
+    xB = sample_lattice(gB.origin, dx_B, (lo_c, lo_c), (hi_c, hi_c), ppc_1d,
+                        lambda x: _box((0.1, 0.1), (0.9, 0.9))(x) & (_r2(x, c) >= r_hole ** 2))
+    sB = dx_B / ppc_1d
+    flB = np.where(_r2(xB, c) < (r_hole + sB) ** 2, FLAG_BOUNDARY, 0).astype(np.uint8)
+    pB = make_particles(xB, dx_B, ppc_1d, rho, E, nu, flB)
+    v_top = -top_disp / dT
+    dirB = [
+        Dirichlet(lo=(-BIG, -BIG), hi=(BIG, 0.1 + 0.5 * dx_B), comp_mask=0b11),
+        Dirichlet(lo=(-BIG, 0.9 - 0.5 * dx_B), hi=(BIG, BIG), comp_mask=0b10, vel=(0.0, v_top, 0.0)),
+    ]
+    coarse = DomainSpec("inclusion_coarse", gB, pB, (0.0, 0.0), dirB,
+                        newton_tol=newton_tol, cg_rtol=cg_rtol)
+    # fine domain
+    nS = int(round(0.4 / dx_S)) + 1
+    gS = Grid(2, (0.3, 0.3), dx_S, (nS, nS))
+    ncS = nS - 1
+    xS = sample_lattice(gS.origin, dx_S, (0, 0), (ncS, ncS), ppc_1d,
+                        lambda x: _r2(x, c) < r_fine ** 2)
+    sS = dx_S / ppc_1d
+    flS = np.where(_r2(xS, c) >= (r_fine - sS) ** 2, FLAG_BOUNDARY, 0).astype(np.uint8)
+    Es = np.where(_r2(xS, c) < r_inc ** 2, E_inc, E)
+    pS = make_particles(xS, dx_S, ppc_1d, rho, Es, nu, flS)
+    fine = DomainSpec("inclusion_fine", gS, pS, (0.0, 0.0), [],
+                      newton_tol=newton_tol, cg_rtol=cg_rtol)
+    sch = SchwarzSpec(M=M, k_max=50, eps_conv=1e-5,
+                      tau_B=rho * dx_B ** 2 / ppc_1d ** 2,
+                      tau_S=rho * dx_S ** 2 / ppc_1d ** 2,
+                      eps_tol=1e-12 * rho * dx_S ** 2)
+    return coarse, fine, sch, dT
+
+
+def block(dim: int = 2, n_cells=(6, 5), dx: float = 0.1, ppc_1d: int = 2,
+          E: float = 1e5, nu: float = 0.3, rho: float = 1000.0, margin: int = 3,
+          gravity=None) -> DomainSpec:
+    """A box of material of n_cells cells starting at the origin, with a grid
+    that leaves ``margin`` empty cells on every side.  No Dirichlet rules."""
+    nc = tuple(n_cells[:dim])
+    x = sample_lattice((0.0,) * dim, dx, (0,) * dim, nc, ppc_1d,
+                       _box((0.0,) * dim, tuple(n * dx for n in nc)))
+    p = make_particles(x, dx, ppc_1d, rho, E, nu)
+    origin = tuple(-margin * dx for _ in range(dim))
+    res = tuple(n + 2 * margin + 1 for n in nc)
+    g = tuple(gravity) if gravity is not None else (0.0,) * dim
+    return DomainSpec(f"block{dim}d", Grid(dim, origin, dx, res), p, g, [])
+
+
+def perturb(spec: DomainSpec, seed: int, v_scale=0.1, B_scale=0.0025, F_scale=0.02) -> DomainSpec:
+    """Seeded random particle velocities, affine matrices and deformation
+    gradients near identity (for unit tests of the transfers and the solver)."""
+    rng = np.random.default_rng(seed)
+    p = spec.particles.copy()
+    n, d = p.x.shape
+    p.v = v_scale * rng.standard_normal((n, d))
+    p.B = B_scale * rng.standard_normal((n, d, d))
+    p.F = np.eye(d)[None] + F_scale * rng.standard_normal((n, d, d))
+    return dataclasses.replace(spec, particles=p)
+
+
+def jitter_positions(spec: DomainSpec, seed: int, frac: float = 0.2) -> DomainSpec:
+    """Seeded random displacement of every particle by up to ``frac`` of a
+    cell along each axis (breaks the lattice's symmetry)."""
+    rng = np.random.default_rng(seed)
+    p = spec.particles.copy()
+    p.x = p.x + frac * spec.grid.dx * rng.uniform(-1.0, 1.0, p.x.shape)
+    return dataclasses.replace(spec, particles=p)
+
+
+def splitmix64(seed: int) -> Tuple[int, int]:
+    """One step of the SplitMix64 generator (Steele, Lea, Flood 2014):
+    returns (next_state, output)."""
+    mask = (1 << 64) - 1
+    state = (seed + 0x9E3779B97F4A7C15) & mask
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+    z = z ^ (z >> 31)
+    return state, z
+
+
+def uniform3(seed: int) -> Tuple[float, float, float]:
+    """Three U[0,1) draws from SplitMix64 started at ``seed`` (53-bit mantissa)."""
+    out = []
+    s = seed
+    for _ in range(3):
+        s, z = splitmix64(s)
+        out.append((z >> 11) * (1.0 / (1 << 53)))
+    return tuple(out)
+
+
+def inclusion_instance(i: int, scaled: bool = False, **kw):
+    """Instance i of the batched inclusion family: r_inc = 0.03 + 0.05 u1,
+    E_inc = 10^(7 + 2 u2), fine dx 0.01 if u3 < 0.5 else 0.005 (literal) or
+    0.0025 / 0.001 (scaled)."""
+    u1, u2, u3 = uniform3(0x05AD0000 + i)
+    r_inc = 0.03 + 0.05 * u1
+    E_inc = 10.0 ** (7.0 + 2.0 * u2)
+    if scaled:
+        dx_S = 0.0025 if u3 < 0.5 else 0.001
+    else:
+        dx_S = 0.01 if u3 < 0.5 else 0.005
+    return inclusion(dx_S=dx_S, M=2, r_inc=r_inc, E_inc=E_inc, **kw)
+
+
+def identical_pair(spec: DomainSpec, M: int = 1):
+    """Two copies of one domain (same grid, same particles, every particle a
+    boundary particle) for the reduction case where every boundary node of
+    one grid coincides with one of the other and the mass tie makes the
+    coarse grid the donor everywhere."""
+    pB = spec.particles.copy()
+    pB.flags = np.full(pB.n, FLAG_BOUNDARY, np.uint8)
+    pS = pB.copy()
+    B = dataclasses.replace(spec, name=spec.name + "_B", particles=pB)
+    S = dataclasses.replace(spec, name=spec.name + "_S", particles=pS)
+    rho_m = float(pB.mass[0])
+    sch = SchwarzSpec(M=M, k_max=20, eps_conv=1e-5, tau_B=rho_m, tau_S=rho_m,
+                      eps_tol=1e-12 * rho_m)
+    return B, S, sch

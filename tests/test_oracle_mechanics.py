@@ -1,0 +1,206 @@
+"""Pins of the oracle's constitutive law, incremental potential, Newton
+solver and single-domain step against textbook facts (no GPU)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import osmpm_oracle as O
+from paper_2605_09097_gb300 import workloads as W
+
+
+def _rand_F(n, d, scale, seed):
+    rng = np.random.default_rng(seed)
+    return np.eye(d)[None] + scale * rng.standard_normal((n, d, d))
+
+
+def test_lame_inverse_relations():
+    E = np.array([1e6, 2e5, 3.3e7])
+    nu = np.array([0.3, 0.4, 0.1])
+    mu, lam = O.lame(E, nu)
+    np.testing.assert_allclose(mu * (3 * lam + 2 * mu) / (lam + mu), E, rtol=1e-14)
+    np.testing.assert_allclose(lam / (2 * (lam + mu)), nu, rtol=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_rest_state_is_stress_free(d):
+    F = np.broadcast_to(np.eye(d), (3, d, d)).copy()
+    mu, lam = np.full(3, 2.0), np.full(3, 3.0)
+    np.testing.assert_array_equal(O.psi(F, mu, lam), 0.0)
+    np.testing.assert_allclose(O.pk1(F, mu, lam), 0.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("scale", [0.05, 0.3])
+def test_pk1_is_derivative_of_psi(d, scale):
+    F = _rand_F(6, d, scale, 11 + d)
+    mu, lam = np.full(6, 1.3), np.full(6, 2.1)
+    P = O.pk1(F, mu, lam)
+    h = 1e-6
+    for a in range(d):
+        for b in range(d):
+            E = np.zeros((d, d))
+            E[a, b] = h
+            fd = (O.psi(F + E, mu, lam) - O.psi(F - E, mu, lam)) / (2 * h)
+            np.testing.assert_allclose(P[:, a, b], fd, rtol=1e-7, atol=1e-8)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_tangent_is_derivative_of_pk1(d):
+    F = _rand_F(5, d, 0.2, 21 + d)
+    mu, lam = np.full(5, 1.3), np.full(5, 2.1)
+    A = O.dpdf(F, mu, lam)
+    h = 1e-6
+    for b in range(d):
+        for e in range(d):
+            E = np.zeros((d, d))
+            E[b, e] = h
+            fd = (O.pk1(F + E, mu, lam) - O.pk1(F - E, mu, lam)) / (2 * h)
+            np.testing.assert_allclose(A[:, :, :, b, e], fd, rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_small_strain_limit_is_hooke(d):
+    rng = np.random.default_rng(3)
+    S = rng.standard_normal((4, d, d))
+    S = 0.5 * (S + np.transpose(S, (0, 2, 1)))
+    eps = 1e-5
+    mu, lam = np.full(4, 1.7), np.full(4, 0.9)
+    e = eps * S
+    hooke = 0.5 * lam * np.trace(e, axis1=1, axis2=2) ** 2 + mu * np.sum(e * e, axis=(1, 2))
+    got = O.psi(np.eye(d)[None] + e, mu, lam)
+    np.testing.assert_allclose(got, hooke, rtol=1e-4)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_frame_indifference(d):
+    F = _rand_F(4, d, 0.2, 31)
+    mu, lam = np.full(4, 1.0), np.full(4, 4.0)
+    R = O.rotation_matrix([1, 2, 3], 0.7, d)
+    RF = np.einsum("ab,pbc->pac", R, F)
+    np.testing.assert_allclose(O.psi(RF, mu, lam), O.psi(F, mu, lam), rtol=1e-12)
+    np.testing.assert_allclose(O.pk1(RF, mu, lam), np.einsum("ab,pbc->pac", R, O.pk1(F, mu, lam)),
+                               atol=1e-12)
+
+
+def test_inverted_element_has_infinite_energy():
+    F = np.array([[[1.0, 0.0], [0.0, -0.5]]])
+    assert np.isinf(O.psi(F, np.ones(1), np.ones(1)))[0]
+
+
+def _problem(dim=2, seed=0, dt=1e-2, E=1e5):
+    spec = W.perturb(W.jitter_positions(W.block(dim, n_cells=(4, 3, 3), dx=0.1, E=E,
+                                                 gravity=(0.3, -9.8, 0.5)[:dim]), seed), seed + 1)
+    gf = O.p2g(spec.particles, spec.grid)
+    mask, vel = O.dirichlet_nodes(spec.grid, [], dt)
+    return O.make_problem(spec.particles, spec.grid, gf, dt, spec.gravity, mask, vel)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gradient_matches_energy_fd(dim):
+    pr = _problem(dim)
+    rng = np.random.default_rng(5)
+    u = O.initial_guess(pr) + 1e-3 * rng.standard_normal((pr.grid.n_nodes, dim)) * pr.gf.active[:, None]
+    g = O.gradient(pr, u)
+    act = np.nonzero(pr.gf.active)[0]
+    h = 1e-7
+    for i in act[:: max(1, act.size // 12)]:
+        for a in range(dim):
+            e = np.zeros_like(u)
+            e[i, a] = h
+            fd = (O.energy(pr, u + e) - O.energy(pr, u - e)) / (2 * h)
+            np.testing.assert_allclose(g[i, a], fd, rtol=2e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_hessian_matches_gradient_fd(dim):
+    pr = _problem(dim, seed=3)
+    rng = np.random.default_rng(6)
+    u = O.initial_guess(pr) + 1e-3 * rng.standard_normal((pr.grid.n_nodes, dim)) * pr.gf.active[:, None]
+    H = O.hessian(pr, u)
+    d = rng.standard_normal(u.shape) * pr.gf.active[:, None]
+    Hd = (H @ d.reshape(-1)).reshape(u.shape)
+    h = 1e-6
+    fd = (O.gradient(pr, u + h * d) - O.gradient(pr, u - h * d)) / (2 * h)
+    np.testing.assert_allclose(Hd, fd, rtol=1e-6, atol=1e-4 * np.abs(Hd).max())
+    # symmetric
+    assert abs(H - H.T).max() <= 1e-9 * abs(H).max()
+
+
+def test_energy_change_equals_difference():
+    pr = _problem(2, seed=8)
+    rng = np.random.default_rng(2)
+    u = O.initial_guess(pr)
+    s = 1e-2 * rng.standard_normal(u.shape) * pr.gf.active[:, None]
+    for alpha in (1.0, 0.25):
+        np.testing.assert_allclose(O.energy_change(pr, u, s, alpha),
+                                   O.energy(pr, u + alpha * s) - O.energy(pr, u), rtol=1e-9)
+
+
+def test_free_flight_is_exact():
+    """Uniform velocity, B = 0, no gravity, no walls: the step is a rigid
+    translation (one Newton iteration, F stays I, x += dt v)."""
+    spec = W.block(2, n_cells=(4, 3), dx=0.1)
+    spec.particles.v[:] = np.array([0.3, -0.2])
+    ds = O.DomainState.create(spec)
+    ns = O.NewtonStats()
+    x0 = ds.p.x.copy()
+    O.step(ds, 0.01, ns)
+    assert ns.iters == 1
+    np.testing.assert_allclose(ds.p.x, x0 + 0.01 * np.array([0.3, -0.2]), atol=1e-15)
+    np.testing.assert_allclose(ds.p.F, np.broadcast_to(np.eye(2), ds.p.F.shape), atol=1e-14)
+    np.testing.assert_allclose(ds.p.v, np.broadcast_to([0.3, -0.2], ds.p.v.shape), atol=1e-14)
+
+
+def test_zero_stiffness_free_fall():
+    """With a vanishing modulus each node falls freely: v^{n+1} = v^n + dt g."""
+    spec = W.block(2, n_cells=(3, 3), dx=0.1, E=1e-12, gravity=(0.0, -9.81))
+    ds = O.DomainState.create(spec)
+    O.step(ds, 0.01)
+    np.testing.assert_allclose(ds.p.v[:, 1], -9.81 * 0.01, rtol=1e-9)
+    np.testing.assert_allclose(ds.p.v[:, 0], 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_prescribed_affine_deformation_is_uniform(dim):
+    """Nodes within two cells of the material's edge follow the affine map
+    (F_t - I)(x - x0); at a quasi-static step (huge dt) the interior nodes
+    follow it too and every particle gets F = F_t (Newton on the nonlinear
+    law, checked against the prescribed value)."""
+    spec = W.block(dim, n_cells=(8, 8, 6), dx=0.1, E=1e5)
+    g = spec.grid
+    Ft = np.eye(dim)
+    Ft[0, 0], Ft[dim - 1, dim - 1] = 1.02, 0.97
+    Ft[0, 1] = 0.01
+    xi = O.node_positions(g)
+    lo = np.zeros(dim) + 1.5 * g.dx
+    hi = np.array([8, 8, 6][:dim]) * g.dx - 1.5 * g.dx
+    interior = np.all((xi > lo) & (xi < hi), axis=1)
+    dt = 1e3
+    vel = (xi @ (Ft - np.eye(dim)).T) / dt
+    ds = O.DomainState.create(spec)
+    gf = O.p2g(ds.p, g)
+    u = O.solve_domain(ds, gf, dt, ~interior, vel)
+    np.testing.assert_allclose(u[gf.active], (xi @ (Ft - np.eye(dim)).T)[gf.active], atol=1e-8)
+    ds.p = O.g2p(ds.p, g, u, dt)
+    np.testing.assert_allclose(ds.p.F, np.broadcast_to(Ft, ds.p.F.shape), atol=1e-8)
+
+
+def test_newton_reports_exhausted_iterations():
+    spec = W.perturb(W.block(2, n_cells=(3, 3), dx=0.1), 1)
+    spec = dataclasses.replace(spec, newton_max=1, newton_tol=1e-30)
+    ds = O.DomainState.create(spec)
+    with pytest.raises(O.NewtonMaxIter):
+        O.step(ds, 0.01)
+
+
+def test_cantilever_first_step_sags():
+    spec = W.cantilever()
+    ds = O.DomainState.create(spec)
+    x0 = ds.p.x.copy()
+    O.step(ds, 1e-3)
+    dy = ds.p.x[:, 1] - x0[:, 1]
+    # free end falls, clamped end barely moves; first step of free fall is g dt^2
+    assert dy[x0[:, 0] > 0.9].mean() < 0
+    np.testing.assert_allclose(dy[x0[:, 0] > 0.5].mean(), -9.81e-6, rtol=0.05)
+    assert abs(dy[x0[:, 0] < 0.0125]).max() < 0.5 * 9.81e-6

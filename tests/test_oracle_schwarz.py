@@ -1,0 +1,136 @@
+"""Pins of the oracle's Schwarz operators and loop (Sec. 3, Alg. 1) against
+facts the paper and the mathematics fix (no GPU)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import osmpm_oracle as O
+from paper_2605_09097_gb300 import workloads as W
+
+
+def _inclusion_small():
+    return W.inclusion(dx_S=0.02, M=2)
+
+
+def test_projection_of_constant_field_is_constant():
+    cB, cS, sch, dT = _inclusion_small()
+    gfS = O.p2g(cS.particles, cS.grid)
+    c = np.array([0.3, -0.7])
+    gfS.vn = np.where(gfS.active[:, None], c[None], 0.0)
+    num, den = O.projection_sums(cB.grid, cS.grid, gfS.m, gfS.vn, gfS.active)
+    recv = den > sch.tau_B
+    assert recv.sum() > 10
+    v = O.project_S2B(cB.grid, cS.grid, gfS, recv, sch.eps_tol)
+    np.testing.assert_allclose(v[recv], np.broadcast_to(c, v[recv].shape), rtol=1e-10)
+    assert np.all(v[~recv] == 0)
+
+
+def test_interpolation_reproduces_linear_field():
+    cB, cS, _, _ = _inclusion_small()
+    xB = O.node_positions(cB.grid)
+    xS = O.node_positions(cS.grid)
+    a = np.array([0.2, -0.1])
+    C = np.array([[0.5, -1.5], [2.0, 0.25]])
+    vB = a[None] + xB @ C.T
+    recv = np.zeros(cS.grid.n_nodes, bool)
+    recv[::7] = True
+    v = O.interp_B2S(cB.grid, cS.grid, vB, recv)
+    np.testing.assert_allclose(v[recv], a[None] + xS[recv] @ C.T, atol=1e-14)
+
+
+def test_temporal_interpolation_is_exact_for_linear_data():
+    v0, v1 = np.array([1.0, -2.0]), np.array([3.0, 6.0])
+    for M in (1, 2, 4):
+        for m in range(1, M + 1):
+            t = m / M
+            np.testing.assert_allclose(O.time_interp(v0, v1, m, M), v0 + t * (v1 - v0), atol=1e-15)
+    np.testing.assert_array_equal(O.time_interp(v0, v1, 2, 2), v1)
+
+
+@pytest.mark.parametrize("dxs,period", [(0.01, 5), (0.02, 5)])
+def test_coincident_nodes_on_nested_and_nonnested_grids(dxs, period):
+    cB, cS, _, _ = W.inclusion(dx_S=dxs)
+    j = O.coincident_fine_node(cB.grid, cS.grid)
+    xB = O.node_positions(cB.grid)
+    inside = np.all((xB >= 0.3 - 1e-12) & (xB <= 0.7 + 1e-12), axis=1)
+    # dx_B / dx_S = 5 (nested): every coarse node in the box coincides;
+    # 2.5 (non-nested): only every second coarse node does
+    if dxs == 0.01:
+        assert np.all(j[inside] >= 0)
+    else:
+        ii = np.rint(xB[inside] / 0.05).astype(int)
+        expect = np.all(ii % 2 == 0, axis=1)
+        np.testing.assert_array_equal(j[inside] >= 0, expect)
+    xS = O.node_positions(cS.grid)
+    ok = j >= 0
+    np.testing.assert_allclose(xS[j[ok]], xB[ok], atol=1e-12)
+    assert np.all(~inside[~ok] | (j[~ok] < 0))
+
+
+def test_rel_change_reading():
+    mask = np.array([True, True, False])
+    new = np.array([[3.0, 4.0], [0.0, 0.0], [9.0, 9.0]])
+    old = np.zeros_like(new)
+    assert O.rel_change(new, old, mask) == 1.0
+    # zero denominator: absolute norm
+    assert O.rel_change(np.zeros_like(new), new, mask) == 5.0
+    # empty set: 0
+    assert O.rel_change(new, old, np.zeros(3, bool)) == 0.0
+
+
+def test_no_boundary_nodes_decouples_domains_exactly():
+    """tau_Gamma = inf: no boundary node on either grid, so each domain takes
+    its own standalone solve: P_B one step of dT, P_S M steps of dT/M."""
+    cB, cS, sch, dT = _inclusion_small()
+    sch = dataclasses.replace(sch, tau_B=np.inf, tau_S=np.inf, k_max=3)
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    st = O.SchwarzStats()
+    O.schwarz_step(B, S, dT, sch, st)
+    B1, S1 = O.DomainState.create(cB), O.DomainState.create(cS)
+    O.step(B1, dT)
+    for _ in range(sch.M):
+        O.step(S1, dT / sch.M)
+    np.testing.assert_array_equal(B.p.x, B1.p.x)
+    np.testing.assert_array_equal(S.p.x, S1.p.x)
+    np.testing.assert_array_equal(S.p.F, S1.p.F)
+    assert st.iters == 2 and st.converged
+
+
+def test_identical_domains_reduce_to_single_domain():
+    """Identical grid and particles, M = 1: every boundary node coincides with
+    one of the other grid and the mass tie makes B the donor (Eq.
+    overlap_donor), so Gamma_hat_B is empty, the coarse result equals the
+    single-domain step exactly and the loop stops at k = 1."""
+    spec = W.perturb(W.block(2, n_cells=(6, 4), dx=0.1, E=1e5, gravity=(0.0, -9.81)), 4)
+    Bs, Ss, sch = W.identical_pair(spec, M=1)
+    B, S = O.DomainState.create(Bs), O.DomainState.create(Ss)
+    st = O.SchwarzStats()
+    so = {}
+    O.schwarz_step(B, S, 0.01, sch, st, so)
+    assert so["sets"].recvB.sum() == 0
+    assert so["sets"].recvS.sum() > 0
+    ref = O.DomainState.create(spec)
+    O.step(ref, 0.01)
+    np.testing.assert_array_equal(B.p.x, ref.p.x)
+    np.testing.assert_array_equal(B.p.F, ref.p.F)
+    assert st.iters == 2 and st.converged
+    # the fine copy is driven by I(v_B) on its receivers (a smoothing, not
+    # an identity for the quadratic B-spline): close, not equal
+    disp = np.abs(ref.p.x - spec.particles.x).max()
+    dev = np.abs(S.p.x - ref.p.x).max()
+    assert 0 < dev < disp
+
+
+def test_schwarz_residuals_decay_geometrically():
+    """Sec. 2.3: the alternating iteration contracts; on the small inclusion
+    both interface residuals fall by a roughly constant factor < 1."""
+    cB, cS, sch, dT = _inclusion_small()
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    st = O.SchwarzStats()
+    O.schwarz_step(B, S, dT, sch, st)
+    h = np.array(st.history)
+    assert st.converged and st.iters < sch.k_max
+    assert st.r_B <= sch.eps_conv and st.r_S <= sch.eps_conv
+    ratios = h[4:, 0] / h[3:-1, 0]
+    assert np.all(ratios < 0.9)
