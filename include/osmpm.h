@@ -1,0 +1,236 @@
+/*
+ * osmpm.h - C ABI of the GB300 OS-MPM hot path.
+ *
+ * The library advances material-point domains with the implicit MPM step of
+ * arxiv 2605.09097 Sec. 2.2 (APIC particle-to-grid transfer, backward-Euler
+ * incremental potential minimised by Newton's method with a halving line
+ * search, APIC grid-to-particle transfer with the deformation-gradient update
+ * and advection) and couples a coarse and a fine domain with the overlapping
+ * Schwarz alternating method of Sec. 3 and Alg. 1.  Every step runs in
+ * hand-written CUDA kernels for sm_103a; nothing runs on the host but loop
+ * control.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an osmpm_status and never throws.  On failure the
+ *    message is available from osmpm_last_error().
+ *  - Domains are opaque and owned by the library.  Their device memory comes
+ *    from the caller's allocator (or cudaMallocAsync when it is NULL) on the
+ *    caller's CUDA stream, which every kernel of the domain is launched on.
+ *  - Host arrays passed in are read during the call and not kept.  Output
+ *    host arrays are caller-owned and written during the call.
+ *  - Per-particle arrays are in the caller's particle order (the "id" order:
+ *    index k of the input is particle id k).  The library keeps its
+ *    particles sorted by the Morton code of their base grid node internally;
+ *    every per-particle output is returned in id order.
+ *  - Array layouts: x, v are n*dim doubles, particle-major (x[p*dim + a]);
+ *    B, F are n*dim*dim doubles, particle-major then row-major
+ *    (F[p*dim*dim + a*dim + b] = F_ab).  Grid fields are node-major with the
+ *    node index i + res0*(j + res1*k) (x fastest), components innermost.
+ *  - A failed osmpm_step or osmpm_schwarz_couple leaves the particles at the
+ *    state they had at the start of the call, except for
+ *    OSMPM_W_SCHWARZ_MAXITER, which commits the last Schwarz iterate.
+ *  - Calls on one domain are not thread-safe; different domains on
+ *    different streams are independent.
+ */
+#ifndef OSMPM_H
+#define OSMPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum osmpm_status {
+  OSMPM_OK = 0,
+  OSMPM_E_INVALID = 1,         /* bad argument or descriptor */
+  OSMPM_E_NOMEM = 2,           /* the allocator returned NULL */
+  OSMPM_E_CUDA = 3,            /* a CUDA runtime call failed */
+  OSMPM_E_NONFINITE = 4,       /* NaN/inf in inputs, or J <= 0 at an accepted iterate */
+  OSMPM_E_NEWTON_MAXITER = 5,  /* Newton did not reach newton_tol in newton_max iterations */
+  OSMPM_E_LINESEARCH = 6,      /* no energy decrease after ls_max halvings */
+  OSMPM_E_OUT_OF_GRID = 7,     /* a particle's 3^dim support left the grid box */
+  OSMPM_E_UNSUPPORTED = 9,     /* a valid request this build does not serve */
+  OSMPM_W_SCHWARZ_MAXITER = 100 /* Schwarz hit k_max; the last iterate was committed */
+} osmpm_status;
+
+/* Caller-supplied device allocator; alloc returns NULL on failure.  The
+ * stream argument is the domain's cudaStream_t. */
+typedef struct osmpm_allocator {
+  void* (*alloc)(size_t bytes, void* ctx, void* stream);
+  void (*free)(void* ptr, size_t bytes, void* ctx, void* stream);
+  void* ctx;
+} osmpm_allocator;
+
+/* Description of one domain: its background grid (Sec. 2.2.2; node
+ * (i,j,k) sits at origin + dx*(i,j,k), res nodes per axis), body force and
+ * solver controls (Sec. 2.2.5). */
+typedef struct osmpm_domain_desc {
+  int32_t dim;              /* 2 or 3 */
+  int32_t precision;        /* 0: FP64 throughout (the only mode of this build) */
+  double origin[3];
+  double dx;
+  int32_t res[3];           /* nodes per axis; each >= 4 */
+  double gravity[3];        /* body-force acceleration g (f_ext = m_i g) */
+  double newton_tol;        /* stop when max |delta x_hat| / dt <= newton_tol */
+  int32_t newton_max;       /* Newton iteration cap */
+  double cg_rtol;           /* PCG stops when |r| <= cg_rtol |r_0| */
+  int32_t cg_max;           /* PCG iteration cap per Newton iteration */
+  int32_t ls_max;           /* line search tries alpha = 1, 1/2, ..., 2^-ls_max */
+  int32_t reserved[8];      /* must be zero */
+} osmpm_domain_desc;
+
+/* Initial particle state, host arrays in id order (layouts above).  flags
+ * bit 0 marks the boundary particle layer P_alpha^partial of Sec. 3.2.1. */
+typedef struct osmpm_particles_in {
+  int64_t n;
+  const double* x;
+  const double* v;
+  const double* B;          /* APIC affine matrix B_p */
+  const double* F;          /* deformation gradient F_p */
+  const double* vol0;       /* V_p^0 */
+  const double* mass;       /* m_p */
+  const double* E;          /* Young's modulus */
+  const double* nu;         /* Poisson's ratio, < 0.5 */
+  const uint8_t* flags;
+} osmpm_particles_in;
+
+/* Prescribed grid-node velocity (Dirichlet data of Eqs. implicit_solve_coarse
+ * and implicit_solve_fine) on the nodes whose position lies in the closed box
+ * [lo, hi].  kind 0: velocity vel on the components set in comp_mask.
+ * kind 1: all components follow the rigid rotation by omega*dt about the
+ * axis through center along axis (in 2D: about z), v = (R - I)(x - c)/dt.
+ * Later rules override earlier ones on the components they set. */
+typedef struct osmpm_dirichlet {
+  int32_t kind;
+  uint32_t comp_mask;
+  double lo[3], hi[3];
+  double vel[3];
+  double center[3];
+  double axis[3];
+  double omega;
+} osmpm_dirichlet;
+
+/* Schwarz controls (Sec. 3): sub-cycling ratio M = dT/dt, iteration cap
+ * k_max (Alg. 1 runs k = 0..k_max), interface tolerance eps_conv (Eq.
+ * convergence_criterion), boundary-node mass thresholds tau_Gamma per grid
+ * (Eq. boundary_grid_set) and the projection regulariser eps_tol (Eq.
+ * spatial_projection). */
+typedef struct osmpm_schwarz_desc {
+  int32_t M;
+  int32_t k_max;
+  double eps_conv;
+  double tau_B;
+  double tau_S;
+  double eps_tol;
+  int32_t reserved[8];      /* must be zero */
+} osmpm_schwarz_desc;
+
+typedef struct osmpm_stats {
+  int32_t newton_iters;     /* summed over every solve of the call */
+  int32_t cg_iters;         /* summed over every PCG of the call */
+  int32_t ls_halvings;
+  int32_t schwarz_iters;    /* k* + 1, 0 for osmpm_step */
+  int32_t solves;           /* implicit solves performed */
+  int32_t converged;        /* Schwarz converged (1) or hit k_max (0) */
+  double r_B, r_S;          /* last interface residuals */
+  double last_dx_inf;       /* max |delta x_hat| of the last Newton iteration */
+  double reserved[6];
+} osmpm_stats;
+
+typedef struct osmpm_domain osmpm_domain;
+
+/* Creates a domain: validates the descriptor and particles, copies the
+ * particles to the device (allocator, stream), sorts them by the Morton code
+ * of their base node (ties keep id order) and computes the Lame parameters
+ * mu = E/(2(1+nu)), lam = E nu/((1+nu)(1-2nu)).  Errors: OSMPM_E_INVALID,
+ * OSMPM_E_NONFINITE, OSMPM_E_OUT_OF_GRID, OSMPM_E_NOMEM, OSMPM_E_CUDA. */
+osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc,
+                                 const osmpm_particles_in* particles,
+                                 const osmpm_allocator* allocator,
+                                 void* cuda_stream,
+                                 osmpm_domain** out);
+
+/* Frees the domain's device memory (through its allocator, on its stream). */
+osmpm_status osmpm_destroy_domain(osmpm_domain* dom);
+
+/* Replaces the domain's physical Dirichlet rules (n_rules may be 0). */
+osmpm_status osmpm_set_dirichlet(osmpm_domain* dom, const osmpm_dirichlet* rules,
+                                 int32_t n_rules);
+
+/* One backward-Euler MPM step of a single domain (Sec. 2.2): P2G (Eq.
+ * p2g_transfer), Newton with line search on E_h (Eq. discrete_energy,
+ * Sec. 2.2.5) with a Jacobi-preconditioned matrix-free CG whose
+ * Hessian-vector product is a particle gather-scatter, then G2P, F update
+ * and advection (Eqs. g2p_v, g2p_B, F_update, advection).  stats may be
+ * NULL. */
+osmpm_status osmpm_step(osmpm_domain* dom, double dt, osmpm_stats* stats);
+
+/* One global step dT of the overlapping Schwarz method, Alg. 1: coarse
+ * domain solved over dT with Pi_{S->B} data on its receiver nodes, fine
+ * domain reset and sub-cycled M times with T_m(I_{B->S}) data, until both
+ * interface residuals are <= eps_conv (k >= 1) or k = k_max; then the coarse
+ * particles take one G2P (Sec. 3.5).  Both domains must have the same dim
+ * and stream; coarse dx >= fine dx.  Returns OSMPM_W_SCHWARZ_MAXITER when
+ * k_max was reached (state committed).  stats may be NULL. */
+osmpm_status osmpm_schwarz_couple(osmpm_domain* coarse, osmpm_domain* fine, double dT,
+                                  const osmpm_schwarz_desc* sdesc, osmpm_stats* stats);
+
+/* Particle count and dimension of a domain. */
+osmpm_status osmpm_get_info(const osmpm_domain* dom, int64_t* n_particles, int32_t* dim);
+
+/* Copies the particle state to host arrays in id order; any pointer may be
+ * NULL to skip that field. */
+osmpm_status osmpm_get_particles(const osmpm_domain* dom, double* x, double* v, double* B,
+                                 double* F);
+
+/* Overwrites the particle state from host arrays in id order (x, v, B, F;
+ * none may be NULL) and re-sorts the particles by Morton code. */
+osmpm_status osmpm_set_particles(osmpm_domain* dom, const double* x, const double* v,
+                                 const double* B, const double* F);
+
+/* Writes the particle id held by each internal (Morton-sorted) slot:
+ * ids[s] = id of the particle in slot s, n entries. */
+osmpm_status osmpm_get_order(const osmpm_domain* dom, uint32_t* ids);
+
+/* Grid fields copied to a host array (doubles).  Fields with one value
+ * per node: OSMPM_FIELD_MASS (m_i of the last P2G), OSMPM_FIELD_BMASS
+ * (boundary-particle mass, Eq. boundary_grid_set), OSMPM_FIELD_RECEIVER
+ * (1.0 on Schwarz receiver nodes Gamma_hat, else 0.0).  Fields with dim
+ * values per node: OSMPM_FIELD_VN (v^n = (mv)/m of the last P2G, 0 on
+ * inactive nodes), OSMPM_FIELD_U (x_hat - x^n of the last solve),
+ * OSMPM_FIELD_BC (Schwarz boundary values last applied). */
+enum {
+  OSMPM_FIELD_MASS = 0,
+  OSMPM_FIELD_VN = 1,
+  OSMPM_FIELD_U = 2,
+  OSMPM_FIELD_BMASS = 3,
+  OSMPM_FIELD_RECEIVER = 4,
+  OSMPM_FIELD_BC = 5
+};
+osmpm_status osmpm_get_grid(const osmpm_domain* dom, int32_t field, double* out);
+
+/* Probes of the discrete operators at the current particle state (one P2G
+ * for step size dt first; no state change).  u, d and the outputs are host
+ * arrays of n_nodes*dim doubles (node-major, components innermost); entries
+ * on inactive nodes are ignored (read) or 0 (written).
+ *  osmpm_probe_gradient: dE_h/du (Eq. grid_residual with the energy-
+ *    consistent internal force) at u = x_hat - x^n, all active DOFs.
+ *  osmpm_probe_hvp: (M/dt^2 + K(u)) d, all active DOFs.
+ *  osmpm_probe_energy_change: E_h(u + alpha d) - E_h(u), +inf if a trial
+ *    inverts an element. */
+osmpm_status osmpm_probe_gradient(osmpm_domain* dom, double dt, const double* u, double* grad);
+osmpm_status osmpm_probe_hvp(osmpm_domain* dom, double dt, const double* u, const double* d,
+                             double* hd);
+osmpm_status osmpm_probe_energy_change(osmpm_domain* dom, double dt, const double* u,
+                                       const double* d, double alpha, double* dE);
+
+/* Message of the last failure on this thread (never NULL). */
+const char* osmpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSMPM_H */

@@ -1,0 +1,854 @@
+// C ABI of the OS-MPM hot path: domain lifetime, the Newton / PCG driver of
+// the implicit step (Sec. 2.2.5) and the Schwarz alternating loop (Alg. 1).
+// All arithmetic of the method runs in the kernels; this file launches them
+// on the domain's stream and reads back the few scalars that steer the loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/osmpm.h"
+#include "osmpm_internal.h"
+
+using namespace osmpm;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+osmpm_status fail(osmpm_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(OSMPM_E_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));         \
+  } while (0)
+
+#define OSMPM_TRY(expr)               \
+  do {                                \
+    osmpm_status st_ = (expr);        \
+    if (st_ != OSMPM_OK) return st_;  \
+  } while (0)
+
+}  // namespace
+
+struct osmpm_domain {
+  osmpm_domain_desc desc{};
+  int dim = 2;
+  GridGeo geo{};
+  int64_t n = 0;
+  cudaStream_t stream = nullptr;
+  osmpm_allocator alloc{};
+  bool have_alloc = false;
+  std::vector<std::pair<void*, size_t>> blocks;
+
+  PartPtrs P{}, A{};  // primary (Morton-sorted) and alternate particle sets
+  double *snap_x = nullptr, *snap_v = nullptr, *snap_B = nullptr, *snap_F = nullptr;
+  double* stage = nullptr;  // host-layout staging for get/set_particles
+  uint64_t *keys = nullptr, *keys_alt = nullptr;
+  uint32_t *vals = nullptr, *vals_alt = nullptr;
+  unsigned* hist = nullptr;
+
+  // grid (component-major)
+  double *m = nullptr, *mv = nullptr, *vn = nullptr, *bm = nullptr, *u = nullptr;
+  double *grad = nullptr, *diag = nullptr;
+  double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr;
+  double* L = nullptr;
+  uint8_t *dofmask = nullptr, *physmask = nullptr, *gam = nullptr, *recv = nullptr;
+  double *bc0 = nullptr, *bc1 = nullptr, *bc_prev = nullptr, *bc_applied = nullptr;
+  double *vtmp = nullptr, *proj_num = nullptr, *proj_den = nullptr;
+
+  DevRule* rules_dev = nullptr;
+  std::vector<osmpm_dirichlet> rules;
+  DevScalars* S = nullptr;
+  DevScalars* S_host = nullptr;  // pinned mirror
+  double* partials = nullptr;
+  int* err = nullptr;
+  int* err_host = nullptr;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// memory
+// ---------------------------------------------------------------------------
+osmpm_status dalloc(osmpm_domain* d, size_t bytes, void** out) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (d->have_alloc) {
+    p = d->alloc.alloc(bytes, d->alloc.ctx, (void*)d->stream);
+    if (!p) return fail(OSMPM_E_NOMEM, "allocator returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, d->stream);
+    if (e != cudaSuccess) return fail(OSMPM_E_NOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  d->blocks.emplace_back(p, bytes);
+  *out = p;
+  return OSMPM_OK;
+}
+
+template <class T>
+osmpm_status dalloc_n(osmpm_domain* d, int64_t count, T** out) {
+  void* p = nullptr;
+  OSMPM_TRY(dalloc(d, sizeof(T) * (size_t)count, &p));
+  *out = (T*)p;
+  return OSMPM_OK;
+}
+
+void free_all(osmpm_domain* d) {
+  for (auto& b : d->blocks) {
+    if (d->have_alloc)
+      d->alloc.free(b.first, b.second, d->alloc.ctx, (void*)d->stream);
+    else
+      cudaFreeAsync(b.first, d->stream);
+  }
+  d->blocks.clear();
+  if (d->S_host) cudaFreeHost(d->S_host);
+  if (d->err_host) cudaFreeHost(d->err_host);
+  d->S_host = nullptr;
+  d->err_host = nullptr;
+}
+
+osmpm_status alloc_parts(osmpm_domain* d, PartPtrs& P) {
+  const int D = d->dim;
+  const int64_t n = d->n;
+  P.n = n;
+  OSMPM_TRY(dalloc_n(d, D * n, &P.x));
+  OSMPM_TRY(dalloc_n(d, D * n, &P.v));
+  OSMPM_TRY(dalloc_n(d, D * D * n, &P.B));
+  OSMPM_TRY(dalloc_n(d, D * D * n, &P.F));
+  OSMPM_TRY(dalloc_n(d, n, &P.vol0));
+  OSMPM_TRY(dalloc_n(d, n, &P.mass));
+  OSMPM_TRY(dalloc_n(d, n, &P.mu));
+  OSMPM_TRY(dalloc_n(d, n, &P.lam));
+  OSMPM_TRY(dalloc_n(d, n, &P.flags));
+  OSMPM_TRY(dalloc_n(d, n, &P.id));
+  return OSMPM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// dimension dispatch
+// ---------------------------------------------------------------------------
+#define DISPATCH(d, call)                  \
+  do {                                     \
+    if ((d)->dim == 2) {                   \
+      using K = Kernels<2>;                \
+      call;                                \
+    } else {                               \
+      using K = Kernels<3>;                \
+      call;                                \
+    }                                      \
+  } while (0)
+
+osmpm_status sync_scalars(osmpm_domain* d) {
+  CUDA_TRY(cudaMemcpyAsync(d->S_host, d->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(d->err_host, d->err, sizeof(int), cudaMemcpyDeviceToHost, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  CUDA_TRY(cudaGetLastError());
+  return OSMPM_OK;
+}
+
+osmpm_status check_err(osmpm_domain* d) {
+  const int e = *d->err_host;
+  if (e & kErrOutOfGrid) return fail(OSMPM_E_OUT_OF_GRID, "a particle's support left the grid box");
+  if (e & kErrNonFinite) return fail(OSMPM_E_NONFINITE, "inverted element (J <= 0) at an accepted iterate");
+  return OSMPM_OK;
+}
+
+// Morton sort of the id-ordered alternate set A into the primary set P.
+osmpm_status sort_into_primary(osmpm_domain* d) {
+  const int64_t n = d->n;
+  DISPATCH(d, K::morton_keys(d->A.x, n, d->geo, d->keys, d->vals, d->err, d->stream));
+  int maxres = d->geo.res[0];
+  for (int a = 1; a < d->dim; ++a) maxres = std::max(maxres, d->geo.res[a]);
+  int bits_axis = 1;
+  while ((1 << bits_axis) < maxres) ++bits_axis;
+  radix_sort_pairs(d->keys, d->vals, d->keys_alt, d->vals_alt, n, bits_axis * d->dim, d->hist,
+                   d->stream);
+  DISPATCH(d, K::permute(d->A, d->P, d->vals, d->stream));
+  OSMPM_TRY(sync_scalars(d));
+  return check_err(d);
+}
+
+osmpm_status upload_rules(osmpm_domain* d, double dt) {
+  DevRule host[kMaxRules];
+  const int nr = (int)d->rules.size();
+  for (int r = 0; r < nr; ++r) {
+    const osmpm_dirichlet& s = d->rules[r];
+    DevRule& t = host[r];
+    memset(&t, 0, sizeof(t));
+    t.kind = s.kind;
+    t.comp_mask = s.comp_mask;
+    for (int a = 0; a < 3; ++a) {
+      t.lo[a] = s.lo[a];
+      t.hi[a] = s.hi[a];
+      t.vel[a] = s.vel[a];
+      t.center[a] = s.center[a];
+    }
+    if (s.kind == 1) {
+      // Rodrigues rotation by omega*dt about the unit axis (2D: about z)
+      const double th = s.omega * dt;
+      const double c = cos(th), sn = sin(th);
+      if (d->dim == 2) {
+        t.R[0] = c;
+        t.R[1] = -sn;
+        t.R[3] = sn;
+        t.R[4] = c;
+      } else {
+        double k[3] = {s.axis[0], s.axis[1], s.axis[2]};
+        const double nk = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        for (int a = 0; a < 3; ++a) k[a] /= nk;
+        const double Kx[9] = {0, -k[2], k[1], k[2], 0, -k[0], -k[1], k[0], 0};
+        double K2[9];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            double acc = 0;
+            for (int l = 0; l < 3; ++l) acc += Kx[i * 3 + l] * Kx[l * 3 + j];
+            K2[i * 3 + j] = acc;
+          }
+        for (int i = 0; i < 9; ++i) t.R[i] = ((i % 4) == 0 ? 1.0 : 0.0) + sn * Kx[i] + (1 - c) * K2[i];
+      }
+    }
+  }
+  if (nr > 0)
+    CUDA_TRY(cudaMemcpyAsync(d->rules_dev, host, sizeof(DevRule) * nr, cudaMemcpyHostToDevice, d->stream));
+  return OSMPM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// grid phases
+// ---------------------------------------------------------------------------
+osmpm_status run_p2g(osmpm_domain* d, bool boundary_mass) {
+  const int64_t nn = d->geo.nn;
+  const int D = d->dim;
+  CUDA_TRY(cudaMemsetAsync(d->m, 0, sizeof(double) * nn, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->mv, 0, sizeof(double) * D * nn, d->stream));
+  if (boundary_mass) CUDA_TRY(cudaMemsetAsync(d->bm, 0, sizeof(double) * nn, d->stream));
+  DISPATCH(d, K::p2g(d->P, d->geo, d->m, d->mv, boundary_mass ? d->bm : nullptr, d->err, d->stream));
+  DISPATCH(d, K::normalize(d->geo, d->m, d->mv, d->vn, d->stream));
+  return OSMPM_OK;
+}
+
+osmpm_status prep(osmpm_domain* d, double dt, bool with_rules, const uint8_t* recv,
+                  const double* bc0, const double* bc1, double a_m, uint8_t* physmask) {
+  OSMPM_TRY(upload_rules(d, dt));
+  PrepArgs a{};
+  a.rules = d->rules_dev;
+  a.n_rules = with_rules ? (int)d->rules.size() : 0;
+  a.recv = recv;
+  a.bc0 = bc0;
+  a.bc1 = bc1;
+  a.a_m = a_m;
+  a.bc_applied = d->bc_applied;
+  a.physmask = physmask;
+  DISPATCH(d, K::grid_prep(d->geo, d->m, d->vn, a, dt, d->dofmask, d->u, d->stream));
+  return OSMPM_OK;
+}
+
+struct SolveStats {
+  int newton = 0, cg = 0, ls = 0, solves = 0;
+  double last_dx = 0.0;
+};
+
+// Gradient + Hessian data at the current iterate, then PCG from x = 0 until
+// |r| <= rtol |r0| (device-side control, host polls once per chunk).
+osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
+  const int64_t nn = d->geo.nn;
+  const int D = d->dim;
+  CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
+  DISPATCH(d, K::grad(d->P, d->geo, d->u, d->dofmask, d->grad, d->diag, d->L, d->err, d->stream));
+  DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
+                             d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
+                             d->cz, d->cp, d->S, d->partials, d->stream));
+  int chunk = 8;
+  for (;;) {
+    for (int c = 0; c < chunk; ++c)
+      DISPATCH(d, K::cg_iteration(d->P, d->geo, d->m, d->dofmask, d->L, d->diag, dt, d->cx,
+                                  d->cr, d->cz, d->cp, d->cq, d->S, d->partials, d->stream));
+    DISPATCH(d, K::copy_if_neg(d->geo, d->cp, d->cx, d->S, d->stream));
+    DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
+    OSMPM_TRY(sync_scalars(d));
+    OSMPM_TRY(check_err(d));
+    if (d->S_host->cg_done) break;
+    if (chunk < 64) chunk *= 2;
+  }
+  st.cg += d->S_host->cg_iter;
+  return OSMPM_OK;
+}
+
+// Newton's method with backtracking line search (Sec. 2.2.5) on the
+// prepared grid (P2G done, Dirichlet data and initial guess in place).
+osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
+  st.solves++;
+  const double tol = d->desc.newton_tol * dt;
+  for (int it = 0; it < d->desc.newton_max; ++it) {
+    st.newton++;
+    OSMPM_TRY(gradient_and_pcg(d, dt, st));
+    const double dxinf = d->S_host->maxabs;
+    st.last_dx = dxinf;
+    if (!std::isfinite(dxinf)) return fail(OSMPM_E_NONFINITE, "non-finite Newton step");
+    if (dxinf <= tol) {
+      DISPATCH(d, K::axpy(d->geo, d->u, d->cx, 1.0, d->stream));
+      return OSMPM_OK;
+    }
+    double alpha = 1.0;
+    bool ok = false;
+    for (int s = 0; s <= d->desc.ls_max; ++s) {
+      DISPATCH(d, K::energy_change(d->P, d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt,
+                                   alpha, d->S, d->partials, d->stream));
+      OSMPM_TRY(sync_scalars(d));
+      if (d->S_host->dE < 0.0) {
+        ok = true;
+        break;
+      }
+      alpha *= 0.5;
+      st.ls++;
+    }
+    if (!ok) return fail(OSMPM_E_LINESEARCH, "no decrease of E_h after %d halvings", d->desc.ls_max);
+    DISPATCH(d, K::axpy(d->geo, d->u, d->cx, alpha, d->stream));
+  }
+  return fail(OSMPM_E_NEWTON_MAXITER, "Newton did not reach %g in %d iterations (last |dx| %g)",
+              d->desc.newton_tol, d->desc.newton_max, st.last_dx);
+}
+
+void fill_stats(osmpm_stats* out, const SolveStats& st, int schwarz_iters, int converged, double rB,
+                double rS) {
+  if (!out) return;
+  memset(out, 0, sizeof(*out));
+  out->newton_iters = st.newton;
+  out->cg_iters = st.cg;
+  out->ls_halvings = st.ls;
+  out->solves = st.solves;
+  out->schwarz_iters = schwarz_iters;
+  out->converged = converged;
+  out->r_B = rB;
+  out->r_S = rS;
+  out->last_dx_inf = st.last_dx;
+}
+
+osmpm_status snapshot(osmpm_domain* d, bool restore) {
+  const int D = d->dim;
+  const int64_t n = d->n;
+  auto cp = [&](double* a, double* b, int64_t cnt) {
+    return cudaMemcpyAsync(restore ? a : b, restore ? b : a, sizeof(double) * cnt,
+                           cudaMemcpyDeviceToDevice, d->stream);
+  };
+  CUDA_TRY(cp(d->P.x, d->snap_x, D * n));
+  CUDA_TRY(cp(d->P.v, d->snap_v, D * n));
+  CUDA_TRY(cp(d->P.B, d->snap_B, D * D * n));
+  CUDA_TRY(cp(d->P.F, d->snap_F, D * D * n));
+  return OSMPM_OK;
+}
+
+bool finite_all(const double* a, int64_t cnt) {
+  for (int64_t i = 0; i < cnt; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+osmpm_status check_domain(const osmpm_domain* d) {
+  if (!d) return fail(OSMPM_E_INVALID, "null domain");
+  return OSMPM_OK;
+}
+
+// Uploads host arrays (id order, particle-major) into A (component-major).
+osmpm_status upload_state(osmpm_domain* d, const double* x, const double* v, const double* B,
+                          const double* F) {
+  const int D = d->dim;
+  const int64_t n = d->n;
+  double* sx = d->stage;
+  double* sv = sx + D * n;
+  double* sB = sv + D * n;
+  double* sF = sB + D * D * n;
+  CUDA_TRY(cudaMemcpyAsync(sx, x, sizeof(double) * D * n, cudaMemcpyHostToDevice, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(sv, v, sizeof(double) * D * n, cudaMemcpyHostToDevice, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(sB, B, sizeof(double) * D * D * n, cudaMemcpyHostToDevice, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(sF, F, sizeof(double) * D * D * n, cudaMemcpyHostToDevice, d->stream));
+  DISPATCH(d, K::unpack_in(sx, sv, sB, sF, d->A, d->stream));
+  return OSMPM_OK;
+}
+
+// host node-major <-> device component-major grid vectors
+osmpm_status upload_grid_vec(osmpm_domain* d, const double* host, double* dev) {
+  const int D = d->dim;
+  const int64_t nn = d->geo.nn;
+  std::vector<double> tmp((size_t)(D * nn));
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < D; ++a) tmp[(size_t)(a * nn + i)] = host[i * D + a];
+  CUDA_TRY(cudaMemcpyAsync(dev, tmp.data(), sizeof(double) * D * nn, cudaMemcpyHostToDevice, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OSMPM_OK;
+}
+
+osmpm_status download_grid_vec(osmpm_domain* d, const double* dev, double* host, int comps) {
+  const int64_t nn = d->geo.nn;
+  std::vector<double> tmp((size_t)(comps * nn));
+  CUDA_TRY(cudaMemcpyAsync(tmp.data(), dev, sizeof(double) * comps * nn, cudaMemcpyDeviceToHost, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  for (int64_t i = 0; i < nn; ++i)
+    for (int a = 0; a < comps; ++a) host[i * comps + a] = tmp[(size_t)(a * nn + i)];
+  return OSMPM_OK;
+}
+
+osmpm_status probe_setup(osmpm_domain* d, double dt, const double* u_host) {
+  if (!(dt > 0.0)) return fail(OSMPM_E_INVALID, "dt must be > 0");
+  CUDA_TRY(cudaMemsetAsync(d->err, 0, sizeof(int), d->stream));
+  OSMPM_TRY(run_p2g(d, false));
+  OSMPM_TRY(prep(d, dt, false, nullptr, nullptr, nullptr, 0.0, nullptr));
+  OSMPM_TRY(upload_grid_vec(d, u_host, d->u));
+  OSMPM_TRY(sync_scalars(d));
+  return check_err(d);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* osmpm_last_error(void) { return g_last_error.c_str(); }
+
+osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_particles_in* pin,
+                                 const osmpm_allocator* allocator, void* cuda_stream,
+                                 osmpm_domain** out) {
+  if (!desc || !pin || !out) return fail(OSMPM_E_INVALID, "null argument");
+  *out = nullptr;
+  if (desc->dim != 2 && desc->dim != 3) return fail(OSMPM_E_INVALID, "dim must be 2 or 3");
+  if (desc->precision != 0) return fail(OSMPM_E_UNSUPPORTED, "only precision 0 (FP64) is built");
+  for (int i = 0; i < 8; ++i)
+    if (desc->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
+  if (!(desc->dx > 0.0) || !std::isfinite(desc->dx)) return fail(OSMPM_E_INVALID, "dx must be > 0");
+  int64_t nn = 1;
+  for (int a = 0; a < desc->dim; ++a) {
+    if (desc->res[a] < 4 || desc->res[a] > (1 << 20))
+      return fail(OSMPM_E_INVALID, "res[%d] = %d out of range [4, 2^20]", a, desc->res[a]);
+    nn *= desc->res[a];
+  }
+  if (!(desc->newton_tol > 0.0) || desc->newton_max < 1 || !(desc->cg_rtol > 0.0) ||
+      desc->cg_max < 1 || desc->ls_max < 0)
+    return fail(OSMPM_E_INVALID, "bad solver controls");
+  if (pin->n < 1 || pin->n > (int64_t)0x7fffffff) return fail(OSMPM_E_INVALID, "particle count out of range");
+  if (!pin->x || !pin->v || !pin->B || !pin->F || !pin->vol0 || !pin->mass || !pin->E || !pin->nu ||
+      !pin->flags)
+    return fail(OSMPM_E_INVALID, "null particle array");
+  const int D = desc->dim;
+  const int64_t n = pin->n;
+  if (!finite_all(pin->x, D * n) || !finite_all(pin->v, D * n) || !finite_all(pin->B, D * D * n) ||
+      !finite_all(pin->F, D * D * n) || !finite_all(pin->vol0, n) || !finite_all(pin->mass, n) ||
+      !finite_all(pin->E, n) || !finite_all(pin->nu, n))
+    return fail(OSMPM_E_NONFINITE, "non-finite particle input");
+  for (int64_t p = 0; p < n; ++p)
+    if (!(pin->nu[p] < 0.5) || !(pin->nu[p] > -1.0) || !(pin->mass[p] > 0.0) || !(pin->vol0[p] > 0.0))
+      return fail(OSMPM_E_INVALID, "particle %lld: need -1 < nu < 0.5, mass > 0, vol0 > 0", (long long)p);
+
+  osmpm_domain* d = new osmpm_domain();
+  d->desc = *desc;
+  d->dim = D;
+  d->n = n;
+  d->stream = (cudaStream_t)cuda_stream;
+  if (allocator && allocator->alloc && allocator->free) {
+    d->alloc = *allocator;
+    d->have_alloc = true;
+  }
+  GridGeo& g = d->geo;
+  for (int a = 0; a < 3; ++a) {
+    g.o[a] = a < D ? desc->origin[a] : 0.0;
+    g.res[a] = a < D ? desc->res[a] : 1;
+  }
+  g.dx = desc->dx;
+  g.inv_dx = 1.0 / desc->dx;
+  g.nn = nn;
+
+  auto cleanup = [&](osmpm_status st) {
+    free_all(d);
+    delete d;
+    return st;
+  };
+#define C_TRY(expr)                          \
+  do {                                       \
+    osmpm_status s_ = (expr);                \
+    if (s_ != OSMPM_OK) return cleanup(s_);  \
+  } while (0)
+
+  C_TRY(alloc_parts(d, d->P));
+  C_TRY(alloc_parts(d, d->A));
+  C_TRY(dalloc_n(d, D * n, &d->snap_x));
+  C_TRY(dalloc_n(d, D * n, &d->snap_v));
+  C_TRY(dalloc_n(d, D * D * n, &d->snap_B));
+  C_TRY(dalloc_n(d, D * D * n, &d->snap_F));
+  C_TRY(dalloc_n(d, (2 * D + 2 * D * D) * n, &d->stage));
+  C_TRY(dalloc_n(d, n, &d->keys));
+  C_TRY(dalloc_n(d, n, &d->keys_alt));
+  C_TRY(dalloc_n(d, n, &d->vals));
+  C_TRY(dalloc_n(d, n, &d->vals_alt));
+  C_TRY(dalloc_n(d, 256 * radix_tiles(n), &d->hist));
+  C_TRY(dalloc_n(d, nn, &d->m));
+  C_TRY(dalloc_n(d, D * nn, &d->mv));
+  C_TRY(dalloc_n(d, D * nn, &d->vn));
+  C_TRY(dalloc_n(d, nn, &d->bm));
+  C_TRY(dalloc_n(d, D * nn, &d->u));
+  C_TRY(dalloc_n(d, D * nn, &d->grad));
+  C_TRY(dalloc_n(d, D * nn, &d->diag));
+  C_TRY(dalloc_n(d, D * nn, &d->cx));
+  C_TRY(dalloc_n(d, D * nn, &d->cr));
+  C_TRY(dalloc_n(d, D * nn, &d->cz));
+  C_TRY(dalloc_n(d, D * nn, &d->cp));
+  C_TRY(dalloc_n(d, D * nn, &d->cq));
+  const int npk = (D * D) * (D * D + 1) / 2;
+  C_TRY(dalloc_n(d, (int64_t)npk * n, &d->L));
+  C_TRY(dalloc_n(d, nn, &d->dofmask));
+  C_TRY(dalloc_n(d, nn, &d->physmask));
+  C_TRY(dalloc_n(d, nn, &d->gam));
+  C_TRY(dalloc_n(d, nn, &d->recv));
+  C_TRY(dalloc_n(d, D * nn, &d->bc0));
+  C_TRY(dalloc_n(d, D * nn, &d->bc1));
+  C_TRY(dalloc_n(d, D * nn, &d->bc_prev));
+  C_TRY(dalloc_n(d, D * nn, &d->bc_applied));
+  C_TRY(dalloc_n(d, D * nn, &d->vtmp));
+  C_TRY(dalloc_n(d, D * nn, &d->proj_num));
+  C_TRY(dalloc_n(d, nn, &d->proj_den));
+  C_TRY(dalloc_n(d, kMaxRules, &d->rules_dev));
+  C_TRY(dalloc_n(d, 1, &d->S));
+  const int64_t maxblk = std::max<int64_t>(red_blocks_for(std::max<int64_t>(n, D * nn)), kRedBlocksMax);
+  C_TRY(dalloc_n(d, 4 * maxblk, &d->partials));
+  C_TRY(dalloc_n(d, 1, &d->err));
+  if (cudaMallocHost(&d->S_host, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&d->err_host, sizeof(int)) != cudaSuccess)
+    return cleanup(fail(OSMPM_E_NOMEM, "cudaMallocHost failed"));
+  if (cudaMemsetAsync(d->S, 0, sizeof(DevScalars), d->stream) != cudaSuccess ||
+      cudaMemsetAsync(d->err, 0, sizeof(int), d->stream) != cudaSuccess ||
+      cudaMemsetAsync(d->recv, 0, nn, d->stream) != cudaSuccess ||
+      cudaMemsetAsync(d->bc_applied, 0, sizeof(double) * D * nn, d->stream) != cudaSuccess ||
+      cudaMemsetAsync(d->u, 0, sizeof(double) * D * nn, d->stream) != cudaSuccess ||
+      cudaMemsetAsync(d->m, 0, sizeof(double) * nn, d->stream) != cudaSuccess ||
+      cudaMemsetAsync(d->vn, 0, sizeof(double) * D * nn, d->stream) != cudaSuccess ||
+      cudaMemsetAsync(d->bm, 0, sizeof(double) * nn, d->stream) != cudaSuccess)
+    return cleanup(fail(OSMPM_E_CUDA, "initial memset failed"));
+
+  // Upload in id order into A, material constants, then Morton sort into P.
+  C_TRY(upload_state(d, pin->x, pin->v, pin->B, pin->F));
+  // E and nu go through the staging area (it holds 2D + 2D^2 >= 2 values per particle)
+  double* sE = d->stage;
+  double* snu = d->stage + n;
+  if (cudaMemcpyAsync(sE, pin->E, sizeof(double) * n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess ||
+      cudaMemcpyAsync(snu, pin->nu, sizeof(double) * n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d->A.vol0, pin->vol0, sizeof(double) * n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d->A.mass, pin->mass, sizeof(double) * n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess ||
+      cudaMemcpyAsync(d->A.flags, pin->flags, n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess)
+    return cleanup(fail(OSMPM_E_CUDA, "particle upload failed"));
+  DISPATCH(d, K::lame(sE, snu, d->A, d->stream));
+  {
+    std::vector<uint32_t> ids((size_t)n);
+    for (int64_t p = 0; p < n; ++p) ids[(size_t)p] = (uint32_t)p;
+    if (cudaMemcpyAsync(d->A.id, ids.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess ||
+        cudaStreamSynchronize(d->stream) != cudaSuccess)
+      return cleanup(fail(OSMPM_E_CUDA, "id upload failed"));
+  }
+  C_TRY(sort_into_primary(d));
+#undef C_TRY
+  *out = d;
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_destroy_domain(osmpm_domain* d) {
+  if (!d) return OSMPM_OK;
+  cudaStreamSynchronize(d->stream);
+  free_all(d);
+  cudaStreamSynchronize(d->stream);
+  delete d;
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_set_dirichlet(osmpm_domain* d, const osmpm_dirichlet* rules, int32_t n_rules) {
+  OSMPM_TRY(check_domain(d));
+  if (n_rules < 0 || n_rules > kMaxRules) return fail(OSMPM_E_INVALID, "n_rules must be in [0, %d]", kMaxRules);
+  if (n_rules > 0 && !rules) return fail(OSMPM_E_INVALID, "null rules");
+  for (int r = 0; r < n_rules; ++r) {
+    if (rules[r].kind != 0 && rules[r].kind != 1) return fail(OSMPM_E_INVALID, "rule %d: unknown kind", r);
+    if (rules[r].kind == 1 && d->dim == 3) {
+      const double* k = rules[r].axis;
+      if (!(k[0] * k[0] + k[1] * k[1] + k[2] * k[2] > 0.0)) return fail(OSMPM_E_INVALID, "rule %d: zero axis", r);
+    }
+  }
+  d->rules.assign(rules, rules + n_rules);
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
+  OSMPM_TRY(check_domain(d));
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(OSMPM_E_INVALID, "dt must be > 0");
+  SolveStats st;
+  CUDA_TRY(cudaMemsetAsync(d->err, 0, sizeof(int), d->stream));
+  OSMPM_TRY(run_p2g(d, false));
+  OSMPM_TRY(sync_scalars(d));
+  OSMPM_TRY(check_err(d));
+  OSMPM_TRY(prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, nullptr));
+  osmpm_status s = newton_solve(d, dt, st);
+  if (s != OSMPM_OK) {
+    fill_stats(stats, st, 0, 0, 0.0, 0.0);
+    return s;
+  }
+  DISPATCH(d, K::g2p(d->P, d->geo, d->u, dt, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  CUDA_TRY(cudaGetLastError());
+  fill_stats(stats, st, 0, 1, 0.0, 0.0);
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
+                                  const osmpm_schwarz_desc* sd, osmpm_stats* stats) {
+  OSMPM_TRY(check_domain(B));
+  OSMPM_TRY(check_domain(S));
+  if (!sd) return fail(OSMPM_E_INVALID, "null schwarz descriptor");
+  if (B == S) return fail(OSMPM_E_INVALID, "coarse and fine must be different domains");
+  if (B->dim != S->dim) return fail(OSMPM_E_INVALID, "domains differ in dim");
+  if (B->stream != S->stream) return fail(OSMPM_E_INVALID, "domains must share one stream");
+  if (!(B->geo.dx >= S->geo.dx)) return fail(OSMPM_E_INVALID, "coarse dx must be >= fine dx");
+  if (sd->M < 1 || sd->k_max < 0 || !(sd->eps_conv > 0.0) || !(sd->eps_tol >= 0.0) ||
+      std::isnan(sd->tau_B) || std::isnan(sd->tau_S))
+    return fail(OSMPM_E_INVALID, "bad Schwarz controls");
+  for (int i = 0; i < 8; ++i)
+    if (sd->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
+  if (!(dT > 0.0) || !std::isfinite(dT)) return fail(OSMPM_E_INVALID, "dT must be > 0");
+  const int M = sd->M;
+  const double dt = dT / M;
+  const int D = B->dim;
+  const GridGeo &gB = B->geo, &gS = S->geo;
+  cudaStream_t s = B->stream;
+  SolveStats st;
+  auto bail = [&](osmpm_status e) {
+    snapshot(S, true);  // the fine particles go back to t_n
+    cudaStreamSynchronize(s);
+    fill_stats(stats, st, 0, 0, 0.0, 0.0);
+    return e;
+  };
+#define S_TRY(expr)                        \
+  do {                                     \
+    osmpm_status s_ = (expr);              \
+    if (s_ != OSMPM_OK) return bail(s_);   \
+  } while (0)
+
+  // Step 0 (Eq. store_states, Alg. 1): snapshot, P2G on both grids with
+  // boundary-particle mass, boundary sets and arbitration.
+  CUDA_TRY(cudaMemsetAsync(B->err, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(S->err, 0, sizeof(int), s));
+  OSMPM_TRY(snapshot(S, false));
+  OSMPM_TRY(run_p2g(B, true));
+  OSMPM_TRY(run_p2g(S, true));
+  OSMPM_TRY(sync_scalars(B));
+  OSMPM_TRY(check_err(B));
+  OSMPM_TRY(sync_scalars(S));
+  OSMPM_TRY(check_err(S));
+  // physical Dirichlet masks of both grids
+  S_TRY(prep(B, dT, true, nullptr, nullptr, nullptr, 0.0, B->physmask));
+  S_TRY(prep(S, dt, true, nullptr, nullptr, nullptr, 0.0, S->physmask));
+  DISPATCH(B, K::gamma(gB, B->m, B->bm, sd->tau_B, B->gam, s));
+  DISPATCH(S, K::gamma(gS, S->m, S->bm, sd->tau_S, S->gam, s));
+  CUDA_TRY(cudaMemcpyAsync(B->recv, B->gam, gB.nn, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(S->recv, S->gam, gS.nn, cudaMemcpyDeviceToDevice, s));
+  DISPATCH(B, K::arbitrate(gB, gS, B->gam, S->gam, B->m, S->m, B->recv, S->recv, s));
+  CUDA_TRY(cudaMemsetAsync(B->proj_num, 0, sizeof(double) * D * gB.nn, s));
+  CUDA_TRY(cudaMemsetAsync(B->proj_den, 0, sizeof(double) * gB.nn, s));
+  DISPATCH(B, K::proj_scatter(gB, gS, S->m, S->vn, B->proj_num, B->proj_den, s));
+  DISPATCH(B, K::recvB_filter(gB, B->proj_den, sd->tau_B, B->physmask, B->recv, s));
+  DISPATCH(B, K::recvS_filter(gB, gS, B->m, S->physmask, S->recv, s));
+  // v_GammaB^(0) = Pi(fine P2G at t_n); v_GammaS^n = I(v_B^n)
+  DISPATCH(B, K::proj_finish(gB, B->recv, B->proj_num, B->proj_den, sd->eps_tol, B->bc0, s));
+  DISPATCH(B, K::interp(gB, gS, B->vn, S->recv, S->bc0, s));
+  CUDA_TRY(cudaMemcpyAsync(S->bc_prev, S->bc0, sizeof(double) * D * gS.nn, cudaMemcpyDeviceToDevice, s));
+
+  int k = 0, converged = 0;
+  double rB = 0.0, rS = 0.0;
+  for (k = 0; k <= sd->k_max; ++k) {
+    // 1. coarse solve over dT with Pi data on Gamma_hat_B (Eq. implicit_solve_coarse)
+    S_TRY(prep(B, dT, true, B->recv, B->bc0, B->bc0, 1.0, nullptr));
+    S_TRY(newton_solve(B, dT, st));
+    DISPATCH(B, K::vel_from_u(gB, B->m, B->u, dT, B->vtmp, s));
+    // 2. fine: restore, P2G, endpoint data I(v_B^n), I(v_B^(k+1)), sub-cycle
+    S_TRY(snapshot(S, true));
+    S_TRY(run_p2g(S, false));
+    DISPATCH(B, K::interp(gB, gS, B->vtmp, S->recv, S->bc1, s));
+    for (int m = 1; m <= M; ++m) {
+      S_TRY(prep(S, dt, true, S->recv, S->bc0, S->bc1, (double)m / (double)M, nullptr));
+      S_TRY(newton_solve(S, dt, st));
+      DISPATCH(S, K::g2p(S->P, gS, S->u, dt, s));
+      S_TRY(run_p2g(S, false));
+      S_TRY(sync_scalars(S));
+      S_TRY(check_err(S));
+    }
+    // 3. convergence: Pi of the fine grid after sub-step M vs the BC in use
+    CUDA_TRY(cudaMemsetAsync(B->proj_num, 0, sizeof(double) * D * gB.nn, s));
+    CUDA_TRY(cudaMemsetAsync(B->proj_den, 0, sizeof(double) * gB.nn, s));
+    DISPATCH(B, K::proj_scatter(gB, gS, S->m, S->vn, B->proj_num, B->proj_den, s));
+    DISPATCH(B, K::proj_finish(gB, B->recv, B->proj_num, B->proj_den, sd->eps_tol, B->bc1, s));
+    DISPATCH(B, K::rel_change(gB, B->bc1, B->bc0, B->recv, 0, B->S, B->partials, s));
+    DISPATCH(S, K::rel_change(gS, S->bc1, S->bc_prev, S->recv, 1, B->S, B->partials, s));
+    S_TRY(sync_scalars(B));
+    {
+      const double nB = sqrt(B->S_host->res_num[0]), dB = sqrt(B->S_host->res_den[0]);
+      const double nS = sqrt(B->S_host->res_num[1]), dS = sqrt(B->S_host->res_den[1]);
+      rB = dB < 1e-14 ? nB : nB / dB;
+      rS = dS < 1e-14 ? nS : nS / dS;
+    }
+    std::swap(B->bc0, B->bc1);
+    std::swap(S->bc_prev, S->bc1);
+    if (k >= 1 && rB <= sd->eps_conv && rS <= sd->eps_conv) {
+      converged = 1;
+      break;
+    }
+  }
+  const int iters = converged ? k + 1 : sd->k_max + 1;
+  // 4. post-convergence coarse update (Sec. 3.5)
+  DISPATCH(B, K::g2p(B->P, gB, B->u, dT, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  CUDA_TRY(cudaGetLastError());
+#undef S_TRY
+  fill_stats(stats, st, iters, converged, rB, rS);
+  if (!converged)
+    return fail(OSMPM_W_SCHWARZ_MAXITER, "Schwarz stopped at k_max = %d (r_B %g, r_S %g)", sd->k_max, rB, rS);
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_get_info(const osmpm_domain* d, int64_t* n, int32_t* dim) {
+  OSMPM_TRY(check_domain(d));
+  if (n) *n = d->n;
+  if (dim) *dim = d->dim;
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_get_particles(const osmpm_domain* dc, double* x, double* v, double* B, double* F) {
+  osmpm_domain* d = const_cast<osmpm_domain*>(dc);
+  OSMPM_TRY(check_domain(d));
+  const int D = d->dim;
+  const int64_t n = d->n;
+  double* sx = d->stage;
+  double* sv = sx + D * n;
+  double* sB = sv + D * n;
+  double* sF = sB + D * D * n;
+  DISPATCH(d, K::pack_out(d->P, sx, sv, sB, sF, d->stream));
+  if (x) CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(double) * D * n, cudaMemcpyDeviceToHost, d->stream));
+  if (v) CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(double) * D * n, cudaMemcpyDeviceToHost, d->stream));
+  if (B) CUDA_TRY(cudaMemcpyAsync(B, sB, sizeof(double) * D * D * n, cudaMemcpyDeviceToHost, d->stream));
+  if (F) CUDA_TRY(cudaMemcpyAsync(F, sF, sizeof(double) * D * D * n, cudaMemcpyDeviceToHost, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_set_particles(osmpm_domain* d, const double* x, const double* v, const double* B,
+                                 const double* F) {
+  OSMPM_TRY(check_domain(d));
+  if (!x || !v || !B || !F) return fail(OSMPM_E_INVALID, "null array");
+  const int D = d->dim;
+  const int64_t n = d->n;
+  if (!finite_all(x, D * n) || !finite_all(v, D * n) || !finite_all(B, D * D * n) || !finite_all(F, D * D * n))
+    return fail(OSMPM_E_NONFINITE, "non-finite particle input");
+  // materials and ids back to id order in A, then the new kinematic state
+  DISPATCH(d, K::scatter_by_id(d->P, d->A, d->stream));
+  OSMPM_TRY(upload_state(d, x, v, B, F));
+  CUDA_TRY(cudaMemsetAsync(d->err, 0, sizeof(int), d->stream));
+  return sort_into_primary(d);
+}
+
+osmpm_status osmpm_get_order(const osmpm_domain* d, uint32_t* ids) {
+  OSMPM_TRY(check_domain(d));
+  if (!ids) return fail(OSMPM_E_INVALID, "null ids");
+  CUDA_TRY(cudaMemcpyAsync(ids, d->P.id, sizeof(uint32_t) * d->n, cudaMemcpyDeviceToHost, d->stream));
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_get_grid(const osmpm_domain* dc, int32_t field, double* out) {
+  osmpm_domain* d = const_cast<osmpm_domain*>(dc);
+  OSMPM_TRY(check_domain(d));
+  if (!out) return fail(OSMPM_E_INVALID, "null output");
+  const int D = d->dim;
+  const int64_t nn = d->geo.nn;
+  switch (field) {
+    case OSMPM_FIELD_MASS:
+      return download_grid_vec(d, d->m, out, 1);
+    case OSMPM_FIELD_BMASS:
+      return download_grid_vec(d, d->bm, out, 1);
+    case OSMPM_FIELD_VN:
+      return download_grid_vec(d, d->vn, out, D);
+    case OSMPM_FIELD_U:
+      return download_grid_vec(d, d->u, out, D);
+    case OSMPM_FIELD_BC:
+      return download_grid_vec(d, d->bc_applied, out, D);
+    case OSMPM_FIELD_RECEIVER: {
+      std::vector<uint8_t> tmp((size_t)nn);
+      CUDA_TRY(cudaMemcpyAsync(tmp.data(), d->recv, nn, cudaMemcpyDeviceToHost, d->stream));
+      CUDA_TRY(cudaStreamSynchronize(d->stream));
+      for (int64_t i = 0; i < nn; ++i) out[i] = tmp[(size_t)i] ? 1.0 : 0.0;
+      return OSMPM_OK;
+    }
+    default:
+      return fail(OSMPM_E_INVALID, "unknown grid field %d", field);
+  }
+}
+
+osmpm_status osmpm_probe_gradient(osmpm_domain* d, double dt, const double* u, double* grad) {
+  OSMPM_TRY(check_domain(d));
+  if (!u || !grad) return fail(OSMPM_E_INVALID, "null array");
+  OSMPM_TRY(probe_setup(d, dt, u));
+  const int64_t nn = d->geo.nn;
+  const int D = d->dim;
+  CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
+  DISPATCH(d, K::grad(d->P, d->geo, d->u, d->dofmask, d->grad, d->diag, d->L, d->err, d->stream));
+  DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
+                             d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
+                             d->cz, d->cp, d->S, d->partials, d->stream));
+  OSMPM_TRY(sync_scalars(d));
+  OSMPM_TRY(check_err(d));
+  return download_grid_vec(d, d->grad, grad, D);
+}
+
+osmpm_status osmpm_probe_hvp(osmpm_domain* d, double dt, const double* u, const double* dv, double* hd) {
+  OSMPM_TRY(check_domain(d));
+  if (!u || !dv || !hd) return fail(OSMPM_E_INVALID, "null array");
+  OSMPM_TRY(probe_setup(d, dt, u));
+  const int64_t nn = d->geo.nn;
+  const int D = d->dim;
+  CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
+  DISPATCH(d, K::grad(d->P, d->geo, d->u, d->dofmask, d->grad, d->diag, d->L, d->err, d->stream));
+  OSMPM_TRY(upload_grid_vec(d, dv, d->cp));
+  DISPATCH(d, K::set_cg_state(d->S, 0, 0, d->stream));
+  DISPATCH(d, K::hvp_only(d->P, d->geo, d->m, d->dofmask, d->L, dt, d->cp, d->cq, d->S,
+                          d->partials, d->stream));
+  OSMPM_TRY(sync_scalars(d));
+  OSMPM_TRY(check_err(d));
+  return download_grid_vec(d, d->cq, hd, D);
+}
+
+osmpm_status osmpm_probe_energy_change(osmpm_domain* d, double dt, const double* u, const double* dv,
+                                       double alpha, double* dE) {
+  OSMPM_TRY(check_domain(d));
+  if (!u || !dv || !dE) return fail(OSMPM_E_INVALID, "null array");
+  OSMPM_TRY(probe_setup(d, dt, u));
+  OSMPM_TRY(upload_grid_vec(d, dv, d->cx));
+  DISPATCH(d, K::energy_change(d->P, d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt, alpha,
+                               d->S, d->partials, d->stream));
+  OSMPM_TRY(sync_scalars(d));
+  *dE = d->S_host->dE;
+  return OSMPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Host-side interface between the C ABI / drivers and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "osmpm_types.h"
+
+namespace osmpm {
+
+// Launch shape helpers shared by drivers and launchers.
+constexpr int kRedBlocksMax = 1216;  // 152 SMs x 8 resident 256-thread blocks
+inline int blocks_for(int64_t n, int threads = 256) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : b);
+}
+inline int red_blocks_for(int64_t n) {
+  int b = blocks_for(n);
+  return b < kRedBlocksMax ? b : kRedBlocksMax;
+}
+
+// Arguments of the grid-preparation kernel (Dirichlet data, Schwarz
+// receivers and the initial Newton guess).
+struct PrepArgs {
+  const DevRule* rules;
+  int n_rules;
+  const uint8_t* recv;  // Schwarz receiver mask or nullptr
+  const double* bc0;    // receiver velocity at the start of the window
+  const double* bc1;    // receiver velocity at the end of the window
+  double a_m;           // temporal weight: v = (1 - a_m) bc0 + a_m bc1
+  double* bc_applied;   // receiver velocity applied (written), may be null
+  uint8_t* physmask;    // 1 where a physical rule fixes a component (written), may be null
+};
+
+template <int D>
+struct Kernels {
+  static void morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,
+                          uint32_t* vals, int* err, cudaStream_t s);
+  static void permute(const PartPtrs& src, const PartPtrs& dst, const uint32_t* perm,
+                      cudaStream_t s);
+  static void scatter_by_id(const PartPtrs& src, const PartPtrs& dst, cudaStream_t s);
+  static void lame(const double* E, const double* nu, PartPtrs P, cudaStream_t s);
+  static void pack_out(const PartPtrs& P, double* x, double* v, double* B, double* F,
+                       cudaStream_t s);
+  static void unpack_in(const double* x, const double* v, const double* B, const double* F,
+                        PartPtrs dst, cudaStream_t s);
+  static void p2g(const PartPtrs& P, const GridGeo& g, double* m, double* mv, double* bm,
+                  int* err, cudaStream_t s);
+  static void normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
+                        cudaStream_t s);
+  static void grid_prep(const GridGeo& g, const double* m, const double* vn, const PrepArgs& a,
+                        double dt, uint8_t* dofmask, double* u, cudaStream_t s);
+  static void grad(const PartPtrs& P, const GridGeo& g, const double* u, const uint8_t* dofmask,
+                   double* grad, double* diag, double* L, int* err, cudaStream_t s);
+  static void grad_finish(const GridGeo& g, const double* m, const double* vn, const double* u,
+                          const uint8_t* dofmask, const double* gravity, double dt, double cg_rtol,
+                          int cg_max, double* grad, double* diag, double* x, double* r, double* z,
+                          double* p, DevScalars* S, double* partials, cudaStream_t s);
+  static void cg_iteration(const PartPtrs& P, const GridGeo& g, const double* m,
+                           const uint8_t* dofmask, const double* L, const double* diag, double dt,
+                           double* x, double* r, double* z, double* p, double* q, DevScalars* S,
+                           double* partials, cudaStream_t s);
+  static void hvp_only(const PartPtrs& P, const GridGeo& g, const double* m,
+                       const uint8_t* dofmask, const double* L, double dt, double* p, double* q,
+                       DevScalars* S, double* partials, cudaStream_t s);
+  static void maxabs(const GridGeo& g, const uint8_t* dofmask, const double* x, DevScalars* S,
+                     double* partials, cudaStream_t s);
+  static void energy_change(const PartPtrs& P, const GridGeo& g, const double* m,
+                            const double* vn, const double* u, const double* x,
+                            const double* gravity, double dt, double alpha, DevScalars* S,
+                            double* partials, cudaStream_t s);
+  static void axpy(const GridGeo& g, double* u, const double* x, double alpha, cudaStream_t s);
+  static void g2p(const PartPtrs& P, const GridGeo& g, const double* u, double dt,
+                  cudaStream_t s);
+  // Schwarz interface operators (Sec. 3.2)
+  static void gamma(const GridGeo& g, const double* m, const double* bm, double tau,
+                    uint8_t* gam, cudaStream_t s);
+  static void arbitrate(const GridGeo& gB, const GridGeo& gS, const uint8_t* gamB,
+                        const uint8_t* gamS, const double* mB, const double* mS, uint8_t* recvB,
+                        uint8_t* recvS, cudaStream_t s);
+  static void proj_scatter(const GridGeo& gB, const GridGeo& gS, const double* mS,
+                           const double* vS, double* num, double* den, cudaStream_t s);
+  static void recvB_filter(const GridGeo& gB, const double* den, double tau,
+                           const uint8_t* physB, uint8_t* recvB, cudaStream_t s);
+  static void recvS_filter(const GridGeo& gB, const GridGeo& gS, const double* mB,
+                           const uint8_t* physS, uint8_t* recvS, cudaStream_t s);
+  static void proj_finish(const GridGeo& gB, const uint8_t* recvB, const double* num,
+                          const double* den, double eps_tol, double* out, cudaStream_t s);
+  static void interp(const GridGeo& gB, const GridGeo& gS, const double* vB,
+                     const uint8_t* recvS, double* out, cudaStream_t s);
+  static void vel_from_u(const GridGeo& g, const double* m, const double* u, double dt,
+                         double* v, cudaStream_t s);
+  static void rel_change(const GridGeo& g, const double* vnew, const double* vold,
+                         const uint8_t* recv, int slot, DevScalars* S, double* partials,
+                         cudaStream_t s);
+  static void copy_if_neg(const GridGeo& g, const double* p, double* x, const DevScalars* S,
+                          cudaStream_t s);
+  static void set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s);
+};
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// keys; result ends in (keys, vals).  hist needs 256 * radix_tiles(n) words.
+int64_t radix_tiles(int64_t n);
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                      int64_t n, int bits, unsigned* hist, cudaStream_t s);
+
+}  // namespace osmpm

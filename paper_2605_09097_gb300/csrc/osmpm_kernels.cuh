@@ -1,0 +1,1061 @@
+// Kernels of the OS-MPM hot path, templated on the dimension D.  Included
+// by kernels_d2.cu and kernels_d3.cu, which instantiate Kernels<2>/<3>.
+//
+// Layouts: particle fields component-major (x[a*n + p]); grid fields
+// component-major over the dense node box (u[a*nn + i]); per-particle
+// Hessian blocks L packed symmetric, entry-major (L[e*n + p]).
+#pragma once
+
+#include "osmpm_device.cuh"
+#include "osmpm_internal.h"
+
+namespace osmpm {
+
+template <int D>
+struct Pow3 {
+  static constexpr int K = (D == 2) ? 9 : 27;
+};
+
+__device__ __forceinline__ int64_t gtid() {
+  return (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+template <int D>
+__device__ __forceinline__ void load_x(const PartPtrs& P, int64_t p, double* x) {
+#pragma unroll
+  for (int a = 0; a < D; ++a) x[a] = P.x[a * P.n + p];
+}
+template <int D>
+__device__ __forceinline__ void load_F(const PartPtrs& P, int64_t p, double* F) {
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) F[e] = P.F[e * P.n + p];
+}
+
+// F(u) = (I + G) F^n with G = sum_i u_i grad N_i^T (Eq. F_update).
+template <int D>
+__device__ __forceinline__ void deform(const double* G, const double* Fn, double* F) {
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      double t = Fn[a * D + b];
+#pragma unroll
+      for (int c = 0; c < D; ++c) t += G[a * D + c] * Fn[c * D + b];
+      F[a * D + b] = t;
+    }
+}
+
+// G = sum over the stencil of w_i grad N_i^T for a grid vector field w.
+template <int D>
+__device__ __forceinline__ void gather_grad(const Stencil<D>& s, const GridGeo& g,
+                                            const double* w, double* G) {
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) G[e] = 0.0;
+#pragma unroll 3
+  for (int k = 0; k < Pow3<D>::K; ++k) {
+    double N, dN[D];
+    const int64_t node = stencil_node<D>(s, g, k, N, dN);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double wa = w[a * g.nn + node];
+#pragma unroll
+      for (int b = 0; b < D; ++b) G[a * D + b] += wa * dN[b];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Particle bookkeeping
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_morton_keys(const double* x, int64_t n, GridGeo g, uint64_t* keys,
+                              uint32_t* vals, int* err) {
+  const int64_t p = gtid();
+  if (p >= n) return;
+  double xp[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) xp[a] = x[a * n + p];
+  Stencil<D> s;
+  uint64_t code = 0;
+  if (!make_stencil<D>(xp, g, s)) {
+    atomicOr(err, kErrOutOfGrid);
+  } else {
+    for (int bit = 0; bit < 21; ++bit)
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+        code |= (uint64_t)(((unsigned)s.base[a] >> bit) & 1u) << (bit * D + a);
+  }
+  keys[p] = code;
+  vals[p] = (uint32_t)p;
+}
+
+template <int D>
+__global__ void k_permute(PartPtrs src, PartPtrs dst, const uint32_t* perm) {
+  const int64_t s = gtid();
+  const int64_t n = src.n;
+  if (s >= n) return;
+  const int64_t q = perm[s];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    dst.x[a * n + s] = src.x[a * n + q];
+    dst.v[a * n + s] = src.v[a * n + q];
+  }
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) {
+    dst.B[e * n + s] = src.B[e * n + q];
+    dst.F[e * n + s] = src.F[e * n + q];
+  }
+  dst.vol0[s] = src.vol0[q];
+  dst.mass[s] = src.mass[q];
+  dst.mu[s] = src.mu[q];
+  dst.lam[s] = src.lam[q];
+  dst.flags[s] = src.flags[q];
+  dst.id[s] = src.id[q];
+}
+
+template <int D>
+__global__ void k_scatter_by_id(PartPtrs src, PartPtrs dst) {
+  const int64_t s = gtid();
+  const int64_t n = src.n;
+  if (s >= n) return;
+  const int64_t q = src.id[s];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    dst.x[a * n + q] = src.x[a * n + s];
+    dst.v[a * n + q] = src.v[a * n + s];
+  }
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) {
+    dst.B[e * n + q] = src.B[e * n + s];
+    dst.F[e * n + q] = src.F[e * n + s];
+  }
+  dst.vol0[q] = src.vol0[s];
+  dst.mass[q] = src.mass[s];
+  dst.mu[q] = src.mu[s];
+  dst.lam[q] = src.lam[s];
+  dst.flags[q] = src.flags[s];
+  dst.id[q] = (uint32_t)q;
+}
+
+template <int D>
+__global__ void k_lame(const double* E, const double* nu, PartPtrs P) {
+  const int64_t p = gtid();
+  if (p >= P.n) return;
+  const double e = E[p], v = nu[p];
+  P.mu[p] = e / (2.0 * (1.0 + v));
+  P.lam[p] = e * v / ((1.0 + v) * (1.0 - 2.0 * v));
+}
+
+// Sorted component-major state -> id-ordered particle-major host layout.
+template <int D>
+__global__ void k_pack_out(PartPtrs P, double* x, double* v, double* B, double* F) {
+  const int64_t s = gtid();
+  const int64_t n = P.n;
+  if (s >= n) return;
+  const int64_t q = P.id[s];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    x[q * D + a] = P.x[a * n + s];
+    v[q * D + a] = P.v[a * n + s];
+  }
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) {
+    B[q * D * D + e] = P.B[e * n + s];
+    F[q * D * D + e] = P.F[e * n + s];
+  }
+}
+
+template <int D>
+__global__ void k_unpack_in(const double* x, const double* v, const double* B, const double* F,
+                            PartPtrs dst) {
+  const int64_t q = gtid();
+  const int64_t n = dst.n;
+  if (q >= n) return;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    dst.x[a * n + q] = x[q * D + a];
+    dst.v[a * n + q] = v[q * D + a];
+  }
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) {
+    dst.B[e * n + q] = B[q * D * D + e];
+    dst.F[e * n + q] = F[q * D * D + e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// APIC particle-to-grid transfer (Eq. p2g_transfer, Eq. p2g_substep); with
+// bm != nullptr also the boundary-particle mass of Eq. boundary_grid_set.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_p2g(PartPtrs P, GridGeo g, double* m, double* mv,
+                                                  double* bm, int* err) {
+  const int64_t p = gtid();
+  if (p >= P.n) return;
+  double xp[D], vp[D], Bp[D * D];
+  load_x<D>(P, p, xp);
+#pragma unroll
+  for (int a = 0; a < D; ++a) vp[a] = P.v[a * P.n + p];
+#pragma unroll
+  for (int e = 0; e < D * D; ++e) Bp[e] = P.B[e * P.n + p];
+  Stencil<D> s;
+  if (!make_stencil<D>(xp, g, s)) {
+    atomicOr(err, kErrOutOfGrid);
+    return;
+  }
+  const double mp = P.mass[p];
+  const double Dinv = 4.0 * g.inv_dx * g.inv_dx;  // D_p^-1 of the quadratic B-spline
+  const bool isb = (bm != nullptr) && (P.flags[p] & 1u);
+#pragma unroll 3
+  for (int k = 0; k < Pow3<D>::K; ++k) {
+    double N, dN[D];
+    const int64_t node = stencil_node<D>(s, g, k, N, dN);
+    double r[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) r[a] = stencil_node_pos<D>(s, g, k, a) - xp[a];
+    const double wm = mp * N;
+    atomicAdd(&m[node], wm);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      double va = 0.0;
+#pragma unroll
+      for (int b = 0; b < D; ++b) va += Bp[a * D + b] * r[b];
+      atomicAdd(&mv[a * g.nn + node], wm * (vp[a] + Dinv * va));
+    }
+    if (isb) atomicAdd(&bm[node], wm);
+  }
+}
+
+template <int D>
+__global__ void k_normalize(GridGeo g, const double* m, const double* mv, double* vn) {
+  for (int64_t i = gtid(); i < g.nn; i += gstride()) {
+    const double mi = m[i];
+#pragma unroll
+    for (int a = 0; a < D; ++a) vn[a * g.nn + i] = mi > 0.0 ? mv[a * g.nn + i] / mi : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grid preparation: Dirichlet data (physical rules, then Schwarz receivers
+// with temporally interpolated values, Eq. temporal_interp), the free-DOF
+// mask and the initial guess x_hat^(0) = x^n + dt v^n on free DOFs.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_grid_prep(GridGeo g, const double* m, const double* vn, PrepArgs A, double dt,
+                            uint8_t* dofmask, double* u) {
+  const unsigned all = (1u << D) - 1u;
+  for (int64_t i = gtid(); i < g.nn; i += gstride()) {
+    const bool active = m[i] > 0.0;
+    double xi[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xi[a] = node_pos(g, i, a);
+    unsigned fixed = 0u;
+    double vel[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) vel[a] = 0.0;
+    for (int r = 0; r < A.n_rules; ++r) {
+      const DevRule& R = A.rules[r];
+      bool in = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) in = in && (xi[a] >= R.lo[a]) && (xi[a] <= R.hi[a]);
+      if (!in) continue;
+      if (R.kind == 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          if ((R.comp_mask >> a) & 1u) {
+            fixed |= 1u << a;
+            vel[a] = R.vel[a];
+          }
+      } else {
+        double rel[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) rel[a] = xi[a] - R.center[a];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          double t = 0.0;
+#pragma unroll
+          for (int b = 0; b < D; ++b) t += R.R[a * 3 + b] * rel[b];
+          vel[a] = (t - rel[a]) / dt;
+        }
+        fixed = all;
+      }
+    }
+    if (A.physmask) A.physmask[i] = fixed != 0u ? 1 : 0;
+    if (A.recv && A.recv[i] && fixed == 0u) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        vel[a] = (1.0 - A.a_m) * A.bc0[a * g.nn + i] + A.a_m * A.bc1[a * g.nn + i];
+        if (A.bc_applied) A.bc_applied[a * g.nn + i] = vel[a];
+      }
+      fixed = all;
+    } else if (A.bc_applied) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) A.bc_applied[a * g.nn + i] = 0.0;
+    }
+    dofmask[i] = active ? (uint8_t)(~fixed & all) : (uint8_t)0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      u[a * g.nn + i] = !active ? 0.0 : (((fixed >> a) & 1u) ? dt * vel[a] : dt * vn[a * g.nn + i]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of E_h (Eq. grid_residual with the energy-consistent internal
+// force sum_p V0 P F^nT grad N_i), Jacobi diagonal, and the per-particle
+// Hessian block L(G) = V0 dP[G F^n] F^nT used by every HVP of the Newton
+// iteration (K = Hessian of sum_p V0 Psi(F_p(u)), Sec. 2.2.5).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_grad(PartPtrs P, GridGeo g, const double* u,
+                                                   const uint8_t* dofmask, double* grad,
+                                                   double* diag, double* L, int* err) {
+  constexpr int DD = D * D;
+  const int64_t p = gtid();
+  if (p >= P.n) return;
+  double xp[D], Fn[DD], G[DD], F[DD];
+  load_x<D>(P, p, xp);
+  load_F<D>(P, p, Fn);
+  Stencil<D> s;
+  if (!make_stencil<D>(xp, g, s)) {
+    atomicOr(err, kErrOutOfGrid);
+    return;
+  }
+  gather_grad<D>(s, g, u, G);
+  deform<D>(G, Fn, F);
+  const double mu = P.mu[p], lam = P.lam[p], V0 = P.vol0[p];
+  NeoHookean<D> nh;
+  if (!neo_hookean<D>(F, mu, lam, nh)) {
+    atomicOr(err, kErrNonFinite);
+    return;
+  }
+  double Pk[DD], Y[DD];
+  pk1<D>(F, mu, lam, nh, Pk);
+  // Y = V0 P F^nT
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      double t = 0.0;
+#pragma unroll
+      for (int b = 0; b < D; ++b) t += Pk[a * D + b] * Fn[c * D + b];
+      Y[a * D + c] = V0 * t;
+    }
+  // L columns: basis G = e_a e_b^T -> dF = e_a (row b of F^n)
+  double Lfull[DD * DD];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      double dF[DD], dP[DD];
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int d = 0; d < D; ++d) dF[c * D + d] = (c == a) ? Fn[b * D + d] : 0.0;
+      dpdf_apply<D>(dF, mu, lam, nh, dP);
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+          double t = 0.0;
+#pragma unroll
+          for (int d = 0; d < D; ++d) t += dP[c * D + d] * Fn[e * D + d];
+          Lfull[(c * D + e) * DD + (a * D + b)] = V0 * t;
+        }
+    }
+#pragma unroll
+  for (int i = 0; i < DD; ++i)
+#pragma unroll
+    for (int j = i; j < DD; ++j)
+      L[(int64_t)Sym<D>::idx(i, j) * P.n + p] = 0.5 * (Lfull[i * DD + j] + Lfull[j * DD + i]);
+  // scatter gradient and diagonal
+#pragma unroll 3
+  for (int k = 0; k < Pow3<D>::K; ++k) {
+    double N, dN[D];
+    const int64_t node = stencil_node<D>(s, g, k, N, dN);
+    const unsigned fm = dofmask[node];
+    if (!fm) continue;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (!((fm >> a) & 1u)) continue;
+      double f = 0.0, dg = 0.0;
+#pragma unroll
+      for (int c = 0; c < D; ++c) f += Y[a * D + c] * dN[c];
+#pragma unroll
+      for (int b = 0; b < D; ++b)
+#pragma unroll
+        for (int c = 0; c < D; ++c) dg += Lfull[(a * D + b) * DD + (a * D + c)] * dN[b] * dN[c];
+      atomicAdd(&grad[a * g.nn + node], f);
+      atomicAdd(&diag[a * g.nn + node], dg);
+    }
+  }
+}
+
+// Completes the gradient on the free DOFs (inertia and external force),
+// adds m/dt^2 to the diagonal and starts PCG from x = 0: r = -g, z = r/diag,
+// p = z; reduces r.z and r.r.
+template <int D>
+__global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, const double* u,
+                              const uint8_t* dofmask, double gx, double gy, double gz, double dt,
+                              double cg_rtol, int cg_max, double* grad, double* diag, double* x,
+                              double* r, double* z, double* p, DevScalars* S, double* partials) {
+  const double inv_dt2 = 1.0 / (dt * dt);
+  const double gv[3] = {gx, gy, gz};
+  double acc[2] = {0.0, 0.0};
+  const int64_t total = g.nn * D;
+  for (int64_t idx = gtid(); idx < total; idx += gstride()) {
+    const int a = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)a * g.nn;
+    const double mi = m[i];
+    const bool active = mi > 0.0;
+    const bool fr = (dofmask[i] >> a) & 1u;
+    double gi = 0.0;
+    if (active) gi = grad[idx] + mi * inv_dt2 * (u[idx] - dt * vn[idx]) - mi * gv[a];
+    grad[idx] = gi;
+    x[idx] = 0.0;
+    if (fr) {
+      const double dg = diag[idx] + mi * inv_dt2;
+      diag[idx] = dg;
+      const double ri = -gi;
+      const double zi = ri / dg;
+      r[idx] = ri;
+      z[idx] = zi;
+      p[idx] = zi;
+      acc[0] += ri * zi;
+      acc[1] += ri * ri;
+    } else {
+      diag[idx] = 1.0;
+      r[idx] = 0.0;
+      z[idx] = 0.0;
+      p[idx] = 0.0;
+    }
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, partials, &S->counter, tot) && threadIdx.x == 0) {
+    S->rz = tot[0];
+    S->rr = tot[1];
+    S->rr0 = tot[1];
+    S->tol2 = cg_rtol * cg_rtol * tot[1];
+    S->cg_iter = 0;
+    S->cg_max = cg_max;
+    S->cg_neg = 0;
+    S->cg_done = (tot[1] == 0.0) ? 1 : 0;
+    S->beta = 0.0;
+  }
+}
+
+// PCG step A: p = z + beta p (after the first iteration); q = (m/dt^2) p on
+// free DOFs; reduces the diagonal part of p.Hp.
+template <int D>
+__global__ void k_cg_a(GridGeo g, const double* m, const uint8_t* dofmask, double inv_dt2,
+                       const double* z, double* p, double* q, DevScalars* S, double* partials) {
+  if (*((volatile int*)&S->cg_done)) return;
+  const int it = S->cg_iter;
+  const double beta = S->beta;
+  double acc[1] = {0.0};
+  const int64_t total = g.nn * D;
+  for (int64_t idx = gtid(); idx < total; idx += gstride()) {
+    const int a = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)a * g.nn;
+    if ((dofmask[i] >> a) & 1u) {
+      double pv = p[idx];
+      if (it > 0) {
+        pv = z[idx] + beta * pv;
+        p[idx] = pv;
+      }
+      const double md = m[i] * inv_dt2;
+      q[idx] = md * pv;
+      acc[0] += md * pv * pv;
+    } else {
+      q[idx] = 0.0;
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, &S->counter, tot) && threadIdx.x == 0) S->pq_diag = tot[0];
+}
+
+// PCG step B: the matrix-free Hessian-vector product, a particle gather of
+// p (G = sum_j p_j grad N_j^T), Y = L G, scatter q_i += Y grad N_i, and the
+// particle part of p.Hp = sum_p G : L G.  The last block forms alpha.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_cg_b(PartPtrs P, GridGeo g, const uint8_t* dofmask,
+                                                   const double* L, const double* p, double* q,
+                                                   DevScalars* S, double* partials) {
+  constexpr int DD = D * D;
+  if (*((volatile int*)&S->cg_done)) return;
+  double acc[1] = {0.0};
+  for (int64_t pi = gtid(); pi < P.n; pi += gstride()) {
+    double xp[D];
+    load_x<D>(P, pi, xp);
+    Stencil<D> s;
+    make_stencil<D>(xp, g, s);
+    double G[DD], Y[DD];
+    gather_grad<D>(s, g, p, G);
+#pragma unroll
+    for (int i = 0; i < DD; ++i) {
+      double t = 0.0;
+#pragma unroll
+      for (int j = 0; j < DD; ++j) t += L[(int64_t)Sym<D>::idx(i, j) * P.n + pi] * G[j];
+      Y[i] = t;
+    }
+    double qf = 0.0;
+#pragma unroll
+    for (int i = 0; i < DD; ++i) qf += G[i] * Y[i];
+    acc[0] += qf;
+#pragma unroll 3
+    for (int k = 0; k < Pow3<D>::K; ++k) {
+      double N, dN[D];
+      const int64_t node = stencil_node<D>(s, g, k, N, dN);
+      const unsigned fm = dofmask[node];
+      if (!fm) continue;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (!((fm >> a) & 1u)) continue;
+        double f = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) f += Y[a * D + c] * dN[c];
+        atomicAdd(&q[a * g.nn + node], f);
+      }
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, &S->counter, tot) && threadIdx.x == 0) {
+    const double pq = S->pq_diag + tot[0];
+    S->pq = pq;
+    if (!(pq > 0.0)) {
+      S->cg_neg = 1;
+      S->cg_done = 1;
+    } else {
+      S->alpha = S->rz / pq;
+    }
+  }
+}
+
+// PCG step C: x += alpha p, r -= alpha q, z = r/diag; the last block forms
+// beta and the stopping test |r| <= rtol |r0| or the iteration cap.
+template <int D>
+__global__ void k_cg_c(GridGeo g, const uint8_t* dofmask, const double* diag, const double* p,
+                       const double* q, double* x, double* r, double* z, DevScalars* S,
+                       double* partials) {
+  if (*((volatile int*)&S->cg_done)) return;
+  const double alpha = S->alpha;
+  double acc[2] = {0.0, 0.0};
+  const int64_t total = g.nn * D;
+  for (int64_t idx = gtid(); idx < total; idx += gstride()) {
+    const int a = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)a * g.nn;
+    if ((dofmask[i] >> a) & 1u) {
+      x[idx] += alpha * p[idx];
+      const double ri = r[idx] - alpha * q[idx];
+      r[idx] = ri;
+      const double zi = ri / diag[idx];
+      z[idx] = zi;
+      acc[0] += ri * zi;
+      acc[1] += ri * ri;
+    }
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, partials, &S->counter, tot) && threadIdx.x == 0) {
+    S->beta = tot[0] / S->rz;
+    S->rz = tot[0];
+    S->rr = tot[1];
+    const int it = S->cg_iter + 1;
+    S->cg_iter = it;
+    S->cg_done = (tot[1] <= S->tol2 || it >= S->cg_max) ? 1 : 0;
+  }
+}
+
+template <int D>
+__global__ void k_copy_if_neg(GridGeo g, const double* p, double* x, const DevScalars* S) {
+  if (!(S->cg_neg && S->cg_iter == 0)) return;
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) x[idx] = p[idx];
+}
+
+template <int D>
+__global__ void k_set_cg_state(DevScalars* S, int iter, int done) {
+  S->cg_iter = iter;
+  S->cg_done = done;
+  S->cg_neg = 0;
+}
+
+template <int D>
+__global__ void k_maxabs(GridGeo g, const uint8_t* dofmask, const double* x, DevScalars* S,
+                         double* partials) {
+  double v = 0.0;
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
+    const int a = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)a * g.nn;
+    if ((dofmask[i] >> a) & 1u) v = fmax(v, fabs(x[idx]));
+  }
+  double tot;
+  if (grid_max(v, partials, &S->counter, tot) && threadIdx.x == 0) S->maxabs = tot;
+}
+
+// E_h(u + alpha x) - E_h(u) summed term by term (the line-search test of
+// Sec. 2.2.5): per particle V0 (Psi(F(u + alpha x)) - Psi(F(u))), per node
+// m/(2dt^2) s.(2(u - dt v^n) + s) - s.f_ext with s = alpha x.  +inf when a
+// trial inverts an element.
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrs P, GridGeo g, const double* m,
+                                                            const double* vn, const double* u,
+                                                            const double* x, double gx, double gy,
+                                                            double gz, double dt, double alpha,
+                                                            DevScalars* S, double* partials) {
+  constexpr int DD = D * D;
+  double acc[1] = {0.0};
+  for (int64_t pi = gtid(); pi < P.n; pi += gstride()) {
+    double xp[D], Fn[DD], Gu[DD], Gs[DD], F0[DD], F1[DD];
+    load_x<D>(P, pi, xp);
+    load_F<D>(P, pi, Fn);
+    Stencil<D> s;
+    make_stencil<D>(xp, g, s);
+    gather_grad<D>(s, g, u, Gu);
+    gather_grad<D>(s, g, x, Gs);
+    deform<D>(Gu, Fn, F0);
+#pragma unroll
+    for (int e = 0; e < DD; ++e) Gs[e] = Gu[e] + alpha * Gs[e];
+    deform<D>(Gs, Fn, F1);
+    const double mu = P.mu[pi], lam = P.lam[pi];
+    NeoHookean<D> n0, n1;
+    const bool ok0 = neo_hookean<D>(F0, mu, lam, n0);
+    const bool ok1 = neo_hookean<D>(F1, mu, lam, n1);
+    if (!ok1 || !ok0) {
+      acc[0] += INFINITY;
+    } else {
+      acc[0] += P.vol0[pi] * (n1.psi - n0.psi);
+    }
+  }
+  const double inv_2dt2 = 0.5 / (dt * dt);
+  const double gv[3] = {gx, gy, gz};
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
+    const int a = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)a * g.nn;
+    const double mi = m[i];
+    if (!(mi > 0.0)) continue;
+    const double sv = alpha * x[idx];
+    acc[0] += mi * inv_2dt2 * sv * (2.0 * (u[idx] - dt * vn[idx]) + sv) - sv * mi * gv[a];
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, &S->counter, tot) && threadIdx.x == 0) S->dE = tot[0];
+}
+
+template <int D>
+__global__ void k_axpy(GridGeo g, double* u, const double* x, double alpha) {
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) u[idx] += alpha * x[idx];
+}
+
+// ---------------------------------------------------------------------------
+// APIC grid-to-particle transfer with v_i = u_i/dt (Eqs. g2p_v, g2p_B), the
+// F update (Eq. F_update) and advection (Eq. advection).
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_g2p(PartPtrs P, GridGeo g, const double* u,
+                                                  double dt) {
+  constexpr int DD = D * D;
+  const int64_t p = gtid();
+  if (p >= P.n) return;
+  double xp[D], Fn[DD];
+  load_x<D>(P, p, xp);
+  load_F<D>(P, p, Fn);
+  Stencil<D> s;
+  make_stencil<D>(xp, g, s);
+  double vnew[D], Bnew[DD], G[DD];
+#pragma unroll
+  for (int a = 0; a < D; ++a) vnew[a] = 0.0;
+#pragma unroll
+  for (int e = 0; e < DD; ++e) {
+    Bnew[e] = 0.0;
+    G[e] = 0.0;
+  }
+#pragma unroll 3
+  for (int k = 0; k < Pow3<D>::K; ++k) {
+    double N, dN[D], r[D], vi[D];
+    const int64_t node = stencil_node<D>(s, g, k, N, dN);
+#pragma unroll
+    for (int a = 0; a < D; ++a) r[a] = stencil_node_pos<D>(s, g, k, a) - xp[a];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double ua = u[a * g.nn + node];
+      vi[a] = ua / dt;
+      vnew[a] += N * vi[a];
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        Bnew[a * D + b] += N * vi[a] * r[b];
+        G[a * D + b] += ua * dN[b];
+      }
+    }
+  }
+  double F[DD];
+  deform<D>(G, Fn, F);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    P.v[a * P.n + p] = vnew[a];
+    P.x[a * P.n + p] = xp[a] + dt * vnew[a];
+  }
+#pragma unroll
+  for (int e = 0; e < DD; ++e) {
+    P.B[e * P.n + p] = Bnew[e];
+    P.F[e * P.n + p] = F[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Schwarz interface operators (Sec. 3.2)
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_gamma(int64_t nn, const double* m, const double* bm, double tau, uint8_t* gam) {
+  for (int64_t i = gtid(); i < nn; i += gstride())
+    gam[i] = (m[i] > 0.0 && bm[i] > tau) ? 1 : 0;
+}
+
+// Eq. overlap_donor on coincident boundary nodes (|x_B - x_S|_inf <= 1e-9
+// dx_S): the larger grid mass donates, ties (within 1e-12 relative) to B.
+template <int D>
+__global__ void k_arbitrate(GridGeo gB, GridGeo gS, const uint8_t* gamB, const uint8_t* gamS,
+                            const double* mB, const double* mS, uint8_t* recvB, uint8_t* recvS) {
+  for (int64_t I = gtid(); I < gB.nn; I += gstride()) {
+    if (!gamB[I]) continue;
+    bool ok = true;
+    int64_t j = 0, stride = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double xb = node_pos(gB, I, a);
+      const double jf = rint(__ddiv_rn(__dsub_rn(xb, gS.o[a]), gS.dx));
+      const bool inside = jf >= 0.0 && jf < (double)gS.res[a];
+      const double xs = __dadd_rn(gS.o[a], __dmul_rn(jf, gS.dx));
+      ok = ok && inside && (fabs(xs - xb) <= 1e-9 * gS.dx);
+      j += (int64_t)(inside ? jf : 0.0) * stride;
+      stride *= gS.res[a];
+    }
+    if (!ok || !gamS[j]) continue;
+    if (mS[j] > mB[I] * (1.0 + 1e-12))
+      recvS[j] = 0;
+    else
+      recvB[I] = 0;
+  }
+}
+
+// Numerator and denominator of Eq. spatial_projection: every active fine
+// node j scatters m_Sj N_BI(x_Sj) (times v_Sj) to its coarse support.
+template <int D>
+__global__ void k_proj_scatter(GridGeo gB, GridGeo gS, const double* mS, const double* vS,
+                               double* num, double* den) {
+  for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
+    const double mj = mS[j];
+    if (!(mj > 0.0)) continue;
+    double xs[D], vj[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      xs[a] = node_pos(gS, j, a);
+      vj[a] = vS[a * gS.nn + j];
+    }
+    int base[D];
+    double w[D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double t = __dmul_rn(__dsub_rn(xs[a], gB.o[a]), gB.inv_dx);
+      const double b = floor(__dsub_rn(t, 0.5));
+      base[a] = (int)b;
+      const double fx = t - b;
+      const double e0 = 1.5 - fx, e1 = fx - 1.0, e2 = fx - 0.5;
+      w[a][0] = 0.5 * e0 * e0;
+      w[a][1] = 0.75 - e1 * e1;
+      w[a][2] = 0.5 * e2 * e2;
+    }
+    for (int k = 0; k < Pow3<D>::K; ++k) {
+      const int off[3] = {k % 3, (k / 3) % 3, k / 9};
+      bool in = true;
+      int64_t node = 0, stride = 1;
+      double N = mj;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int c = base[a] + off[a];
+        in = in && c >= 0 && c < gB.res[a];
+        node += (int64_t)c * stride;
+        stride *= gB.res[a];
+        N *= w[a][off[a]];
+      }
+      if (!in) continue;
+      atomicAdd(&den[node], N);
+#pragma unroll
+      for (int a = 0; a < D; ++a) atomicAdd(&num[a * gB.nn + node], N * vj[a]);
+    }
+  }
+}
+
+template <int D>
+__global__ void k_recvB_filter(int64_t nn, const double* den, double tau, const uint8_t* physB,
+                               uint8_t* recvB) {
+  for (int64_t I = gtid(); I < nn; I += gstride())
+    if (recvB[I] && (!(den[I] > tau) || physB[I])) recvB[I] = 0;
+}
+
+// Gamma_hat_S keeps fine nodes whose coarse support lies in the box and is
+// all active; no receiver carries a physical rule.
+template <int D>
+__global__ void k_recvS_filter(GridGeo gB, GridGeo gS, const double* mB, const uint8_t* physS,
+                               uint8_t* recvS) {
+  for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
+    if (!recvS[j]) continue;
+    if (physS[j]) {
+      recvS[j] = 0;
+      continue;
+    }
+    int base[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double xs = node_pos(gS, j, a);
+      const double t = __dmul_rn(__dsub_rn(xs, gB.o[a]), gB.inv_dx);
+      base[a] = (int)floor(__dsub_rn(t, 0.5));
+    }
+    bool all = true;
+    for (int k = 0; k < Pow3<D>::K && all; ++k) {
+      const int off[3] = {k % 3, (k / 3) % 3, k / 9};
+      int64_t node = 0, stride = 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int c = base[a] + off[a];
+        all = all && c >= 0 && c < gB.res[a];
+        node += (int64_t)c * stride;
+        stride *= gB.res[a];
+      }
+      all = all && (mB[node] > 0.0);
+    }
+    if (!all) recvS[j] = 0;
+  }
+}
+
+template <int D>
+__global__ void k_proj_finish(GridGeo gB, const uint8_t* recvB, const double* num,
+                              const double* den, double eps_tol, double* out) {
+  for (int64_t I = gtid(); I < gB.nn; I += gstride()) {
+    const bool r = recvB[I];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      out[a * gB.nn + I] = r ? num[a * gB.nn + I] / (den[I] + eps_tol) : 0.0;
+  }
+}
+
+// I_{B->S} of Eq. interp_BtoS on the fine receivers.
+template <int D>
+__global__ void k_interp(GridGeo gB, GridGeo gS, const double* vB, const uint8_t* recvS,
+                         double* out) {
+  for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
+    double acc[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = 0.0;
+    if (recvS[j]) {
+      double xs[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) xs[a] = node_pos(gS, j, a);
+      Stencil<D> s;
+      make_stencil<D>(xs, gB, s);
+      for (int k = 0; k < Pow3<D>::K; ++k) {
+        double N, dN[D];
+        const int64_t node = stencil_node<D>(s, gB, k, N, dN);
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[a] += N * vB[a * gB.nn + node];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) out[a * gS.nn + j] = acc[a];
+  }
+}
+
+template <int D>
+__global__ void k_vel_from_u(GridGeo g, const double* m, const double* u, double dt, double* v) {
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
+    const int64_t i = idx % g.nn;
+    v[idx] = m[i] > 0.0 ? u[idx] / dt : 0.0;
+  }
+}
+
+// Sums of |new - old|^2 and |new|^2 over a receiver set (Eq.
+// convergence_residuals), written to slot `slot` of the scalars.
+template <int D>
+__global__ void k_rel_change(GridGeo g, const double* vnew, const double* vold,
+                             const uint8_t* recv, int slot, DevScalars* S, double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
+    const int64_t i = idx % g.nn;
+    if (!recv[i]) continue;
+    const double a = vnew[idx], b = vold[idx];
+    acc[0] += (a - b) * (a - b);
+    acc[1] += a * a;
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, partials, &S->counter, tot) && threadIdx.x == 0) {
+    S->res_num[slot] = tot[0];
+    S->res_den[slot] = tot[1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+#define OSMPM_NB(n) blocks_for(n), kThreads, 0, s
+#define OSMPM_RB(n) red_blocks_for(n), kThreads, 0, s
+
+template <int D>
+void Kernels<D>::morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,
+                             uint32_t* vals, int* err, cudaStream_t s) {
+  k_morton_keys<D><<<OSMPM_NB(n)>>>(x, n, g, keys, vals, err);
+}
+template <int D>
+void Kernels<D>::permute(const PartPtrs& src, const PartPtrs& dst, const uint32_t* perm,
+                         cudaStream_t s) {
+  k_permute<D><<<OSMPM_NB(src.n)>>>(src, dst, perm);
+}
+template <int D>
+void Kernels<D>::scatter_by_id(const PartPtrs& src, const PartPtrs& dst, cudaStream_t s) {
+  k_scatter_by_id<D><<<OSMPM_NB(src.n)>>>(src, dst);
+}
+template <int D>
+void Kernels<D>::lame(const double* E, const double* nu, PartPtrs P, cudaStream_t s) {
+  k_lame<D><<<OSMPM_NB(P.n)>>>(E, nu, P);
+}
+template <int D>
+void Kernels<D>::pack_out(const PartPtrs& P, double* x, double* v, double* B, double* F,
+                          cudaStream_t s) {
+  k_pack_out<D><<<OSMPM_NB(P.n)>>>(P, x, v, B, F);
+}
+template <int D>
+void Kernels<D>::unpack_in(const double* x, const double* v, const double* B, const double* F,
+                           PartPtrs dst, cudaStream_t s) {
+  k_unpack_in<D><<<OSMPM_NB(dst.n)>>>(x, v, B, F, dst);
+}
+template <int D>
+void Kernels<D>::p2g(const PartPtrs& P, const GridGeo& g, double* m, double* mv, double* bm,
+                     int* err, cudaStream_t s) {
+  k_p2g<D><<<OSMPM_NB(P.n)>>>(P, g, m, mv, bm, err);
+}
+template <int D>
+void Kernels<D>::normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
+                           cudaStream_t s) {
+  k_normalize<D><<<OSMPM_RB(g.nn)>>>(g, m, mv, vn);
+}
+template <int D>
+void Kernels<D>::grid_prep(const GridGeo& g, const double* m, const double* vn,
+                           const PrepArgs& a, double dt, uint8_t* dofmask, double* u,
+                           cudaStream_t s) {
+  k_grid_prep<D><<<OSMPM_RB(g.nn)>>>(g, m, vn, a, dt, dofmask, u);
+}
+template <int D>
+void Kernels<D>::grad(const PartPtrs& P, const GridGeo& g, const double* u,
+                      const uint8_t* dofmask, double* grad, double* diag, double* L, int* err,
+                      cudaStream_t s) {
+  k_grad<D><<<OSMPM_NB(P.n)>>>(P, g, u, dofmask, grad, diag, L, err);
+}
+template <int D>
+void Kernels<D>::grad_finish(const GridGeo& g, const double* m, const double* vn,
+                             const double* u, const uint8_t* dofmask, const double* gravity,
+                             double dt, double cg_rtol, int cg_max, double* grad, double* diag,
+                             double* x, double* r, double* z, double* p, DevScalars* S,
+                             double* partials, cudaStream_t s) {
+  k_grad_finish<D><<<OSMPM_RB(g.nn * D)>>>(g, m, vn, u, dofmask, gravity[0], gravity[1],
+                                           gravity[2], dt, cg_rtol, cg_max, grad, diag, x, r, z,
+                                           p, S, partials);
+}
+template <int D>
+void Kernels<D>::cg_iteration(const PartPtrs& P, const GridGeo& g, const double* m,
+                              const uint8_t* dofmask, const double* L, const double* diag,
+                              double dt, double* x, double* r, double* z, double* p, double* q,
+                              DevScalars* S, double* partials, cudaStream_t s) {
+  const double inv_dt2 = 1.0 / (dt * dt);
+  k_cg_a<D><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, inv_dt2, z, p, q, S, partials);
+  k_cg_b<D><<<OSMPM_RB(P.n)>>>(P, g, dofmask, L, p, q, S, partials);
+  k_cg_c<D><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, diag, p, q, x, r, z, S, partials);
+}
+template <int D>
+void Kernels<D>::hvp_only(const PartPtrs& P, const GridGeo& g, const double* m,
+                          const uint8_t* dofmask, const double* L, double dt, double* p,
+                          double* q, DevScalars* S, double* partials, cudaStream_t s) {
+  const double inv_dt2 = 1.0 / (dt * dt);
+  k_cg_a<D><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, inv_dt2, p, p, q, S, partials);
+  k_cg_b<D><<<OSMPM_RB(P.n)>>>(P, g, dofmask, L, p, q, S, partials);
+}
+template <int D>
+void Kernels<D>::maxabs(const GridGeo& g, const uint8_t* dofmask, const double* x,
+                        DevScalars* S, double* partials, cudaStream_t s) {
+  k_maxabs<D><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, x, S, partials);
+}
+template <int D>
+void Kernels<D>::energy_change(const PartPtrs& P, const GridGeo& g, const double* m,
+                               const double* vn, const double* u, const double* x,
+                               const double* gravity, double dt, double alpha, DevScalars* S,
+                               double* partials, cudaStream_t s) {
+  const int64_t work = P.n > g.nn * D ? P.n : g.nn * D;
+  k_energy_change<D><<<OSMPM_RB(work)>>>(P, g, m, vn, u, x, gravity[0], gravity[1], gravity[2],
+                                         dt, alpha, S, partials);
+}
+template <int D>
+void Kernels<D>::axpy(const GridGeo& g, double* u, const double* x, double alpha,
+                      cudaStream_t s) {
+  k_axpy<D><<<OSMPM_RB(g.nn * D)>>>(g, u, x, alpha);
+}
+template <int D>
+void Kernels<D>::g2p(const PartPtrs& P, const GridGeo& g, const double* u, double dt,
+                     cudaStream_t s) {
+  k_g2p<D><<<OSMPM_NB(P.n)>>>(P, g, u, dt);
+}
+template <int D>
+void Kernels<D>::gamma(const GridGeo& g, const double* m, const double* bm, double tau,
+                       uint8_t* gam, cudaStream_t s) {
+  k_gamma<D><<<OSMPM_RB(g.nn)>>>(g.nn, m, bm, tau, gam);
+}
+template <int D>
+void Kernels<D>::arbitrate(const GridGeo& gB, const GridGeo& gS, const uint8_t* gamB,
+                           const uint8_t* gamS, const double* mB, const double* mS,
+                           uint8_t* recvB, uint8_t* recvS, cudaStream_t s) {
+  k_arbitrate<D><<<OSMPM_RB(gB.nn)>>>(gB, gS, gamB, gamS, mB, mS, recvB, recvS);
+}
+template <int D>
+void Kernels<D>::proj_scatter(const GridGeo& gB, const GridGeo& gS, const double* mS,
+                              const double* vS, double* num, double* den, cudaStream_t s) {
+  k_proj_scatter<D><<<OSMPM_RB(gS.nn)>>>(gB, gS, mS, vS, num, den);
+}
+template <int D>
+void Kernels<D>::recvB_filter(const GridGeo& gB, const double* den, double tau,
+                              const uint8_t* physB, uint8_t* recvB, cudaStream_t s) {
+  k_recvB_filter<D><<<OSMPM_RB(gB.nn)>>>(gB.nn, den, tau, physB, recvB);
+}
+template <int D>
+void Kernels<D>::recvS_filter(const GridGeo& gB, const GridGeo& gS, const double* mB,
+                              const uint8_t* physS, uint8_t* recvS, cudaStream_t s) {
+  k_recvS_filter<D><<<OSMPM_RB(gS.nn)>>>(gB, gS, mB, physS, recvS);
+}
+template <int D>
+void Kernels<D>::proj_finish(const GridGeo& gB, const uint8_t* recvB, const double* num,
+                             const double* den, double eps_tol, double* out, cudaStream_t s) {
+  k_proj_finish<D><<<OSMPM_RB(gB.nn)>>>(gB, recvB, num, den, eps_tol, out);
+}
+template <int D>
+void Kernels<D>::interp(const GridGeo& gB, const GridGeo& gS, const double* vB,
+                        const uint8_t* recvS, double* out, cudaStream_t s) {
+  k_interp<D><<<OSMPM_RB(gS.nn)>>>(gB, gS, vB, recvS, out);
+}
+template <int D>
+void Kernels<D>::vel_from_u(const GridGeo& g, const double* m, const double* u, double dt,
+                            double* v, cudaStream_t s) {
+  k_vel_from_u<D><<<OSMPM_RB(g.nn * D)>>>(g, m, u, dt, v);
+}
+template <int D>
+void Kernels<D>::rel_change(const GridGeo& g, const double* vnew, const double* vold,
+                            const uint8_t* recv, int slot, DevScalars* S, double* partials,
+                            cudaStream_t s) {
+  k_rel_change<D><<<OSMPM_RB(g.nn * D)>>>(g, vnew, vold, recv, slot, S, partials);
+}
+template <int D>
+void Kernels<D>::copy_if_neg(const GridGeo& g, const double* p, double* x, const DevScalars* S,
+                             cudaStream_t s) {
+  k_copy_if_neg<D><<<OSMPM_RB(g.nn * D)>>>(g, p, x, S);
+}
+template <int D>
+void Kernels<D>::set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s) {
+  k_set_cg_state<D><<<1, 1, 0, s>>>(S, iter, done);
+}
+
+#undef OSMPM_NB
+#undef OSMPM_RB
+
+}  // namespace osmpm

@@ -1,0 +1,64 @@
+// Plain structures shared by the host drivers and the kernels.
+#pragma once
+
+#include <stdint.h>
+
+namespace osmpm {
+
+// Structured background grid (Sec. 2.2.2): node (i,j,k) at o + dx (i,j,k),
+// flat index i + res0 (j + res1 k).
+struct GridGeo {
+  double o[3];
+  double dx, inv_dx;
+  int res[3];
+  int64_t nn;
+};
+
+// Particle state, structure of arrays, component-major (x[a*n + p]).
+struct PartPtrs {
+  int64_t n;
+  double* x;      // D
+  double* v;      // D
+  double* B;      // D*D (row-major entry e at B[e*n + p])
+  double* F;      // D*D
+  double* vol0;
+  double* mass;
+  double* mu;
+  double* lam;
+  uint8_t* flags;
+  uint32_t* id;
+};
+
+// Device-side Dirichlet rule (mirrors osmpm_dirichlet; for kind 1 the
+// rotation matrix R of the step is precomputed on the host).
+struct DevRule {
+  int kind;
+  unsigned comp_mask;
+  double lo[3], hi[3];
+  double vel[3];
+  double center[3];
+  double R[9];
+};
+
+constexpr int kMaxRules = 16;
+
+// Scalars of the solver loop, kept on the device so that PCG iterations run
+// back to back without host round trips.
+struct DevScalars {
+  double rz, pq, alpha, beta, rr, rr0, tol2;
+  double pq_diag;
+  double maxabs;
+  double dE;
+  double res_num[2], res_den[2];
+  int cg_iter, cg_done, cg_neg, cg_max;
+  int err;
+  unsigned counter;
+  int pad[2];
+};
+
+enum : int {
+  kErrOutOfGrid = 1,
+  kErrNonFinite = 2,
+};
+
+}  // namespace osmpm

@@ -1,0 +1,348 @@
+"""Thin Python binding of the C ABI in ``include/osmpm.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Device memory comes from PyTorch's caching allocator and kernels
+run on a PyTorch CUDA stream (the current one unless another is given).
+Importing this module loads ``_build/libosmpm.so``; it raises if the library
+has not been built, and there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (CFUNCTYPE, POINTER, Structure, c_char_p, c_double, c_int32, c_int64,
+                    c_size_t, c_uint8, c_uint32, c_void_p)
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"the OS-MPM CUDA library is not built ({LIB_PATH}); run "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes
+OSMPM_OK = 0
+OSMPM_E_INVALID = 1
+OSMPM_E_NOMEM = 2
+OSMPM_E_CUDA = 3
+OSMPM_E_NONFINITE = 4
+OSMPM_E_NEWTON_MAXITER = 5
+OSMPM_E_LINESEARCH = 6
+OSMPM_E_OUT_OF_GRID = 7
+OSMPM_E_UNSUPPORTED = 9
+OSMPM_W_SCHWARZ_MAXITER = 100
+
+OSMPM_FIELD_MASS = 0
+OSMPM_FIELD_VN = 1
+OSMPM_FIELD_U = 2
+OSMPM_FIELD_BMASS = 3
+OSMPM_FIELD_RECEIVER = 4
+OSMPM_FIELD_BC = 5
+
+_ALLOC = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+_FREE = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
+class osmpm_allocator(Structure):
+    _fields_ = [("alloc", _ALLOC), ("free", _FREE), ("ctx", c_void_p)]
+
+
+class osmpm_domain_desc(Structure):
+    _fields_ = [("dim", c_int32), ("precision", c_int32), ("origin", c_double * 3),
+                ("dx", c_double), ("res", c_int32 * 3), ("gravity", c_double * 3),
+                ("newton_tol", c_double), ("newton_max", c_int32), ("cg_rtol", c_double),
+                ("cg_max", c_int32), ("ls_max", c_int32), ("reserved", c_int32 * 8)]
+
+
+class osmpm_particles_in(Structure):
+    _fields_ = [("n", c_int64), ("x", POINTER(c_double)), ("v", POINTER(c_double)),
+                ("B", POINTER(c_double)), ("F", POINTER(c_double)),
+                ("vol0", POINTER(c_double)), ("mass", POINTER(c_double)),
+                ("E", POINTER(c_double)), ("nu", POINTER(c_double)),
+                ("flags", POINTER(c_uint8))]
+
+
+class osmpm_dirichlet(Structure):
+    _fields_ = [("kind", c_int32), ("comp_mask", c_uint32), ("lo", c_double * 3),
+                ("hi", c_double * 3), ("vel", c_double * 3), ("center", c_double * 3),
+                ("axis", c_double * 3), ("omega", c_double)]
+
+
+class osmpm_schwarz_desc(Structure):
+    _fields_ = [("M", c_int32), ("k_max", c_int32), ("eps_conv", c_double), ("tau_B", c_double),
+                ("tau_S", c_double), ("eps_tol", c_double), ("reserved", c_int32 * 8)]
+
+
+class osmpm_stats(Structure):
+    _fields_ = [("newton_iters", c_int32), ("cg_iters", c_int32), ("ls_halvings", c_int32),
+                ("schwarz_iters", c_int32), ("solves", c_int32), ("converged", c_int32),
+                ("r_B", c_double), ("r_S", c_double), ("last_dx_inf", c_double),
+                ("reserved", c_double * 6)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+_DP = POINTER(c_double)
+_sig = {
+    "osmpm_create_domain": (c_int32, [POINTER(osmpm_domain_desc), POINTER(osmpm_particles_in),
+                                      POINTER(osmpm_allocator), c_void_p, POINTER(c_void_p)]),
+    "osmpm_destroy_domain": (c_int32, [c_void_p]),
+    "osmpm_set_dirichlet": (c_int32, [c_void_p, POINTER(osmpm_dirichlet), c_int32]),
+    "osmpm_step": (c_int32, [c_void_p, c_double, POINTER(osmpm_stats)]),
+    "osmpm_schwarz_couple": (c_int32, [c_void_p, c_void_p, c_double, POINTER(osmpm_schwarz_desc),
+                                       POINTER(osmpm_stats)]),
+    "osmpm_get_info": (c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32)]),
+    "osmpm_get_particles": (c_int32, [c_void_p, _DP, _DP, _DP, _DP]),
+    "osmpm_set_particles": (c_int32, [c_void_p, _DP, _DP, _DP, _DP]),
+    "osmpm_get_order": (c_int32, [c_void_p, POINTER(c_uint32)]),
+    "osmpm_get_grid": (c_int32, [c_void_p, c_int32, _DP]),
+    "osmpm_probe_gradient": (c_int32, [c_void_p, c_double, _DP, _DP]),
+    "osmpm_probe_hvp": (c_int32, [c_void_p, c_double, _DP, _DP, _DP]),
+    "osmpm_probe_energy_change": (c_int32, [c_void_p, c_double, _DP, _DP, c_double, _DP]),
+    "osmpm_last_error": (c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sig)
+
+
+class OsmpmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.osmpm_last_error().decode()
+        super().__init__(f"{where}: status {status}: {msg}")
+
+
+def _check(status: int, where: str, warn_ok: bool = False) -> int:
+    if status == OSMPM_OK or (warn_ok and status == OSMPM_W_SCHWARZ_MAXITER):
+        return status
+    raise OsmpmError(status, where)
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_DP)
+
+
+def osmpm_last_error() -> str:
+    return _lib.osmpm_last_error().decode()
+
+
+# ----------------------------------------------------------------------------
+# device memory and streams from PyTorch
+# ----------------------------------------------------------------------------
+def torch_allocator(device: int = 0):
+    """An osmpm_allocator backed by torch.cuda's caching allocator."""
+    import torch
+
+    def _a(size, ctx, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), device, int(stream or 0))
+        except Exception:  # the C side reports OSMPM_E_NOMEM
+            return None
+
+    def _f(ptr, size, ctx, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cb_a, cb_f = _ALLOC(_a), _FREE(_f)
+    return osmpm_allocator(cb_a, cb_f, None), (cb_a, cb_f)
+
+
+def current_stream() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+# ----------------------------------------------------------------------------
+# marshalling of the workload descriptions
+# ----------------------------------------------------------------------------
+def make_desc(spec) -> osmpm_domain_desc:
+    g = spec.grid
+    d = osmpm_domain_desc()
+    d.dim = g.dim
+    d.precision = 0
+    for a in range(3):
+        d.origin[a] = g.origin[a] if a < g.dim else 0.0
+        d.res[a] = g.res[a] if a < g.dim else 1
+        d.gravity[a] = spec.gravity[a] if a < g.dim else 0.0
+    d.dx = g.dx
+    d.newton_tol = spec.newton_tol
+    d.newton_max = spec.newton_max
+    d.cg_rtol = spec.cg_rtol
+    d.cg_max = spec.cg_max
+    d.ls_max = spec.ls_max
+    return d
+
+
+def make_rules(rules) -> "ctypes.Array":
+    arr = (osmpm_dirichlet * max(1, len(rules)))()
+    for i, r in enumerate(rules):
+        t = arr[i]
+        t.kind = r.kind
+        t.comp_mask = r.comp_mask
+        for a in range(3):
+            t.lo[a] = r.lo[a] if a < len(r.lo) else -1e30
+            t.hi[a] = r.hi[a] if a < len(r.hi) else 1e30
+            t.vel[a] = r.vel[a] if a < len(r.vel) else 0.0
+            t.center[a] = r.center[a] if a < len(r.center) else 0.0
+            t.axis[a] = r.axis[a] if a < len(r.axis) else 0.0
+        t.omega = r.omega
+    return arr
+
+
+def make_schwarz_desc(sch) -> osmpm_schwarz_desc:
+    s = osmpm_schwarz_desc()
+    s.M = sch.M
+    s.k_max = sch.k_max
+    s.eps_conv = sch.eps_conv
+    s.tau_B = sch.tau_B
+    s.tau_S = sch.tau_S
+    s.eps_tol = sch.eps_tol
+    return s
+
+
+class Domain:
+    """Owns one osmpm_domain handle (and the callbacks its allocator needs)."""
+
+    def __init__(self, spec, stream: Optional[int] = None, use_torch_allocator: bool = True,
+                 device: int = 0):
+        p = spec.particles
+        self.spec = spec
+        self.dim = spec.grid.dim
+        self.n = p.n
+        self._arrays = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                        (p.x, p.v, p.B, p.F, p.vol0, p.mass, p.E, p.nu)]
+        flags = np.ascontiguousarray(p.flags, dtype=np.uint8)
+        pin = osmpm_particles_in(p.n, *(_dp(a) for a in self._arrays),
+                                 flags.ctypes.data_as(POINTER(c_uint8)))
+        desc = make_desc(spec)
+        self._cbs = None
+        alloc_ptr = None
+        if use_torch_allocator:
+            alloc, self._cbs = torch_allocator(device)
+            self._alloc = alloc
+            alloc_ptr = ctypes.byref(alloc)
+        self.stream = current_stream() if stream is None else stream
+        h = c_void_p()
+        _check(_lib.osmpm_create_domain(ctypes.byref(desc), ctypes.byref(pin), alloc_ptr,
+                                        c_void_p(self.stream), ctypes.byref(h)),
+               "osmpm_create_domain")
+        self.h = h
+        self.set_dirichlet(spec.dirichlet)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.osmpm_destroy_domain(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls
+    def set_dirichlet(self, rules):
+        arr = make_rules(rules)
+        _check(_lib.osmpm_set_dirichlet(self.h, arr, len(rules)), "osmpm_set_dirichlet")
+
+    def step(self, dt: float) -> dict:
+        st = osmpm_stats()
+        _check(_lib.osmpm_step(self.h, dt, ctypes.byref(st)), "osmpm_step")
+        return st.as_dict()
+
+    def get_particles(self):
+        n, d = self.n, self.dim
+        x = np.empty((n, d))
+        v = np.empty((n, d))
+        B = np.empty((n, d, d))
+        F = np.empty((n, d, d))
+        _check(_lib.osmpm_get_particles(self.h, _dp(x), _dp(v), _dp(B), _dp(F)),
+               "osmpm_get_particles")
+        return x, v, B, F
+
+    def set_particles(self, x, v, B, F):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, v, B, F)]
+        _check(_lib.osmpm_set_particles(self.h, *(_dp(a) for a in arrs)), "osmpm_set_particles")
+
+    def get_order(self) -> np.ndarray:
+        ids = np.empty(self.n, dtype=np.uint32)
+        _check(_lib.osmpm_get_order(self.h, ids.ctypes.data_as(POINTER(c_uint32))), "osmpm_get_order")
+        return ids
+
+    def get_grid(self, field: int) -> np.ndarray:
+        nn = int(np.prod(self.spec.grid.res))
+        comps = self.dim if field in (OSMPM_FIELD_VN, OSMPM_FIELD_U, OSMPM_FIELD_BC) else 1
+        out = np.empty((nn, comps)) if comps > 1 else np.empty(nn)
+        _check(_lib.osmpm_get_grid(self.h, field, _dp(out)), "osmpm_get_grid")
+        return out
+
+    def probe_gradient(self, dt: float, u: np.ndarray) -> np.ndarray:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.empty_like(u)
+        _check(_lib.osmpm_probe_gradient(self.h, dt, _dp(u), _dp(out)), "osmpm_probe_gradient")
+        return out
+
+    def probe_hvp(self, dt: float, u: np.ndarray, d: np.ndarray) -> np.ndarray:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        out = np.empty_like(u)
+        _check(_lib.osmpm_probe_hvp(self.h, dt, _dp(u), _dp(d), _dp(out)), "osmpm_probe_hvp")
+        return out
+
+    def probe_energy_change(self, dt: float, u: np.ndarray, d: np.ndarray, alpha: float) -> float:
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        d = np.ascontiguousarray(d, dtype=np.float64)
+        out = c_double()
+        _check(_lib.osmpm_probe_energy_change(self.h, dt, _dp(u), _dp(d), alpha, ctypes.byref(out)),
+               "osmpm_probe_energy_change")
+        return out.value
+
+
+def osmpm_create_domain(spec, stream: Optional[int] = None, use_torch_allocator: bool = True) -> Domain:
+    return Domain(spec, stream, use_torch_allocator)
+
+
+def osmpm_destroy_domain(dom: Domain) -> None:
+    dom.close()
+
+
+def osmpm_step(dom: Domain, dt: float) -> dict:
+    return dom.step(dt)
+
+
+def osmpm_schwarz_couple(coarse: Domain, fine: Domain, dT: float, sch) -> dict:
+    """One global Schwarz step; returns the stats (``converged`` = 0 when
+    k_max was reached, in which case the last iterate was committed)."""
+    sd = make_schwarz_desc(sch)
+    st = osmpm_stats()
+    _check(_lib.osmpm_schwarz_couple(coarse.h, fine.h, dT, ctypes.byref(sd), ctypes.byref(st)),
+           "osmpm_schwarz_couple", warn_ok=True)
+    return st.as_dict()
+
+
+def osmpm_get_particles(dom: Domain):
+    return dom.get_particles()
+
+
+def osmpm_set_particles(dom: Domain, x, v, B, F):
+    dom.set_particles(x, v, B, F)
+
+
+def osmpm_get_order(dom: Domain):
+    return dom.get_order()
+
+
+def osmpm_get_grid(dom: Domain, field: int):
+    return dom.get_grid(field)
