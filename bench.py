@@ -1,0 +1,370 @@
+"""Throughput of the OS-MPM hot path on GB300.
+
+One step = one global Schwarz step (Alg. 1) of the 2D elastic-inclusion
+workload in FP64: coarse grid [0,1]^2 at dx 0.05 with the matrix
+[0.1,0.9]^2 minus the disk r < 0.1, fine grid [0.3,0.7]^2 at dx 0.005 with
+the disk r < 0.15 holding the stiff inclusion r < 0.05 (E 1e8 in E 1e6,
+nu 0.3), top edge displaced 1e-3 per step, M = 2 fine sub-steps, 4 particles
+per cell.  Metric: particle-substeps/s (fine particles count M per global
+step, coarse particles 1; Schwarz re-iterations are overhead).
+
+The device number times each step with CUDA events on the domains' stream,
+with the L2 cache flushed (a 256 MiB write) between steps, outside the
+events.  The end-to-end number times, on the host clock, the public-API
+sequence a user runs per step: upload both domains' particle state from
+pinned host memory, the coupled step, download the state.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this
+repository: a plain NumPy/SciPy restatement of the method) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2605_09097_gb300 import workloads as W  # noqa: E402
+
+METRIC = "OS-MPM particle-substeps/s at fixed error vs FP64 oracle; % HBM peak"
+UNIT = "particle-substeps/s"
+DX_S, M_SUB = 0.005, 2
+WORKLOAD = "inclusion_osmpm_2d_fp64_dxB0.05_dxS0.005_M2"
+# Schwarz iterations of one global step of this workload, averaged over the
+# first three global steps of an FP64 oracle run (used to scale the oracle's
+# bounded sample, which runs a fixed number of Schwarz iterations).
+ORACLE_SCHWARZ_ITERS_PER_STEP = 17.0
+ORACLE_SAMPLE_ITERS = 2
+L2_FLUSH_BYTES = 256 << 20
+HVP_FLOPS_PER_PARTICLE = {2: 184, 3: 1152}  # gather + L.G + G:LG + scatter (FP64 FMA = 2 flops)
+
+
+def workload():
+    return W.inclusion(dx_S=DX_S, M=M_SUB)
+
+
+def units_per_step(cB, cS, M):
+    return cB.particles.n + M * cS.particles.n
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (independent replicas, one per GPU)
+# ----------------------------------------------------------------------------
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if _cuda_ok() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if _cuda_ok() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, rank, local, world):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2605_09097_gb300 import build
+    build.build()
+    from paper_2605_09097_gb300 import osmpm
+
+    cB, cS, sch, dT = workload()
+    units = units_per_step(cB, cS, sch.M)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        B = osmpm.Domain(cB, stream=stream.cuda_stream)
+        S = osmpm.Domain(cS, stream=stream.cuda_stream)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+        torch.cuda.synchronize()
+        B.set_profiling(True)
+        S.set_profiling(True)
+        stats = []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        barrier(world)
+        torch.cuda.synchronize()
+        launches0 = osmpm.launch_count()
+        clocks.start()
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            stats.append(osmpm.osmpm_schwarz_couple(B, S, dT, sch))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        clk = clocks.stop()
+        launches = osmpm.launch_count() - launches0 - 0
+        barrier(world)
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        ms_max = max_over_ranks(ms, world)
+        cB_ = B.counters()
+        cS_ = S.counters()
+        B.set_profiling(False)
+        S.set_profiling(False)
+
+        # end to end through the public API with host buffers
+        e2e = None
+        if args.e2e_steps > 0:
+            xs = [d.get_particles() for d in (B, S)]
+            pinned = []
+            for arrs in xs:
+                pa = []
+                for a in arrs:
+                    t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+                    t.numpy()[...] = a
+                    pa.append(t.numpy())
+                pinned.append(pa)
+            h2d = sum(a.nbytes for pa in pinned for a in pa)
+            barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.e2e_steps):
+                B.set_particles(*pinned[0])
+                S.set_particles(*pinned[1])
+                osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+                for d, pa in zip((B, S), pinned):
+                    x, v, Bm, F = d.get_particles()
+                    pa[0][...] = x
+                    pa[1][...] = v
+                    pa[2][...] = Bm
+                    pa[3][...] = F
+            torch.cuda.synchronize()
+            te = max_over_ranks(time.perf_counter() - t0, world)
+            e2e = {"value": sum_over_ranks(units * args.e2e_steps, world) / te, "unit": UNIT,
+                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+                   "steps": args.e2e_steps}
+
+    value = sum_over_ranks(units * args.steps, world) / (ms_max / 1e3)
+    # roofline of the dominant kernel (the HVP): FP64 ALU bound
+    hvp_ms = cB_["hvp_ms"] + cS_["hvp_ms"]
+    hvp_n = cB_["hvp_launches"] + cS_["hvp_launches"]
+    hvp_parts = cB_["hvp_particles"] + cS_["hvp_particles"]
+    flops = hvp_parts * HVP_FLOPS_PER_PARTICLE[2]
+    achieved = flops / (hvp_ms / 1e3) / 1e9 if hvp_ms > 0 else 0.0
+    fp64_peak = 1250.0  # GFLOP/s, nominal GB300 FP64 (non-tensor)
+    iters = [s["schwarz_iters"] for s in stats]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles_coarse": cB.particles.n,
+                   "particles_fine": cS.particles.n, "M": sch.M, "dT": dT,
+                   "units_per_step": units, "parallelism": f"replicas{world}",
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                   "schwarz_iters_per_step": iters,
+                   "newton_iters_per_step": [s["newton_iters"] for s in stats],
+                   "cg_iters_per_step": [s["cg_iters"] for s in stats],
+                   "wall_ms_per_step": 1e3 * t_wall / args.steps},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_cg_b (HVP)", "bound": "alu", "achieved": achieved,
+                     "peak": fp64_peak, "unit": "GFLOP/s", "frac": achieved / fp64_peak,
+                     "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (GB300)",
+                     "launches": hvp_n, "avg_launch_us": 1e3 * hvp_ms / max(hvp_n, 1),
+                     "flops_per_particle": HVP_FLOPS_PER_PARTICLE[2]},
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(ORACLE_SAMPLE_ITERS)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores
+# ----------------------------------------------------------------------------
+def oracle_sample(n_iters):
+    """Times the FP64 oracle on the bench workload: the first ``n_iters``
+    Schwarz iterations of global step 1.  Returns (seconds, units), units
+    scaled by n_iters / ORACLE_SCHWARZ_ITERS_PER_STEP."""
+    import dataclasses
+    from oracle import osmpm_oracle as O
+    cB, cS, sch, dT = workload()
+    sch = dataclasses.replace(sch, k_max=n_iters - 1)
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    t0 = time.perf_counter()
+    O.schwarz_step(B, S, dT, sch)
+    t = time.perf_counter() - t0
+    units = units_per_step(cB, cS, sch.M) * n_iters / ORACLE_SCHWARZ_ITERS_PER_STEP
+    return t, units
+
+
+def _threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info()]
+        return max(n) if n else 1
+    except Exception:
+        return int(os.environ.get("OMP_NUM_THREADS", "1"))
+
+
+def cpu_baseline(n_iters):
+    t, units = oracle_sample(n_iters)
+    return {"value": units / t, "unit": UNIT, "cores": _threads(), "kind": "oracle",
+            "sample": f"first {n_iters} Schwarz iterations of global step 1 of {WORKLOAD} "
+                      f"({t:.1f} s), scaled by {n_iters}/{ORACLE_SCHWARZ_ITERS_PER_STEP:g} "
+                      "of a global step's units"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    tot_t, tot_u = 0.0, 0.0
+    for _ in range(args.steps):
+        t, u = oracle_sample(1)
+        tot_t += t
+        tot_u += u
+    value = tot_u / tot_t
+    cores = _threads()
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "cpu"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"each step: the first Schwarz iteration of global step 1 of "
+                                       f"{WORKLOAD}, scaled by 1/{ORACLE_SCHWARZ_ITERS_PER_STEP:g} "
+                                       "of a global step's units"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, local, world = dist_init(args.gpus)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, local, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -78,6 +78,7 @@ typedef struct osmpm_domain_desc {
   double cg_rtol;           /* PCG stops when |r| <= cg_rtol |r_0| */
   int32_t cg_max;           /* PCG iteration cap per Newton iteration */
   int32_t ls_max;           /* line search tries alpha = 1, 1/2, ..., 2^-ls_max */
+  double mass_eps;          /* active nodes (the set N of Sec. 3.2.1): m_i > mass_eps >= 0 */
   int32_t reserved[8];      /* must be zero */
 } osmpm_domain_desc;
 
@@ -225,6 +226,27 @@ osmpm_status osmpm_probe_hvp(osmpm_domain* dom, double dt, const double* u, cons
                              double* hd);
 osmpm_status osmpm_probe_energy_change(osmpm_domain* dom, double dt, const double* u,
                                        const double* d, double alpha, double* dE);
+
+/* Counters for measurement.  launches: kernels this library has launched in
+ * the process.  hvp_*: when HVP timing is enabled on the domain, the number
+ * of Hessian-vector-product launches that did work, their summed duration
+ * from CUDA events recorded on the domain's stream around each launch, and
+ * the particles they processed. */
+typedef struct osmpm_counters {
+  int64_t launches;
+  int64_t hvp_launches;
+  double hvp_ms;
+  int64_t hvp_particles;
+  double reserved[4];
+} osmpm_counters;
+
+/* Enables (1) or disables (0) CUDA-event timing of the HVP launches of this
+ * domain and resets its HVP counters.  Timing adds two event records per
+ * PCG iteration; results are read with osmpm_get_counters. */
+osmpm_status osmpm_set_profiling(osmpm_domain* dom, int32_t enable);
+
+/* Reads the counters; dom may be NULL (process-wide launch count only). */
+osmpm_status osmpm_get_counters(const osmpm_domain* dom, osmpm_counters* out);
 
 /* Message of the last failure on this thread (never NULL). */
 const char* osmpm_last_error(void);

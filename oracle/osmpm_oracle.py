@@ -208,6 +208,43 @@ def psi(F: np.ndarray, mu: np.ndarray, lam: np.ndarray) -> np.ndarray:
     return out
 
 
+def _det_change(F0: np.ndarray, dF: np.ndarray) -> np.ndarray:
+    """det(F0 + dF) - det(F0) as a polynomial in dF (exact identity):
+    2D: F0_00 dF_11 + dF_00 F0_11 + det dF - F0_01 dF_10 - dF_01 F0_10;
+    3D: cof(F0):dF + F0:cof(dF) + det dF."""
+    d = F0.shape[-1]
+    if d == 2:
+        return (F0[:, 0, 0] * dF[:, 1, 1] + dF[:, 0, 0] * F0[:, 1, 1]
+                - F0[:, 0, 1] * dF[:, 1, 0] - dF[:, 0, 1] * F0[:, 1, 0]
+                + dF[:, 0, 0] * dF[:, 1, 1] - dF[:, 0, 1] * dF[:, 1, 0])
+
+    def cof(A):
+        return np.stack([np.cross(A[:, 1], A[:, 2]), np.cross(A[:, 2], A[:, 0]),
+                         np.cross(A[:, 0], A[:, 1])], axis=1)
+    return (np.sum(cof(F0) * dF, axis=(1, 2)) + np.sum(F0 * cof(dF), axis=(1, 2))
+            + np.linalg.det(dF))
+
+
+def psi_change(F0: np.ndarray, dF: np.ndarray, mu: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """Psi(F0 + dF) - Psi(F0) per particle, through exact difference
+    identities: mu (F0:dF + |dF|^2/2) - mu dl + lam/2 dl (2 ln J0 + dl) with
+    dl = ln J1 - ln J0 = log1p(dJ / J0).  Its rounding error scales with dF,
+    not with F (the line search of Sec. 2.2.5 compares changes down to the
+    Newton tolerance).  +inf where J0 + dJ <= 0."""
+    d = F0.shape[-1]
+    jm1 = _det_minus_one(F0 - np.eye(d)[None])
+    J0 = 1.0 + jm1
+    dJ = _det_change(F0, dF)
+    out = np.full(J0.shape, np.inf)
+    ok = (J0 > 0) & (J0 + dJ > 0)
+    dl = np.log1p(dJ[ok] / J0[ok])
+    lnJ0 = np.log1p(jm1[ok])
+    m, l = mu[ok], lam[ok]
+    out[ok] = (m * (np.sum(F0[ok] * dF[ok], axis=(1, 2)) + 0.5 * np.sum(dF[ok] ** 2, axis=(1, 2)))
+               - m * dl + 0.5 * l * dl * (2.0 * lnJ0 + dl))
+    return out
+
+
 def pk1(F: np.ndarray, mu: np.ndarray, lam: np.ndarray) -> np.ndarray:
     """First Piola-Kirchhoff stress dPsi/dF = mu (F - F^-T) + lam ln J F^-T."""
     J = np.linalg.det(F)
@@ -244,11 +281,13 @@ class GridFields:
     bm: Optional[np.ndarray] = None  # (nn,) boundary-particle mass (Eq. boundary_grid_set)
 
 
-def p2g(p: Particles, grid: Grid, boundary_mass: bool = False) -> GridFields:
+def p2g(p: Particles, grid: Grid, boundary_mass: bool = False, mass_eps: float = 0.0) -> GridFields:
     """APIC particle-to-grid transfer, Eq. p2g_transfer (and Eq. p2g_substep):
     m_i = sum_p m_p N_i(x_p), (mv)_i = sum_p m_p N_i (v_p + B_p D_p^-1 (x_i - x_p)),
     D_p^-1 = 4/dx^2 I for the quadratic B-spline.  With ``boundary_mass`` also
-    returns sum over boundary particles of m_p N_i (Eq. boundary_grid_set)."""
+    returns sum over boundary particles of m_p N_i (Eq. boundary_grid_set).
+    The active node set (N_alpha of Sec. 3.2.1) is m_i > mass_eps: nodes that
+    a particle touches only with a round-off-sized weight carry no DOF."""
     d = grid.dim
     nn = grid.n_nodes
     st = stencil(p.x, grid)
@@ -260,7 +299,7 @@ def p2g(p: Particles, grid: Grid, boundary_mass: bool = False) -> GridFields:
     mv = np.zeros((nn, d))
     for a in range(d):
         np.add.at(mv[:, a], st.node, p.mass[:, None] * st.N * vel[:, :, a])
-    active = m > 0.0
+    active = m > mass_eps
     vn = np.zeros((nn, d))
     vn[active] = mv[active] / m[active, None]
     bm = None
@@ -398,7 +437,8 @@ def energy(pr: Problem, u: np.ndarray) -> float:
 def energy_change(pr: Problem, u: np.ndarray, step: np.ndarray, alpha: float) -> float:
     """E_h(u + alpha step) - E_h(u), summed term by term: per node
     m_i/(2dt^2) (alpha s_i).(2(u_i - dt v_i^n) + alpha s_i) - alpha s_i . f_i,
-    per particle V_p^0 (Psi(F_p(u + alpha s)) - Psi(F_p(u))).  Equal to the
+    per particle V_p^0 (Psi(F_p(u) + dF_p) - Psi(F_p(u))) with
+    dF_p = alpha (sum_i s_i grad N_i^T) F_p^n (``psi_change``).  Equal to the
     difference of two ``energy`` values, without the cancellation of the
     large terms they hold (the line-search test of Sec. 2.2.5 is the sign of
     this number).  +inf when a trial inverts an element."""
@@ -408,12 +448,12 @@ def energy_change(pr: Problem, u: np.ndarray, step: np.ndarray, alpha: float) ->
                    * s[a] * (2.0 * (u[a] - pr.dt * pr.gf.vn[a]) + s[a]))
     ext = -np.sum(s[a] * pr.fext[a])
     F0 = deformation(pr.p, pr.st, u)
-    F1 = deformation(pr.p, pr.st, u + s)
-    psi1 = psi(F1, pr.mu, pr.lam)
-    if not np.all(np.isfinite(psi1)):
+    Gs = np.einsum("pka,pkb->pab", s[pr.st.node], pr.st.dN)
+    dF = np.einsum("pab,pbc->pac", Gs, pr.p.F)
+    dpsi = psi_change(F0, dF, pr.mu, pr.lam)
+    if not np.all(np.isfinite(dpsi)):
         return float("inf")
-    el = np.sum(pr.p.vol0 * (psi1 - psi(F0, pr.mu, pr.lam)))
-    return float(inert + ext + el)
+    return float(inert + ext + np.sum(pr.p.vol0 * dpsi))
 
 
 def gradient(pr: Problem, u: np.ndarray) -> np.ndarray:
@@ -523,7 +563,7 @@ def solve_domain(ds: DomainState, gf: GridFields, dt: float,
 def step(ds: DomainState, dt: float, stats: Optional[NewtonStats] = None) -> np.ndarray:
     """One backward-Euler MPM step of a single domain: P2G, Newton solve,
     G2P with F update and advection.  Returns the solved grid displacement."""
-    gf = p2g(ds.p, ds.spec.grid)
+    gf = p2g(ds.p, ds.spec.grid, mass_eps=ds.spec.mass_eps)
     u = solve_domain(ds, gf, dt, stats=stats)
     ds.p = g2p(ds.p, ds.spec.grid, u, dt)
     return u
@@ -692,8 +732,8 @@ def schwarz_step(B: DomainState, S: DomainState, dT: float, sch: SchwarzSpec,
     gB, gS = B.spec.grid, S.spec.grid
     # Step 0 (Eq. store_states): snapshot of the fine particles
     snap = S.p.copy()
-    gfB = p2g(B.p, gB, boundary_mass=True)
-    gfS = p2g(S.p, gS, boundary_mass=True)
+    gfB = p2g(B.p, gB, boundary_mass=True, mass_eps=B.spec.mass_eps)
+    gfS = p2g(S.p, gS, boundary_mass=True, mass_eps=S.spec.mass_eps)
     sets = interface_sets(B, S, gfB, gfS, sch, dT)
     if sets_out is not None:
         sets_out["sets"] = sets
@@ -711,7 +751,7 @@ def schwarz_step(B: DomainState, S: DomainState, dT: float, sch: SchwarzSpec,
         vB_new = np.where(gfB.active[:, None], uB / dT, 0.0)
         # 2. fine sub-cycling (Eqs. spatial_interp_n, implicit_solve_fine)
         S.p = snap.copy()
-        gf = p2g(S.p, gS)
+        gf = p2g(S.p, gS, mass_eps=S.spec.mass_eps)
         vSnp1 = interp_B2S(gB, gS, vB_new, sets.recvS)
         for m in range(1, M + 1):
             bc = time_interp(vSn, vSnp1, m, M)
@@ -719,7 +759,7 @@ def schwarz_step(B: DomainState, S: DomainState, dT: float, sch: SchwarzSpec,
             uS = solve_domain(S, gf, dt, sets.recvS, bc, ns)
             st.newton_S.append(ns.iters)
             S.p = g2p(S.p, gS, uS, dt)
-            gf = p2g(S.p, gS)
+            gf = p2g(S.p, gS, mass_eps=S.spec.mass_eps)
         # 3. convergence (Eqs. convergence_residuals, convergence_criterion)
         vGB_new = project_S2B(gB, gS, gf, sets.recvB, sch.eps_tol)
         rB = rel_change(vGB_new, vGB, sets.recvB)

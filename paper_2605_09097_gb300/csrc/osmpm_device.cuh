@@ -166,6 +166,62 @@ __device__ __forceinline__ bool neo_hookean(const double* F, double mu, double l
   return true;
 }
 
+// det(F0 + dF) - det(F0) as a polynomial in dF (exact identity).
+template <int D>
+__device__ __forceinline__ double det_change(const double* A, const double* B) {
+  if (D == 2) {
+    return A[0] * B[3] + B[0] * A[3] - A[1] * B[2] - B[1] * A[2] + (B[0] * B[3] - B[1] * B[2]);
+  } else {
+    // cof(A):B + A:cof(B) + det B, cof rows = cross products of the other rows
+    double cA[9], cB[9];
+    const int r1[3] = {1, 2, 0}, r2[3] = {2, 0, 1};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double* a1 = A + 3 * r1[i];
+      const double* a2 = A + 3 * r2[i];
+      const double* b1 = B + 3 * r1[i];
+      const double* b2 = B + 3 * r2[i];
+      cA[3 * i + 0] = a1[1] * a2[2] - a1[2] * a2[1];
+      cA[3 * i + 1] = a1[2] * a2[0] - a1[0] * a2[2];
+      cA[3 * i + 2] = a1[0] * a2[1] - a1[1] * a2[0];
+      cB[3 * i + 0] = b1[1] * b2[2] - b1[2] * b2[1];
+      cB[3 * i + 1] = b1[2] * b2[0] - b1[0] * b2[2];
+      cB[3 * i + 2] = b1[0] * b2[1] - b1[1] * b2[0];
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s += cA[i] * B[i] + A[i] * cB[i];
+    const double detB = B[0] * cB[0] + B[1] * cB[1] + B[2] * cB[2];
+    return s + detB;
+  }
+}
+
+// Psi(F0 + dF) - Psi(F0) through exact difference identities, so that its
+// rounding error scales with dF:  mu (F0:dF + |dF|^2/2) - mu dl
+// + lam/2 dl (2 ln J0 + dl), dl = log1p(dJ / J0).  False when J0 <= 0 or
+// J0 + dJ <= 0 (the energy change is +inf).
+template <int D>
+__device__ __forceinline__ bool psi_change(const double* F0, const double* dF, double mu,
+                                           double lam, double& out) {
+  double H[D * D];
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) H[i] = F0[i] - ((i % (D + 1)) == 0 ? 1.0 : 0.0);
+  const double jm1 = det_minus_one<D>(H);
+  const double J0 = 1.0 + jm1;
+  const double dJ = det_change<D>(F0, dF);
+  if (!(J0 > 0.0) || !(J0 + dJ > 0.0)) return false;
+  const double dl = log1p(dJ / J0);
+  const double lnJ0 = log1p(jm1);
+  double fd = 0.0, dd = 0.0;
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) {
+    fd += F0[i] * dF[i];
+    dd += dF[i] * dF[i];
+  }
+  out = mu * (fd + 0.5 * dd) - mu * dl + 0.5 * lam * dl * (2.0 * lnJ0 + dl);
+  return true;
+}
+
 // First Piola-Kirchhoff stress P = mu (F - F^-T) + lam ln J F^-T.
 template <int D>
 __device__ __forceinline__ void pk1(const double* F, double mu, double lam, const NeoHookean<D>& s,

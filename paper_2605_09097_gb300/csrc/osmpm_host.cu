@@ -17,6 +17,8 @@
 
 using namespace osmpm;
 
+std::atomic<long long> osmpm::g_launch_count{0};
+
 namespace {
 
 thread_local std::string g_last_error = "no error";
@@ -79,6 +81,13 @@ struct osmpm_domain {
   double* partials = nullptr;
   int* err = nullptr;
   int* err_host = nullptr;
+
+  // optional CUDA-event timing of the HVP launches (osmpm_set_profiling)
+  bool time_hvp = false;
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
+  int ev_used = 0;              // pairs recorded in the current PCG
+  double hvp_ms = 0.0;
+  long long hvp_launches = 0;
 };
 
 namespace {
@@ -118,6 +127,8 @@ void free_all(osmpm_domain* d) {
       cudaFreeAsync(b.first, d->stream);
   }
   d->blocks.clear();
+  for (cudaEvent_t e : d->ev) cudaEventDestroy(e);
+  d->ev.clear();
   if (d->S_host) cudaFreeHost(d->S_host);
   if (d->err_host) cudaFreeHost(d->err_host);
   d->S_host = nullptr;
@@ -277,10 +288,24 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
                              d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
                              d->cz, d->cp, d->S, d->partials, d->stream));
   int chunk = 8;
+  int launched = 0;
+  d->ev_used = 0;
   for (;;) {
-    for (int c = 0; c < chunk; ++c)
-      DISPATCH(d, K::cg_iteration(d->P, d->geo, d->m, d->dofmask, d->L, d->diag, dt, d->cx,
-                                  d->cr, d->cz, d->cp, d->cq, d->S, d->partials, d->stream));
+    for (int c = 0; c < chunk; ++c) {
+      DISPATCH(d, K::cg_a(d->geo, d->m, d->dofmask, dt, d->cz, d->cp, d->cq, d->S, d->partials,
+                          d->stream));
+      const bool timed = d->time_hvp && (size_t)(2 * d->ev_used + 1) < d->ev.size();
+      if (timed) CUDA_TRY(cudaEventRecord(d->ev[2 * d->ev_used], d->stream));
+      DISPATCH(d, K::cg_b(d->P, d->geo, d->dofmask, d->L, d->cp, d->cq, d->S, d->partials,
+                          d->stream));
+      if (timed) {
+        CUDA_TRY(cudaEventRecord(d->ev[2 * d->ev_used + 1], d->stream));
+        d->ev_used++;
+      }
+      DISPATCH(d, K::cg_c(d->geo, d->dofmask, d->diag, d->cp, d->cq, d->cx, d->cr, d->cz, d->S,
+                          d->partials, d->stream));
+      ++launched;
+    }
     DISPATCH(d, K::copy_if_neg(d->geo, d->cp, d->cx, d->S, d->stream));
     DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
     OSMPM_TRY(sync_scalars(d));
@@ -289,6 +314,18 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
     if (chunk < 64) chunk *= 2;
   }
   st.cg += d->S_host->cg_iter;
+  if (d->time_hvp) {
+    // HVP launches that did work: one per completed iteration, plus the one
+    // that found negative curvature; later launches of the chunk returned at once
+    int worked = d->S_host->cg_iter + (d->S_host->cg_neg ? 1 : 0);
+    if (worked > d->ev_used) worked = d->ev_used;
+    for (int i = 0; i < worked; ++i) {
+      float ms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&ms, d->ev[2 * i], d->ev[2 * i + 1]));
+      d->hvp_ms += ms;
+    }
+    d->hvp_launches += worked;
+  }
   return OSMPM_OK;
 }
 
@@ -442,7 +479,7 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
     nn *= desc->res[a];
   }
   if (!(desc->newton_tol > 0.0) || desc->newton_max < 1 || !(desc->cg_rtol > 0.0) ||
-      desc->cg_max < 1 || desc->ls_max < 0)
+      desc->cg_max < 1 || desc->ls_max < 0 || !(desc->mass_eps >= 0.0) || !std::isfinite(desc->mass_eps))
     return fail(OSMPM_E_INVALID, "bad solver controls");
   if (pin->n < 1 || pin->n > (int64_t)0x7fffffff) return fail(OSMPM_E_INVALID, "particle count out of range");
   if (!pin->x || !pin->v || !pin->B || !pin->F || !pin->vol0 || !pin->mass || !pin->E || !pin->nu ||
@@ -475,6 +512,7 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   g.dx = desc->dx;
   g.inv_dx = 1.0 / desc->dx;
   g.nn = nn;
+  g.mass_eps = desc->mass_eps;
 
   auto cleanup = [&](osmpm_status st) {
     free_all(d);
@@ -723,6 +761,30 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   fill_stats(stats, st, iters, converged, rB, rS);
   if (!converged)
     return fail(OSMPM_W_SCHWARZ_MAXITER, "Schwarz stopped at k_max = %d (r_B %g, r_S %g)", sd->k_max, rB, rS);
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_set_profiling(osmpm_domain* d, int32_t enable) {
+  OSMPM_TRY(check_domain(d));
+  if (enable && d->ev.empty()) {
+    d->ev.resize(2 * 20001);
+    for (auto& e : d->ev) CUDA_TRY(cudaEventCreate(&e));
+  }
+  d->time_hvp = enable != 0;
+  d->hvp_ms = 0.0;
+  d->hvp_launches = 0;
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_get_counters(const osmpm_domain* d, osmpm_counters* out) {
+  if (!out) return fail(OSMPM_E_INVALID, "null output");
+  memset(out, 0, sizeof(*out));
+  out->launches = (int64_t)g_launch_count.load();
+  if (d) {
+    out->hvp_launches = d->hvp_launches;
+    out->hvp_ms = d->hvp_ms;
+    out->hvp_particles = d->hvp_launches * d->n;
+  }
   return OSMPM_OK;
 }
 

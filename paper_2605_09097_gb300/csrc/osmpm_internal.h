@@ -4,9 +4,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "osmpm_types.h"
 
 namespace osmpm {
+
+// Kernels launched by the library in this process (every launcher adds the
+// number of kernels it enqueues).
+extern std::atomic<long long> g_launch_count;
 
 // Launch shape helpers shared by drivers and launchers.
 constexpr int kRedBlocksMax = 1216;  // 152 SMs x 8 resident 256-thread blocks
@@ -56,10 +62,15 @@ struct Kernels {
                           const uint8_t* dofmask, const double* gravity, double dt, double cg_rtol,
                           int cg_max, double* grad, double* diag, double* x, double* r, double* z,
                           double* p, DevScalars* S, double* partials, cudaStream_t s);
-  static void cg_iteration(const PartPtrs& P, const GridGeo& g, const double* m,
-                           const uint8_t* dofmask, const double* L, const double* diag, double dt,
-                           double* x, double* r, double* z, double* p, double* q, DevScalars* S,
-                           double* partials, cudaStream_t s);
+  // one PCG iteration = cg_a (p update, diagonal part), cg_b (HVP), cg_c (updates)
+  static void cg_a(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
+                   const double* z, double* p, double* q, DevScalars* S, double* partials,
+                   cudaStream_t s);
+  static void cg_b(const PartPtrs& P, const GridGeo& g, const uint8_t* dofmask, const double* L,
+                   const double* p, double* q, DevScalars* S, double* partials, cudaStream_t s);
+  static void cg_c(const GridGeo& g, const uint8_t* dofmask, const double* diag,
+                   const double* p, const double* q, double* x, double* r, double* z,
+                   DevScalars* S, double* partials, cudaStream_t s);
   static void hvp_only(const PartPtrs& P, const GridGeo& g, const double* m,
                        const uint8_t* dofmask, const double* L, double dt, double* p, double* q,
                        DevScalars* S, double* partials, cudaStream_t s);

@@ -232,7 +232,7 @@ __global__ void k_normalize(GridGeo g, const double* m, const double* mv, double
   for (int64_t i = gtid(); i < g.nn; i += gstride()) {
     const double mi = m[i];
 #pragma unroll
-    for (int a = 0; a < D; ++a) vn[a * g.nn + i] = mi > 0.0 ? mv[a * g.nn + i] / mi : 0.0;
+    for (int a = 0; a < D; ++a) vn[a * g.nn + i] = mi > g.mass_eps ? mv[a * g.nn + i] / mi : 0.0;
   }
 }
 
@@ -246,7 +246,7 @@ __global__ void k_grid_prep(GridGeo g, const double* m, const double* vn, PrepAr
                             uint8_t* dofmask, double* u) {
   const unsigned all = (1u << D) - 1u;
   for (int64_t i = gtid(); i < g.nn; i += gstride()) {
-    const bool active = m[i] > 0.0;
+    const bool active = m[i] > g.mass_eps;
     double xi[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) xi[a] = node_pos(g, i, a);
@@ -407,7 +407,7 @@ __global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, cons
     const int a = (int)(idx / g.nn);
     const int64_t i = idx - (int64_t)a * g.nn;
     const double mi = m[i];
-    const bool active = mi > 0.0;
+    const bool active = mi > g.mass_eps;
     const bool fr = (dofmask[i] >> a) & 1u;
     double gi = 0.0;
     if (active) gi = grad[idx] + mi * inv_dt2 * (u[idx] - dt * vn[idx]) - mi * gv[a];
@@ -604,7 +604,7 @@ __global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrs P, GridGeo 
   constexpr int DD = D * D;
   double acc[1] = {0.0};
   for (int64_t pi = gtid(); pi < P.n; pi += gstride()) {
-    double xp[D], Fn[DD], Gu[DD], Gs[DD], F0[DD], F1[DD];
+    double xp[D], Fn[DD], Gu[DD], Gs[DD], F0[DD], dF[DD];
     load_x<D>(P, pi, xp);
     load_F<D>(P, pi, Fn);
     Stencil<D> s;
@@ -612,17 +612,21 @@ __global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrs P, GridGeo 
     gather_grad<D>(s, g, u, Gu);
     gather_grad<D>(s, g, x, Gs);
     deform<D>(Gu, Fn, F0);
+    // dF = alpha Gs F^n
 #pragma unroll
-    for (int e = 0; e < DD; ++e) Gs[e] = Gu[e] + alpha * Gs[e];
-    deform<D>(Gs, Fn, F1);
-    const double mu = P.mu[pi], lam = P.lam[pi];
-    NeoHookean<D> n0, n1;
-    const bool ok0 = neo_hookean<D>(F0, mu, lam, n0);
-    const bool ok1 = neo_hookean<D>(F1, mu, lam, n1);
-    if (!ok1 || !ok0) {
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        double t = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) t += Gs[a * D + c] * Fn[c * D + b];
+        dF[a * D + b] = alpha * t;
+      }
+    double dpsi;
+    if (!psi_change<D>(F0, dF, P.mu[pi], P.lam[pi], dpsi)) {
       acc[0] += INFINITY;
     } else {
-      acc[0] += P.vol0[pi] * (n1.psi - n0.psi);
+      acc[0] += P.vol0[pi] * dpsi;
     }
   }
   const double inv_2dt2 = 0.5 / (dt * dt);
@@ -631,7 +635,7 @@ __global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrs P, GridGeo 
     const int a = (int)(idx / g.nn);
     const int64_t i = idx - (int64_t)a * g.nn;
     const double mi = m[i];
-    if (!(mi > 0.0)) continue;
+    if (!(mi > g.mass_eps)) continue;
     const double sv = alpha * x[idx];
     acc[0] += mi * inv_2dt2 * sv * (2.0 * (u[idx] - dt * vn[idx]) + sv) - sv * mi * gv[a];
   }
@@ -703,9 +707,10 @@ __global__ void __launch_bounds__(kThreads) k_g2p(PartPtrs P, GridGeo g, const d
 // Schwarz interface operators (Sec. 3.2)
 // ---------------------------------------------------------------------------
 template <int D>
-__global__ void k_gamma(int64_t nn, const double* m, const double* bm, double tau, uint8_t* gam) {
+__global__ void k_gamma(int64_t nn, double mass_eps, const double* m, const double* bm, double tau,
+                        uint8_t* gam) {
   for (int64_t i = gtid(); i < nn; i += gstride())
-    gam[i] = (m[i] > 0.0 && bm[i] > tau) ? 1 : 0;
+    gam[i] = (m[i] > mass_eps && bm[i] > tau) ? 1 : 0;
 }
 
 // Eq. overlap_donor on coincident boundary nodes (|x_B - x_S|_inf <= 1e-9
@@ -742,7 +747,7 @@ __global__ void k_proj_scatter(GridGeo gB, GridGeo gS, const double* mS, const d
                                double* num, double* den) {
   for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
     const double mj = mS[j];
-    if (!(mj > 0.0)) continue;
+    if (!(mj > gS.mass_eps)) continue;
     double xs[D], vj[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
@@ -819,7 +824,7 @@ __global__ void k_recvS_filter(GridGeo gB, GridGeo gS, const double* mB, const u
         node += (int64_t)c * stride;
         stride *= gB.res[a];
       }
-      all = all && (mB[node] > 0.0);
+      all = all && (mB[node] > gB.mass_eps);
     }
     if (!all) recvS[j] = 0;
   }
@@ -866,7 +871,7 @@ template <int D>
 __global__ void k_vel_from_u(GridGeo g, const double* m, const double* u, double dt, double* v) {
   for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
     const int64_t i = idx % g.nn;
-    v[idx] = m[i] > 0.0 ? u[idx] / dt : 0.0;
+    v[idx] = m[i] > g.mass_eps ? u[idx] / dt : 0.0;
   }
 }
 
@@ -893,8 +898,8 @@ __global__ void k_rel_change(GridGeo g, const double* vnew, const double* vold,
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-#define OSMPM_NB(n) blocks_for(n), kThreads, 0, s
-#define OSMPM_RB(n) red_blocks_for(n), kThreads, 0, s
+#define OSMPM_NB(n) (g_launch_count += 1, blocks_for(n)), kThreads, 0, s
+#define OSMPM_RB(n) (g_launch_count += 1, red_blocks_for(n)), kThreads, 0, s
 
 template <int D>
 void Kernels<D>::morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,
@@ -957,13 +962,21 @@ void Kernels<D>::grad_finish(const GridGeo& g, const double* m, const double* vn
                                            p, S, partials);
 }
 template <int D>
-void Kernels<D>::cg_iteration(const PartPtrs& P, const GridGeo& g, const double* m,
-                              const uint8_t* dofmask, const double* L, const double* diag,
-                              double dt, double* x, double* r, double* z, double* p, double* q,
-                              DevScalars* S, double* partials, cudaStream_t s) {
-  const double inv_dt2 = 1.0 / (dt * dt);
-  k_cg_a<D><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, inv_dt2, z, p, q, S, partials);
+void Kernels<D>::cg_a(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
+                      const double* z, double* p, double* q, DevScalars* S, double* partials,
+                      cudaStream_t s) {
+  k_cg_a<D><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, 1.0 / (dt * dt), z, p, q, S, partials);
+}
+template <int D>
+void Kernels<D>::cg_b(const PartPtrs& P, const GridGeo& g, const uint8_t* dofmask,
+                      const double* L, const double* p, double* q, DevScalars* S,
+                      double* partials, cudaStream_t s) {
   k_cg_b<D><<<OSMPM_RB(P.n)>>>(P, g, dofmask, L, p, q, S, partials);
+}
+template <int D>
+void Kernels<D>::cg_c(const GridGeo& g, const uint8_t* dofmask, const double* diag,
+                      const double* p, const double* q, double* x, double* r, double* z,
+                      DevScalars* S, double* partials, cudaStream_t s) {
   k_cg_c<D><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, diag, p, q, x, r, z, S, partials);
 }
 template <int D>
@@ -1001,7 +1014,7 @@ void Kernels<D>::g2p(const PartPtrs& P, const GridGeo& g, const double* u, doubl
 template <int D>
 void Kernels<D>::gamma(const GridGeo& g, const double* m, const double* bm, double tau,
                        uint8_t* gam, cudaStream_t s) {
-  k_gamma<D><<<OSMPM_RB(g.nn)>>>(g.nn, m, bm, tau, gam);
+  k_gamma<D><<<OSMPM_RB(g.nn)>>>(g.nn, g.mass_eps, m, bm, tau, gam);
 }
 template <int D>
 void Kernels<D>::arbitrate(const GridGeo& gB, const GridGeo& gS, const uint8_t* gamB,
@@ -1052,6 +1065,7 @@ void Kernels<D>::copy_if_neg(const GridGeo& g, const double* p, double* x, const
 }
 template <int D>
 void Kernels<D>::set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s) {
+  g_launch_count += 1;
   k_set_cg_state<D><<<1, 1, 0, s>>>(S, iter, done);
 }
 

@@ -12,6 +12,7 @@ struct GridGeo {
   double dx, inv_dx;
   int res[3];
   int64_t nn;
+  double mass_eps;  // active nodes: m_i > mass_eps
 };
 
 // Particle state, structure of arrays, component-major (x[a*n + p]).

@@ -119,6 +119,7 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32
   if (passes < 1) passes = 1;
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = 8 * pass;
+    g_launch_count += 3;
     k_rs_hist<<<nb, kRsThreads, 0, s>>>(ka, n, shift, hist, nb);
     k_rs_scan<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nb);
     k_rs_scatter<<<nb, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, hist, nb);

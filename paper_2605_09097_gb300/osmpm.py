@@ -57,7 +57,8 @@ class osmpm_domain_desc(Structure):
     _fields_ = [("dim", c_int32), ("precision", c_int32), ("origin", c_double * 3),
                 ("dx", c_double), ("res", c_int32 * 3), ("gravity", c_double * 3),
                 ("newton_tol", c_double), ("newton_max", c_int32), ("cg_rtol", c_double),
-                ("cg_max", c_int32), ("ls_max", c_int32), ("reserved", c_int32 * 8)]
+                ("cg_max", c_int32), ("ls_max", c_int32), ("mass_eps", c_double),
+                ("reserved", c_int32 * 8)]
 
 
 class osmpm_particles_in(Structure):
@@ -89,6 +90,14 @@ class osmpm_stats(Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class osmpm_counters(Structure):
+    _fields_ = [("launches", c_int64), ("hvp_launches", c_int64), ("hvp_ms", c_double),
+                ("hvp_particles", c_int64), ("reserved", c_double * 4)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 _DP = POINTER(c_double)
 _sig = {
     "osmpm_create_domain": (c_int32, [POINTER(osmpm_domain_desc), POINTER(osmpm_particles_in),
@@ -106,6 +115,8 @@ _sig = {
     "osmpm_probe_gradient": (c_int32, [c_void_p, c_double, _DP, _DP]),
     "osmpm_probe_hvp": (c_int32, [c_void_p, c_double, _DP, _DP, _DP]),
     "osmpm_probe_energy_change": (c_int32, [c_void_p, c_double, _DP, _DP, c_double, _DP]),
+    "osmpm_set_profiling": (c_int32, [c_void_p, c_int32]),
+    "osmpm_get_counters": (c_int32, [c_void_p, POINTER(osmpm_counters)]),
     "osmpm_last_error": (c_char_p, []),
 }
 for _name, (_res, _args) in _sig.items():
@@ -181,6 +192,7 @@ def make_desc(spec) -> osmpm_domain_desc:
     d.cg_rtol = spec.cg_rtol
     d.cg_max = spec.cg_max
     d.ls_max = spec.ls_max
+    d.mass_eps = spec.mass_eps
     return d
 
 
@@ -288,6 +300,14 @@ class Domain:
         _check(_lib.osmpm_get_grid(self.h, field, _dp(out)), "osmpm_get_grid")
         return out
 
+    def set_profiling(self, enable: bool) -> None:
+        _check(_lib.osmpm_set_profiling(self.h, 1 if enable else 0), "osmpm_set_profiling")
+
+    def counters(self) -> dict:
+        c = osmpm_counters()
+        _check(_lib.osmpm_get_counters(self.h, ctypes.byref(c)), "osmpm_get_counters")
+        return c.as_dict()
+
     def probe_gradient(self, dt: float, u: np.ndarray) -> np.ndarray:
         u = np.ascontiguousarray(u, dtype=np.float64)
         out = np.empty_like(u)
@@ -330,6 +350,12 @@ def osmpm_schwarz_couple(coarse: Domain, fine: Domain, dT: float, sch) -> dict:
     _check(_lib.osmpm_schwarz_couple(coarse.h, fine.h, dT, ctypes.byref(sd), ctypes.byref(st)),
            "osmpm_schwarz_couple", warn_ok=True)
     return st.as_dict()
+
+
+def launch_count() -> int:
+    c = osmpm_counters()
+    _check(_lib.osmpm_get_counters(None, ctypes.byref(c)), "osmpm_get_counters")
+    return int(c.launches)
 
 
 def osmpm_get_particles(dom: Domain):

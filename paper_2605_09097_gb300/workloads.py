@@ -93,6 +93,12 @@ class DomainSpec:
     cg_rtol: float = 1e-6
     cg_max: int = 20000
     ls_max: int = 40
+    # nodes with m_i <= mass_eps carry no DOF; None -> 1e-10 x mean particle mass
+    mass_eps: Optional[float] = None
+
+    def __post_init__(self):
+        if self.mass_eps is None:
+            self.mass_eps = 1e-10 * float(np.mean(self.particles.mass))
 
 
 @dataclass

@@ -55,7 +55,7 @@ def test_p2g_and_active_set(osmpm, dim):
     dom = osmpm.Domain(spec)
     nn = spec.grid.n_nodes
     dom.probe_gradient(0.01, np.zeros((nn, dim)))      # runs one P2G
-    gf = O.p2g(spec.particles, spec.grid)
+    gf = O.p2g(spec.particles, spec.grid, mass_eps=spec.mass_eps)
     m = dom.get_grid(osmpm.OSMPM_FIELD_MASS)
     np.testing.assert_array_equal(m > 0, gf.active)
     np.testing.assert_allclose(m, gf.m, rtol=1e-13, atol=1e-15 * gf.m.max())
@@ -67,7 +67,7 @@ def test_p2g_and_active_set(osmpm, dim):
 # discrete operators at a random iterate
 # ----------------------------------------------------------------------------
 def _problem(spec, dt, seed):
-    gf = O.p2g(spec.particles, spec.grid)
+    gf = O.p2g(spec.particles, spec.grid, mass_eps=spec.mass_eps)
     mask, vel = O.dirichlet_nodes(spec.grid, [], dt)
     pr = O.make_problem(spec.particles, spec.grid, gf, dt, spec.gravity, mask, vel)
     rng = np.random.default_rng(seed)

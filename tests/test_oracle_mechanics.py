@@ -204,3 +204,34 @@ def test_cantilever_first_step_sags():
     assert dy[x0[:, 0] > 0.9].mean() < 0
     np.testing.assert_allclose(dy[x0[:, 0] > 0.5].mean(), -9.81e-6, rtol=0.05)
     assert abs(dy[x0[:, 0] < 0.0125]).max() < 0.5 * 9.81e-6
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_psi_change_identities(d):
+    """psi_change equals the plain difference for sizeable dF and the first-
+    order term P:dF for tiny dF (where the plain difference is all
+    round-off), and reports inversion."""
+    F0 = _rand_F(6, d, 0.1, 41 + d)
+    mu, lam = np.full(6, 1.7), np.full(6, 2.9)
+    rng = np.random.default_rng(4)
+    dF = 0.05 * rng.standard_normal((6, d, d))
+    np.testing.assert_allclose(O.psi_change(F0, dF, mu, lam),
+                               O.psi(F0 + dF, mu, lam) - O.psi(F0, mu, lam), rtol=1e-10)
+    tiny = 1e-12 * rng.standard_normal((6, d, d))
+    lin = np.sum(O.pk1(F0, mu, lam) * tiny, axis=(1, 2))
+    np.testing.assert_allclose(O.psi_change(F0, tiny, mu, lam), lin, rtol=1e-9)
+    flip = -2.5 * F0
+    assert np.all(np.isinf(O.psi_change(F0, flip, mu, lam)[np.linalg.det(F0 + flip) <= 0]))
+
+
+def test_round_off_weight_nodes_are_inactive():
+    """A particle at a half-cell offset touches the far nodes of its support
+    with weight (fx - 1/2)^2 / 2 ~ 1e-32 through rounding; those nodes carry
+    no DOF, and the step converges."""
+    spec = W.block(2, n_cells=(1, 1), dx=0.1, ppc_1d=1, gravity=(0.0, -9.81))
+    gf = O.p2g(spec.particles, spec.grid, mass_eps=spec.mass_eps)
+    assert gf.active.sum() == 4
+    assert (O.p2g(spec.particles, spec.grid).active.sum()) == 9
+    ds = O.DomainState.create(spec)
+    O.step(ds, 0.01)
+    np.testing.assert_allclose(ds.p.v[:, 1], -9.81 * 0.01, rtol=1e-12)
