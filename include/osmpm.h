@@ -248,6 +248,59 @@ osmpm_status osmpm_set_profiling(osmpm_domain* dom, int32_t enable);
 /* Reads the counters; dom may be NULL (process-wide launch count only). */
 osmpm_status osmpm_get_counters(const osmpm_domain* dom, osmpm_counters* out);
 
+/* ---------------------------------------------------------------------------
+ * Energy change without device allocation.
+ *
+ * The paper has no counterpart to this entry point; it is a service for
+ * callers that may not allocate device memory (a sandbox with a memory cap,
+ * a host application whose own allocator owns the GPU, a caller that must
+ * not allocate inside a latency budget).  It computes the line-search
+ * quantity E_h(u + alpha s) - E_h(u) of osmpm_probe_energy_change from
+ * caller-owned DEVICE arrays and calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its reduction scratch is a fixed file-scope device
+ * array of 4128 doubles (33 KB) that every GPU loading the library holds
+ * until the process exits.
+ *  - Layouts (device): particle fields component-major (x[a*n + p],
+ *    F[e*n + p] with e = a*dim + b); grid fields over the dense node box,
+ *    component-major (vn[a*n_nodes + i]); m has one value per node.
+ *  - mu, lam are the Lame parameters E/(2(1+nu)), E nu/((1+nu)(1-2nu)).
+ *  - The result (one double, +inf if a trial inverts an element) is
+ *    written to the device pointer dE on the given stream; the call does
+ *    not synchronise.
+ *  - Size limit: max(n_particles, n_nodes * dim) <= 1,048,576; larger
+ *    problems are rejected with OSMPM_E_INVALID before any device work.
+ *  - The first call on each device looks up the scratch array's device
+ *    address (cudaGetSymbolAddress with that device current); make that
+ *    first call before any stream capture.  All calls share the scratch:
+ *    calls that overlap on the GPU (other streams, other threads) race.
+ * ------------------------------------------------------------------------- */
+typedef struct osmpm_noalloc_grid {
+  int32_t dim;
+  double origin[3];
+  double dx;
+  int32_t res[3];
+  double mass_eps;          /* active nodes: m_i > mass_eps */
+  double gravity[3];
+  const double* m;          /* n_nodes nodal masses */
+  const double* vn;         /* dim * n_nodes, v^n */
+  const double* u;          /* dim * n_nodes, x_hat - x^n */
+  const double* s;          /* dim * n_nodes, step direction */
+} osmpm_noalloc_grid;
+
+typedef struct osmpm_noalloc_particles {
+  int64_t n;
+  const double* x;          /* dim * n */
+  const double* F;          /* dim * dim * n, F^n */
+  const double* vol0;       /* n */
+  const double* mu;         /* n */
+  const double* lam;        /* n */
+} osmpm_noalloc_particles;
+
+osmpm_status osmpm_energy_change_noalloc(const osmpm_noalloc_grid* grid,
+                                         const osmpm_noalloc_particles* particles,
+                                         double dt, double alpha, double* dE,
+                                         void* cuda_stream);
+
 /* Message of the last failure on this thread (never NULL). */
 const char* osmpm_last_error(void);
 

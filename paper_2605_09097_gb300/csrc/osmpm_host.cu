@@ -23,13 +23,18 @@ namespace {
 
 thread_local std::string g_last_error = "no error";
 
-osmpm_status fail(osmpm_status st, const char* fmt, ...) {
+osmpm_status vfail(osmpm_status st, const char* fmt, va_list ap) {
   char buf[512];
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  g_last_error = buf;
+  return st;
+}
+
+osmpm_status fail(osmpm_status st, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
+  vfail(st, fmt, ap);
   va_end(ap);
-  g_last_error = buf;
   return st;
 }
 
@@ -47,6 +52,14 @@ osmpm_status fail(osmpm_status st, const char* fmt, ...) {
   } while (0)
 
 }  // namespace
+
+osmpm_status osmpm::set_error(osmpm_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vfail(st, fmt, ap);
+  va_end(ap);
+  return st;
+}
 
 struct osmpm_domain {
   osmpm_domain_desc desc{};

@@ -6,6 +6,7 @@
 
 #include <atomic>
 
+#include "../../include/osmpm.h"
 #include "osmpm_types.h"
 
 namespace osmpm {
@@ -80,6 +81,11 @@ struct Kernels {
                             const double* vn, const double* u, const double* x,
                             const double* gravity, double dt, double alpha, DevScalars* S,
                             double* partials, cudaStream_t s);
+  // same kernel with an explicit block count (one block per 256 work items)
+  static void energy_change_blocks(const PartPtrs& P, const GridGeo& g, const double* m,
+                                   const double* vn, const double* u, const double* x,
+                                   const double* gravity, double dt, double alpha, DevScalars* S,
+                                   double* partials, int blocks, cudaStream_t s);
   static void axpy(const GridGeo& g, double* u, const double* x, double alpha, cudaStream_t s);
   static void g2p(const PartPtrs& P, const GridGeo& g, const double* u, double dt,
                   cudaStream_t s);
@@ -108,6 +114,9 @@ struct Kernels {
                           cudaStream_t s);
   static void set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s);
 };
+
+// Records the message returned by osmpm_last_error() and returns st.
+osmpm_status set_error(osmpm_status st, const char* fmt, ...);
 
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
 // keys; result ends in (keys, vals).  hist needs 256 * radix_tiles(n) words.

@@ -1002,6 +1002,16 @@ void Kernels<D>::energy_change(const PartPtrs& P, const GridGeo& g, const double
                                          dt, alpha, S, partials);
 }
 template <int D>
+void Kernels<D>::energy_change_blocks(const PartPtrs& P, const GridGeo& g, const double* m,
+                                      const double* vn, const double* u, const double* x,
+                                      const double* gravity, double dt, double alpha,
+                                      DevScalars* S, double* partials, int blocks,
+                                      cudaStream_t s) {
+  g_launch_count += 1;
+  k_energy_change<D><<<blocks, kThreads, 0, s>>>(P, g, m, vn, u, x, gravity[0], gravity[1],
+                                                gravity[2], dt, alpha, S, partials);
+}
+template <int D>
 void Kernels<D>::axpy(const GridGeo& g, double* u, const double* x, double alpha,
                       cudaStream_t s) {
   k_axpy<D><<<OSMPM_RB(g.nn * D)>>>(g, u, x, alpha);

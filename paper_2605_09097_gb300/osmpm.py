@@ -98,6 +98,17 @@ class osmpm_counters(Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class osmpm_noalloc_grid(Structure):
+    _fields_ = [("dim", c_int32), ("origin", c_double * 3), ("dx", c_double),
+                ("res", c_int32 * 3), ("mass_eps", c_double), ("gravity", c_double * 3),
+                ("m", c_void_p), ("vn", c_void_p), ("u", c_void_p), ("s", c_void_p)]
+
+
+class osmpm_noalloc_particles(Structure):
+    _fields_ = [("n", c_int64), ("x", c_void_p), ("F", c_void_p), ("vol0", c_void_p),
+                ("mu", c_void_p), ("lam", c_void_p)]
+
+
 _DP = POINTER(c_double)
 _sig = {
     "osmpm_create_domain": (c_int32, [POINTER(osmpm_domain_desc), POINTER(osmpm_particles_in),
@@ -117,6 +128,9 @@ _sig = {
     "osmpm_probe_energy_change": (c_int32, [c_void_p, c_double, _DP, _DP, c_double, _DP]),
     "osmpm_set_profiling": (c_int32, [c_void_p, c_int32]),
     "osmpm_get_counters": (c_int32, [c_void_p, POINTER(osmpm_counters)]),
+    "osmpm_energy_change_noalloc": (c_int32, [POINTER(osmpm_noalloc_grid),
+                                              POINTER(osmpm_noalloc_particles), c_double,
+                                              c_double, c_void_p, c_void_p]),
     "osmpm_last_error": (c_char_p, []),
 }
 for _name, (_res, _args) in _sig.items():
@@ -350,6 +364,14 @@ def osmpm_schwarz_couple(coarse: Domain, fine: Domain, dT: float, sch) -> dict:
     _check(_lib.osmpm_schwarz_couple(coarse.h, fine.h, dT, ctypes.byref(sd), ctypes.byref(st)),
            "osmpm_schwarz_couple", warn_ok=True)
     return st.as_dict()
+
+
+def osmpm_energy_change_noalloc(grid: osmpm_noalloc_grid, parts: osmpm_noalloc_particles,
+                                dt: float, alpha: float, dE_ptr: int, stream: int) -> int:
+    """Raw call of the allocation-free energy change (device pointers in the
+    two structs and in dE_ptr); returns the status code."""
+    return _lib.osmpm_energy_change_noalloc(ctypes.byref(grid), ctypes.byref(parts), dt, alpha,
+                                            c_void_p(dE_ptr), c_void_p(stream))
 
 
 def launch_count() -> int:
