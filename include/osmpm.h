@@ -51,6 +51,7 @@ typedef enum osmpm_status {
   OSMPM_E_NEWTON_MAXITER = 5,  /* Newton did not reach newton_tol in newton_max iterations */
   OSMPM_E_LINESEARCH = 6,      /* no energy decrease after ls_max halvings */
   OSMPM_E_OUT_OF_GRID = 7,     /* a particle's 3^dim support left the grid box */
+  OSMPM_E_TIMEOUT = 8,         /* a device-side wait gave up (the kernel returned early) */
   OSMPM_E_UNSUPPORTED = 9,     /* a valid request this build does not serve */
   OSMPM_W_SCHWARZ_MAXITER = 100 /* Schwarz hit k_max; the last iterate was committed */
 } osmpm_status;
@@ -228,22 +229,31 @@ osmpm_status osmpm_probe_energy_change(osmpm_domain* dom, double dt, const doubl
                                        const double* d, double alpha, double* dE);
 
 /* Counters for measurement.  launches: kernels this library has launched in
- * the process.  hvp_*: when HVP timing is enabled on the domain, the number
- * of Hessian-vector-product launches that did work, their summed duration
- * from CUDA events recorded on the domain's stream around each launch, and
- * the particles they processed. */
+ * the process.  pcg_*: when timing is enabled on the domain, the number of
+ * persistent PCG launches (one per Newton iteration), their summed
+ * duration from CUDA events recorded on the domain's stream around each
+ * launch, and the PCG iterations they ran; particles and dofs are the
+ * per-iteration work units of the domain (n and n_nodes * dim). */
 typedef struct osmpm_counters {
   int64_t launches;
-  int64_t hvp_launches;
-  double hvp_ms;
-  int64_t hvp_particles;
-  double reserved[4];
+  int64_t pcg_launches;
+  double pcg_ms;
+  int64_t pcg_iters;
+  int64_t particles;
+  int64_t dofs;
+  double reserved[2];
 } osmpm_counters;
 
-/* Enables (1) or disables (0) CUDA-event timing of the HVP launches of this
- * domain and resets its HVP counters.  Timing adds two event records per
- * PCG iteration; results are read with osmpm_get_counters. */
+/* Enables (1) or disables (0) CUDA-event timing of this domain's PCG
+ * launches and resets its counters; read them with osmpm_get_counters. */
 osmpm_status osmpm_set_profiling(osmpm_domain* dom, int32_t enable);
+
+/* Diagnostic of the device-side waits: launches the PCG kernel's grid
+ * barrier so that it waits for a block that does not exist; its bounded
+ * spin gives up after about two seconds and the kernel returns.  Returns
+ * OSMPM_E_TIMEOUT when the kernel reported the timeout (the expected
+ * result; the CUDA context stays usable), OSMPM_E_CUDA otherwise. */
+osmpm_status osmpm_check_wait_timeout(void* cuda_stream);
 
 /* Reads the counters; dom may be NULL (process-wide launch count only). */
 osmpm_status osmpm_get_counters(const osmpm_domain* dom, osmpm_counters* out);

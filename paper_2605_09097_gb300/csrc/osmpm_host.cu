@@ -81,11 +81,14 @@ struct osmpm_domain {
   // grid (component-major)
   double *m = nullptr, *mv = nullptr, *vn = nullptr, *bm = nullptr, *u = nullptr;
   double *grad = nullptr, *diag = nullptr;
-  double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cq = nullptr;
+  double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cp1 = nullptr, *cq = nullptr;
   double* L = nullptr;
   uint8_t *dofmask = nullptr, *physmask = nullptr, *gam = nullptr, *recv = nullptr;
   double *bc0 = nullptr, *bc1 = nullptr, *bc_prev = nullptr, *bc_applied = nullptr;
   double *vtmp = nullptr, *proj_num = nullptr, *proj_den = nullptr;
+  // Schwarz warm starts: previous solutions (coarse: 1, fine: one per sub-step)
+  double* u_keep = nullptr;
+  int n_keep = 0;
 
   DevRule* rules_dev = nullptr;
   std::vector<osmpm_dirichlet> rules;
@@ -95,12 +98,11 @@ struct osmpm_domain {
   int* err = nullptr;
   int* err_host = nullptr;
 
-  // optional CUDA-event timing of the HVP launches (osmpm_set_profiling)
+  // optional CUDA-event timing of the PCG launches (osmpm_set_profiling)
   bool time_hvp = false;
-  std::vector<cudaEvent_t> ev;  // start/stop pairs
-  int ev_used = 0;              // pairs recorded in the current PCG
-  double hvp_ms = 0.0;
-  long long hvp_launches = 0;
+  std::vector<cudaEvent_t> ev;  // one start/stop pair
+  double pcg_ms = 0.0;
+  long long pcg_launches = 0, pcg_iters = 0;
 };
 
 namespace {
@@ -191,6 +193,7 @@ osmpm_status check_err(osmpm_domain* d) {
   const int e = *d->err_host;
   if (e & kErrOutOfGrid) return fail(OSMPM_E_OUT_OF_GRID, "a particle's support left the grid box");
   if (e & kErrNonFinite) return fail(OSMPM_E_NONFINITE, "inverted element (J <= 0) at an accepted iterate");
+  if (e & kErrBarrierTimeout) return fail(OSMPM_E_TIMEOUT, "a grid barrier of the PCG kernel gave up waiting");
   return OSMPM_OK;
 }
 
@@ -300,44 +303,47 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
                              d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
                              d->cz, d->cp, d->S, d->partials, d->stream));
-  int chunk = 8;
-  int launched = 0;
-  d->ev_used = 0;
-  for (;;) {
-    for (int c = 0; c < chunk; ++c) {
-      DISPATCH(d, K::cg_a(d->geo, d->m, d->dofmask, dt, d->cz, d->cp, d->cq, d->S, d->partials,
-                          d->stream));
-      const bool timed = d->time_hvp && (size_t)(2 * d->ev_used + 1) < d->ev.size();
-      if (timed) CUDA_TRY(cudaEventRecord(d->ev[2 * d->ev_used], d->stream));
-      DISPATCH(d, K::cg_b(d->P, d->geo, d->dofmask, d->L, d->cp, d->cq, d->S, d->partials,
-                          d->stream));
-      if (timed) {
-        CUDA_TRY(cudaEventRecord(d->ev[2 * d->ev_used + 1], d->stream));
-        d->ev_used++;
-      }
-      DISPATCH(d, K::cg_c(d->geo, d->dofmask, d->diag, d->cp, d->cq, d->cx, d->cr, d->cz, d->S,
-                          d->partials, d->stream));
-      ++launched;
-    }
-    DISPATCH(d, K::copy_if_neg(d->geo, d->cp, d->cx, d->S, d->stream));
-    DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
-    OSMPM_TRY(sync_scalars(d));
-    OSMPM_TRY(check_err(d));
-    if (d->S_host->cg_done) break;
-    if (chunk < 64) chunk *= 2;
-  }
+  // whole PCG in one cooperative launch (p1, q and the barrier start at zero)
+  CUDA_TRY(cudaMemsetAsync(d->cp1, 0, sizeof(double) * D * nn, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cq, 0, sizeof(double) * D * nn, d->stream));
+  CUDA_TRY(cudaMemsetAsync(&d->S->bar_count, 0, sizeof(unsigned), d->stream));
+  PcgArgs a{};
+  a.P = d->P;
+  a.g = d->geo;
+  a.m = d->m;
+  a.dofmask = d->dofmask;
+  a.L = d->L;
+  a.diag = d->diag;
+  a.inv_dt2 = 1.0 / (dt * dt);
+  a.x = d->cx;
+  a.r = d->cr;
+  a.z = d->cz;
+  a.p0 = d->cp;
+  a.p1 = d->cp1;
+  a.q = d->cq;
+  a.S = d->S;
+  a.partials = d->partials;
+  a.err = d->err;
+  const int threads = kPcgThreads;
+  const int64_t work = std::max<int64_t>(d->n, D * nn);
+  int blocks = 0;
+  DISPATCH(d, blocks = K::pcg_blocks(work, threads));
+  const bool timed = d->time_hvp && !d->ev.empty();
+  if (timed) CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
+  cudaError_t le = cudaSuccess;
+  DISPATCH(d, le = K::pcg(a, blocks, threads, d->stream));
+  if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(le));
+  if (timed) CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
+  DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
+  OSMPM_TRY(sync_scalars(d));
+  OSMPM_TRY(check_err(d));
   st.cg += d->S_host->cg_iter;
-  if (d->time_hvp) {
-    // HVP launches that did work: one per completed iteration, plus the one
-    // that found negative curvature; later launches of the chunk returned at once
-    int worked = d->S_host->cg_iter + (d->S_host->cg_neg ? 1 : 0);
-    if (worked > d->ev_used) worked = d->ev_used;
-    for (int i = 0; i < worked; ++i) {
-      float ms = 0.f;
-      CUDA_TRY(cudaEventElapsedTime(&ms, d->ev[2 * i], d->ev[2 * i + 1]));
-      d->hvp_ms += ms;
-    }
-    d->hvp_launches += worked;
+  if (timed) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]));
+    d->pcg_ms += ms;
+    d->pcg_launches += 1;
+    d->pcg_iters += d->S_host->cg_iter;
   }
   return OSMPM_OK;
 }
@@ -391,6 +397,15 @@ void fill_stats(osmpm_stats* out, const SolveStats& st, int schwarz_iters, int c
   out->r_S = rS;
   out->last_dx_inf = st.last_dx;
 }
+
+osmpm_status ensure_keep(osmpm_domain* d, int slots) {
+  if (d->n_keep >= slots) return OSMPM_OK;
+  OSMPM_TRY(dalloc_n(d, (int64_t)slots * d->dim * d->geo.nn, &d->u_keep));
+  d->n_keep = slots;
+  return OSMPM_OK;
+}
+
+double* keep_slot(osmpm_domain* d, int slot) { return d->u_keep + (int64_t)slot * d->dim * d->geo.nn; }
 
 osmpm_status snapshot(osmpm_domain* d, bool restore) {
   const int D = d->dim;
@@ -561,6 +576,7 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(dalloc_n(d, D * nn, &d->cr));
   C_TRY(dalloc_n(d, D * nn, &d->cz));
   C_TRY(dalloc_n(d, D * nn, &d->cp));
+  C_TRY(dalloc_n(d, D * nn, &d->cp1));
   C_TRY(dalloc_n(d, D * nn, &d->cq));
   const int npk = (D * D) * (D * D + 1) / 2;
   C_TRY(dalloc_n(d, (int64_t)npk * n, &d->L));
@@ -578,7 +594,7 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(dalloc_n(d, kMaxRules, &d->rules_dev));
   C_TRY(dalloc_n(d, 1, &d->S));
   const int64_t maxblk = std::max<int64_t>(red_blocks_for(std::max<int64_t>(n, D * nn)), kRedBlocksMax);
-  C_TRY(dalloc_n(d, 4 * maxblk, &d->partials));
+  C_TRY(dalloc_n(d, 4 * std::max<int64_t>(maxblk, 152 * 64), &d->partials));
   C_TRY(dalloc_n(d, 1, &d->err));
   if (cudaMallocHost(&d->S_host, sizeof(DevScalars)) != cudaSuccess ||
       cudaMallocHost(&d->err_host, sizeof(int)) != cudaSuccess)
@@ -725,12 +741,20 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   DISPATCH(B, K::interp(gB, gS, B->vn, S->recv, S->bc0, s));
   CUDA_TRY(cudaMemcpyAsync(S->bc_prev, S->bc0, sizeof(double) * D * gS.nn, cudaMemcpyDeviceToDevice, s));
 
+  // Newton warm starts for the re-solves of iterations k >= 1: the coarse
+  // solve from its previous solution, fine sub-step m from the previous
+  // iteration's sub-step m (same minimisers; the first solve is cold)
+  S_TRY(ensure_keep(B, 1));
+  S_TRY(ensure_keep(S, M));
+  const size_t bytesB = sizeof(double) * D * gB.nn, bytesS = sizeof(double) * D * gS.nn;
   int k = 0, converged = 0;
   double rB = 0.0, rS = 0.0;
   for (k = 0; k <= sd->k_max; ++k) {
     // 1. coarse solve over dT with Pi data on Gamma_hat_B (Eq. implicit_solve_coarse)
     S_TRY(prep(B, dT, true, B->recv, B->bc0, B->bc0, 1.0, nullptr));
+    if (k > 0) DISPATCH(B, K::warm_start(gB, B->dofmask, keep_slot(B, 0), B->u, s));
     S_TRY(newton_solve(B, dT, st));
+    CUDA_TRY(cudaMemcpyAsync(keep_slot(B, 0), B->u, bytesB, cudaMemcpyDeviceToDevice, s));
     DISPATCH(B, K::vel_from_u(gB, B->m, B->u, dT, B->vtmp, s));
     // 2. fine: restore, P2G, endpoint data I(v_B^n), I(v_B^(k+1)), sub-cycle
     S_TRY(snapshot(S, true));
@@ -738,7 +762,9 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
     DISPATCH(B, K::interp(gB, gS, B->vtmp, S->recv, S->bc1, s));
     for (int m = 1; m <= M; ++m) {
       S_TRY(prep(S, dt, true, S->recv, S->bc0, S->bc1, (double)m / (double)M, nullptr));
+      if (k > 0) DISPATCH(S, K::warm_start(gS, S->dofmask, keep_slot(S, m - 1), S->u, s));
       S_TRY(newton_solve(S, dt, st));
+      CUDA_TRY(cudaMemcpyAsync(keep_slot(S, m - 1), S->u, bytesS, cudaMemcpyDeviceToDevice, s));
       DISPATCH(S, K::g2p(S->P, gS, S->u, dt, s));
       S_TRY(run_p2g(S, false));
       S_TRY(sync_scalars(S));
@@ -780,12 +806,13 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
 osmpm_status osmpm_set_profiling(osmpm_domain* d, int32_t enable) {
   OSMPM_TRY(check_domain(d));
   if (enable && d->ev.empty()) {
-    d->ev.resize(2 * 20001);
+    d->ev.resize(2);
     for (auto& e : d->ev) CUDA_TRY(cudaEventCreate(&e));
   }
   d->time_hvp = enable != 0;
-  d->hvp_ms = 0.0;
-  d->hvp_launches = 0;
+  d->pcg_ms = 0.0;
+  d->pcg_launches = 0;
+  d->pcg_iters = 0;
   return OSMPM_OK;
 }
 
@@ -794,11 +821,32 @@ osmpm_status osmpm_get_counters(const osmpm_domain* d, osmpm_counters* out) {
   memset(out, 0, sizeof(*out));
   out->launches = (int64_t)g_launch_count.load();
   if (d) {
-    out->hvp_launches = d->hvp_launches;
-    out->hvp_ms = d->hvp_ms;
-    out->hvp_particles = d->hvp_launches * d->n;
+    out->pcg_launches = d->pcg_launches;
+    out->pcg_ms = d->pcg_ms;
+    out->pcg_iters = d->pcg_iters;
+    out->particles = d->n;
+    out->dofs = d->geo.nn * d->dim;
   }
   return OSMPM_OK;
+}
+
+osmpm_status osmpm_check_wait_timeout(void* cuda_stream) {
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  void* mem = nullptr;
+  CUDA_TRY(cudaMallocAsync(&mem, 64, s));
+  CUDA_TRY(cudaMemsetAsync(mem, 0, 64, s));
+  unsigned* words = (unsigned*)mem;
+  int* err = (int*)((char*)mem + 32);
+  Kernels<2>::barrier_timeout_check(words, err, s);
+  int host_err = 0;
+  cudaError_t e = cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(mem, s);
+  cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(OSMPM_E_CUDA, "timeout check: %s", cudaGetErrorString(e));
+  if (host_err & kErrBarrierTimeout)
+    return fail(OSMPM_E_TIMEOUT, "the device-side wait gave up as designed");
+  return fail(OSMPM_E_CUDA, "the device-side wait did not report its timeout");
 }
 
 osmpm_status osmpm_get_info(const osmpm_domain* d, int64_t* n, int32_t* dim) {

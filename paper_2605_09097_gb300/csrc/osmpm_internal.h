@@ -17,6 +17,7 @@ extern std::atomic<long long> g_launch_count;
 
 // Launch shape helpers shared by drivers and launchers.
 constexpr int kRedBlocksMax = 1216;  // 152 SMs x 8 resident 256-thread blocks
+constexpr int kPcgThreads = 128;     // block size of the persistent PCG kernel
 inline int blocks_for(int64_t n, int threads = 256) {
   int64_t b = (n + threads - 1) / threads;
   return (int)(b < 1 ? 1 : b);
@@ -72,6 +73,9 @@ struct Kernels {
   static void cg_c(const GridGeo& g, const uint8_t* dofmask, const double* diag,
                    const double* p, const double* q, double* x, double* r, double* z,
                    DevScalars* S, double* partials, cudaStream_t s);
+  // persistent cooperative PCG (whole solve in one launch)
+  static int pcg_blocks(int64_t work, int threads);
+  static cudaError_t pcg(const PcgArgs& a, int blocks, int threads, cudaStream_t s);
   static void hvp_only(const PartPtrs& P, const GridGeo& g, const double* m,
                        const uint8_t* dofmask, const double* L, double dt, double* p, double* q,
                        DevScalars* S, double* partials, cudaStream_t s);
@@ -86,6 +90,8 @@ struct Kernels {
                                    const double* vn, const double* u, const double* x,
                                    const double* gravity, double dt, double alpha, DevScalars* S,
                                    double* partials, int blocks, cudaStream_t s);
+  static void warm_start(const GridGeo& g, const uint8_t* dofmask, const double* src, double* u,
+                         cudaStream_t s);
   static void axpy(const GridGeo& g, double* u, const double* x, double alpha, cudaStream_t s);
   static void g2p(const PartPtrs& P, const GridGeo& g, const double* u, double dt,
                   cudaStream_t s);
@@ -113,6 +119,7 @@ struct Kernels {
   static void copy_if_neg(const GridGeo& g, const double* p, double* x, const DevScalars* S,
                           cudaStream_t s);
   static void set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s);
+  static void barrier_timeout_check(unsigned* words, int* err, cudaStream_t s);
 };
 
 // Records the message returned by osmpm_last_error() and returns st.

@@ -8,6 +8,7 @@
 
 #include "osmpm_device.cuh"
 #include "osmpm_internal.h"
+#include "osmpm_pcg.cuh"
 
 namespace osmpm {
 
@@ -643,6 +644,17 @@ __global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrs P, GridGeo 
   if (grid_sum<1>(acc, partials, &S->counter, tot) && threadIdx.x == 0) S->dE = tot[0];
 }
 
+// Warm start: free DOFs take a previous solution, fixed DOFs keep the
+// prepared Dirichlet values.
+template <int D>
+__global__ void k_warm_start(GridGeo g, const uint8_t* dofmask, const double* src, double* u) {
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
+    const int a = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)a * g.nn;
+    if ((dofmask[i] >> a) & 1u) u[idx] = src[idx];
+  }
+}
+
 template <int D>
 __global__ void k_axpy(GridGeo g, double* u, const double* x, double alpha) {
   for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) u[idx] += alpha * x[idx];
@@ -1012,6 +1024,11 @@ void Kernels<D>::energy_change_blocks(const PartPtrs& P, const GridGeo& g, const
                                                 gravity[2], dt, alpha, S, partials);
 }
 template <int D>
+void Kernels<D>::warm_start(const GridGeo& g, const uint8_t* dofmask, const double* src, double* u,
+                            cudaStream_t s) {
+  k_warm_start<D><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, src, u);
+}
+template <int D>
 void Kernels<D>::axpy(const GridGeo& g, double* u, const double* x, double alpha,
                       cudaStream_t s) {
   k_axpy<D><<<OSMPM_RB(g.nn * D)>>>(g, u, x, alpha);
@@ -1077,6 +1094,38 @@ template <int D>
 void Kernels<D>::set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s) {
   g_launch_count += 1;
   k_set_cg_state<D><<<1, 1, 0, s>>>(S, iter, done);
+}
+
+template <int D>
+int Kernels<D>::pcg_blocks(int64_t work, int threads) {
+  static int per_sm[2] = {-1, -1};
+  static int sms = 0;
+  const int slot = threads == 128 ? 0 : 1;
+  if (per_sm[slot] < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg<D>, threads, 0);
+    per_sm[slot] = nb;
+  }
+  const int64_t cap = (int64_t)per_sm[slot] * sms;
+  int64_t want = (work + threads - 1) / threads;
+  if (want < 1) want = 1;
+  return (int)(want < cap ? want : cap);
+}
+template <int D>
+cudaError_t Kernels<D>::pcg(const PcgArgs& a, int blocks, int threads, cudaStream_t s) {
+  PcgArgs copy = a;
+  void* args[] = {(void*)&copy};
+  g_launch_count += 1;
+  return cudaLaunchCooperativeKernel((const void*)k_pcg<D>, dim3(blocks), dim3(threads), args, 0, s);
+}
+
+template <int D>
+void Kernels<D>::barrier_timeout_check(unsigned* words, int* err, cudaStream_t s) {
+  g_launch_count += 1;
+  k_barrier_timeout_check<D><<<2, 32, 0, s>>>(words, err);
 }
 
 #undef OSMPM_NB

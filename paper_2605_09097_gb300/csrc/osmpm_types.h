@@ -54,12 +54,33 @@ struct DevScalars {
   int cg_iter, cg_done, cg_neg, cg_max;
   int err;
   unsigned counter;
-  int pad[2];
+  unsigned bar_count, bar_gen;  // grid barrier of the persistent PCG kernel
 };
 
 enum : int {
   kErrOutOfGrid = 1,
   kErrNonFinite = 2,
+  kErrBarrierTimeout = 4,
+};
+
+// Arguments of the persistent PCG kernel.
+struct PcgArgs {
+  PartPtrs P;
+  GridGeo g;
+  const double* m;
+  const uint8_t* dofmask;
+  const double* L;
+  const double* diag;
+  double inv_dt2;
+  double* x;
+  double* r;
+  double* z;
+  double* p0;
+  double* p1;
+  double* q;
+  DevScalars* S;
+  double* partials;  // 3 * gridDim.x doubles
+  int* err;
 };
 
 }  // namespace osmpm

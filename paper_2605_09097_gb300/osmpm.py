@@ -35,6 +35,7 @@ OSMPM_E_NONFINITE = 4
 OSMPM_E_NEWTON_MAXITER = 5
 OSMPM_E_LINESEARCH = 6
 OSMPM_E_OUT_OF_GRID = 7
+OSMPM_E_TIMEOUT = 8
 OSMPM_E_UNSUPPORTED = 9
 OSMPM_W_SCHWARZ_MAXITER = 100
 
@@ -91,8 +92,9 @@ class osmpm_stats(Structure):
 
 
 class osmpm_counters(Structure):
-    _fields_ = [("launches", c_int64), ("hvp_launches", c_int64), ("hvp_ms", c_double),
-                ("hvp_particles", c_int64), ("reserved", c_double * 4)]
+    _fields_ = [("launches", c_int64), ("pcg_launches", c_int64), ("pcg_ms", c_double),
+                ("pcg_iters", c_int64), ("particles", c_int64), ("dofs", c_int64),
+                ("reserved", c_double * 2)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -128,6 +130,7 @@ _sig = {
     "osmpm_probe_energy_change": (c_int32, [c_void_p, c_double, _DP, _DP, c_double, _DP]),
     "osmpm_set_profiling": (c_int32, [c_void_p, c_int32]),
     "osmpm_get_counters": (c_int32, [c_void_p, POINTER(osmpm_counters)]),
+    "osmpm_check_wait_timeout": (c_int32, [c_void_p]),
     "osmpm_energy_change_noalloc": (c_int32, [POINTER(osmpm_noalloc_grid),
                                               POINTER(osmpm_noalloc_particles), c_double,
                                               c_double, c_void_p, c_void_p]),
@@ -372,6 +375,11 @@ def osmpm_energy_change_noalloc(grid: osmpm_noalloc_grid, parts: osmpm_noalloc_p
     two structs and in dE_ptr); returns the status code."""
     return _lib.osmpm_energy_change_noalloc(ctypes.byref(grid), ctypes.byref(parts), dt, alpha,
                                             c_void_p(dE_ptr), c_void_p(stream))
+
+
+def osmpm_check_wait_timeout(stream: int) -> int:
+    """Runs the bounded-wait diagnostic; returns the status code."""
+    return _lib.osmpm_check_wait_timeout(c_void_p(stream))
 
 
 def launch_count() -> int:
