@@ -83,6 +83,8 @@ struct osmpm_domain {
   double *grad = nullptr, *diag = nullptr;
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cp1 = nullptr, *cq = nullptr;
   double* L = nullptr;
+  int* sbase = nullptr;    // stencil cache of the last P2G (base node, grad N)
+  double* sdn = nullptr;
   uint8_t *dofmask = nullptr, *physmask = nullptr, *gam = nullptr, *recv = nullptr;
   double *bc0 = nullptr, *bc1 = nullptr, *bc_prev = nullptr, *bc_applied = nullptr;
   double *vtmp = nullptr, *proj_num = nullptr, *proj_den = nullptr;
@@ -266,7 +268,8 @@ osmpm_status run_p2g(osmpm_domain* d, bool boundary_mass) {
   CUDA_TRY(cudaMemsetAsync(d->m, 0, sizeof(double) * nn, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->mv, 0, sizeof(double) * D * nn, d->stream));
   if (boundary_mass) CUDA_TRY(cudaMemsetAsync(d->bm, 0, sizeof(double) * nn, d->stream));
-  DISPATCH(d, K::p2g(d->P, d->geo, d->m, d->mv, boundary_mass ? d->bm : nullptr, d->err, d->stream));
+  DISPATCH(d, K::p2g(d->P, d->geo, d->m, d->mv, boundary_mass ? d->bm : nullptr, d->err, d->sbase,
+                     d->sdn, d->stream));
   DISPATCH(d, K::normalize(d->geo, d->m, d->mv, d->vn, d->stream));
   return OSMPM_OK;
 }
@@ -324,10 +327,11 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
   a.S = d->S;
   a.partials = d->partials;
   a.err = d->err;
-  const int threads = kPcgThreads;
+  a.sbase = d->sbase;
+  a.sdn = d->sdn;
   const int64_t work = std::max<int64_t>(d->n, D * nn);
-  int blocks = 0;
-  DISPATCH(d, blocks = K::pcg_blocks(work, threads));
+  int blocks = 0, threads = 0;
+  DISPATCH(d, K::pcg_shape(work, &blocks, &threads));
   const bool timed = d->time_hvp && !d->ev.empty();
   if (timed) CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
   cudaError_t le = cudaSuccess;
@@ -580,6 +584,8 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(dalloc_n(d, D * nn, &d->cq));
   const int npk = (D * D) * (D * D + 1) / 2;
   C_TRY(dalloc_n(d, (int64_t)npk * n, &d->L));
+  C_TRY(dalloc_n(d, n, &d->sbase));
+  C_TRY(dalloc_n(d, (int64_t)D * (D == 2 ? 9 : 27) * n, &d->sdn));
   C_TRY(dalloc_n(d, nn, &d->dofmask));
   C_TRY(dalloc_n(d, nn, &d->physmask));
   C_TRY(dalloc_n(d, nn, &d->gam));

@@ -17,7 +17,6 @@ extern std::atomic<long long> g_launch_count;
 
 // Launch shape helpers shared by drivers and launchers.
 constexpr int kRedBlocksMax = 1216;  // 152 SMs x 8 resident 256-thread blocks
-constexpr int kPcgThreads = 128;     // block size of the persistent PCG kernel
 inline int blocks_for(int64_t n, int threads = 256) {
   int64_t b = (n + threads - 1) / threads;
   return (int)(b < 1 ? 1 : b);
@@ -52,8 +51,10 @@ struct Kernels {
                        cudaStream_t s);
   static void unpack_in(const double* x, const double* v, const double* B, const double* F,
                         PartPtrs dst, cudaStream_t s);
+  // P2G; with sbase/sdn also caches each particle's stencil (base node and
+  // grad N) for the PCG of the step
   static void p2g(const PartPtrs& P, const GridGeo& g, double* m, double* mv, double* bm,
-                  int* err, cudaStream_t s);
+                  int* err, int* sbase, double* sdn, cudaStream_t s);
   static void normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
                         cudaStream_t s);
   static void grid_prep(const GridGeo& g, const double* m, const double* vn, const PrepArgs& a,
@@ -74,7 +75,7 @@ struct Kernels {
                    const double* p, const double* q, double* x, double* r, double* z,
                    DevScalars* S, double* partials, cudaStream_t s);
   // persistent cooperative PCG (whole solve in one launch)
-  static int pcg_blocks(int64_t work, int threads);
+  static void pcg_shape(int64_t work, int* blocks, int* threads);
   static cudaError_t pcg(const PcgArgs& a, int blocks, int threads, cudaStream_t s);
   static void hvp_only(const PartPtrs& P, const GridGeo& g, const double* m,
                        const uint8_t* dofmask, const double* L, double dt, double* p, double* q,

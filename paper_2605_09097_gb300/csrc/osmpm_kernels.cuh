@@ -191,7 +191,7 @@ __global__ void k_unpack_in(const double* x, const double* v, const double* B, c
 // ---------------------------------------------------------------------------
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_p2g(PartPtrs P, GridGeo g, double* m, double* mv,
-                                                  double* bm, int* err) {
+                                                  double* bm, int* err, int* sbase, double* sdn) {
   const int64_t p = gtid();
   if (p >= P.n) return;
   double xp[D], vp[D], Bp[D * D];
@@ -208,10 +208,22 @@ __global__ void __launch_bounds__(kThreads) k_p2g(PartPtrs P, GridGeo g, double*
   const double mp = P.mass[p];
   const double Dinv = 4.0 * g.inv_dx * g.inv_dx;  // D_p^-1 of the quadratic B-spline
   const bool isb = (bm != nullptr) && (P.flags[p] & 1u);
+  if (sbase) {
+    int64_t b = 0, stride = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      b += (int64_t)s.base[a] * stride;
+      stride *= g.res[a];
+    }
+    sbase[p] = (int)b;
+  }
 #pragma unroll 3
   for (int k = 0; k < Pow3<D>::K; ++k) {
     double N, dN[D];
     const int64_t node = stencil_node<D>(s, g, k, N, dN);
+    if (sdn)
+#pragma unroll
+      for (int a = 0; a < D; ++a) sdn[(int64_t)(a * Pow3<D>::K + k) * P.n + p] = dN[a];
     double r[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) r[a] = stencil_node_pos<D>(s, g, k, a) - xp[a];
@@ -943,8 +955,8 @@ void Kernels<D>::unpack_in(const double* x, const double* v, const double* B, co
 }
 template <int D>
 void Kernels<D>::p2g(const PartPtrs& P, const GridGeo& g, double* m, double* mv, double* bm,
-                     int* err, cudaStream_t s) {
-  k_p2g<D><<<OSMPM_NB(P.n)>>>(P, g, m, mv, bm, err);
+                     int* err, int* sbase, double* sdn, cudaStream_t s) {
+  k_p2g<D><<<OSMPM_NB(P.n)>>>(P, g, m, mv, bm, err, sbase, sdn);
 }
 template <int D>
 void Kernels<D>::normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
@@ -1097,22 +1109,29 @@ void Kernels<D>::set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s)
 }
 
 template <int D>
-int Kernels<D>::pcg_blocks(int64_t work, int threads) {
-  static int per_sm[2] = {-1, -1};
-  static int sms = 0;
-  const int slot = threads == 128 ? 0 : 1;
-  if (per_sm[slot] < 0) {
+void Kernels<D>::pcg_shape(int64_t work, int* blocks, int* threads) {
+  // One block per SM while the work fits (the FP64 pipe of every SM is used
+  // and each grid barrier spans as few blocks as possible); threads per
+  // block sized to the work, a multiple of 32 in [64, 256].  Larger problems
+  // use the co-resident maximum and grid-stride loops.
+  static int sms = 0, per_sm256 = 0;
+  if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pcg<D>, threads, 0);
-    per_sm[slot] = nb;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm256, k_pcg<D>, 256, 0);
+    if (per_sm256 < 1) per_sm256 = 1;
   }
-  const int64_t cap = (int64_t)per_sm[slot] * sms;
-  int64_t want = (work + threads - 1) / threads;
-  if (want < 1) want = 1;
-  return (int)(want < cap ? want : cap);
+  int64_t t = (work + sms - 1) / sms;
+  t = ((t + 31) / 32) * 32;
+  if (t < 64) t = 64;
+  if (t > 256) t = 256;
+  int64_t b = (work + t - 1) / t;
+  const int64_t cap = (int64_t)sms * per_sm256;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  *blocks = (int)b;
+  *threads = (int)t;
 }
 template <int D>
 cudaError_t Kernels<D>::pcg(const PcgArgs& a, int blocks, int threads, cudaStream_t s) {

@@ -90,6 +90,13 @@ __global__ void k_barrier_timeout_check(unsigned* words, int* err) {
   grid_barrier(&words[0], &words[1], err, gridDim.x + 1);
 }
 
+// Flat offset of stencil node k (x fastest) from the base node.
+template <int D>
+__device__ __forceinline__ int64_t stencil_offset(const GridGeo& g, int k) {
+  const int64_t ox = k % 3, oy = (k / 3) % 3, oz = k / 9;
+  return D == 2 ? ox + oy * g.res[0] : ox + (oy + oz * g.res[1]) * (int64_t)g.res[0];
+}
+
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
   constexpr int DD = D * D;
@@ -123,24 +130,24 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
       }
     }
     for (int64_t pi = tid; pi < a.P.n; pi += stride) {
-      double xp[D];
+      const int64_t base = a.sbase[pi];
+      double dN[K][D];
 #pragma unroll
-      for (int c = 0; c < D; ++c) xp[c] = a.P.x[c * a.P.n + pi];
-      Stencil<D> s;
-      make_stencil<D>(xp, g, s);
+      for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int c = 0; c < D; ++c) dN[k][c] = a.sdn[(int64_t)(c * K + k) * a.P.n + pi];
       double G[DD];
 #pragma unroll
       for (int e = 0; e < DD; ++e) G[e] = 0.0;
-#pragma unroll 3
+#pragma unroll
       for (int k = 0; k < K; ++k) {
-        double N, dN[D];
-        const int64_t node = stencil_node<D>(s, g, k, N, dN);
+        const int64_t node = base + stencil_offset<D>(g, k);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           const int64_t j = c * g.nn + node;
           const double pv = __ldcg(&a.z[j]) + beta * __ldcg(&pold[j]);
 #pragma unroll
-          for (int b = 0; b < D; ++b) G[c * D + b] += pv * dN[b];
+          for (int b = 0; b < D; ++b) G[c * D + b] += pv * dN[k][b];
         }
       }
       double Y[DD];
@@ -153,10 +160,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
       }
 #pragma unroll
       for (int i = 0; i < DD; ++i) acc1[0] += G[i] * Y[i];
-#pragma unroll 3
+#pragma unroll
       for (int k = 0; k < K; ++k) {
-        double N, dN[D];
-        const int64_t node = stencil_node<D>(s, g, k, N, dN);
+        const int64_t node = base + stencil_offset<D>(g, k);
         const unsigned fm = a.dofmask[node];
         if (!fm) continue;
 #pragma unroll
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
           if (!((fm >> c) & 1u)) continue;
           double f = 0.0;
 #pragma unroll
-          for (int b = 0; b < D; ++b) f += Y[c * D + b] * dN[b];
+          for (int b = 0; b < D; ++b) f += Y[c * D + b] * dN[k][b];
           atomicAdd(&a.q[c * g.nn + node], f);
         }
       }

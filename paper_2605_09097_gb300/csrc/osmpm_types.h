@@ -81,6 +81,8 @@ struct PcgArgs {
   DevScalars* S;
   double* partials;  // 3 * gridDim.x doubles
   int* err;
+  const int* sbase;     // per particle: flat index of the stencil's base node
+  const double* sdn;    // per particle: grad N of the 3^D stencil nodes, [(c*K + k)*n + p]
 };
 
 }  // namespace osmpm
