@@ -81,7 +81,9 @@ struct osmpm_domain {
   // grid (component-major)
   double *m = nullptr, *mv = nullptr, *vn = nullptr, *bm = nullptr, *u = nullptr;
   double *grad = nullptr, *diag = nullptr;
+  // PCG vectors: x, r (2), s (2), w (3), p; cz/cp double as r[1]/s[0]
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cp1 = nullptr, *cq = nullptr;
+  double *cw1 = nullptr, *cw2 = nullptr, *cpp = nullptr;
   double* L = nullptr;
   int* sbase = nullptr;    // stencil cache of the last P2G (base node, grad N)
   double* sdn = nullptr;
@@ -306,9 +308,14 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
                              d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
                              d->cz, d->cp, d->S, d->partials, d->stream));
-  // whole PCG in one cooperative launch (p1, q and the barrier start at zero)
-  CUDA_TRY(cudaMemsetAsync(d->cp1, 0, sizeof(double) * D * nn, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cq, 0, sizeof(double) * D * nn, d->stream));
+  // whole PCG in one cooperative launch: s[1], w[0..2], p and the barrier
+  // counter start at zero; x = 0 and r[0] = -g come from grad_finish
+  const size_t vb = sizeof(double) * D * nn;
+  CUDA_TRY(cudaMemsetAsync(d->cp1, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cq, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cw1, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cw2, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cpp, 0, vb, d->stream));
   CUDA_TRY(cudaMemsetAsync(&d->S->bar_count, 0, sizeof(unsigned), d->stream));
   PcgArgs a{};
   a.P = d->P;
@@ -319,11 +326,14 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
   a.diag = d->diag;
   a.inv_dt2 = 1.0 / (dt * dt);
   a.x = d->cx;
-  a.r = d->cr;
-  a.z = d->cz;
-  a.p0 = d->cp;
-  a.p1 = d->cp1;
-  a.q = d->cq;
+  a.r[0] = d->cr;
+  a.r[1] = d->cz;
+  a.s[0] = d->cp;
+  a.s[1] = d->cp1;
+  a.w[0] = d->cq;
+  a.w[1] = d->cw1;
+  a.w[2] = d->cw2;
+  a.p = d->cpp;
   a.S = d->S;
   a.partials = d->partials;
   a.err = d->err;
@@ -581,6 +591,9 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(dalloc_n(d, D * nn, &d->cz));
   C_TRY(dalloc_n(d, D * nn, &d->cp));
   C_TRY(dalloc_n(d, D * nn, &d->cp1));
+  C_TRY(dalloc_n(d, D * nn, &d->cw1));
+  C_TRY(dalloc_n(d, D * nn, &d->cw2));
+  C_TRY(dalloc_n(d, D * nn, &d->cpp));
   C_TRY(dalloc_n(d, D * nn, &d->cq));
   const int npk = (D * D) * (D * D + 1) / 2;
   C_TRY(dalloc_n(d, (int64_t)npk * n, &d->L));

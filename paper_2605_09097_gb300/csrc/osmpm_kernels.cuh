@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(PartPtrs P, GridGeo g, const 
 }
 
 // Completes the gradient on the free DOFs (inertia and external force),
-// adds m/dt^2 to the diagonal and starts PCG from x = 0: r = -g, z = r/diag,
-// p = z; reduces r.z and r.r.
+// adds m/dt^2 to the diagonal and stores its inverse, and starts PCG from
+// x = 0: r = -g, z = D^-1 r, p = z; reduces r.z and r.r.
 template <int D>
 __global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, const double* u,
                               const uint8_t* dofmask, double gx, double gy, double gz, double dt,
@@ -427,10 +427,10 @@ __global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, cons
     grad[idx] = gi;
     x[idx] = 0.0;
     if (fr) {
-      const double dg = diag[idx] + mi * inv_dt2;
+      const double dg = 1.0 / (diag[idx] + mi * inv_dt2);  // stored inverted
       diag[idx] = dg;
       const double ri = -gi;
-      const double zi = ri / dg;
+      const double zi = ri * dg;
       r[idx] = ri;
       z[idx] = zi;
       p[idx] = zi;
@@ -561,7 +561,7 @@ __global__ void k_cg_c(GridGeo g, const uint8_t* dofmask, const double* diag, co
       x[idx] += alpha * p[idx];
       const double ri = r[idx] - alpha * q[idx];
       r[idx] = ri;
-      const double zi = ri / diag[idx];
+      const double zi = ri * diag[idx];  // diag holds the inverse
       z[idx] = zi;
       acc[0] += ri * zi;
       acc[1] += ri * ri;

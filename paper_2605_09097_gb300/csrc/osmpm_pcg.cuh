@@ -1,15 +1,17 @@
 // Persistent Jacobi-preconditioned CG for the Newton system
-// (M/dt^2 + K) delta = -g of Sec. 2.2.5, one cooperative launch per solve.
-//
-// Each iteration has two phases separated by grid barriers:
-//  1. p_new = z + beta p_old on the free DOFs owned by this thread (double-
-//     buffered p), q += (m/dt^2) p_new, and the particle Hessian-vector
-//     product: every particle gathers p at its stencil as z + beta p_old
-//     (so no barrier is needed between the p update and the gather), forms
-//     Y = L G and scatters Y grad N_i into q.  Partial sums of p.Hp.
-//  2. alpha = r.z / p.Hp, x += alpha p, r -= alpha q, z = r/diag, q = 0;
-//     partial sums of r.z and r.r.
-// Every block sums the partials of the previous phase itself, in block
+// (M/dt^2 + K) delta = -g of Sec. 2.2.5, one cooperative launch per solve,
+// in the Chronopoulos-Gear arrangement: one fused reduction, hence one grid
+// barrier, per iteration.  With u = D^-1 r and w = A u:
+//   gamma = r.u, delta = u.w, beta = gamma/gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old),
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.
+// Phase k (after barrier k) does the owner updates above and, in the same
+// phase, the particle Hessian-vector product w_{k+1} = A u_{k+1}: each
+// particle gathers u_{k+1} at its stencil as (r_k - alpha (w_k + beta
+// s_{k-1})) D^-1 from buffers that were complete at barrier k (r and s
+// double-buffered, w triple-buffered), and delta_{k+1} = u.Au is the
+// particle quadratic form sum_p G:LG plus sum m/dt^2 u^2, so it does not
+// wait for the scatter.  Every block sums the partials itself, in block
 // order, so all blocks take the same branch and the result is
 // deterministic.  Arrays that other blocks write during the launch are
 // read with __ldcg (L2, not the non-coherent L1).
@@ -21,34 +23,33 @@ namespace osmpm {
 
 constexpr unsigned long long kBarrierSpinLimit = 1ull << 22;
 
-// Sense-reversing grid barrier over `expected` (= gridDim.x) co-resident
-// blocks.  The spin gives up after kBarrierSpinLimit polls (about two
-// seconds) and reports kErrBarrierTimeout.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err,
+// Grid barrier over `expected` co-resident blocks on a monotonic counter:
+// each block adds 1 with release semantics and waits (acquire loads) until
+// the counter reaches its running target, which grows by `expected` per
+// barrier (kept per block in *target).  One round trip to L2 per barrier;
+// the spin gives up after kBarrierSpinLimit polls (about a second) and
+// reports kErrBarrierTimeout.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* target, int* err,
                                              unsigned expected) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g0 = *((volatile unsigned*)gen);
+    const unsigned goal = *target + expected;
+    *target = goal;
     __threadfence();
-    const unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == expected - 1) {
-      *((volatile unsigned*)count) = 0u;
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      unsigned long long spins = 0;
-      while (*((volatile unsigned*)gen) == g0) {
-        if (++spins > kBarrierSpinLimit) {
-          atomicOr(err, kErrBarrierTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+    unsigned long long spins = 0;
+    for (;;) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if ((int)(v - goal) >= 0) break;
+      if (++spins > kBarrierSpinLimit) {
+        atomicOr(err, kErrBarrierTimeout);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;
@@ -87,7 +88,9 @@ __device__ __forceinline__ void publish_partials(double (&v)[NV], double* partia
 // so its bounded spin can only run out.
 template <int D>
 __global__ void k_barrier_timeout_check(unsigned* words, int* err) {
-  grid_barrier(&words[0], &words[1], err, gridDim.x + 1);
+  __shared__ unsigned goal;
+  if (threadIdx.x == 0) goal = 0u;
+  grid_barrier(&words[0], &goal, err, gridDim.x + 1);
 }
 
 // Flat offset of stencil node k (x fastest) from the base node.
@@ -97,10 +100,63 @@ __device__ __forceinline__ int64_t stencil_offset(const GridGeo& g, int k) {
   return D == 2 ? ox + oy * g.res[0] : ox + (oy + oz * g.res[1]) * (int64_t)g.res[0];
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
+// Particle Hessian-vector product: gathers u at the stencil through
+// `ufun(j)` (j = flat DOF index), scatters (L G) grad N_i into w on the free
+// DOFs and returns the quadratic form G : L G.
+template <int D, class UF>
+__device__ __forceinline__ double particle_hvp(const PcgArgs& a, int64_t pi, UF ufun, double* w) {
   constexpr int DD = D * D;
   constexpr int K = (D == 2) ? 9 : 27;
+  const GridGeo& g = a.g;
+  const int64_t base = a.sbase[pi];
+  double dN[K][D];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < D; ++c) dN[k][c] = a.sdn[(int64_t)(c * K + k) * a.P.n + pi];
+  double G[DD];
+#pragma unroll
+  for (int e = 0; e < DD; ++e) G[e] = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t node = base + stencil_offset<D>(g, k);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const double uv = ufun(c * g.nn + node);
+#pragma unroll
+      for (int b = 0; b < D; ++b) G[c * D + b] += uv * dN[k][b];
+    }
+  }
+  double Y[DD];
+#pragma unroll
+  for (int i = 0; i < DD; ++i) {
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < DD; ++j) t += a.L[(int64_t)Sym<D>::idx(i, j) * a.P.n + pi] * G[j];
+    Y[i] = t;
+  }
+  double qf = 0.0;
+#pragma unroll
+  for (int i = 0; i < DD; ++i) qf += G[i] * Y[i];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int64_t node = base + stencil_offset<D>(g, k);
+    const unsigned fm = a.dofmask[node];
+    if (!fm) continue;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      if (!((fm >> c) & 1u)) continue;
+      double f = 0.0;
+#pragma unroll
+      for (int b = 0; b < D; ++b) f += Y[c * D + b] * dN[k][b];
+      atomicAdd(&w[c * g.nn + node], f);
+    }
+  }
+  return qf;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
   const GridGeo& g = a.g;
   const int64_t ndof = g.nn * D;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -108,119 +164,118 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
   DevScalars* S = a.S;
   const int max_it = S->cg_max;
   const double tol2 = S->tol2;
-  double rz = S->rz;
-  int done = S->cg_done;
-  int neg = 0;
-  double beta = 0.0;
-  int it = 0;
+  const double* idiag = a.diag;  // inverse Jacobi diagonal
+  __shared__ unsigned bar_target;  // this block's running barrier goal (count starts at 0)
+  if (threadIdx.x == 0) bar_target = 0u;
+  int it = 0, neg = 0;
+  double sums[3];
+
+  // ---- phase 0: w_0 = A u_0, gamma_0 = r0.u0, delta_0 = u0.w0
+  {
+    double acc[3] = {0.0, 0.0, 0.0};
+    const double* r0 = a.r[0];
+    for (int64_t idx = tid; idx < ndof; idx += stride) {
+      const int c = (int)(idx / g.nn);
+      const int64_t i = idx - (int64_t)c * g.nn;
+      if ((a.dofmask[i] >> c) & 1u) {
+        const double ri = r0[idx];
+        const double ui = ri * idiag[idx];
+        acc[0] += ri * ui;
+        acc[2] += a.m[i] * a.inv_dt2 * ui * ui;
+        atomicAdd(&a.w[0][idx], a.m[i] * a.inv_dt2 * ui);
+      }
+    }
+    for (int64_t pi = tid; pi < a.P.n; pi += stride)
+      acc[2] += particle_hvp<D>(a, pi, [&](int64_t j) { return __ldcg(&r0[j]) * idiag[j]; }, a.w[0]);
+    publish_partials<3>(acc, a.partials, 0);
+    if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
+    sum_partials<3>(a.partials, sums);
+  }
+  double gamma = sums[0], delta = sums[2];
+  double alpha_old = 1.0, gamma_old = 1.0;
+  int done = (gamma == 0.0) || (S->cg_done != 0);
   for (; it < max_it && !done; ++it) {
-    const double* pold = (it & 1) ? a.p1 : a.p0;
-    double* pnew = (it & 1) ? a.p0 : a.p1;
-    // ---- phase 1: p update, diagonal term, particle HVP
-    double acc1[1] = {0.0};
+    double beta, alpha;
+    if (it == 0) {
+      beta = 0.0;
+      if (!(delta > 0.0)) {
+        neg = 1;
+        break;
+      }
+      alpha = gamma / delta;
+    } else {
+      beta = gamma / gamma_old;
+      const double den = delta - beta * gamma / alpha_old;
+      if (!(den > 0.0)) {
+        neg = 1;
+        break;
+      }
+      alpha = gamma / den;
+    }
+    const double* rk = a.r[it & 1];
+    double* rn = a.r[(it + 1) & 1];
+    double* sk = a.s[it & 1];
+    const double* sp = a.s[(it + 1) & 1];
+    const double* wk = a.w[it % 3];
+    double* wn = a.w[(it + 1) % 3];
+    double* wz = a.w[(it + 2) % 3];
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t idx = tid; idx < ndof; idx += stride) {
       const int c = (int)(idx / g.nn);
       const int64_t i = idx - (int64_t)c * g.nn;
       if ((a.dofmask[i] >> c) & 1u) {
-        const double pn = __ldcg(&a.z[idx]) + beta * __ldcg(&pold[idx]);
-        pnew[idx] = pn;
+        const double id = idiag[idx];
+        const double rki = __ldcg(&rk[idx]);
+        const double ski = __ldcg(&wk[idx]) + beta * __ldcg(&sp[idx]);
+        sk[idx] = ski;
+        const double pk = rki * id + beta * a.p[idx];
+        a.p[idx] = pk;
+        a.x[idx] += alpha * pk;
+        const double rni = rki - alpha * ski;
+        rn[idx] = rni;
+        const double ui = rni * id;
+        acc[0] += rni * ui;
+        acc[1] += rni * rni;
         const double md = a.m[i] * a.inv_dt2;
-        atomicAdd(&a.q[idx], md * pn);
-        acc1[0] += md * pn * pn;
+        acc[2] += md * ui * ui;
+        atomicAdd(&wn[idx], md * ui);
       }
+      wz[idx] = 0.0;
     }
-    for (int64_t pi = tid; pi < a.P.n; pi += stride) {
-      const int64_t base = a.sbase[pi];
-      double dN[K][D];
-#pragma unroll
-      for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int c = 0; c < D; ++c) dN[k][c] = a.sdn[(int64_t)(c * K + k) * a.P.n + pi];
-      double G[DD];
-#pragma unroll
-      for (int e = 0; e < DD; ++e) G[e] = 0.0;
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int64_t node = base + stencil_offset<D>(g, k);
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          const int64_t j = c * g.nn + node;
-          const double pv = __ldcg(&a.z[j]) + beta * __ldcg(&pold[j]);
-#pragma unroll
-          for (int b = 0; b < D; ++b) G[c * D + b] += pv * dN[k][b];
-        }
-      }
-      double Y[DD];
-#pragma unroll
-      for (int i = 0; i < DD; ++i) {
-        double t = 0.0;
-#pragma unroll
-        for (int j = 0; j < DD; ++j) t += a.L[(int64_t)Sym<D>::idx(i, j) * a.P.n + pi] * G[j];
-        Y[i] = t;
-      }
-#pragma unroll
-      for (int i = 0; i < DD; ++i) acc1[0] += G[i] * Y[i];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int64_t node = base + stencil_offset<D>(g, k);
-        const unsigned fm = a.dofmask[node];
-        if (!fm) continue;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          if (!((fm >> c) & 1u)) continue;
-          double f = 0.0;
-#pragma unroll
-          for (int b = 0; b < D; ++b) f += Y[c * D + b] * dN[k][b];
-          atomicAdd(&a.q[c * g.nn + node], f);
-        }
-      }
-    }
-    publish_partials<1>(acc1, a.partials, 0);
-    if (!grid_barrier(&S->bar_count, &S->bar_gen, a.err, gridDim.x)) return;
-    double pq[1];
-    sum_partials<1>(a.partials, pq);
-    if (!(pq[0] > 0.0)) {
-      // negative curvature: keep the current iterate, or take the
-      // preconditioned steepest-descent direction if there is none yet
-      neg = 1;
-      if (it == 0)
-        for (int64_t idx = tid; idx < ndof; idx += stride) a.x[idx] = __ldcg(&pnew[idx]);
-      break;
-    }
-    const double alpha = rz / pq[0];
-    // ---- phase 2: updates
-    double acc2[2] = {0.0, 0.0};
-    for (int64_t idx = tid; idx < ndof; idx += stride) {
-      const int c = (int)(idx / g.nn);
-      const int64_t i = idx - (int64_t)c * g.nn;
-      if ((a.dofmask[i] >> c) & 1u) {
-        a.x[idx] += alpha * __ldcg(&pnew[idx]);
-        const double ri = __ldcg(&a.r[idx]) - alpha * __ldcg(&a.q[idx]);
-        a.r[idx] = ri;
-        const double zi = ri / a.diag[idx];
-        a.z[idx] = zi;
-        acc2[0] += ri * zi;
-        acc2[1] += ri * ri;
-      }
-      a.q[idx] = 0.0;
-    }
-    publish_partials<2>(acc2, a.partials, 1);
-    if (!grid_barrier(&S->bar_count, &S->bar_gen, a.err, gridDim.x)) return;
-    double rr[2];
-    sum_partials<2>(a.partials + gridDim.x, rr);
-    beta = rr[0] / rz;
-    rz = rr[0];
-    done = (rr[1] <= tol2) ? 1 : 0;
-    if (done) {
+    for (int64_t pi = tid; pi < a.P.n; pi += stride)
+      acc[2] += particle_hvp<D>(
+          a, pi,
+          [&](int64_t j) {
+            return (__ldcg(&rk[j]) - alpha * (__ldcg(&wk[j]) + beta * __ldcg(&sp[j]))) * idiag[j];
+          },
+          wn);
+    publish_partials<3>(acc, a.partials, 0);
+    if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
+    sum_partials<3>(a.partials, sums);
+    gamma_old = gamma;
+    alpha_old = alpha;
+    gamma = sums[0];
+    delta = sums[2];
+    if (sums[1] <= tol2) {
+      done = 1;
       ++it;
       break;
+    }
+  }
+  if (neg && it == 0) {
+    // no direction yet: take the preconditioned steepest descent u_0
+    const double* r0 = a.r[0];
+    for (int64_t idx = tid; idx < ndof; idx += stride) {
+      const int c = (int)(idx / g.nn);
+      const int64_t i = idx - (int64_t)c * g.nn;
+      if ((a.dofmask[i] >> c) & 1u) a.x[idx] = r0[idx] * idiag[idx];
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->cg_iter = it;
     S->cg_done = 1;
     S->cg_neg = neg;
-    S->rz = rz;
+    S->rz = gamma;
   }
 }
 

@@ -54,7 +54,7 @@ struct DevScalars {
   int cg_iter, cg_done, cg_neg, cg_max;
   int err;
   unsigned counter;
-  unsigned bar_count, bar_gen;  // grid barrier of the persistent PCG kernel
+  unsigned bar_count, bar_spare;  // grid-barrier counter of the persistent PCG kernel
 };
 
 enum : int {
@@ -70,14 +70,13 @@ struct PcgArgs {
   const double* m;
   const uint8_t* dofmask;
   const double* L;
-  const double* diag;
+  const double* diag;   // inverse Jacobi diagonal
   double inv_dt2;
   double* x;
-  double* r;
-  double* z;
-  double* p0;
-  double* p1;
-  double* q;
+  double* r[2];      // residual, double-buffered (r[0] holds -g at launch)
+  double* s[2];      // s = A p, double-buffered
+  double* w[3];      // w = A u, triple-buffered (w[0], w[1] zero at launch)
+  double* p;
   DevScalars* S;
   double* partials;  // 3 * gridDim.x doubles
   int* err;

@@ -292,3 +292,22 @@ def test_single_particle(osmpm):
     dom.step(0.01)
     O.step(ref, 0.01)
     np.testing.assert_allclose(dom.get_particles()[0], ref.p.x, atol=1e-15)
+
+
+def test_bench_workload_full_size_one_global_step(osmpm):
+    """The configuration bench.py times (inclusion, coarse dx 0.05, fine dx
+    0.005, M = 2, FP64), one global Schwarz step, every particle compared
+    with the oracle (rel-L2 of displacement <= 1e-6), receiver sets bit for
+    bit."""
+    cB, cS, sch, dT = W.inclusion(dx_S=0.005, M=2)
+    B, S, rB, rS, out = _run_schwarz(osmpm, cB, cS, sch, dT, 1)
+    st, ost, so = out[0]
+    np.testing.assert_array_equal(B.get_grid(osmpm.OSMPM_FIELD_RECEIVER) > 0, so["sets"].recvB)
+    np.testing.assert_array_equal(S.get_grid(osmpm.OSMPM_FIELD_RECEIVER) > 0, so["sets"].recvS)
+    assert st["converged"] == 1 and ost.converged
+    assert abs(st["schwarz_iters"] - ost.iters) <= 1
+    xB, _, _, _ = B.get_particles()
+    xS, _, _, FS = S.get_particles()
+    assert rel_disp(xB, rB.p.x, cB.particles.x) <= DISP_TOL
+    assert rel_disp(xS, rS.p.x, cS.particles.x) <= DISP_TOL
+    np.testing.assert_allclose(FS, rS.p.F, atol=1e-8)
