@@ -69,7 +69,11 @@ typedef struct osmpm_allocator {
  * solver controls (Sec. 2.2.5). */
 typedef struct osmpm_domain_desc {
   int32_t dim;              /* 2 or 3 */
-  int32_t precision;        /* 0: FP64 throughout (the only mode of this build) */
+  int32_t precision;        /* 0: FP64 throughout; 1: mixed - particle v, B, F stored in
+                               FP32, the PCG's Hessian-vector product (per-particle Hessian
+                               blocks, grad N, arithmetic) in FP32; positions, grid vectors,
+                               the Newton residual, line-search energy change, PCG dot
+                               products and Schwarz residuals stay FP64 */
   double origin[3];
   double dx;
   int32_t res[3];           /* nodes per axis; each >= 4 */

@@ -1,4 +1,4 @@
-// Kernels and launchers of the 2D path.
+// Kernels and launchers of the 2D FP64 path.
 #include "osmpm_kernels.cuh"
 
-template struct osmpm::Kernels<2>;
+template struct osmpm::Kernels<2, double>;

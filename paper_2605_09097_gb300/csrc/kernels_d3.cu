@@ -1,4 +1,4 @@
-// Kernels and launchers of the 3D path.
+// Kernels and launchers of the 3D FP64 path.
 #include "osmpm_kernels.cuh"
 
-template struct osmpm::Kernels<3>;
+template struct osmpm::Kernels<3, double>;

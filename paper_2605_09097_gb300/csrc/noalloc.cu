@@ -116,10 +116,10 @@ extern "C" osmpm_status osmpm_energy_change_noalloc(const osmpm_noalloc_grid* gr
   P.lam = const_cast<double*>(parts->lam);
   const double gravity[3] = {grid->gravity[0], grid->gravity[1], grid->gravity[2]};
   if (D == 2)
-    Kernels<2>::energy_change_blocks(P, g, grid->m, grid->vn, grid->u, grid->s, gravity, dt, alpha,
+    Kernels<2, double>::energy_change_blocks(P, g, grid->m, grid->vn, grid->u, grid->s, gravity, dt, alpha,
                                      S, partials, (int)blocks, s);
   else
-    Kernels<3>::energy_change_blocks(P, g, grid->m, grid->vn, grid->u, grid->s, gravity, dt, alpha,
+    Kernels<3, double>::energy_change_blocks(P, g, grid->m, grid->vn, grid->u, grid->s, gravity, dt, alpha,
                                      S, partials, (int)blocks, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(OSMPM_E_CUDA, "launch: %s", cudaGetErrorString(e));

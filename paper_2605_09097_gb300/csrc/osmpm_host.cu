@@ -61,6 +61,39 @@ osmpm_status osmpm::set_error(osmpm_status st, const char* fmt, ...) {
   return st;
 }
 
+// Particle memory with the storage type of v, B, F erased; typed<R>()
+// gives the kernels' view.
+struct PartMem {
+  int64_t n;
+  double* x;
+  void* v;
+  void* B;
+  void* F;
+  double* vol0;
+  double* mass;
+  double* mu;
+  double* lam;
+  uint8_t* flags;
+  uint32_t* id;
+};
+
+template <class R>
+PartPtrsT<R> typed(const PartMem& m) {
+  PartPtrsT<R> p;
+  p.n = m.n;
+  p.x = m.x;
+  p.v = (R*)m.v;
+  p.B = (R*)m.B;
+  p.F = (R*)m.F;
+  p.vol0 = m.vol0;
+  p.mass = m.mass;
+  p.mu = m.mu;
+  p.lam = m.lam;
+  p.flags = m.flags;
+  p.id = m.id;
+  return p;
+}
+
 struct osmpm_domain {
   osmpm_domain_desc desc{};
   int dim = 2;
@@ -71,8 +104,11 @@ struct osmpm_domain {
   bool have_alloc = false;
   std::vector<std::pair<void*, size_t>> blocks;
 
-  PartPtrs P{}, A{};  // primary (Morton-sorted) and alternate particle sets
-  double *snap_x = nullptr, *snap_v = nullptr, *snap_B = nullptr, *snap_F = nullptr;
+  int prec = 0;        // 0: FP64, 1: mixed (v, B, F, L, grad N and the HVP in FP32)
+  size_t rsize = 8;    // bytes of the particle-state type
+  PartMem P{}, A{};    // primary (Morton-sorted) and alternate particle sets
+  double* snap_x = nullptr;
+  void *snap_v = nullptr, *snap_B = nullptr, *snap_F = nullptr;
   double* stage = nullptr;  // host-layout staging for get/set_particles
   uint64_t *keys = nullptr, *keys_alt = nullptr;
   uint32_t *vals = nullptr, *vals_alt = nullptr;
@@ -84,9 +120,9 @@ struct osmpm_domain {
   // PCG vectors: x, r (2), s (2), w (3), p; cz/cp double as r[1]/s[0]
   double *cx = nullptr, *cr = nullptr, *cz = nullptr, *cp = nullptr, *cp1 = nullptr, *cq = nullptr;
   double *cw1 = nullptr, *cw2 = nullptr, *cpp = nullptr;
-  double* L = nullptr;
+  void* L = nullptr;       // per-particle Hessian blocks (particle-state type)
   int* sbase = nullptr;    // stencil cache of the last P2G (base node, grad N)
-  double* sdn = nullptr;
+  void* sdn = nullptr;
   uint8_t *dofmask = nullptr, *physmask = nullptr, *gam = nullptr, *recv = nullptr;
   double *bc0 = nullptr, *bc1 = nullptr, *bc_prev = nullptr, *bc_applied = nullptr;
   double *vtmp = nullptr, *proj_num = nullptr, *proj_den = nullptr;
@@ -154,14 +190,15 @@ void free_all(osmpm_domain* d) {
   d->err_host = nullptr;
 }
 
-osmpm_status alloc_parts(osmpm_domain* d, PartPtrs& P) {
+osmpm_status alloc_parts(osmpm_domain* d, PartMem& P) {
   const int D = d->dim;
   const int64_t n = d->n;
+  const size_t rs = d->rsize;
   P.n = n;
   OSMPM_TRY(dalloc_n(d, D * n, &P.x));
-  OSMPM_TRY(dalloc_n(d, D * n, &P.v));
-  OSMPM_TRY(dalloc_n(d, D * D * n, &P.B));
-  OSMPM_TRY(dalloc_n(d, D * D * n, &P.F));
+  OSMPM_TRY(dalloc(d, rs * D * n, &P.v));
+  OSMPM_TRY(dalloc(d, rs * D * D * n, &P.B));
+  OSMPM_TRY(dalloc(d, rs * D * D * n, &P.F));
   OSMPM_TRY(dalloc_n(d, n, &P.vol0));
   OSMPM_TRY(dalloc_n(d, n, &P.mass));
   OSMPM_TRY(dalloc_n(d, n, &P.mu));
@@ -172,17 +209,33 @@ osmpm_status alloc_parts(osmpm_domain* d, PartPtrs& P) {
 }
 
 // ---------------------------------------------------------------------------
-// dimension dispatch
+// dispatch over dimension and precision: inside `call`, K is the launcher
+// class, R the particle-state type, P_/A_ the typed particle sets, L_ and
+// SDN_ the typed Hessian blocks and stencil gradients of domain d
 // ---------------------------------------------------------------------------
-#define DISPATCH(d, call)                  \
-  do {                                     \
-    if ((d)->dim == 2) {                   \
-      using K = Kernels<2>;                \
-      call;                                \
-    } else {                               \
-      using K = Kernels<3>;                \
-      call;                                \
-    }                                      \
+#define DISPATCH_R(d, Dim, RT, call)           \
+  do {                                          \
+    using K = Kernels<Dim, RT>;                 \
+    using R = RT;                               \
+    const PartPtrsT<RT> P_ = typed<RT>((d)->P); \
+    const PartPtrsT<RT> A_ = typed<RT>((d)->A); \
+    RT* L_ = (RT*)(d)->L;                       \
+    RT* SDN_ = (RT*)(d)->sdn;                   \
+    (void)P_;                                   \
+    (void)A_;                                   \
+    (void)L_;                                   \
+    (void)SDN_;                                 \
+    call;                                       \
+  } while (0)
+#define DISPATCH(d, call)                                     \
+  do {                                                        \
+    if ((d)->prec == 0) {                                     \
+      if ((d)->dim == 2) DISPATCH_R(d, 2, double, call);      \
+      else DISPATCH_R(d, 3, double, call);                    \
+    } else {                                                  \
+      if ((d)->dim == 2) DISPATCH_R(d, 2, float, call);       \
+      else DISPATCH_R(d, 3, float, call);                     \
+    }                                                         \
   } while (0)
 
 osmpm_status sync_scalars(osmpm_domain* d) {
@@ -211,7 +264,7 @@ osmpm_status sort_into_primary(osmpm_domain* d) {
   while ((1 << bits_axis) < maxres) ++bits_axis;
   radix_sort_pairs(d->keys, d->vals, d->keys_alt, d->vals_alt, n, bits_axis * d->dim, d->hist,
                    d->stream);
-  DISPATCH(d, K::permute(d->A, d->P, d->vals, d->stream));
+  DISPATCH(d, K::permute(A_, P_, d->vals, d->stream));
   OSMPM_TRY(sync_scalars(d));
   return check_err(d);
 }
@@ -270,8 +323,8 @@ osmpm_status run_p2g(osmpm_domain* d, bool boundary_mass) {
   CUDA_TRY(cudaMemsetAsync(d->m, 0, sizeof(double) * nn, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->mv, 0, sizeof(double) * D * nn, d->stream));
   if (boundary_mass) CUDA_TRY(cudaMemsetAsync(d->bm, 0, sizeof(double) * nn, d->stream));
-  DISPATCH(d, K::p2g(d->P, d->geo, d->m, d->mv, boundary_mass ? d->bm : nullptr, d->err, d->sbase,
-                     d->sdn, d->stream));
+  DISPATCH(d, K::p2g(P_, d->geo, d->m, d->mv, boundary_mass ? d->bm : nullptr, d->err, d->sbase,
+                     SDN_, d->stream));
   DISPATCH(d, K::normalize(d->geo, d->m, d->mv, d->vn, d->stream));
   return OSMPM_OK;
 }
@@ -299,30 +352,16 @@ struct SolveStats {
 
 // Gradient + Hessian data at the current iterate, then PCG from x = 0 until
 // |r| <= rtol |r0| (device-side control, host polls once per chunk).
-osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
-  const int64_t nn = d->geo.nn;
-  const int D = d->dim;
-  CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
-  DISPATCH(d, K::grad(d->P, d->geo, d->u, d->dofmask, d->grad, d->diag, d->L, d->err, d->stream));
-  DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
-                             d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
-                             d->cz, d->cp, d->S, d->partials, d->stream));
-  // whole PCG in one cooperative launch: s[1], w[0..2], p and the barrier
-  // counter start at zero; x = 0 and r[0] = -g come from grad_finish
-  const size_t vb = sizeof(double) * D * nn;
-  CUDA_TRY(cudaMemsetAsync(d->cp1, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cq, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cw1, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cw2, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cpp, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(&d->S->bar_count, 0, sizeof(unsigned), d->stream));
-  PcgArgs a{};
-  a.P = d->P;
+// Launches the persistent PCG kernel with the domain's buffers (x, r[2],
+// s[2], w[3], p) and one block per SM; records the timing events if asked.
+template <class K, class R>
+cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
+  PcgArgsT<R> a{};
+  a.P = typed<R>(d->P);
   a.g = d->geo;
   a.m = d->m;
   a.dofmask = d->dofmask;
-  a.L = d->L;
+  a.L = (const R*)d->L;
   a.diag = d->diag;
   a.inv_dt2 = 1.0 / (dt * dt);
   a.x = d->cx;
@@ -338,16 +377,42 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
   a.partials = d->partials;
   a.err = d->err;
   a.sbase = d->sbase;
-  a.sdn = d->sdn;
-  const int64_t work = std::max<int64_t>(d->n, D * nn);
+  a.sdn = (const R*)d->sdn;
   int blocks = 0, threads = 0;
-  DISPATCH(d, K::pcg_shape(work, &blocks, &threads));
+  K::pcg_shape(work, &blocks, &threads);
+  if (timed) {
+    const cudaError_t e = cudaEventRecord(d->ev[0], d->stream);
+    if (e != cudaSuccess) return e;
+  }
+  const cudaError_t le = K::pcg(a, blocks, threads, d->stream);
+  if (le != cudaSuccess) return le;
+  if (timed) return cudaEventRecord(d->ev[1], d->stream);
+  return cudaSuccess;
+}
+
+osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
+  const int64_t nn = d->geo.nn;
+  const int D = d->dim;
+  CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
+  DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
+  DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
+                             d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
+                             d->cz, d->cp, d->S, d->partials, d->stream));
+  // whole PCG in one cooperative launch: s[1], w[0..2], p and the barrier
+  // counter start at zero; x = 0 and r[0] = -g come from grad_finish
+  const size_t vb = sizeof(double) * D * nn;
+  CUDA_TRY(cudaMemsetAsync(d->cp1, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cq, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cw1, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cw2, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(d->cpp, 0, vb, d->stream));
+  CUDA_TRY(cudaMemsetAsync(&d->S->bar_count, 0, sizeof(unsigned), d->stream));
+  const int64_t work = std::max<int64_t>(d->n, D * nn);
   const bool timed = d->time_hvp && !d->ev.empty();
-  if (timed) CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
   cudaError_t le = cudaSuccess;
-  DISPATCH(d, le = K::pcg(a, blocks, threads, d->stream));
+  DISPATCH(d, (le = launch_pcg<K, R>(d, dt, work, timed)));
   if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(le));
-  if (timed) CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
   DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
   OSMPM_TRY(sync_scalars(d));
   OSMPM_TRY(check_err(d));
@@ -380,7 +445,7 @@ osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
     double alpha = 1.0;
     bool ok = false;
     for (int s = 0; s <= d->desc.ls_max; ++s) {
-      DISPATCH(d, K::energy_change(d->P, d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt,
+      DISPATCH(d, K::energy_change(P_, d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt,
                                    alpha, d->S, d->partials, d->stream));
       OSMPM_TRY(sync_scalars(d));
       if (d->S_host->dE < 0.0) {
@@ -424,14 +489,15 @@ double* keep_slot(osmpm_domain* d, int slot) { return d->u_keep + (int64_t)slot 
 osmpm_status snapshot(osmpm_domain* d, bool restore) {
   const int D = d->dim;
   const int64_t n = d->n;
-  auto cp = [&](double* a, double* b, int64_t cnt) {
-    return cudaMemcpyAsync(restore ? a : b, restore ? b : a, sizeof(double) * cnt,
-                           cudaMemcpyDeviceToDevice, d->stream);
+  const size_t rs = d->rsize;
+  auto cp = [&](void* a, void* b, size_t bytes) {
+    return cudaMemcpyAsync(restore ? a : b, restore ? b : a, bytes, cudaMemcpyDeviceToDevice,
+                           d->stream);
   };
-  CUDA_TRY(cp(d->P.x, d->snap_x, D * n));
-  CUDA_TRY(cp(d->P.v, d->snap_v, D * n));
-  CUDA_TRY(cp(d->P.B, d->snap_B, D * D * n));
-  CUDA_TRY(cp(d->P.F, d->snap_F, D * D * n));
+  CUDA_TRY(cp(d->P.x, d->snap_x, sizeof(double) * D * n));
+  CUDA_TRY(cp(d->P.v, d->snap_v, rs * D * n));
+  CUDA_TRY(cp(d->P.B, d->snap_B, rs * D * D * n));
+  CUDA_TRY(cp(d->P.F, d->snap_F, rs * D * D * n));
   return OSMPM_OK;
 }
 
@@ -459,7 +525,7 @@ osmpm_status upload_state(osmpm_domain* d, const double* x, const double* v, con
   CUDA_TRY(cudaMemcpyAsync(sv, v, sizeof(double) * D * n, cudaMemcpyHostToDevice, d->stream));
   CUDA_TRY(cudaMemcpyAsync(sB, B, sizeof(double) * D * D * n, cudaMemcpyHostToDevice, d->stream));
   CUDA_TRY(cudaMemcpyAsync(sF, F, sizeof(double) * D * D * n, cudaMemcpyHostToDevice, d->stream));
-  DISPATCH(d, K::unpack_in(sx, sv, sB, sF, d->A, d->stream));
+  DISPATCH(d, K::unpack_in(sx, sv, sB, sF, A_, d->stream));
   return OSMPM_OK;
 }
 
@@ -510,7 +576,8 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   if (!desc || !pin || !out) return fail(OSMPM_E_INVALID, "null argument");
   *out = nullptr;
   if (desc->dim != 2 && desc->dim != 3) return fail(OSMPM_E_INVALID, "dim must be 2 or 3");
-  if (desc->precision != 0) return fail(OSMPM_E_UNSUPPORTED, "only precision 0 (FP64) is built");
+  if (desc->precision != 0 && desc->precision != 1)
+    return fail(OSMPM_E_INVALID, "precision must be 0 (FP64) or 1 (mixed)");
   for (int i = 0; i < 8; ++i)
     if (desc->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
   if (!(desc->dx > 0.0) || !std::isfinite(desc->dx)) return fail(OSMPM_E_INVALID, "dx must be > 0");
@@ -541,6 +608,8 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   d->desc = *desc;
   d->dim = D;
   d->n = n;
+  d->prec = desc->precision;
+  d->rsize = d->prec == 0 ? sizeof(double) : sizeof(float);
   d->stream = (cudaStream_t)cuda_stream;
   if (allocator && allocator->alloc && allocator->free) {
     d->alloc = *allocator;
@@ -570,9 +639,9 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(alloc_parts(d, d->P));
   C_TRY(alloc_parts(d, d->A));
   C_TRY(dalloc_n(d, D * n, &d->snap_x));
-  C_TRY(dalloc_n(d, D * n, &d->snap_v));
-  C_TRY(dalloc_n(d, D * D * n, &d->snap_B));
-  C_TRY(dalloc_n(d, D * D * n, &d->snap_F));
+  C_TRY(dalloc(d, d->rsize * D * n, &d->snap_v));
+  C_TRY(dalloc(d, d->rsize * D * D * n, &d->snap_B));
+  C_TRY(dalloc(d, d->rsize * D * D * n, &d->snap_F));
   C_TRY(dalloc_n(d, (2 * D + 2 * D * D) * n, &d->stage));
   C_TRY(dalloc_n(d, n, &d->keys));
   C_TRY(dalloc_n(d, n, &d->keys_alt));
@@ -596,9 +665,9 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(dalloc_n(d, D * nn, &d->cpp));
   C_TRY(dalloc_n(d, D * nn, &d->cq));
   const int npk = (D * D) * (D * D + 1) / 2;
-  C_TRY(dalloc_n(d, (int64_t)npk * n, &d->L));
+  C_TRY(dalloc(d, d->rsize * npk * n, &d->L));
   C_TRY(dalloc_n(d, n, &d->sbase));
-  C_TRY(dalloc_n(d, (int64_t)D * (D == 2 ? 9 : 27) * n, &d->sdn));
+  C_TRY(dalloc(d, d->rsize * D * (D == 2 ? 9 : 27) * n, &d->sdn));
   C_TRY(dalloc_n(d, nn, &d->dofmask));
   C_TRY(dalloc_n(d, nn, &d->physmask));
   C_TRY(dalloc_n(d, nn, &d->gam));
@@ -639,7 +708,7 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
       cudaMemcpyAsync(d->A.mass, pin->mass, sizeof(double) * n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess ||
       cudaMemcpyAsync(d->A.flags, pin->flags, n, cudaMemcpyHostToDevice, d->stream) != cudaSuccess)
     return cleanup(fail(OSMPM_E_CUDA, "particle upload failed"));
-  DISPATCH(d, K::lame(sE, snu, d->A, d->stream));
+  DISPATCH(d, K::lame(sE, snu, A_, d->stream));
   {
     std::vector<uint32_t> ids((size_t)n);
     for (int64_t p = 0; p < n; ++p) ids[(size_t)p] = (uint32_t)p;
@@ -691,7 +760,7 @@ osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
     fill_stats(stats, st, 0, 0, 0.0, 0.0);
     return s;
   }
-  DISPATCH(d, K::g2p(d->P, d->geo, d->u, dt, d->stream));
+  DISPATCH(d, K::g2p(P_, d->geo, d->u, dt, d->stream));
   CUDA_TRY(cudaStreamSynchronize(d->stream));
   CUDA_TRY(cudaGetLastError());
   fill_stats(stats, st, 0, 1, 0.0, 0.0);
@@ -706,6 +775,7 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   if (B == S) return fail(OSMPM_E_INVALID, "coarse and fine must be different domains");
   if (B->dim != S->dim) return fail(OSMPM_E_INVALID, "domains differ in dim");
   if (B->stream != S->stream) return fail(OSMPM_E_INVALID, "domains must share one stream");
+  if (B->prec != S->prec) return fail(OSMPM_E_INVALID, "domains differ in precision");
   if (!(B->geo.dx >= S->geo.dx)) return fail(OSMPM_E_INVALID, "coarse dx must be >= fine dx");
   if (sd->M < 1 || sd->k_max < 0 || !(sd->eps_conv > 0.0) || !(sd->eps_tol >= 0.0) ||
       std::isnan(sd->tau_B) || std::isnan(sd->tau_S))
@@ -784,7 +854,7 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
       if (k > 0) DISPATCH(S, K::warm_start(gS, S->dofmask, keep_slot(S, m - 1), S->u, s));
       S_TRY(newton_solve(S, dt, st));
       CUDA_TRY(cudaMemcpyAsync(keep_slot(S, m - 1), S->u, bytesS, cudaMemcpyDeviceToDevice, s));
-      DISPATCH(S, K::g2p(S->P, gS, S->u, dt, s));
+      DISPATCH(S, K::g2p(P_, gS, S->u, dt, s));
       S_TRY(run_p2g(S, false));
       S_TRY(sync_scalars(S));
       S_TRY(check_err(S));
@@ -812,7 +882,7 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   }
   const int iters = converged ? k + 1 : sd->k_max + 1;
   // 4. post-convergence coarse update (Sec. 3.5)
-  DISPATCH(B, K::g2p(B->P, gB, B->u, dT, s));
+  DISPATCH(B, K::g2p(P_, gB, B->u, dT, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   CUDA_TRY(cudaGetLastError());
 #undef S_TRY
@@ -856,7 +926,7 @@ osmpm_status osmpm_check_wait_timeout(void* cuda_stream) {
   CUDA_TRY(cudaMemsetAsync(mem, 0, 64, s));
   unsigned* words = (unsigned*)mem;
   int* err = (int*)((char*)mem + 32);
-  Kernels<2>::barrier_timeout_check(words, err, s);
+  Kernels<2, double>::barrier_timeout_check(words, err, s);
   int host_err = 0;
   cudaError_t e = cudaMemcpyAsync(&host_err, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -884,7 +954,7 @@ osmpm_status osmpm_get_particles(const osmpm_domain* dc, double* x, double* v, d
   double* sv = sx + D * n;
   double* sB = sv + D * n;
   double* sF = sB + D * D * n;
-  DISPATCH(d, K::pack_out(d->P, sx, sv, sB, sF, d->stream));
+  DISPATCH(d, K::pack_out(P_, sx, sv, sB, sF, d->stream));
   if (x) CUDA_TRY(cudaMemcpyAsync(x, sx, sizeof(double) * D * n, cudaMemcpyDeviceToHost, d->stream));
   if (v) CUDA_TRY(cudaMemcpyAsync(v, sv, sizeof(double) * D * n, cudaMemcpyDeviceToHost, d->stream));
   if (B) CUDA_TRY(cudaMemcpyAsync(B, sB, sizeof(double) * D * D * n, cudaMemcpyDeviceToHost, d->stream));
@@ -902,7 +972,7 @@ osmpm_status osmpm_set_particles(osmpm_domain* d, const double* x, const double*
   if (!finite_all(x, D * n) || !finite_all(v, D * n) || !finite_all(B, D * D * n) || !finite_all(F, D * D * n))
     return fail(OSMPM_E_NONFINITE, "non-finite particle input");
   // materials and ids back to id order in A, then the new kinematic state
-  DISPATCH(d, K::scatter_by_id(d->P, d->A, d->stream));
+  DISPATCH(d, K::scatter_by_id(P_, A_, d->stream));
   OSMPM_TRY(upload_state(d, x, v, B, F));
   CUDA_TRY(cudaMemsetAsync(d->err, 0, sizeof(int), d->stream));
   return sort_into_primary(d);
@@ -953,7 +1023,7 @@ osmpm_status osmpm_probe_gradient(osmpm_domain* d, double dt, const double* u, d
   const int D = d->dim;
   CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
-  DISPATCH(d, K::grad(d->P, d->geo, d->u, d->dofmask, d->grad, d->diag, d->L, d->err, d->stream));
+  DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
                              d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
                              d->cz, d->cp, d->S, d->partials, d->stream));
@@ -970,10 +1040,10 @@ osmpm_status osmpm_probe_hvp(osmpm_domain* d, double dt, const double* u, const 
   const int D = d->dim;
   CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
-  DISPATCH(d, K::grad(d->P, d->geo, d->u, d->dofmask, d->grad, d->diag, d->L, d->err, d->stream));
+  DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
   OSMPM_TRY(upload_grid_vec(d, dv, d->cp));
   DISPATCH(d, K::set_cg_state(d->S, 0, 0, d->stream));
-  DISPATCH(d, K::hvp_only(d->P, d->geo, d->m, d->dofmask, d->L, dt, d->cp, d->cq, d->S,
+  DISPATCH(d, K::hvp_only(P_, d->geo, d->m, d->dofmask, L_, dt, d->cp, d->cq, d->S,
                           d->partials, d->stream));
   OSMPM_TRY(sync_scalars(d));
   OSMPM_TRY(check_err(d));
@@ -986,7 +1056,7 @@ osmpm_status osmpm_probe_energy_change(osmpm_domain* d, double dt, const double*
   if (!u || !dv || !dE) return fail(OSMPM_E_INVALID, "null array");
   OSMPM_TRY(probe_setup(d, dt, u));
   OSMPM_TRY(upload_grid_vec(d, dv, d->cx));
-  DISPATCH(d, K::energy_change(d->P, d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt, alpha,
+  DISPATCH(d, K::energy_change(P_, d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt, alpha,
                                d->S, d->partials, d->stream));
   OSMPM_TRY(sync_scalars(d));
   *dE = d->S_host->dE;

@@ -39,28 +39,28 @@ struct PrepArgs {
   uint8_t* physmask;    // 1 where a physical rule fixes a component (written), may be null
 };
 
-template <int D>
+template <int D, typename R>
 struct Kernels {
   static void morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,
                           uint32_t* vals, int* err, cudaStream_t s);
-  static void permute(const PartPtrs& src, const PartPtrs& dst, const uint32_t* perm,
+  static void permute(const PartPtrsT<R>& src, const PartPtrsT<R>& dst, const uint32_t* perm,
                       cudaStream_t s);
-  static void scatter_by_id(const PartPtrs& src, const PartPtrs& dst, cudaStream_t s);
-  static void lame(const double* E, const double* nu, PartPtrs P, cudaStream_t s);
-  static void pack_out(const PartPtrs& P, double* x, double* v, double* B, double* F,
+  static void scatter_by_id(const PartPtrsT<R>& src, const PartPtrsT<R>& dst, cudaStream_t s);
+  static void lame(const double* E, const double* nu, PartPtrsT<R> P, cudaStream_t s);
+  static void pack_out(const PartPtrsT<R>& P, double* x, double* v, double* B, double* F,
                        cudaStream_t s);
   static void unpack_in(const double* x, const double* v, const double* B, const double* F,
-                        PartPtrs dst, cudaStream_t s);
+                        PartPtrsT<R> dst, cudaStream_t s);
   // P2G; with sbase/sdn also caches each particle's stencil (base node and
   // grad N) for the PCG of the step
-  static void p2g(const PartPtrs& P, const GridGeo& g, double* m, double* mv, double* bm,
-                  int* err, int* sbase, double* sdn, cudaStream_t s);
+  static void p2g(const PartPtrsT<R>& P, const GridGeo& g, double* m, double* mv, double* bm,
+                  int* err, int* sbase, R* sdn, cudaStream_t s);
   static void normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
                         cudaStream_t s);
   static void grid_prep(const GridGeo& g, const double* m, const double* vn, const PrepArgs& a,
                         double dt, uint8_t* dofmask, double* u, cudaStream_t s);
-  static void grad(const PartPtrs& P, const GridGeo& g, const double* u, const uint8_t* dofmask,
-                   double* grad, double* diag, double* L, int* err, cudaStream_t s);
+  static void grad(const PartPtrsT<R>& P, const GridGeo& g, const double* u, const uint8_t* dofmask,
+                   double* grad, double* diag, R* L, int* err, cudaStream_t s);
   static void grad_finish(const GridGeo& g, const double* m, const double* vn, const double* u,
                           const uint8_t* dofmask, const double* gravity, double dt, double cg_rtol,
                           int cg_max, double* grad, double* diag, double* x, double* r, double* z,
@@ -69,32 +69,32 @@ struct Kernels {
   static void cg_a(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
                    const double* z, double* p, double* q, DevScalars* S, double* partials,
                    cudaStream_t s);
-  static void cg_b(const PartPtrs& P, const GridGeo& g, const uint8_t* dofmask, const double* L,
+  static void cg_b(const PartPtrsT<R>& P, const GridGeo& g, const uint8_t* dofmask, const R* L,
                    const double* p, double* q, DevScalars* S, double* partials, cudaStream_t s);
   static void cg_c(const GridGeo& g, const uint8_t* dofmask, const double* diag,
                    const double* p, const double* q, double* x, double* r, double* z,
                    DevScalars* S, double* partials, cudaStream_t s);
   // persistent cooperative PCG (whole solve in one launch)
   static void pcg_shape(int64_t work, int* blocks, int* threads);
-  static cudaError_t pcg(const PcgArgs& a, int blocks, int threads, cudaStream_t s);
-  static void hvp_only(const PartPtrs& P, const GridGeo& g, const double* m,
-                       const uint8_t* dofmask, const double* L, double dt, double* p, double* q,
+  static cudaError_t pcg(const PcgArgsT<R>& a, int blocks, int threads, cudaStream_t s);
+  static void hvp_only(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
+                       const uint8_t* dofmask, const R* L, double dt, double* p, double* q,
                        DevScalars* S, double* partials, cudaStream_t s);
   static void maxabs(const GridGeo& g, const uint8_t* dofmask, const double* x, DevScalars* S,
                      double* partials, cudaStream_t s);
-  static void energy_change(const PartPtrs& P, const GridGeo& g, const double* m,
+  static void energy_change(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
                             const double* vn, const double* u, const double* x,
                             const double* gravity, double dt, double alpha, DevScalars* S,
                             double* partials, cudaStream_t s);
   // same kernel with an explicit block count (one block per 256 work items)
-  static void energy_change_blocks(const PartPtrs& P, const GridGeo& g, const double* m,
+  static void energy_change_blocks(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
                                    const double* vn, const double* u, const double* x,
                                    const double* gravity, double dt, double alpha, DevScalars* S,
                                    double* partials, int blocks, cudaStream_t s);
   static void warm_start(const GridGeo& g, const uint8_t* dofmask, const double* src, double* u,
                          cudaStream_t s);
   static void axpy(const GridGeo& g, double* u, const double* x, double alpha, cudaStream_t s);
-  static void g2p(const PartPtrs& P, const GridGeo& g, const double* u, double dt,
+  static void g2p(const PartPtrsT<R>& P, const GridGeo& g, const double* u, double dt,
                   cudaStream_t s);
   // Schwarz interface operators (Sec. 3.2)
   static void gamma(const GridGeo& g, const double* m, const double* bm, double tau,

@@ -22,13 +22,13 @@ __device__ __forceinline__ int64_t gtid() {
 }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
-template <int D>
-__device__ __forceinline__ void load_x(const PartPtrs& P, int64_t p, double* x) {
+template <int D, class PP>
+__device__ __forceinline__ void load_x(const PP& P, int64_t p, double* x) {
 #pragma unroll
   for (int a = 0; a < D; ++a) x[a] = P.x[a * P.n + p];
 }
-template <int D>
-__device__ __forceinline__ void load_F(const PartPtrs& P, int64_t p, double* F) {
+template <int D, class PP>
+__device__ __forceinline__ void load_F(const PP& P, int64_t p, double* F) {
 #pragma unroll
   for (int e = 0; e < D * D; ++e) F[e] = P.F[e * P.n + p];
 }
@@ -69,7 +69,7 @@ __device__ __forceinline__ void gather_grad(const Stencil<D>& s, const GridGeo& 
 // ---------------------------------------------------------------------------
 // Particle bookkeeping
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, typename R>
 __global__ void k_morton_keys(const double* x, int64_t n, GridGeo g, uint64_t* keys,
                               uint32_t* vals, int* err) {
   const int64_t p = gtid();
@@ -91,8 +91,8 @@ __global__ void k_morton_keys(const double* x, int64_t n, GridGeo g, uint64_t* k
   vals[p] = (uint32_t)p;
 }
 
-template <int D>
-__global__ void k_permute(PartPtrs src, PartPtrs dst, const uint32_t* perm) {
+template <int D, typename R>
+__global__ void k_permute(PartPtrsT<R> src, PartPtrsT<R> dst, const uint32_t* perm) {
   const int64_t s = gtid();
   const int64_t n = src.n;
   if (s >= n) return;
@@ -115,8 +115,8 @@ __global__ void k_permute(PartPtrs src, PartPtrs dst, const uint32_t* perm) {
   dst.id[s] = src.id[q];
 }
 
-template <int D>
-__global__ void k_scatter_by_id(PartPtrs src, PartPtrs dst) {
+template <int D, typename R>
+__global__ void k_scatter_by_id(PartPtrsT<R> src, PartPtrsT<R> dst) {
   const int64_t s = gtid();
   const int64_t n = src.n;
   if (s >= n) return;
@@ -139,8 +139,8 @@ __global__ void k_scatter_by_id(PartPtrs src, PartPtrs dst) {
   dst.id[q] = (uint32_t)q;
 }
 
-template <int D>
-__global__ void k_lame(const double* E, const double* nu, PartPtrs P) {
+template <int D, typename R>
+__global__ void k_lame(const double* E, const double* nu, PartPtrsT<R> P) {
   const int64_t p = gtid();
   if (p >= P.n) return;
   const double e = E[p], v = nu[p];
@@ -149,8 +149,8 @@ __global__ void k_lame(const double* E, const double* nu, PartPtrs P) {
 }
 
 // Sorted component-major state -> id-ordered particle-major host layout.
-template <int D>
-__global__ void k_pack_out(PartPtrs P, double* x, double* v, double* B, double* F) {
+template <int D, typename R>
+__global__ void k_pack_out(PartPtrsT<R> P, double* x, double* v, double* B, double* F) {
   const int64_t s = gtid();
   const int64_t n = P.n;
   if (s >= n) return;
@@ -167,21 +167,21 @@ __global__ void k_pack_out(PartPtrs P, double* x, double* v, double* B, double* 
   }
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_unpack_in(const double* x, const double* v, const double* B, const double* F,
-                            PartPtrs dst) {
+                            PartPtrsT<R> dst) {
   const int64_t q = gtid();
   const int64_t n = dst.n;
   if (q >= n) return;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     dst.x[a * n + q] = x[q * D + a];
-    dst.v[a * n + q] = v[q * D + a];
+    dst.v[a * n + q] = (R)v[q * D + a];
   }
 #pragma unroll
   for (int e = 0; e < D * D; ++e) {
-    dst.B[e * n + q] = B[q * D * D + e];
-    dst.F[e * n + q] = F[q * D * D + e];
+    dst.B[e * n + q] = (R)B[q * D * D + e];
+    dst.F[e * n + q] = (R)F[q * D * D + e];
   }
 }
 
@@ -189,9 +189,9 @@ __global__ void k_unpack_in(const double* x, const double* v, const double* B, c
 // APIC particle-to-grid transfer (Eq. p2g_transfer, Eq. p2g_substep); with
 // bm != nullptr also the boundary-particle mass of Eq. boundary_grid_set.
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_p2g(PartPtrs P, GridGeo g, double* m, double* mv,
-                                                  double* bm, int* err, int* sbase, double* sdn) {
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_p2g(PartPtrsT<R> P, GridGeo g, double* m, double* mv,
+                                                  double* bm, int* err, int* sbase, R* sdn) {
   const int64_t p = gtid();
   if (p >= P.n) return;
   double xp[D], vp[D], Bp[D * D];
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kThreads) k_p2g(PartPtrs P, GridGeo g, double*
     const int64_t node = stencil_node<D>(s, g, k, N, dN);
     if (sdn)
 #pragma unroll
-      for (int a = 0; a < D; ++a) sdn[(int64_t)(a * Pow3<D>::K + k) * P.n + p] = dN[a];
+      for (int a = 0; a < D; ++a) sdn[(int64_t)(a * Pow3<D>::K + k) * P.n + p] = (R)dN[a];
     double r[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) r[a] = stencil_node_pos<D>(s, g, k, a) - xp[a];
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_p2g(PartPtrs P, GridGeo g, double*
   }
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_normalize(GridGeo g, const double* m, const double* mv, double* vn) {
   for (int64_t i = gtid(); i < g.nn; i += gstride()) {
     const double mi = m[i];
@@ -254,7 +254,7 @@ __global__ void k_normalize(GridGeo g, const double* m, const double* mv, double
 // with temporally interpolated values, Eq. temporal_interp), the free-DOF
 // mask and the initial guess x_hat^(0) = x^n + dt v^n on free DOFs.
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, typename R>
 __global__ void k_grid_prep(GridGeo g, const double* m, const double* vn, PrepArgs A, double dt,
                             uint8_t* dofmask, double* u) {
   const unsigned all = (1u << D) - 1u;
@@ -268,27 +268,27 @@ __global__ void k_grid_prep(GridGeo g, const double* m, const double* vn, PrepAr
 #pragma unroll
     for (int a = 0; a < D; ++a) vel[a] = 0.0;
     for (int r = 0; r < A.n_rules; ++r) {
-      const DevRule& R = A.rules[r];
+      const DevRule& rule = A.rules[r];
       bool in = true;
 #pragma unroll
-      for (int a = 0; a < D; ++a) in = in && (xi[a] >= R.lo[a]) && (xi[a] <= R.hi[a]);
+      for (int a = 0; a < D; ++a) in = in && (xi[a] >= rule.lo[a]) && (xi[a] <= rule.hi[a]);
       if (!in) continue;
-      if (R.kind == 0) {
+      if (rule.kind == 0) {
 #pragma unroll
         for (int a = 0; a < D; ++a)
-          if ((R.comp_mask >> a) & 1u) {
+          if ((rule.comp_mask >> a) & 1u) {
             fixed |= 1u << a;
-            vel[a] = R.vel[a];
+            vel[a] = rule.vel[a];
           }
       } else {
         double rel[D];
 #pragma unroll
-        for (int a = 0; a < D; ++a) rel[a] = xi[a] - R.center[a];
+        for (int a = 0; a < D; ++a) rel[a] = xi[a] - rule.center[a];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           double t = 0.0;
 #pragma unroll
-          for (int b = 0; b < D; ++b) t += R.R[a * 3 + b] * rel[b];
+          for (int b = 0; b < D; ++b) t += rule.R[a * 3 + b] * rel[b];
           vel[a] = (t - rel[a]) / dt;
         }
         fixed = all;
@@ -319,10 +319,10 @@ __global__ void k_grid_prep(GridGeo g, const double* m, const double* vn, PrepAr
 // Hessian block L(G) = V0 dP[G F^n] F^nT used by every HVP of the Newton
 // iteration (K = Hessian of sum_p V0 Psi(F_p(u)), Sec. 2.2.5).
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_grad(PartPtrs P, GridGeo g, const double* u,
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_grad(PartPtrsT<R> P, GridGeo g, const double* u,
                                                    const uint8_t* dofmask, double* grad,
-                                                   double* diag, double* L, int* err) {
+                                                   double* diag, R* L, int* err) {
   constexpr int DD = D * D;
   const int64_t p = gtid();
   if (p >= P.n) return;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(PartPtrs P, GridGeo g, const 
   for (int i = 0; i < DD; ++i)
 #pragma unroll
     for (int j = i; j < DD; ++j)
-      L[(int64_t)Sym<D>::idx(i, j) * P.n + p] = 0.5 * (Lfull[i * DD + j] + Lfull[j * DD + i]);
+      L[(int64_t)Sym<D>::idx(i, j) * P.n + p] = (R)(0.5 * (Lfull[i * DD + j] + Lfull[j * DD + i]));
   // scatter gradient and diagonal
 #pragma unroll 3
   for (int k = 0; k < Pow3<D>::K; ++k) {
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(PartPtrs P, GridGeo g, const 
 // Completes the gradient on the free DOFs (inertia and external force),
 // adds m/dt^2 to the diagonal and stores its inverse, and starts PCG from
 // x = 0: r = -g, z = D^-1 r, p = z; reduces r.z and r.r.
-template <int D>
+template <int D, typename R>
 __global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, const double* u,
                               const uint8_t* dofmask, double gx, double gy, double gz, double dt,
                               double cg_rtol, int cg_max, double* grad, double* diag, double* x,
@@ -459,7 +459,7 @@ __global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, cons
 
 // PCG step A: p = z + beta p (after the first iteration); q = (m/dt^2) p on
 // free DOFs; reduces the diagonal part of p.Hp.
-template <int D>
+template <int D, typename R>
 __global__ void k_cg_a(GridGeo g, const double* m, const uint8_t* dofmask, double inv_dt2,
                        const double* z, double* p, double* q, DevScalars* S, double* partials) {
   if (*((volatile int*)&S->cg_done)) return;
@@ -490,9 +490,9 @@ __global__ void k_cg_a(GridGeo g, const double* m, const uint8_t* dofmask, doubl
 // PCG step B: the matrix-free Hessian-vector product, a particle gather of
 // p (G = sum_j p_j grad N_j^T), Y = L G, scatter q_i += Y grad N_i, and the
 // particle part of p.Hp = sum_p G : L G.  The last block forms alpha.
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_cg_b(PartPtrs P, GridGeo g, const uint8_t* dofmask,
-                                                   const double* L, const double* p, double* q,
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_cg_b(PartPtrsT<R> P, GridGeo g, const uint8_t* dofmask,
+                                                   const R* L, const double* p, double* q,
                                                    DevScalars* S, double* partials) {
   constexpr int DD = D * D;
   if (*((volatile int*)&S->cg_done)) return;
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_b(PartPtrs P, GridGeo g, const 
     for (int i = 0; i < DD; ++i) {
       double t = 0.0;
 #pragma unroll
-      for (int j = 0; j < DD; ++j) t += L[(int64_t)Sym<D>::idx(i, j) * P.n + pi] * G[j];
+      for (int j = 0; j < DD; ++j) t += (double)L[(int64_t)Sym<D>::idx(i, j) * P.n + pi] * G[j];
       Y[i] = t;
     }
     double qf = 0.0;
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_b(PartPtrs P, GridGeo g, const 
 
 // PCG step C: x += alpha p, r -= alpha q, z = r/diag; the last block forms
 // beta and the stopping test |r| <= rtol |r0| or the iteration cap.
-template <int D>
+template <int D, typename R>
 __global__ void k_cg_c(GridGeo g, const uint8_t* dofmask, const double* diag, const double* p,
                        const double* q, double* x, double* r, double* z, DevScalars* S,
                        double* partials) {
@@ -578,20 +578,20 @@ __global__ void k_cg_c(GridGeo g, const uint8_t* dofmask, const double* diag, co
   }
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_copy_if_neg(GridGeo g, const double* p, double* x, const DevScalars* S) {
   if (!(S->cg_neg && S->cg_iter == 0)) return;
   for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) x[idx] = p[idx];
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_set_cg_state(DevScalars* S, int iter, int done) {
   S->cg_iter = iter;
   S->cg_done = done;
   S->cg_neg = 0;
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_maxabs(GridGeo g, const uint8_t* dofmask, const double* x, DevScalars* S,
                          double* partials) {
   double v = 0.0;
@@ -608,8 +608,8 @@ __global__ void k_maxabs(GridGeo g, const uint8_t* dofmask, const double* x, Dev
 // Sec. 2.2.5): per particle V0 (Psi(F(u + alpha x)) - Psi(F(u))), per node
 // m/(2dt^2) s.(2(u - dt v^n) + s) - s.f_ext with s = alpha x.  +inf when a
 // trial inverts an element.
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrs P, GridGeo g, const double* m,
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrsT<R> P, GridGeo g, const double* m,
                                                             const double* vn, const double* u,
                                                             const double* x, double gx, double gy,
                                                             double gz, double dt, double alpha,
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrs P, GridGeo 
 
 // Warm start: free DOFs take a previous solution, fixed DOFs keep the
 // prepared Dirichlet values.
-template <int D>
+template <int D, typename R>
 __global__ void k_warm_start(GridGeo g, const uint8_t* dofmask, const double* src, double* u) {
   for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
     const int a = (int)(idx / g.nn);
@@ -667,7 +667,7 @@ __global__ void k_warm_start(GridGeo g, const uint8_t* dofmask, const double* sr
   }
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_axpy(GridGeo g, double* u, const double* x, double alpha) {
   for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) u[idx] += alpha * x[idx];
 }
@@ -676,8 +676,8 @@ __global__ void k_axpy(GridGeo g, double* u, const double* x, double alpha) {
 // APIC grid-to-particle transfer with v_i = u_i/dt (Eqs. g2p_v, g2p_B), the
 // F update (Eq. F_update) and advection (Eq. advection).
 // ---------------------------------------------------------------------------
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_g2p(PartPtrs P, GridGeo g, const double* u,
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_g2p(PartPtrsT<R> P, GridGeo g, const double* u,
                                                   double dt) {
   constexpr int DD = D * D;
   const int64_t p = gtid();
@@ -717,20 +717,20 @@ __global__ void __launch_bounds__(kThreads) k_g2p(PartPtrs P, GridGeo g, const d
   deform<D>(G, Fn, F);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    P.v[a * P.n + p] = vnew[a];
+    P.v[a * P.n + p] = (R)vnew[a];
     P.x[a * P.n + p] = xp[a] + dt * vnew[a];
   }
 #pragma unroll
   for (int e = 0; e < DD; ++e) {
-    P.B[e * P.n + p] = Bnew[e];
-    P.F[e * P.n + p] = F[e];
+    P.B[e * P.n + p] = (R)Bnew[e];
+    P.F[e * P.n + p] = (R)F[e];
   }
 }
 
 // ---------------------------------------------------------------------------
 // Schwarz interface operators (Sec. 3.2)
 // ---------------------------------------------------------------------------
-template <int D>
+template <int D, typename R>
 __global__ void k_gamma(int64_t nn, double mass_eps, const double* m, const double* bm, double tau,
                         uint8_t* gam) {
   for (int64_t i = gtid(); i < nn; i += gstride())
@@ -739,7 +739,7 @@ __global__ void k_gamma(int64_t nn, double mass_eps, const double* m, const doub
 
 // Eq. overlap_donor on coincident boundary nodes (|x_B - x_S|_inf <= 1e-9
 // dx_S): the larger grid mass donates, ties (within 1e-12 relative) to B.
-template <int D>
+template <int D, typename R>
 __global__ void k_arbitrate(GridGeo gB, GridGeo gS, const uint8_t* gamB, const uint8_t* gamS,
                             const double* mB, const double* mS, uint8_t* recvB, uint8_t* recvS) {
   for (int64_t I = gtid(); I < gB.nn; I += gstride()) {
@@ -766,7 +766,7 @@ __global__ void k_arbitrate(GridGeo gB, GridGeo gS, const uint8_t* gamB, const u
 
 // Numerator and denominator of Eq. spatial_projection: every active fine
 // node j scatters m_Sj N_BI(x_Sj) (times v_Sj) to its coarse support.
-template <int D>
+template <int D, typename R>
 __global__ void k_proj_scatter(GridGeo gB, GridGeo gS, const double* mS, const double* vS,
                                double* num, double* den) {
   for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
@@ -812,7 +812,7 @@ __global__ void k_proj_scatter(GridGeo gB, GridGeo gS, const double* mS, const d
   }
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_recvB_filter(int64_t nn, const double* den, double tau, const uint8_t* physB,
                                uint8_t* recvB) {
   for (int64_t I = gtid(); I < nn; I += gstride())
@@ -821,7 +821,7 @@ __global__ void k_recvB_filter(int64_t nn, const double* den, double tau, const 
 
 // Gamma_hat_S keeps fine nodes whose coarse support lies in the box and is
 // all active; no receiver carries a physical rule.
-template <int D>
+template <int D, typename R>
 __global__ void k_recvS_filter(GridGeo gB, GridGeo gS, const double* mB, const uint8_t* physS,
                                uint8_t* recvS) {
   for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
@@ -854,7 +854,7 @@ __global__ void k_recvS_filter(GridGeo gB, GridGeo gS, const double* mB, const u
   }
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_proj_finish(GridGeo gB, const uint8_t* recvB, const double* num,
                               const double* den, double eps_tol, double* out) {
   for (int64_t I = gtid(); I < gB.nn; I += gstride()) {
@@ -866,7 +866,7 @@ __global__ void k_proj_finish(GridGeo gB, const uint8_t* recvB, const double* nu
 }
 
 // I_{B->S} of Eq. interp_BtoS on the fine receivers.
-template <int D>
+template <int D, typename R>
 __global__ void k_interp(GridGeo gB, GridGeo gS, const double* vB, const uint8_t* recvS,
                          double* out) {
   for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
@@ -891,7 +891,7 @@ __global__ void k_interp(GridGeo gB, GridGeo gS, const double* vB, const uint8_t
   }
 }
 
-template <int D>
+template <int D, typename R>
 __global__ void k_vel_from_u(GridGeo g, const double* m, const double* u, double dt, double* v) {
   for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
     const int64_t i = idx % g.nn;
@@ -901,7 +901,7 @@ __global__ void k_vel_from_u(GridGeo g, const double* m, const double* u, double
 
 // Sums of |new - old|^2 and |new|^2 over a receiver set (Eq.
 // convergence_residuals), written to slot `slot` of the scalars.
-template <int D>
+template <int D, typename R>
 __global__ void k_rel_change(GridGeo g, const double* vnew, const double* vold,
                              const uint8_t* recv, int slot, DevScalars* S, double* partials) {
   double acc[2] = {0.0, 0.0};
@@ -925,191 +925,191 @@ __global__ void k_rel_change(GridGeo g, const double* vnew, const double* vold,
 #define OSMPM_NB(n) (g_launch_count += 1, blocks_for(n)), kThreads, 0, s
 #define OSMPM_RB(n) (g_launch_count += 1, red_blocks_for(n)), kThreads, 0, s
 
-template <int D>
-void Kernels<D>::morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,
+template <int D, typename R>
+void Kernels<D, R>::morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,
                              uint32_t* vals, int* err, cudaStream_t s) {
-  k_morton_keys<D><<<OSMPM_NB(n)>>>(x, n, g, keys, vals, err);
+  k_morton_keys<D, R><<<OSMPM_NB(n)>>>(x, n, g, keys, vals, err);
 }
-template <int D>
-void Kernels<D>::permute(const PartPtrs& src, const PartPtrs& dst, const uint32_t* perm,
+template <int D, typename R>
+void Kernels<D, R>::permute(const PartPtrsT<R>& src, const PartPtrsT<R>& dst, const uint32_t* perm,
                          cudaStream_t s) {
-  k_permute<D><<<OSMPM_NB(src.n)>>>(src, dst, perm);
+  k_permute<D, R><<<OSMPM_NB(src.n)>>>(src, dst, perm);
 }
-template <int D>
-void Kernels<D>::scatter_by_id(const PartPtrs& src, const PartPtrs& dst, cudaStream_t s) {
-  k_scatter_by_id<D><<<OSMPM_NB(src.n)>>>(src, dst);
+template <int D, typename R>
+void Kernels<D, R>::scatter_by_id(const PartPtrsT<R>& src, const PartPtrsT<R>& dst, cudaStream_t s) {
+  k_scatter_by_id<D, R><<<OSMPM_NB(src.n)>>>(src, dst);
 }
-template <int D>
-void Kernels<D>::lame(const double* E, const double* nu, PartPtrs P, cudaStream_t s) {
-  k_lame<D><<<OSMPM_NB(P.n)>>>(E, nu, P);
+template <int D, typename R>
+void Kernels<D, R>::lame(const double* E, const double* nu, PartPtrsT<R> P, cudaStream_t s) {
+  k_lame<D, R><<<OSMPM_NB(P.n)>>>(E, nu, P);
 }
-template <int D>
-void Kernels<D>::pack_out(const PartPtrs& P, double* x, double* v, double* B, double* F,
+template <int D, typename R>
+void Kernels<D, R>::pack_out(const PartPtrsT<R>& P, double* x, double* v, double* B, double* F,
                           cudaStream_t s) {
-  k_pack_out<D><<<OSMPM_NB(P.n)>>>(P, x, v, B, F);
+  k_pack_out<D, R><<<OSMPM_NB(P.n)>>>(P, x, v, B, F);
 }
-template <int D>
-void Kernels<D>::unpack_in(const double* x, const double* v, const double* B, const double* F,
-                           PartPtrs dst, cudaStream_t s) {
-  k_unpack_in<D><<<OSMPM_NB(dst.n)>>>(x, v, B, F, dst);
+template <int D, typename R>
+void Kernels<D, R>::unpack_in(const double* x, const double* v, const double* B, const double* F,
+                           PartPtrsT<R> dst, cudaStream_t s) {
+  k_unpack_in<D, R><<<OSMPM_NB(dst.n)>>>(x, v, B, F, dst);
 }
-template <int D>
-void Kernels<D>::p2g(const PartPtrs& P, const GridGeo& g, double* m, double* mv, double* bm,
-                     int* err, int* sbase, double* sdn, cudaStream_t s) {
-  k_p2g<D><<<OSMPM_NB(P.n)>>>(P, g, m, mv, bm, err, sbase, sdn);
+template <int D, typename R>
+void Kernels<D, R>::p2g(const PartPtrsT<R>& P, const GridGeo& g, double* m, double* mv, double* bm,
+                     int* err, int* sbase, R* sdn, cudaStream_t s) {
+  k_p2g<D, R><<<OSMPM_NB(P.n)>>>(P, g, m, mv, bm, err, sbase, sdn);
 }
-template <int D>
-void Kernels<D>::normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
+template <int D, typename R>
+void Kernels<D, R>::normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
                            cudaStream_t s) {
-  k_normalize<D><<<OSMPM_RB(g.nn)>>>(g, m, mv, vn);
+  k_normalize<D, R><<<OSMPM_RB(g.nn)>>>(g, m, mv, vn);
 }
-template <int D>
-void Kernels<D>::grid_prep(const GridGeo& g, const double* m, const double* vn,
+template <int D, typename R>
+void Kernels<D, R>::grid_prep(const GridGeo& g, const double* m, const double* vn,
                            const PrepArgs& a, double dt, uint8_t* dofmask, double* u,
                            cudaStream_t s) {
-  k_grid_prep<D><<<OSMPM_RB(g.nn)>>>(g, m, vn, a, dt, dofmask, u);
+  k_grid_prep<D, R><<<OSMPM_RB(g.nn)>>>(g, m, vn, a, dt, dofmask, u);
 }
-template <int D>
-void Kernels<D>::grad(const PartPtrs& P, const GridGeo& g, const double* u,
-                      const uint8_t* dofmask, double* grad, double* diag, double* L, int* err,
+template <int D, typename R>
+void Kernels<D, R>::grad(const PartPtrsT<R>& P, const GridGeo& g, const double* u,
+                      const uint8_t* dofmask, double* grad, double* diag, R* L, int* err,
                       cudaStream_t s) {
-  k_grad<D><<<OSMPM_NB(P.n)>>>(P, g, u, dofmask, grad, diag, L, err);
+  k_grad<D, R><<<OSMPM_NB(P.n)>>>(P, g, u, dofmask, grad, diag, L, err);
 }
-template <int D>
-void Kernels<D>::grad_finish(const GridGeo& g, const double* m, const double* vn,
+template <int D, typename R>
+void Kernels<D, R>::grad_finish(const GridGeo& g, const double* m, const double* vn,
                              const double* u, const uint8_t* dofmask, const double* gravity,
                              double dt, double cg_rtol, int cg_max, double* grad, double* diag,
                              double* x, double* r, double* z, double* p, DevScalars* S,
                              double* partials, cudaStream_t s) {
-  k_grad_finish<D><<<OSMPM_RB(g.nn * D)>>>(g, m, vn, u, dofmask, gravity[0], gravity[1],
+  k_grad_finish<D, R><<<OSMPM_RB(g.nn * D)>>>(g, m, vn, u, dofmask, gravity[0], gravity[1],
                                            gravity[2], dt, cg_rtol, cg_max, grad, diag, x, r, z,
                                            p, S, partials);
 }
-template <int D>
-void Kernels<D>::cg_a(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
+template <int D, typename R>
+void Kernels<D, R>::cg_a(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
                       const double* z, double* p, double* q, DevScalars* S, double* partials,
                       cudaStream_t s) {
-  k_cg_a<D><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, 1.0 / (dt * dt), z, p, q, S, partials);
+  k_cg_a<D, R><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, 1.0 / (dt * dt), z, p, q, S, partials);
 }
-template <int D>
-void Kernels<D>::cg_b(const PartPtrs& P, const GridGeo& g, const uint8_t* dofmask,
-                      const double* L, const double* p, double* q, DevScalars* S,
+template <int D, typename R>
+void Kernels<D, R>::cg_b(const PartPtrsT<R>& P, const GridGeo& g, const uint8_t* dofmask,
+                      const R* L, const double* p, double* q, DevScalars* S,
                       double* partials, cudaStream_t s) {
-  k_cg_b<D><<<OSMPM_RB(P.n)>>>(P, g, dofmask, L, p, q, S, partials);
+  k_cg_b<D, R><<<OSMPM_RB(P.n)>>>(P, g, dofmask, L, p, q, S, partials);
 }
-template <int D>
-void Kernels<D>::cg_c(const GridGeo& g, const uint8_t* dofmask, const double* diag,
+template <int D, typename R>
+void Kernels<D, R>::cg_c(const GridGeo& g, const uint8_t* dofmask, const double* diag,
                       const double* p, const double* q, double* x, double* r, double* z,
                       DevScalars* S, double* partials, cudaStream_t s) {
-  k_cg_c<D><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, diag, p, q, x, r, z, S, partials);
+  k_cg_c<D, R><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, diag, p, q, x, r, z, S, partials);
 }
-template <int D>
-void Kernels<D>::hvp_only(const PartPtrs& P, const GridGeo& g, const double* m,
-                          const uint8_t* dofmask, const double* L, double dt, double* p,
+template <int D, typename R>
+void Kernels<D, R>::hvp_only(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
+                          const uint8_t* dofmask, const R* L, double dt, double* p,
                           double* q, DevScalars* S, double* partials, cudaStream_t s) {
   const double inv_dt2 = 1.0 / (dt * dt);
-  k_cg_a<D><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, inv_dt2, p, p, q, S, partials);
-  k_cg_b<D><<<OSMPM_RB(P.n)>>>(P, g, dofmask, L, p, q, S, partials);
+  k_cg_a<D, R><<<OSMPM_RB(g.nn * D)>>>(g, m, dofmask, inv_dt2, p, p, q, S, partials);
+  k_cg_b<D, R><<<OSMPM_RB(P.n)>>>(P, g, dofmask, L, p, q, S, partials);
 }
-template <int D>
-void Kernels<D>::maxabs(const GridGeo& g, const uint8_t* dofmask, const double* x,
+template <int D, typename R>
+void Kernels<D, R>::maxabs(const GridGeo& g, const uint8_t* dofmask, const double* x,
                         DevScalars* S, double* partials, cudaStream_t s) {
-  k_maxabs<D><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, x, S, partials);
+  k_maxabs<D, R><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, x, S, partials);
 }
-template <int D>
-void Kernels<D>::energy_change(const PartPtrs& P, const GridGeo& g, const double* m,
+template <int D, typename R>
+void Kernels<D, R>::energy_change(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
                                const double* vn, const double* u, const double* x,
                                const double* gravity, double dt, double alpha, DevScalars* S,
                                double* partials, cudaStream_t s) {
   const int64_t work = P.n > g.nn * D ? P.n : g.nn * D;
-  k_energy_change<D><<<OSMPM_RB(work)>>>(P, g, m, vn, u, x, gravity[0], gravity[1], gravity[2],
+  k_energy_change<D, R><<<OSMPM_RB(work)>>>(P, g, m, vn, u, x, gravity[0], gravity[1], gravity[2],
                                          dt, alpha, S, partials);
 }
-template <int D>
-void Kernels<D>::energy_change_blocks(const PartPtrs& P, const GridGeo& g, const double* m,
+template <int D, typename R>
+void Kernels<D, R>::energy_change_blocks(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
                                       const double* vn, const double* u, const double* x,
                                       const double* gravity, double dt, double alpha,
                                       DevScalars* S, double* partials, int blocks,
                                       cudaStream_t s) {
   g_launch_count += 1;
-  k_energy_change<D><<<blocks, kThreads, 0, s>>>(P, g, m, vn, u, x, gravity[0], gravity[1],
+  k_energy_change<D, R><<<blocks, kThreads, 0, s>>>(P, g, m, vn, u, x, gravity[0], gravity[1],
                                                 gravity[2], dt, alpha, S, partials);
 }
-template <int D>
-void Kernels<D>::warm_start(const GridGeo& g, const uint8_t* dofmask, const double* src, double* u,
+template <int D, typename R>
+void Kernels<D, R>::warm_start(const GridGeo& g, const uint8_t* dofmask, const double* src, double* u,
                             cudaStream_t s) {
-  k_warm_start<D><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, src, u);
+  k_warm_start<D, R><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, src, u);
 }
-template <int D>
-void Kernels<D>::axpy(const GridGeo& g, double* u, const double* x, double alpha,
+template <int D, typename R>
+void Kernels<D, R>::axpy(const GridGeo& g, double* u, const double* x, double alpha,
                       cudaStream_t s) {
-  k_axpy<D><<<OSMPM_RB(g.nn * D)>>>(g, u, x, alpha);
+  k_axpy<D, R><<<OSMPM_RB(g.nn * D)>>>(g, u, x, alpha);
 }
-template <int D>
-void Kernels<D>::g2p(const PartPtrs& P, const GridGeo& g, const double* u, double dt,
+template <int D, typename R>
+void Kernels<D, R>::g2p(const PartPtrsT<R>& P, const GridGeo& g, const double* u, double dt,
                      cudaStream_t s) {
-  k_g2p<D><<<OSMPM_NB(P.n)>>>(P, g, u, dt);
+  k_g2p<D, R><<<OSMPM_NB(P.n)>>>(P, g, u, dt);
 }
-template <int D>
-void Kernels<D>::gamma(const GridGeo& g, const double* m, const double* bm, double tau,
+template <int D, typename R>
+void Kernels<D, R>::gamma(const GridGeo& g, const double* m, const double* bm, double tau,
                        uint8_t* gam, cudaStream_t s) {
-  k_gamma<D><<<OSMPM_RB(g.nn)>>>(g.nn, g.mass_eps, m, bm, tau, gam);
+  k_gamma<D, R><<<OSMPM_RB(g.nn)>>>(g.nn, g.mass_eps, m, bm, tau, gam);
 }
-template <int D>
-void Kernels<D>::arbitrate(const GridGeo& gB, const GridGeo& gS, const uint8_t* gamB,
+template <int D, typename R>
+void Kernels<D, R>::arbitrate(const GridGeo& gB, const GridGeo& gS, const uint8_t* gamB,
                            const uint8_t* gamS, const double* mB, const double* mS,
                            uint8_t* recvB, uint8_t* recvS, cudaStream_t s) {
-  k_arbitrate<D><<<OSMPM_RB(gB.nn)>>>(gB, gS, gamB, gamS, mB, mS, recvB, recvS);
+  k_arbitrate<D, R><<<OSMPM_RB(gB.nn)>>>(gB, gS, gamB, gamS, mB, mS, recvB, recvS);
 }
-template <int D>
-void Kernels<D>::proj_scatter(const GridGeo& gB, const GridGeo& gS, const double* mS,
+template <int D, typename R>
+void Kernels<D, R>::proj_scatter(const GridGeo& gB, const GridGeo& gS, const double* mS,
                               const double* vS, double* num, double* den, cudaStream_t s) {
-  k_proj_scatter<D><<<OSMPM_RB(gS.nn)>>>(gB, gS, mS, vS, num, den);
+  k_proj_scatter<D, R><<<OSMPM_RB(gS.nn)>>>(gB, gS, mS, vS, num, den);
 }
-template <int D>
-void Kernels<D>::recvB_filter(const GridGeo& gB, const double* den, double tau,
+template <int D, typename R>
+void Kernels<D, R>::recvB_filter(const GridGeo& gB, const double* den, double tau,
                               const uint8_t* physB, uint8_t* recvB, cudaStream_t s) {
-  k_recvB_filter<D><<<OSMPM_RB(gB.nn)>>>(gB.nn, den, tau, physB, recvB);
+  k_recvB_filter<D, R><<<OSMPM_RB(gB.nn)>>>(gB.nn, den, tau, physB, recvB);
 }
-template <int D>
-void Kernels<D>::recvS_filter(const GridGeo& gB, const GridGeo& gS, const double* mB,
+template <int D, typename R>
+void Kernels<D, R>::recvS_filter(const GridGeo& gB, const GridGeo& gS, const double* mB,
                               const uint8_t* physS, uint8_t* recvS, cudaStream_t s) {
-  k_recvS_filter<D><<<OSMPM_RB(gS.nn)>>>(gB, gS, mB, physS, recvS);
+  k_recvS_filter<D, R><<<OSMPM_RB(gS.nn)>>>(gB, gS, mB, physS, recvS);
 }
-template <int D>
-void Kernels<D>::proj_finish(const GridGeo& gB, const uint8_t* recvB, const double* num,
+template <int D, typename R>
+void Kernels<D, R>::proj_finish(const GridGeo& gB, const uint8_t* recvB, const double* num,
                              const double* den, double eps_tol, double* out, cudaStream_t s) {
-  k_proj_finish<D><<<OSMPM_RB(gB.nn)>>>(gB, recvB, num, den, eps_tol, out);
+  k_proj_finish<D, R><<<OSMPM_RB(gB.nn)>>>(gB, recvB, num, den, eps_tol, out);
 }
-template <int D>
-void Kernels<D>::interp(const GridGeo& gB, const GridGeo& gS, const double* vB,
+template <int D, typename R>
+void Kernels<D, R>::interp(const GridGeo& gB, const GridGeo& gS, const double* vB,
                         const uint8_t* recvS, double* out, cudaStream_t s) {
-  k_interp<D><<<OSMPM_RB(gS.nn)>>>(gB, gS, vB, recvS, out);
+  k_interp<D, R><<<OSMPM_RB(gS.nn)>>>(gB, gS, vB, recvS, out);
 }
-template <int D>
-void Kernels<D>::vel_from_u(const GridGeo& g, const double* m, const double* u, double dt,
+template <int D, typename R>
+void Kernels<D, R>::vel_from_u(const GridGeo& g, const double* m, const double* u, double dt,
                             double* v, cudaStream_t s) {
-  k_vel_from_u<D><<<OSMPM_RB(g.nn * D)>>>(g, m, u, dt, v);
+  k_vel_from_u<D, R><<<OSMPM_RB(g.nn * D)>>>(g, m, u, dt, v);
 }
-template <int D>
-void Kernels<D>::rel_change(const GridGeo& g, const double* vnew, const double* vold,
+template <int D, typename R>
+void Kernels<D, R>::rel_change(const GridGeo& g, const double* vnew, const double* vold,
                             const uint8_t* recv, int slot, DevScalars* S, double* partials,
                             cudaStream_t s) {
-  k_rel_change<D><<<OSMPM_RB(g.nn * D)>>>(g, vnew, vold, recv, slot, S, partials);
+  k_rel_change<D, R><<<OSMPM_RB(g.nn * D)>>>(g, vnew, vold, recv, slot, S, partials);
 }
-template <int D>
-void Kernels<D>::copy_if_neg(const GridGeo& g, const double* p, double* x, const DevScalars* S,
+template <int D, typename R>
+void Kernels<D, R>::copy_if_neg(const GridGeo& g, const double* p, double* x, const DevScalars* S,
                              cudaStream_t s) {
-  k_copy_if_neg<D><<<OSMPM_RB(g.nn * D)>>>(g, p, x, S);
+  k_copy_if_neg<D, R><<<OSMPM_RB(g.nn * D)>>>(g, p, x, S);
 }
-template <int D>
-void Kernels<D>::set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s) {
+template <int D, typename R>
+void Kernels<D, R>::set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s) {
   g_launch_count += 1;
-  k_set_cg_state<D><<<1, 1, 0, s>>>(S, iter, done);
+  k_set_cg_state<D, R><<<1, 1, 0, s>>>(S, iter, done);
 }
 
-template <int D>
-void Kernels<D>::pcg_shape(int64_t work, int* blocks, int* threads) {
+template <int D, typename R>
+void Kernels<D, R>::pcg_shape(int64_t work, int* blocks, int* threads) {
   // One block per SM while the work fits (the FP64 pipe of every SM is used
   // and each grid barrier spans as few blocks as possible); threads per
   // block sized to the work, a multiple of 32 in [64, 256].  Larger problems
@@ -1119,7 +1119,7 @@ void Kernels<D>::pcg_shape(int64_t work, int* blocks, int* threads) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm256, k_pcg<D>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm256, k_pcg<D, R>, 256, 0);
     if (per_sm256 < 1) per_sm256 = 1;
   }
   int64_t t = (work + sms - 1) / sms;
@@ -1133,18 +1133,18 @@ void Kernels<D>::pcg_shape(int64_t work, int* blocks, int* threads) {
   *blocks = (int)b;
   *threads = (int)t;
 }
-template <int D>
-cudaError_t Kernels<D>::pcg(const PcgArgs& a, int blocks, int threads, cudaStream_t s) {
-  PcgArgs copy = a;
+template <int D, typename R>
+cudaError_t Kernels<D, R>::pcg(const PcgArgsT<R>& a, int blocks, int threads, cudaStream_t s) {
+  PcgArgsT<R> copy = a;
   void* args[] = {(void*)&copy};
   g_launch_count += 1;
-  return cudaLaunchCooperativeKernel((const void*)k_pcg<D>, dim3(blocks), dim3(threads), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_pcg<D, R>, dim3(blocks), dim3(threads), args, 0, s);
 }
 
-template <int D>
-void Kernels<D>::barrier_timeout_check(unsigned* words, int* err, cudaStream_t s) {
+template <int D, typename R>
+void Kernels<D, R>::barrier_timeout_check(unsigned* words, int* err, cudaStream_t s) {
   g_launch_count += 1;
-  k_barrier_timeout_check<D><<<2, 32, 0, s>>>(words, err);
+  k_barrier_timeout_check<D, R><<<2, 32, 0, s>>>(words, err);
 }
 
 #undef OSMPM_NB

@@ -86,7 +86,7 @@ __device__ __forceinline__ void publish_partials(double (&v)[NV], double* partia
 
 // Diagnostic: a barrier that waits for one block more than the launch has,
 // so its bounded spin can only run out.
-template <int D>
+template <int D, typename R>
 __global__ void k_barrier_timeout_check(unsigned* words, int* err) {
   __shared__ unsigned goal;
   if (threadIdx.x == 0) goal = 0u;
@@ -100,44 +100,44 @@ __device__ __forceinline__ int64_t stencil_offset(const GridGeo& g, int k) {
   return D == 2 ? ox + oy * g.res[0] : ox + (oy + oz * g.res[1]) * (int64_t)g.res[0];
 }
 
-// Particle Hessian-vector product: gathers u at the stencil through
-// `ufun(j)` (j = flat DOF index), scatters (L G) grad N_i into w on the free
-// DOFs and returns the quadratic form G : L G.
-template <int D, class UF>
-__device__ __forceinline__ double particle_hvp(const PcgArgs& a, int64_t pi, UF ufun, double* w) {
+// Particle Hessian-vector product in arithmetic type R: gathers u at the
+// stencil through `ufun(j)` (j = flat DOF index), scatters (L G) grad N_i
+// into w on the free DOFs and returns the quadratic form G : L G.
+template <int D, typename R, class UF>
+__device__ __forceinline__ double particle_hvp(const PcgArgsT<R>& a, int64_t pi, UF ufun, double* w) {
   constexpr int DD = D * D;
   constexpr int K = (D == 2) ? 9 : 27;
   const GridGeo& g = a.g;
   const int64_t base = a.sbase[pi];
-  double dN[K][D];
+  R dN[K][D];
 #pragma unroll
   for (int k = 0; k < K; ++k)
 #pragma unroll
     for (int c = 0; c < D; ++c) dN[k][c] = a.sdn[(int64_t)(c * K + k) * a.P.n + pi];
-  double G[DD];
+  R G[DD];
 #pragma unroll
-  for (int e = 0; e < DD; ++e) G[e] = 0.0;
+  for (int e = 0; e < DD; ++e) G[e] = R(0);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int64_t node = base + stencil_offset<D>(g, k);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      const double uv = ufun(c * g.nn + node);
+      const R uv = (R)ufun(c * g.nn + node);
 #pragma unroll
       for (int b = 0; b < D; ++b) G[c * D + b] += uv * dN[k][b];
     }
   }
-  double Y[DD];
+  R Y[DD];
 #pragma unroll
   for (int i = 0; i < DD; ++i) {
-    double t = 0.0;
+    R t = R(0);
 #pragma unroll
     for (int j = 0; j < DD; ++j) t += a.L[(int64_t)Sym<D>::idx(i, j) * a.P.n + pi] * G[j];
     Y[i] = t;
   }
   double qf = 0.0;
 #pragma unroll
-  for (int i = 0; i < DD; ++i) qf += G[i] * Y[i];
+  for (int i = 0; i < DD; ++i) qf += (double)G[i] * (double)Y[i];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int64_t node = base + stencil_offset<D>(g, k);
@@ -146,17 +146,17 @@ __device__ __forceinline__ double particle_hvp(const PcgArgs& a, int64_t pi, UF 
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       if (!((fm >> c) & 1u)) continue;
-      double f = 0.0;
+      R f = R(0);
 #pragma unroll
       for (int b = 0; b < D; ++b) f += Y[c * D + b] * dN[k][b];
-      atomicAdd(&w[c * g.nn + node], f);
+      atomicAdd(&w[c * g.nn + node], (double)f);
     }
   }
   return qf;
 }
 
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
   const GridGeo& g = a.g;
   const int64_t ndof = g.nn * D;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
       }
     }
     for (int64_t pi = tid; pi < a.P.n; pi += stride)
-      acc[2] += particle_hvp<D>(a, pi, [&](int64_t j) { return __ldcg(&r0[j]) * idiag[j]; }, a.w[0]);
+      acc[2] += particle_hvp<D, R>(a, pi, [&](int64_t j) { return __ldcg(&r0[j]) * idiag[j]; }, a.w[0]);
     publish_partials<3>(acc, a.partials, 0);
     if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
     sum_partials<3>(a.partials, sums);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgs a) {
       wz[idx] = 0.0;
     }
     for (int64_t pi = tid; pi < a.P.n; pi += stride)
-      acc[2] += particle_hvp<D>(
+      acc[2] += particle_hvp<D, R>(
           a, pi,
           [&](int64_t j) {
             return (__ldcg(&rk[j]) - alpha * (__ldcg(&wk[j]) + beta * __ldcg(&sp[j]))) * idiag[j];

@@ -15,13 +15,16 @@ struct GridGeo {
   double mass_eps;  // active nodes: m_i > mass_eps
 };
 
-// Particle state, structure of arrays, component-major (x[a*n + p]).
-struct PartPtrs {
+// Particle state, structure of arrays, component-major (x[a*n + p]).  R is
+// the storage type of v, B and F: double in FP64 mode, float in mixed mode
+// (positions, masses and material constants stay double).
+template <typename R>
+struct PartPtrsT {
   int64_t n;
   double* x;      // D
-  double* v;      // D
-  double* B;      // D*D (row-major entry e at B[e*n + p])
-  double* F;      // D*D
+  R* v;           // D
+  R* B;           // D*D (row-major entry e at B[e*n + p])
+  R* F;           // D*D
   double* vol0;
   double* mass;
   double* mu;
@@ -29,6 +32,7 @@ struct PartPtrs {
   uint8_t* flags;
   uint32_t* id;
 };
+using PartPtrs = PartPtrsT<double>;
 
 // Device-side Dirichlet rule (mirrors osmpm_dirichlet; for kind 1 the
 // rotation matrix R of the step is precomputed on the host).
@@ -63,13 +67,15 @@ enum : int {
   kErrBarrierTimeout = 4,
 };
 
-// Arguments of the persistent PCG kernel.
-struct PcgArgs {
-  PartPtrs P;
+// Arguments of the persistent PCG kernel (R: storage and arithmetic type of
+// the Hessian-vector product).
+template <typename R>
+struct PcgArgsT {
+  PartPtrsT<R> P;
   GridGeo g;
   const double* m;
   const uint8_t* dofmask;
-  const double* L;
+  const R* L;
   const double* diag;   // inverse Jacobi diagonal
   double inv_dt2;
   double* x;
@@ -81,7 +87,7 @@ struct PcgArgs {
   double* partials;  // 3 * gridDim.x doubles
   int* err;
   const int* sbase;     // per particle: flat index of the stencil's base node
-  const double* sdn;    // per particle: grad N of the 3^D stencil nodes, [(c*K + k)*n + p]
+  const R* sdn;         // per particle: grad N of the 3^D stencil nodes, [(c*K + k)*n + p]
 };
 
 }  // namespace osmpm

@@ -198,7 +198,7 @@ def make_desc(spec) -> osmpm_domain_desc:
     g = spec.grid
     d = osmpm_domain_desc()
     d.dim = g.dim
-    d.precision = 0
+    d.precision = getattr(spec, "precision", 0)
     for a in range(3):
         d.origin[a] = g.origin[a] if a < g.dim else 0.0
         d.res[a] = g.res[a] if a < g.dim else 1

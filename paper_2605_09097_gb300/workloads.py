@@ -95,6 +95,7 @@ class DomainSpec:
     ls_max: int = 40
     # nodes with m_i <= mass_eps carry no DOF; None -> 1e-10 x mean particle mass
     mass_eps: Optional[float] = None
+    precision: int = 0            # 0: FP64; 1: mixed (FP32 particle state and HVP)
 
     def __post_init__(self):
         if self.mass_eps is None:
@@ -236,6 +237,77 @@ def inclusion(dx_S: float = 0.005, M: int = 2, dx_B: float = 0.05,
                       tau_B=rho * dx_B ** 2 / ppc_1d ** 2,
                       tau_S=rho * dx_S ** 2 / ppc_1d ** 2,
                       eps_tol=1e-12 * rho * dx_S ** 2)
+    return coarse, fine, sch, dT
+
+
+def hertz(dx_c: float = 1.0 / 64, ratio: int = 4, M: int = 4, E_block: float = 1e6,
+          E_cyl: float = 1e7, nu: float = 0.3, rho: float = 1000.0, R: float = 0.5,
+          dT: float = 2e-4, indent: float = 0.02, n_steps: int = 100, ppc_1d: int = 2,
+          box_lo=(1.75, 1.875), box_hi=(2.25, 2.125), precision: int = 1,
+          newton_tol: float = 1e-8, cg_rtol: float = 1e-6):
+    """2D Hertzian contact for OS-MPM (Sec. 4.2 setting with an elastic
+    block instead of the rigid plane): block [0,4]x[0,2] on a coarse grid
+    covering [0,4]x[0,3] plus a 3-cell margin, half-disk cylinder
+    r < R, y < 2 + R centred at (2, 2 + R) (flat face up, lowest point
+    touching the block top at (2, 2)), both on one grid per domain.  The
+    cylinder's flat face is pushed down by ``indent`` over ``n_steps`` global
+    steps of dT; the block bottom is fixed.  Fine subdomain: the box
+    [box_lo, box_hi] at dx_c / ratio; coarse: all material minus the box
+    shrunk by 2 dx_c.  Returns (coarse, fine, schwarz, dT)."""
+    c = np.array([2.0, 2.0 + R])
+    dx_f = dx_c / ratio
+    blo, bhi = np.asarray(box_lo), np.asarray(box_hi)
+
+    def body(x):
+        in_block = np.all((x >= 0.0) & (x < np.array([4.0, 2.0])), axis=1)
+        in_cyl = (_r2(x, c) < R * R) & (x[:, 1] < c[1])
+        return in_block, in_cyl
+
+    def in_box(x, lo, hi):
+        return np.all((x >= lo) & (x < hi), axis=1)
+
+    hole_lo, hole_hi = blo + 2 * dx_c, bhi - 2 * dx_c
+    # coarse domain on [0,4] x [0,3] with a 3-cell margin
+    nBx, nBy = int(round(4.0 / dx_c)), int(round(3.0 / dx_c))
+    mB = 3
+    gB = Grid(2, (-mB * dx_c, -mB * dx_c), dx_c, (nBx + 2 * mB + 1, nBy + 2 * mB + 1))
+
+    def coarse_in(x):
+        a, b = body(x)
+        return (a | b) & ~in_box(x, hole_lo, hole_hi)
+    xB = sample_lattice((0.0, 0.0), dx_c, (0, 0), (nBx, nBy), ppc_1d, coarse_in)
+    sB = dx_c / ppc_1d
+    flB = np.where(in_box(xB, hole_lo - sB, hole_hi + sB), FLAG_BOUNDARY, 0).astype(np.uint8)
+    EB = np.where(body(xB)[1], E_cyl, E_block)
+    pB = make_particles(xB, dx_c, ppc_1d, rho, EB, nu, flB)
+    v_push = -indent / (n_steps * dT)
+    dirB = [
+        Dirichlet(lo=(-BIG, -BIG), hi=(BIG, 0.5 * dx_c), comp_mask=0b11),
+        Dirichlet(lo=(-BIG, c[1] - 0.5 * dx_c), hi=(BIG, BIG), comp_mask=0b11,
+                  vel=(0.0, v_push, 0.0)),
+    ]
+    coarse = DomainSpec("hertz_coarse", gB, pB, (0.0, 0.0), dirB, newton_tol=newton_tol,
+                        cg_rtol=cg_rtol, precision=precision)
+    # fine domain: the box with a 3-cell margin
+    margin = 3
+    o = tuple(blo - margin * dx_f)
+    nfx = int(round((bhi[0] - blo[0]) / dx_f)) + 2 * margin
+    nfy = int(round((bhi[1] - blo[1]) / dx_f)) + 2 * margin
+    gS = Grid(2, o, dx_f, (nfx + 1, nfy + 1))
+
+    def fine_in(x):
+        a, b = body(x)
+        return (a | b) & in_box(x, blo, bhi)
+    xS = sample_lattice(o, dx_f, (0, 0), (nfx, nfy), ppc_1d, fine_in)
+    sS = dx_f / ppc_1d
+    flS = np.where(~in_box(xS, blo + sS, bhi - sS), FLAG_BOUNDARY, 0).astype(np.uint8)
+    ES = np.where(body(xS)[1], E_cyl, E_block)
+    pS = make_particles(xS, dx_f, ppc_1d, rho, ES, nu, flS)
+    fine = DomainSpec("hertz_fine", gS, pS, (0.0, 0.0), [], newton_tol=newton_tol,
+                      cg_rtol=cg_rtol, precision=precision)
+    sch = SchwarzSpec(M=M, k_max=50, eps_conv=1e-5,
+                      tau_B=rho * dx_c ** 2 / ppc_1d ** 2, tau_S=rho * dx_f ** 2 / ppc_1d ** 2,
+                      eps_tol=1e-12 * rho * dx_f ** 2)
     return coarse, fine, sch, dT
 
 

@@ -1,0 +1,74 @@
+"""Mixed precision (FP32 particle state and Hessian-vector product, FP64
+residual, energy, dots and Schwarz check) against the FP64 oracle: particle
+displacement within rel-L2 1e-4 after 100 steps."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import osmpm_oracle as O
+from paper_2605_09097_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def osmpm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_09097_gb300 import build
+    build.build()
+    from paper_2605_09097_gb300 import osmpm as m
+    return m
+
+
+def rel_disp(x_gpu, x_ref, x0):
+    return np.linalg.norm(x_gpu - x_ref) / max(np.linalg.norm(x_ref - x0), 1e-300)
+
+
+def test_mixed_cantilever_100_steps(osmpm):
+    spec = dataclasses.replace(W.cantilever(), precision=1)
+    dom = osmpm.Domain(spec)
+    ref = O.DomainState.create(W.cantilever())
+    x0 = spec.particles.x.copy()
+    for _ in range(100):
+        dom.step(1e-3)
+        O.step(ref, 1e-3)
+    x, v, B, F = dom.get_particles()
+    err = rel_disp(x, ref.p.x, x0)
+    assert err <= MIXED_TOL, err
+    np.testing.assert_allclose(F, ref.p.F, atol=1e-5)
+
+
+def test_mixed_state_is_stored_in_fp32(osmpm):
+    spec = W.perturb(W.block(2, n_cells=(4, 3), dx=0.1), 3)
+    spec = dataclasses.replace(spec, precision=1)
+    dom = osmpm.Domain(spec)
+    x, v, B, F = dom.get_particles()
+    np.testing.assert_array_equal(x, spec.particles.x)                  # x stays FP64
+    np.testing.assert_array_equal(v, spec.particles.v.astype(np.float32).astype(np.float64))
+    np.testing.assert_array_equal(F, spec.particles.F.astype(np.float32).astype(np.float64))
+
+
+def test_mixed_schwarz_inclusion(osmpm):
+    cB, cS, sch, dT = W.inclusion(dx_S=0.02, M=2)
+    mB, mS = dataclasses.replace(cB, precision=1), dataclasses.replace(cS, precision=1)
+    B, S = osmpm.Domain(mB), osmpm.Domain(mS)
+    rB, rS = O.DomainState.create(cB), O.DomainState.create(cS)
+    for _ in range(5):
+        st = osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+        O.schwarz_step(rB, rS, dT, sch)
+        assert st["converged"] == 1
+    assert rel_disp(B.get_particles()[0], rB.p.x, cB.particles.x) <= MIXED_TOL
+    assert rel_disp(S.get_particles()[0], rS.p.x, cS.particles.x) <= MIXED_TOL
+
+
+def test_mixed_and_fp64_domains_do_not_couple(osmpm):
+    cB, cS, sch, dT = W.inclusion(dx_S=0.02, M=2)
+    B, S = osmpm.Domain(cB), osmpm.Domain(dataclasses.replace(cS, precision=1))
+    with pytest.raises(osmpm.OsmpmError) as e:
+        osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+    assert e.value.status == osmpm.OSMPM_E_INVALID
