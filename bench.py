@@ -328,6 +328,55 @@ def cpu_baseline(n_iters):
                       "of a global step's units"}
 
 
+def run_batched(args, rank, local, world):
+    """Aggregate throughput of ``--instances`` independent inclusion pairs of
+    the batched family (uneven fine resolutions), each on its own stream,
+    advanced together by osmpm_schwarz_couple_batch (host wall clock around
+    each batched step, the device synchronised on both sides)."""
+    import dataclasses
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2605_09097_gb300 import build
+    build.build()
+    from paper_2605_09097_gb300 import osmpm
+    specs = [W.inclusion_instance(i) for i in range(args.instances)]
+    prec = 1 if args.precision == "mixed" else 0
+    B, S, streams = [], [], []
+    for cB, cS, sch, dT in specs:
+        st = torch.cuda.Stream()
+        streams.append(st)
+        B.append(osmpm.Domain(dataclasses.replace(cB, precision=prec), stream=st.cuda_stream))
+        S.append(osmpm.Domain(dataclasses.replace(cS, precision=prec), stream=st.cuda_stream))
+    schs = [s[2] for s in specs]
+    dT = specs[0][3]
+    units = sum(units_per_step(s[0], s[1], s[2].M) for s in specs)
+    for _ in range(args.warmup):
+        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=args.threads)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = osmpm.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=args.threads)
+    torch.cuda.synchronize()
+    t = max_over_ranks(time.perf_counter() - t0, world)
+    clk = clocks.stop()
+    value = sum_over_ranks(units * args.steps, world) / t
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": f"batched_inclusion_{args.instances}_literal",
+                       "instances": args.instances, "host_threads": args.threads,
+                       "particles": sum(s[0].particles.n + s[1].particles.n for s in specs),
+                       "units_per_step": units, "precision": args.precision,
+                       "timing": "host wall clock around each batched step",
+                       "parallelism": f"replicas{world}"},
+            "gpu_launches": int(osmpm.launch_count() - launches0), "clocks": clk}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -360,10 +409,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["inclusion", "batched"], default="inclusion",
+                    help="inclusion: the headline FP64 configuration; batched: many instances")
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=16)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     args = ap.parse_args()
     rank, local, world = dist_init(args.gpus)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "batched":
+        out = run_batched(args, rank, local, world)
     else:
         out = run_ours(args, rank, local, world)
     if rank == 0 and out is not None:

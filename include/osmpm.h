@@ -29,8 +29,9 @@
  *  - A failed osmpm_step or osmpm_schwarz_couple leaves the particles at the
  *    state they had at the start of the call, except for
  *    OSMPM_W_SCHWARZ_MAXITER, which commits the last Schwarz iterate.
- *  - Calls on one domain are not thread-safe; different domains on
- *    different streams are independent.
+ *  - Calls on one domain are not thread-safe.  To advance several domains
+ *    concurrently, use osmpm_schwarz_couple_batch, which sizes the
+ *    persistent PCG grids so that they can run side by side.
  */
 #ifndef OSMPM_H
 #define OSMPM_H
@@ -182,6 +183,26 @@ osmpm_status osmpm_step(osmpm_domain* dom, double dt, osmpm_stats* stats);
  * k_max was reached (state committed).  stats may be NULL. */
 osmpm_status osmpm_schwarz_couple(osmpm_domain* coarse, osmpm_domain* fine, double dT,
                                   const osmpm_schwarz_desc* sdesc, osmpm_stats* stats);
+
+/* Batched global steps (not in the paper; a service for running many
+ * independent OS-MPM instances): advances the n coupled pairs (coarse[i],
+ * fine[i]) by one global step dT each with its Schwarz controls sdesc[i]
+ * (n descriptors), as osmpm_schwarz_couple does, with
+ * up to n_threads host worker threads (0: 8) driving the pairs
+ * concurrently; each pair must own its two domains and should have its own
+ * stream, so that kernels of different pairs overlap on the GPU.  While the
+ * call runs, each pair's persistent PCG grid is limited to 1/n_threads of
+ * the device's co-resident capacity, so that the concurrent cooperative
+ * grids can all be resident together (their grid barriers never wait on a
+ * block another grid keeps out).  Calls that drive domains concurrently
+ * from several host threads must go through this entry point.  stats and
+ * status (either may be NULL) receive n entries.  Returns OSMPM_OK, or the
+ * status of the first failing pair (message names the pair), or
+ * OSMPM_W_SCHWARZ_MAXITER when some pair hit k_max and none failed. */
+osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domain* const* fine,
+                                        int32_t n, double dT, const osmpm_schwarz_desc* sdesc,
+                                        int32_t n_threads, osmpm_stats* stats,
+                                        osmpm_status* status);
 
 /* Particle count and dimension of a domain. */
 osmpm_status osmpm_get_info(const osmpm_domain* dom, int64_t* n_particles, int32_t* dim);

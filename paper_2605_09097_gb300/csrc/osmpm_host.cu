@@ -8,7 +8,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -137,6 +139,10 @@ struct osmpm_domain {
   double* partials = nullptr;
   int* err = nullptr;
   int* err_host = nullptr;
+
+  // cooperative PCG grids that may run at once (set by the batched entry
+  // point); each PCG grid uses at most 1/pcg_share of the device
+  int pcg_share = 1;
 
   // optional CUDA-event timing of the PCG launches (osmpm_set_profiling)
   bool time_hvp = false;
@@ -379,7 +385,7 @@ cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
   a.sbase = d->sbase;
   a.sdn = (const R*)d->sdn;
   int blocks = 0, threads = 0;
-  K::pcg_shape(work, &blocks, &threads);
+  K::pcg_shape(work, d->pcg_share, &blocks, &threads);
   if (timed) {
     const cudaError_t e = cudaEventRecord(d->ev[0], d->stream);
     if (e != cudaSuccess) return e;
@@ -390,15 +396,18 @@ cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
   return cudaSuccess;
 }
 
-osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, SolveStats& st) {
+// Newton forcing bound: PCG tolerance eta |r0| with eta <= kEtaMax.
+constexpr double kEtaMax = 1e-3;
+
+osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, SolveStats& st) {
   const int64_t nn = d->geo.nn;
   const int D = d->dim;
   CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
   DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
-                             d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
-                             d->cz, d->cp, d->S, d->partials, d->stream));
+                             d->desc.cg_rtol, kEtaMax, first ? 1 : 0, d->desc.cg_max, d->grad,
+                             d->diag, d->cx, d->cr, d->cz, d->cp, d->S, d->partials, d->stream));
   // whole PCG in one cooperative launch: s[1], w[0..2], p and the barrier
   // counter start at zero; x = 0 and r[0] = -g come from grad_finish
   const size_t vb = sizeof(double) * D * nn;
@@ -434,7 +443,7 @@ osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
   const double tol = d->desc.newton_tol * dt;
   for (int it = 0; it < d->desc.newton_max; ++it) {
     st.newton++;
-    OSMPM_TRY(gradient_and_pcg(d, dt, st));
+    OSMPM_TRY(gradient_and_pcg(d, dt, it == 0, st));
     const double dxinf = d->S_host->maxabs;
     st.last_dx = dxinf;
     if (!std::isfinite(dxinf)) return fail(OSMPM_E_NONFINITE, "non-finite Newton step");
@@ -938,6 +947,57 @@ osmpm_status osmpm_check_wait_timeout(void* cuda_stream) {
   return fail(OSMPM_E_CUDA, "the device-side wait did not report its timeout");
 }
 
+osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domain* const* fine,
+                                        int32_t n, double dT, const osmpm_schwarz_desc* sdesc,
+                                        int32_t n_threads, osmpm_stats* stats,
+                                        osmpm_status* status) {
+  if (n < 0 || !coarse || !fine || !sdesc) return fail(OSMPM_E_INVALID, "null argument or n < 0");
+  if (n == 0) return OSMPM_OK;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!coarse[i] || !fine[i]) return fail(OSMPM_E_INVALID, "pair %d: null domain", i);
+    for (int32_t j = 0; j < i; ++j)
+      if (coarse[i] == coarse[j] || fine[i] == fine[j] || coarse[i] == fine[j] || fine[i] == coarse[j])
+        return fail(OSMPM_E_INVALID, "pairs %d and %d share a domain", j, i);
+  }
+  int threads = n_threads > 0 ? n_threads : 8;
+  if (threads > n) threads = n;
+  std::vector<osmpm_status> st((size_t)n, OSMPM_OK);
+  std::vector<std::string> msg((size_t)n);
+  for (int32_t i = 0; i < n; ++i) coarse[i]->pcg_share = fine[i]->pcg_share = threads;
+  std::atomic<int32_t> next{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int32_t i = next.fetch_add(1);
+      if (i >= n) break;
+      osmpm_stats s;
+      st[(size_t)i] = osmpm_schwarz_couple(coarse[i], fine[i], dT, &sdesc[i], &s);
+      if (stats) stats[i] = s;
+      if (st[(size_t)i] != OSMPM_OK) msg[(size_t)i] = g_last_error;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& t : pool) t.join();
+  for (int32_t i = 0; i < n; ++i) coarse[i]->pcg_share = fine[i]->pcg_share = 1;
+  osmpm_status worst = OSMPM_OK;
+  int32_t first_bad = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    if (status) status[i] = st[(size_t)i];
+    if (st[(size_t)i] != OSMPM_OK && st[(size_t)i] != OSMPM_W_SCHWARZ_MAXITER && first_bad < 0) {
+      first_bad = i;
+      worst = st[(size_t)i];
+    }
+    if (worst == OSMPM_OK && st[(size_t)i] == OSMPM_W_SCHWARZ_MAXITER) worst = OSMPM_W_SCHWARZ_MAXITER;
+  }
+  if (first_bad >= 0) return fail(worst, "pair %d: %s", first_bad, msg[(size_t)first_bad].c_str());
+  if (worst != OSMPM_OK) return fail(worst, "at least one pair hit k_max");
+  return OSMPM_OK;
+}
+
 osmpm_status osmpm_get_info(const osmpm_domain* d, int64_t* n, int32_t* dim) {
   OSMPM_TRY(check_domain(d));
   if (n) *n = d->n;
@@ -1025,8 +1085,8 @@ osmpm_status osmpm_probe_gradient(osmpm_domain* d, double dt, const double* u, d
   CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
   DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
-                             d->desc.cg_rtol, d->desc.cg_max, d->grad, d->diag, d->cx, d->cr,
-                             d->cz, d->cp, d->S, d->partials, d->stream));
+                             d->desc.cg_rtol, d->desc.cg_rtol, 1, d->desc.cg_max, d->grad,
+                             d->diag, d->cx, d->cr, d->cz, d->cp, d->S, d->partials, d->stream));
   OSMPM_TRY(sync_scalars(d));
   OSMPM_TRY(check_err(d));
   return download_grid_vec(d, d->grad, grad, D);

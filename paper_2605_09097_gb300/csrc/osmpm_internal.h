@@ -61,10 +61,14 @@ struct Kernels {
                         double dt, uint8_t* dofmask, double* u, cudaStream_t s);
   static void grad(const PartPtrsT<R>& P, const GridGeo& g, const double* u, const uint8_t* dofmask,
                    double* grad, double* diag, R* L, int* err, cudaStream_t s);
+  // completes the gradient, inverts the Jacobi diagonal and starts PCG; the
+  // PCG tolerance is eta |r0|, eta = |g|/|g_0| clamped to [cg_rtol, eta_max]
+  // (g_0: the gradient of the solve's first Newton iteration, `first` = 1)
   static void grad_finish(const GridGeo& g, const double* m, const double* vn, const double* u,
                           const uint8_t* dofmask, const double* gravity, double dt, double cg_rtol,
-                          int cg_max, double* grad, double* diag, double* x, double* r, double* z,
-                          double* p, DevScalars* S, double* partials, cudaStream_t s);
+                          double eta_max, int first, int cg_max, double* grad, double* diag,
+                          double* x, double* r, double* z, double* p, DevScalars* S,
+                          double* partials, cudaStream_t s);
   // one PCG iteration = cg_a (p update, diagonal part), cg_b (HVP), cg_c (updates)
   static void cg_a(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
                    const double* z, double* p, double* q, DevScalars* S, double* partials,
@@ -75,7 +79,7 @@ struct Kernels {
                    const double* p, const double* q, double* x, double* r, double* z,
                    DevScalars* S, double* partials, cudaStream_t s);
   // persistent cooperative PCG (whole solve in one launch)
-  static void pcg_shape(int64_t work, int* blocks, int* threads);
+  static void pcg_shape(int64_t work, int share, int* blocks, int* threads);
   static cudaError_t pcg(const PcgArgsT<R>& a, int blocks, int threads, cudaStream_t s);
   static void hvp_only(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
                        const uint8_t* dofmask, const R* L, double dt, double* p, double* q,

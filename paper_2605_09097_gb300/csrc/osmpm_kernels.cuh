@@ -410,8 +410,9 @@ __global__ void __launch_bounds__(kThreads) k_grad(PartPtrsT<R> P, GridGeo g, co
 template <int D, typename R>
 __global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, const double* u,
                               const uint8_t* dofmask, double gx, double gy, double gz, double dt,
-                              double cg_rtol, int cg_max, double* grad, double* diag, double* x,
-                              double* r, double* z, double* p, DevScalars* S, double* partials) {
+                              double cg_rtol, double eta_max, int first, int cg_max, double* grad,
+                              double* diag, double* x, double* r, double* z, double* p,
+                              DevScalars* S, double* partials) {
   const double inv_dt2 = 1.0 / (dt * dt);
   const double gv[3] = {gx, gy, gz};
   double acc[2] = {0.0, 0.0};
@@ -448,7 +449,14 @@ __global__ void k_grad_finish(GridGeo g, const double* m, const double* vn, cons
     S->rz = tot[0];
     S->rr = tot[1];
     S->rr0 = tot[1];
-    S->tol2 = cg_rtol * cg_rtol * tot[1];
+    // inexact Newton: PCG stops at eta |r0| with eta = |g_k|/|g_0| clamped
+    // to [cg_rtol, eta_max] (the Newton stop test decides convergence)
+    if (first) S->g0sq = tot[1];
+    double eta2 = S->g0sq > 0.0 ? tot[1] / S->g0sq : 0.0;
+    const double lo = cg_rtol * cg_rtol, hi = eta_max * eta_max;
+    eta2 = eta2 < lo ? lo : (eta2 > hi ? hi : eta2);
+    if (hi < lo) eta2 = lo;
+    S->tol2 = eta2 * tot[1];
     S->cg_iter = 0;
     S->cg_max = cg_max;
     S->cg_neg = 0;
@@ -977,13 +985,13 @@ void Kernels<D, R>::grad(const PartPtrsT<R>& P, const GridGeo& g, const double* 
 }
 template <int D, typename R>
 void Kernels<D, R>::grad_finish(const GridGeo& g, const double* m, const double* vn,
-                             const double* u, const uint8_t* dofmask, const double* gravity,
-                             double dt, double cg_rtol, int cg_max, double* grad, double* diag,
-                             double* x, double* r, double* z, double* p, DevScalars* S,
-                             double* partials, cudaStream_t s) {
+                                const double* u, const uint8_t* dofmask, const double* gravity,
+                                double dt, double cg_rtol, double eta_max, int first, int cg_max,
+                                double* grad, double* diag, double* x, double* r, double* z,
+                                double* p, DevScalars* S, double* partials, cudaStream_t s) {
   k_grad_finish<D, R><<<OSMPM_RB(g.nn * D)>>>(g, m, vn, u, dofmask, gravity[0], gravity[1],
-                                           gravity[2], dt, cg_rtol, cg_max, grad, diag, x, r, z,
-                                           p, S, partials);
+                                              gravity[2], dt, cg_rtol, eta_max, first, cg_max,
+                                              grad, diag, x, r, z, p, S, partials);
 }
 template <int D, typename R>
 void Kernels<D, R>::cg_a(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
@@ -1109,25 +1117,37 @@ void Kernels<D, R>::set_cg_state(DevScalars* S, int iter, int done, cudaStream_t
 }
 
 template <int D, typename R>
-void Kernels<D, R>::pcg_shape(int64_t work, int* blocks, int* threads) {
+void Kernels<D, R>::pcg_shape(int64_t work, int share, int* blocks, int* threads) {
   // One block per SM while the work fits (the FP64 pipe of every SM is used
   // and each grid barrier spans as few blocks as possible); threads per
-  // block sized to the work, a multiple of 32 in [64, 256].  Larger problems
-  // use the co-resident maximum and grid-stride loops.
-  static int sms = 0, per_sm256 = 0;
-  if (sms == 0) {
+  // block sized to the work, a multiple of 32 in [64, 256]; larger problems
+  // use grid-stride loops.  The grid never exceeds 1/share of the device's
+  // co-resident capacity (counted in 256-thread blocks): when `share`
+  // cooperative grids run concurrently they can then all be resident at
+  // once, so none of their grid barriers can wait on a block that another
+  // grid keeps out.
+  struct Info {
+    int sms = 0, per_sm256 = 1;
+  };
+  static const Info info = [] {  // thread-safe one-time query (first device used)
+    Info i;
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm256, k_pcg<D, R>, 256, 0);
-    if (per_sm256 < 1) per_sm256 = 1;
-  }
-  int64_t t = (work + sms - 1) / sms;
+    cudaDeviceGetAttribute(&i.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&i.per_sm256, k_pcg<D, R>, 256, 0);
+    if (i.per_sm256 < 1) i.per_sm256 = 1;
+    if (i.sms < 1) i.sms = 1;
+    return i;
+  }();
+  if (share < 1) share = 1;
+  int64_t cap = (int64_t)info.sms * info.per_sm256 / share;
+  if (cap < 1) cap = 1;
+  const int64_t sms_share = info.sms / share > 0 ? info.sms / share : 1;
+  int64_t t = (work + sms_share - 1) / sms_share;
   t = ((t + 31) / 32) * 32;
   if (t < 64) t = 64;
   if (t > 256) t = 256;
   int64_t b = (work + t - 1) / t;
-  const int64_t cap = (int64_t)sms * per_sm256;
   if (b > cap) b = cap;
   if (b < 1) b = 1;
   *blocks = (int)b;

@@ -55,6 +55,7 @@ struct DevScalars {
   double maxabs;
   double dE;
   double res_num[2], res_den[2];
+  double g0sq;  // |g|^2 at the first Newton iteration of the current solve
   int cg_iter, cg_done, cg_neg, cg_max;
   int err;
   unsigned counter;

@@ -120,6 +120,9 @@ _sig = {
     "osmpm_step": (c_int32, [c_void_p, c_double, POINTER(osmpm_stats)]),
     "osmpm_schwarz_couple": (c_int32, [c_void_p, c_void_p, c_double, POINTER(osmpm_schwarz_desc),
                                        POINTER(osmpm_stats)]),
+    "osmpm_schwarz_couple_batch": (c_int32, [POINTER(c_void_p), POINTER(c_void_p), c_int32, c_double,
+                                             POINTER(osmpm_schwarz_desc), c_int32,
+                                             POINTER(osmpm_stats), POINTER(c_int32)]),
     "osmpm_get_info": (c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32)]),
     "osmpm_get_particles": (c_int32, [c_void_p, _DP, _DP, _DP, _DP]),
     "osmpm_set_particles": (c_int32, [c_void_p, _DP, _DP, _DP, _DP]),
@@ -386,6 +389,22 @@ def launch_count() -> int:
     c = osmpm_counters()
     _check(_lib.osmpm_get_counters(None, ctypes.byref(c)), "osmpm_get_counters")
     return int(c.launches)
+
+
+def osmpm_schwarz_couple_batch(coarse: List[Domain], fine: List[Domain], dT: float, schs,
+                               n_threads: int = 8):
+    """One global step of every pair (coarse[i], fine[i]) with Schwarz
+    controls schs[i], pairs driven concurrently by host worker threads.
+    Returns (stats list, status list)."""
+    n = len(coarse)
+    cs = (c_void_p * n)(*[d.h.value for d in coarse])
+    fs = (c_void_p * n)(*[d.h.value for d in fine])
+    sd = (osmpm_schwarz_desc * n)(*[make_schwarz_desc(s) for s in schs])
+    st = (osmpm_stats * n)()
+    status = (c_int32 * n)()
+    _check(_lib.osmpm_schwarz_couple_batch(cs, fs, n, dT, sd, n_threads, st, status),
+           "osmpm_schwarz_couple_batch", warn_ok=True)
+    return [s.as_dict() for s in st], list(status)
 
 
 def osmpm_get_particles(dom: Domain):
