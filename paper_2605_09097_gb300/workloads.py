@@ -311,6 +311,94 @@ def hertz(dx_c: float = 1.0 / 64, ratio: int = 4, M: int = 4, E_block: float = 1
     return coarse, fine, sch, dT
 
 
+def fold3d(dx_c: float = 0.02, dx_f: float = 0.005, band=(0.4, 0.6), M: int = 4,
+           size=(1.0, 0.5, 0.02), E: float = 1e6, nu: float = 0.3, rho: float = 1000.0,
+           dT: float = 0.01, fold_steps: int = 400, ppc_1d: int = 2, precision: int = 1,
+           newton_tol: float = 1e-8, cg_rtol: float = 1e-6):
+    """3D folding plate for OS-MPM: plate [0,Lx]x[0,Ly]x[0,Lz], grid nodes
+    with x <= 0 clamped, nodes with x >= Lx - dx_c rotated rigidly about the
+    fold axis (x = (band_lo + band_hi)/2, z = Lz/2, parallel to y) by
+    90 degrees over ``fold_steps`` global steps.  Fine subdomain: the band
+    band_lo <= x < band_hi at dx_f; coarse: the plate minus the band shrunk
+    by 2 dx_c.  The edge rule is a fixed box, so it holds the edge while the
+    edge still lies in it (the first steps of the fold).  Returns
+    (coarse, fine, schwarz, dT)."""
+    Lx, Ly, Lz = size
+    b0, b1 = band
+    axis_x = 0.5 * (b0 + b1)
+    hole = (b0 + 2 * dx_c, b1 - 2 * dx_c)
+    m = 3
+
+    def plate(x):
+        return np.all((x >= 0.0) & (x < np.array([Lx, Ly, Lz])), axis=1)
+
+    ncB = (int(round(Lx / dx_c)), int(round(Ly / dx_c)), max(1, int(round(Lz / dx_c))))
+    gB = Grid(3, (-m * dx_c,) * 3, dx_c, tuple(n + 2 * m + 1 for n in ncB))
+    xB = sample_lattice((0.0, 0.0, 0.0), dx_c, (0, 0, 0), ncB, ppc_1d,
+                        lambda x: plate(x) & ~((x[:, 0] >= hole[0]) & (x[:, 0] < hole[1])))
+    sB = dx_c / ppc_1d
+    flB = ((xB[:, 0] >= hole[0] - sB) & (xB[:, 0] < hole[1] + sB)).astype(np.uint8)
+    pB = make_particles(xB, dx_c, ppc_1d, rho, E, nu, flB)
+    omega = (0.5 * np.pi) / (fold_steps * dT)
+    dirB = [
+        Dirichlet(lo=(-BIG, -BIG, -BIG), hi=(0.5 * dx_c, BIG, BIG), comp_mask=0b111),
+        Dirichlet(lo=(Lx - dx_c - 0.5 * dx_c, -BIG, -BIG), hi=(BIG, BIG, BIG), kind=1,
+                  center=(axis_x, 0.0, 0.5 * Lz), axis=(0.0, 1.0, 0.0), omega=-omega),
+    ]
+    coarse = DomainSpec("fold3d_coarse", gB, pB, (0.0, 0.0, 0.0), dirB,
+                        newton_tol=newton_tol, cg_rtol=cg_rtol, precision=precision)
+    ncS = (int(round((b1 - b0) / dx_f)), int(round(Ly / dx_f)), int(round(Lz / dx_f)))
+    oS = (b0 - m * dx_f, -m * dx_f, -m * dx_f)
+    gS = Grid(3, oS, dx_f, tuple(n + 2 * m + 1 for n in ncS))
+    xS = sample_lattice((b0, 0.0, 0.0), dx_f, (0, 0, 0), ncS, ppc_1d, plate)
+    sS = dx_f / ppc_1d
+    flS = ((xS[:, 0] < b0 + sS) | (xS[:, 0] >= b1 - sS)).astype(np.uint8)
+    pS = make_particles(xS, dx_f, ppc_1d, rho, E, nu, flS)
+    fine = DomainSpec("fold3d_fine", gS, pS, (0.0, 0.0, 0.0), [],
+                      newton_tol=newton_tol, cg_rtol=cg_rtol, precision=precision)
+    sch = SchwarzSpec(M=M, k_max=50, eps_conv=1e-5,
+                      tau_B=rho * dx_c ** 3 / ppc_1d ** 3, tau_S=rho * dx_f ** 3 / ppc_1d ** 3,
+                      eps_tol=1e-12 * rho * dx_f ** 3)
+    return coarse, fine, sch, dT
+
+
+def overlap3d(dx_c: float = 0.1, ratio: int = 2, M: int = 2, E: float = 1e5, nu: float = 0.3,
+              rho: float = 1000.0, dT: float = 0.02, ppc_1d: int = 2, precision: int = 0):
+    """A small clamped 3D bar [0,0.8]x[0,0.2]x[0,0.2] under gravity split in
+    x: coarse (dx_c) covers x < 0.45, fine (dx_c/ratio) covers x >= 0.3;
+    boundary layers at the artificial faces x = 0.45 (coarse) and x = 0.3
+    (fine).  Small enough for the 3D oracle.  Returns (coarse, fine,
+    schwarz, dT)."""
+    dx_f = dx_c / ratio
+    Lx, Ly, Lz = 0.8, 0.2, 0.2
+    xc, xf = 0.45, 0.3
+    m = 3
+
+    def bar(x):
+        return np.all((x >= 0.0) & (x < np.array([Lx, Ly, Lz])), axis=1)
+
+    ncB = (int(round(Lx / dx_c)), int(round(Ly / dx_c)), int(round(Lz / dx_c)))
+    gB = Grid(3, (-m * dx_c,) * 3, dx_c, tuple(n + 2 * m + 1 for n in ncB))
+    xB = sample_lattice((0.0, 0.0, 0.0), dx_c, (0, 0, 0), ncB, ppc_1d,
+                        lambda x: bar(x) & (x[:, 0] < xc))
+    flB = (xB[:, 0] >= xc - dx_c / ppc_1d).astype(np.uint8)
+    pB = make_particles(xB, dx_c, ppc_1d, rho, E, nu, flB)
+    g = (0.0, 0.0, -9.81)
+    coarse = DomainSpec("overlap3d_coarse", gB, pB, g,
+                        [Dirichlet(lo=(-BIG,) * 3, hi=(0.5 * dx_c, BIG, BIG), comp_mask=0b111)],
+                        precision=precision)
+    ncS = (int(round((Lx - xf) / dx_f)), int(round(Ly / dx_f)), int(round(Lz / dx_f)))
+    gS = Grid(3, (xf - m * dx_f, -m * dx_f, -m * dx_f), dx_f, tuple(n + 2 * m + 1 for n in ncS))
+    xS = sample_lattice((xf, 0.0, 0.0), dx_f, (0, 0, 0), ncS, ppc_1d, bar)
+    flS = (xS[:, 0] < xf + dx_f / ppc_1d).astype(np.uint8)
+    pS = make_particles(xS, dx_f, ppc_1d, rho, E, nu, flS)
+    fine = DomainSpec("overlap3d_fine", gS, pS, g, [], precision=precision)
+    sch = SchwarzSpec(M=M, k_max=50, eps_conv=1e-5,
+                      tau_B=rho * dx_c ** 3 / ppc_1d ** 3, tau_S=rho * dx_f ** 3 / ppc_1d ** 3,
+                      eps_tol=1e-12 * rho * dx_f ** 3)
+    return coarse, fine, sch, dT
+
+
 def block(dim: int = 2, n_cells=(6, 5), dx: float = 0.1, ppc_1d: int = 2,
           E: float = 1e5, nu: float = 0.3, rho: float = 1000.0, margin: int = 3,
           gravity=None) -> DomainSpec:
