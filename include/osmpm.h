@@ -123,7 +123,17 @@ typedef struct osmpm_dirichlet {
  * k_max (Alg. 1 runs k = 0..k_max), interface tolerance eps_conv (Eq.
  * convergence_criterion), boundary-node mass thresholds tau_Gamma per grid
  * (Eq. boundary_grid_set) and the projection regulariser eps_tol (Eq.
- * spatial_projection). */
+ * spatial_projection).  pi_source picks the fine state v_S^(k) that Pi_{S->B}
+ * projects for the coarse solve of iteration k >= 1 (Eq.
+ * implicit_solve_coarse; k = 0 always projects the fine P2G at t_n):
+ *   OSMPM_PI_STEP_AVERAGE (0): the solved fine grid velocities of the M
+ *     sub-steps averaged over the coarse step, mass- and momentum-weighted,
+ *     (1/M) sum_m m^(m) v^(m) over (1/M) sum_m m^(m); the coarse boundary
+ *     then moves with the fine material over the same dT;
+ *   OSMPM_PI_LAST_SUBSTEP (1): the fine P2G grid that ends sub-step M (the
+ *     velocity of the last dt only; with M > 1 the two grids drift apart
+ *     during transients, see the validation tests). */
+enum { OSMPM_PI_STEP_AVERAGE = 0, OSMPM_PI_LAST_SUBSTEP = 1 };
 typedef struct osmpm_schwarz_desc {
   int32_t M;
   int32_t k_max;
@@ -131,7 +141,8 @@ typedef struct osmpm_schwarz_desc {
   double tau_B;
   double tau_S;
   double eps_tol;
-  int32_t reserved[8];      /* must be zero */
+  int32_t pi_source;        /* OSMPM_PI_STEP_AVERAGE or OSMPM_PI_LAST_SUBSTEP */
+  int32_t reserved[7];      /* must be zero */
 } osmpm_schwarz_desc;
 
 typedef struct osmpm_stats {

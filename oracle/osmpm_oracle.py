@@ -254,6 +254,12 @@ def pk1(F: np.ndarray, mu: np.ndarray, lam: np.ndarray) -> np.ndarray:
     return mu[:, None, None] * (F - FinvT) + (lam * np.log(J))[:, None, None] * FinvT
 
 
+def cauchy_stress(F: np.ndarray, mu: np.ndarray, lam: np.ndarray) -> np.ndarray:
+    """sigma = P F^T / J (the Cauchy stress of ``pk1``)."""
+    J = np.linalg.det(F)
+    return np.einsum("pab,pcb->pac", pk1(F, mu, lam), F) / J[:, None, None]
+
+
 def dpdf(F: np.ndarray, mu: np.ndarray, lam: np.ndarray) -> np.ndarray:
     """Fourth-order tangent A[p, a, c, b, e] = dP_ac / dF_be of ``pk1``:
     mu d_ab d_ce + (mu - lam ln J) Finv_ea Finv_cb + lam Finv_ca Finv_eb."""
@@ -417,10 +423,19 @@ def make_problem(p: Particles, grid: Grid, gf: GridFields, dt: float,
 
 
 def initial_guess(pr: Problem) -> np.ndarray:
-    """x_hat^(0) = x_tilde = x^n + dt v^n on free DOFs, the prescribed value on
-    Dirichlet DOFs, 0 on inactive nodes (reading: cold start)."""
+    """Newton's starting iterate (reading: the paper does not fix it): on the
+    free DOFs x_tilde = x^n + dt v^n, or x^n itself when that has the strictly
+    lower E_h (E_h(x_tilde) - E_h(x^n) > 0, +inf when x_tilde inverts an
+    element); the prescribed value on Dirichlet DOFs and 0 on inactive nodes
+    either way.  Under large quasi-static steps (dt far above the slowest
+    period, Sec. 2.2.6) x_tilde extrapolates a transient the step removes and
+    x^n is the better start; for resolved dynamics x_tilde wins."""
+    u_n = np.where(pr.fixed, pr.u_fixed, 0.0)
     u = np.where(pr.gf.active[:, None], pr.dt * pr.gf.vn, 0.0)
-    return np.where(pr.fixed, pr.u_fixed, u)
+    u_tilde = np.where(pr.fixed, pr.u_fixed, u)
+    if energy_change(pr, u_n, u_tilde - u_n, 1.0) > 0.0:
+        return u_n
+    return u_tilde
 
 
 def energy(pr: Problem, u: np.ndarray) -> float:
@@ -626,6 +641,27 @@ def project_S2B(gB: Grid, gS: Grid, gfS: GridFields, recvB: np.ndarray, eps_tol:
     return out
 
 
+def substep_average(grids: Sequence[GridFields], vels: Sequence[np.ndarray]) -> GridFields:
+    """Time average over one coarse step of the fine sub-steps' solved grids:
+    mass (1/M) sum_m m^(m) and momentum (1/M) sum_m m^(m) v^(m), each sub-step
+    over its own active nodes.  Reading of v_S^(k) in Eq. implicit_solve_coarse:
+    the coarse solve prescribes a velocity held over the whole step dT, like
+    v_B = (x_B - x_B^n)/dT, so the fine side supplies its motion over the same
+    interval, not its velocity at the last sub-step.  With M = 1 it is the
+    solved fine grid of the single sub-step."""
+    M = len(grids)
+    m = np.zeros_like(grids[0].m)
+    mv = np.zeros_like(grids[0].mv)
+    for gf, v in zip(grids, vels):
+        a = gf.active
+        m[a] += gf.m[a] / M
+        mv[a] += gf.m[a, None] * v[a] / M
+    active = m > 0.0
+    vn = np.zeros_like(mv)
+    vn[active] = mv[active] / m[active, None]
+    return GridFields(m, mv, vn, active)
+
+
 def interp_B2S(gB: Grid, gS: Grid, vB: np.ndarray, recvS: np.ndarray) -> np.ndarray:
     """I_{B->S} (Eq. interp_BtoS) on the fine receiver nodes: sum over the
     coarse support of v_BI N_BI(x_Sj); (nS, d) with zeros off the set."""
@@ -721,9 +757,10 @@ def schwarz_step(B: DomainState, S: DomainState, dT: float, sch: SchwarzSpec,
                  sets_out: Optional[dict] = None) -> None:
     """One global step of the alternating Schwarz method, Alg. 1.
 
-    Readings: the coarse BC of iteration k is Pi of the fine grid produced by
-    the P2G that ends the last sub-step of iteration k-1 (for k = 0, the fine
-    P2G at t_n); v_B^(0) is the coarse P2G velocity at t_n; convergence needs
+    Readings: the coarse BC of iteration k >= 1 is Pi of the fine grid
+    velocity of iteration k-1 averaged over its M sub-steps (substep_average;
+    with ``sch.pi_source == 1`` the P2G grid that ends sub-step M instead;
+    for k = 0, Pi of the fine P2G at t_n); v_B^(0) is the coarse P2G velocity at t_n; convergence needs
     k >= 1; k runs 0..k_max.  P_S is not reset after convergence; P_B takes
     one G2P + advection with the last coarse solution (Sec. 3.5)."""
     st = stats if stats is not None else SchwarzStats()
@@ -753,15 +790,19 @@ def schwarz_step(B: DomainState, S: DomainState, dT: float, sch: SchwarzSpec,
         S.p = snap.copy()
         gf = p2g(S.p, gS, mass_eps=S.spec.mass_eps)
         vSnp1 = interp_B2S(gB, gS, vB_new, sets.recvS)
+        solved, vels = [], []
         for m in range(1, M + 1):
             bc = time_interp(vSn, vSnp1, m, M)
             ns = NewtonStats()
             uS = solve_domain(S, gf, dt, sets.recvS, bc, ns)
             st.newton_S.append(ns.iters)
+            solved.append(gf)
+            vels.append(uS / dt)
             S.p = g2p(S.p, gS, uS, dt)
             gf = p2g(S.p, gS, mass_eps=S.spec.mass_eps)
         # 3. convergence (Eqs. convergence_residuals, convergence_criterion)
-        vGB_new = project_S2B(gB, gS, gf, sets.recvB, sch.eps_tol)
+        src = substep_average(solved, vels) if sch.pi_source == 0 else gf
+        vGB_new = project_S2B(gB, gS, src, sets.recvB, sch.eps_tol)
         rB = rel_change(vGB_new, vGB, sets.recvB)
         rS = rel_change(vSnp1, vGS, sets.recvS)
         st.history.append((rB, rS))

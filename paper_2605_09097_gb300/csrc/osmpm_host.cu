@@ -438,6 +438,19 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, SolveStats
 
 // Newton's method with backtracking line search (Sec. 2.2.5) on the
 // prepared grid (P2G done, Dirichlet data and initial guess in place).
+// Cold start of Newton: of the prepared x_tilde = x^n + dt v^n and x^n (free
+// DOFs; fixed DOFs keep their prescribed values), keep the one with the lower
+// E_h.  x^n is taken only when E_h(x_tilde) - E_h(x^n) > 0 (+inf when x_tilde
+// inverts an element), so x_tilde stays the start whenever it is no worse.
+osmpm_status cold_start(osmpm_domain* d, double dt) {
+  DISPATCH(d, K::split_free(d->geo, d->dofmask, d->u, d->cx, d->stream));
+  DISPATCH(d, K::energy_change(P_, d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt, 1.0,
+                               d->S, d->partials, d->stream));
+  OSMPM_TRY(sync_scalars(d));
+  if (!(d->S_host->dE > 0.0)) DISPATCH(d, K::axpy(d->geo, d->u, d->cx, 1.0, d->stream));
+  return OSMPM_OK;
+}
+
 osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
   st.solves++;
   const double tol = d->desc.newton_tol * dt;
@@ -764,6 +777,7 @@ osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
   OSMPM_TRY(sync_scalars(d));
   OSMPM_TRY(check_err(d));
   OSMPM_TRY(prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, nullptr));
+  OSMPM_TRY(cold_start(d, dt));
   osmpm_status s = newton_solve(d, dt, st);
   if (s != OSMPM_OK) {
     fill_stats(stats, st, 0, 0, 0.0, 0.0);
@@ -787,10 +801,12 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   if (B->prec != S->prec) return fail(OSMPM_E_INVALID, "domains differ in precision");
   if (!(B->geo.dx >= S->geo.dx)) return fail(OSMPM_E_INVALID, "coarse dx must be >= fine dx");
   if (sd->M < 1 || sd->k_max < 0 || !(sd->eps_conv > 0.0) || !(sd->eps_tol >= 0.0) ||
-      std::isnan(sd->tau_B) || std::isnan(sd->tau_S))
+      std::isnan(sd->tau_B) || std::isnan(sd->tau_S) ||
+      (sd->pi_source != OSMPM_PI_STEP_AVERAGE && sd->pi_source != OSMPM_PI_LAST_SUBSTEP))
     return fail(OSMPM_E_INVALID, "bad Schwarz controls");
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 7; ++i)
     if (sd->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
+  const bool pi_avg = sd->pi_source == OSMPM_PI_STEP_AVERAGE;
   if (!(dT > 0.0) || !std::isfinite(dT)) return fail(OSMPM_E_INVALID, "dT must be > 0");
   const int M = sd->M;
   const double dt = dT / M;
@@ -850,7 +866,10 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   for (k = 0; k <= sd->k_max; ++k) {
     // 1. coarse solve over dT with Pi data on Gamma_hat_B (Eq. implicit_solve_coarse)
     S_TRY(prep(B, dT, true, B->recv, B->bc0, B->bc0, 1.0, nullptr));
-    if (k > 0) DISPATCH(B, K::warm_start(gB, B->dofmask, keep_slot(B, 0), B->u, s));
+    if (k > 0)
+      DISPATCH(B, K::warm_start(gB, B->dofmask, keep_slot(B, 0), B->u, s));
+    else
+      S_TRY(cold_start(B, dT));
     S_TRY(newton_solve(B, dT, st));
     CUDA_TRY(cudaMemcpyAsync(keep_slot(B, 0), B->u, bytesB, cudaMemcpyDeviceToDevice, s));
     DISPATCH(B, K::vel_from_u(gB, B->m, B->u, dT, B->vtmp, s));
@@ -858,21 +877,34 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
     S_TRY(snapshot(S, true));
     S_TRY(run_p2g(S, false));
     DISPATCH(B, K::interp(gB, gS, B->vtmp, S->recv, S->bc1, s));
+    // Step-average source: the projection sums collect every sub-step's
+    // solved grid (its mass and u/dt)
+    CUDA_TRY(cudaMemsetAsync(B->proj_num, 0, sizeof(double) * D * gB.nn, s));
+    CUDA_TRY(cudaMemsetAsync(B->proj_den, 0, sizeof(double) * gB.nn, s));
     for (int m = 1; m <= M; ++m) {
       S_TRY(prep(S, dt, true, S->recv, S->bc0, S->bc1, (double)m / (double)M, nullptr));
-      if (k > 0) DISPATCH(S, K::warm_start(gS, S->dofmask, keep_slot(S, m - 1), S->u, s));
+      if (k > 0)
+        DISPATCH(S, K::warm_start(gS, S->dofmask, keep_slot(S, m - 1), S->u, s));
+      else
+        S_TRY(cold_start(S, dt));
       S_TRY(newton_solve(S, dt, st));
       CUDA_TRY(cudaMemcpyAsync(keep_slot(S, m - 1), S->u, bytesS, cudaMemcpyDeviceToDevice, s));
+      if (pi_avg) {
+        DISPATCH(S, K::vel_from_u(gS, S->m, S->u, dt, S->vtmp, s));
+        DISPATCH(B, K::proj_scatter(gB, gS, S->m, S->vtmp, B->proj_num, B->proj_den, s));
+      }
       DISPATCH(S, K::g2p(P_, gS, S->u, dt, s));
       S_TRY(run_p2g(S, false));
       S_TRY(sync_scalars(S));
       S_TRY(check_err(S));
     }
-    // 3. convergence: Pi of the fine grid after sub-step M vs the BC in use
-    CUDA_TRY(cudaMemsetAsync(B->proj_num, 0, sizeof(double) * D * gB.nn, s));
-    CUDA_TRY(cudaMemsetAsync(B->proj_den, 0, sizeof(double) * gB.nn, s));
-    DISPATCH(B, K::proj_scatter(gB, gS, S->m, S->vn, B->proj_num, B->proj_den, s));
-    DISPATCH(B, K::proj_finish(gB, B->recv, B->proj_num, B->proj_den, sd->eps_tol, B->bc1, s));
+    // 3. convergence: the new Pi vs the BC in use.  Step average: the sums
+    // hold M times the time averages, so eps_tol is scaled by M to keep
+    // Pi = avg num / (avg den + eps_tol).  Last sub-step: Pi of the P2G grid.
+    if (!pi_avg)
+      DISPATCH(B, K::proj_scatter(gB, gS, S->m, S->vn, B->proj_num, B->proj_den, s));
+    DISPATCH(B, K::proj_finish(gB, B->recv, B->proj_num, B->proj_den,
+                               pi_avg ? sd->eps_tol * M : sd->eps_tol, B->bc1, s));
     DISPATCH(B, K::rel_change(gB, B->bc1, B->bc0, B->recv, 0, B->S, B->partials, s));
     DISPATCH(S, K::rel_change(gS, S->bc1, S->bc_prev, S->recv, 1, B->S, B->partials, s));
     S_TRY(sync_scalars(B));

@@ -97,6 +97,8 @@ struct Kernels {
                                    double* partials, int blocks, cudaStream_t s);
   static void warm_start(const GridGeo& g, const uint8_t* dofmask, const double* src, double* u,
                          cudaStream_t s);
+  static void split_free(const GridGeo& g, const uint8_t* dofmask, double* u, double* x,
+                         cudaStream_t s);
   static void axpy(const GridGeo& g, double* u, const double* x, double alpha, cudaStream_t s);
   static void g2p(const PartPtrsT<R>& P, const GridGeo& g, const double* u, double dt,
                   cudaStream_t s);

@@ -675,6 +675,22 @@ __global__ void k_warm_start(GridGeo g, const uint8_t* dofmask, const double* sr
   }
 }
 
+// Moves the free-DOF part of u into x (u keeps its fixed DOFs, x is zero
+// on them): u becomes the x_hat = x^n candidate, u + x the prepared one.
+template <int D, typename R>
+__global__ void k_split_free(GridGeo g, const uint8_t* dofmask, double* u, double* x) {
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
+    const int a = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)a * g.nn;
+    if ((dofmask[i] >> a) & 1u) {
+      x[idx] = u[idx];
+      u[idx] = 0.0;
+    } else {
+      x[idx] = 0.0;
+    }
+  }
+}
+
 template <int D, typename R>
 __global__ void k_axpy(GridGeo g, double* u, const double* x, double alpha) {
   for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) u[idx] += alpha * x[idx];
@@ -1042,6 +1058,11 @@ void Kernels<D, R>::energy_change_blocks(const PartPtrsT<R>& P, const GridGeo& g
   g_launch_count += 1;
   k_energy_change<D, R><<<blocks, kThreads, 0, s>>>(P, g, m, vn, u, x, gravity[0], gravity[1],
                                                 gravity[2], dt, alpha, S, partials);
+}
+template <int D, typename R>
+void Kernels<D, R>::split_free(const GridGeo& g, const uint8_t* dofmask, double* u, double* x,
+                               cudaStream_t s) {
+  k_split_free<D, R><<<OSMPM_RB(g.nn * D)>>>(g, dofmask, u, x);
 }
 template <int D, typename R>
 void Kernels<D, R>::warm_start(const GridGeo& g, const uint8_t* dofmask, const double* src, double* u,

@@ -39,6 +39,9 @@ OSMPM_E_TIMEOUT = 8
 OSMPM_E_UNSUPPORTED = 9
 OSMPM_W_SCHWARZ_MAXITER = 100
 
+OSMPM_PI_STEP_AVERAGE = 0
+OSMPM_PI_LAST_SUBSTEP = 1
+
 OSMPM_FIELD_MASS = 0
 OSMPM_FIELD_VN = 1
 OSMPM_FIELD_U = 2
@@ -78,7 +81,8 @@ class osmpm_dirichlet(Structure):
 
 class osmpm_schwarz_desc(Structure):
     _fields_ = [("M", c_int32), ("k_max", c_int32), ("eps_conv", c_double), ("tau_B", c_double),
-                ("tau_S", c_double), ("eps_tol", c_double), ("reserved", c_int32 * 8)]
+                ("tau_S", c_double), ("eps_tol", c_double), ("pi_source", c_int32),
+                ("reserved", c_int32 * 7)]
 
 
 class osmpm_stats(Structure):
@@ -240,6 +244,7 @@ def make_schwarz_desc(sch) -> osmpm_schwarz_desc:
     s.tau_B = sch.tau_B
     s.tau_S = sch.tau_S
     s.eps_tol = sch.eps_tol
+    s.pi_source = sch.pi_source
     return s
 
 

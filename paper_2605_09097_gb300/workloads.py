@@ -110,6 +110,7 @@ class SchwarzSpec:
     tau_B: float = 0.0    # boundary-node mass threshold on the coarse grid
     tau_S: float = 0.0    # same on the fine grid
     eps_tol: float = 0.0  # projection regulariser (Eq. spatial_projection)
+    pi_source: int = 0    # fine state projected for k >= 1: 0 step average, 1 last sub-step's P2G
 
 
 # ----------------------------------------------------------------------------
@@ -198,11 +199,17 @@ def inclusion(dx_S: float = 0.005, M: int = 2, dx_B: float = 0.05,
               r_inc: float = 0.05, E_inc: float = 1e8, E: float = 1e6, nu: float = 0.3,
               rho: float = 1000.0, dT: float = 0.01, top_disp: float = 1e-3,
               r_hole: float = 0.1, r_fine: float = 0.15, ppc_1d: int = 2,
-              newton_tol: float = 1e-8, cg_rtol: float = 1e-6):
+              newton_tol: float = 1e-8, cg_rtol: float = 1e-6, eigenstrain: float = 0.0,
+              free_edges: bool = False):
     """2D elastic inclusion for OS-MPM (Sec. 4.3 geometry with a displaced top
     edge).  Coarse: matrix [0.1,0.9]^2 minus the disk r < r_hole on the grid
-    [0,1]^2 at dx_B.  Fine: disk r < r_fine on the grid [0.3,0.7]^2 at dx_S,
-    with the stiff inclusion r < r_inc.  Returns (coarse, fine, schwarz, dT)."""
+    [0,1]^2 at dx_B.  Fine: disk r < r_fine on the grid [0.3,0.7]^2 at dx_S
+    (wider when r_fine + 4 dx_S exceeds 0.2),
+    with the stiff inclusion r < r_inc.  ``eigenstrain`` delta > 0 starts the
+    inclusion particles at F0 = (1 - delta) I (the loading of Sec. 4.3).
+    The matrix's bottom edge is clamped and its top edge moves by
+    ``top_disp`` in y over dT; ``free_edges`` drops both rules (the traction-
+    free matrix of the eigenstrain problem).  Returns (coarse, fine, schwarz, dT)."""
     c = (0.5, 0.5)
     # coarse domain
     nB = int(round(1.0 / dx_B)) + 1
@@ -215,22 +222,27 @@ def inclusion(dx_S: float = 0.005, M: int = 2, dx_B: float = 0.05,
     flB = np.where(_r2(xB, c) < (r_hole + sB) ** 2, FLAG_BOUNDARY, 0).astype(np.uint8)
     pB = make_particles(xB, dx_B, ppc_1d, rho, E, nu, flB)
     v_top = -top_disp / dT
-    dirB = [
+    dirB = [] if free_edges else [
         Dirichlet(lo=(-BIG, -BIG), hi=(BIG, 0.1 + 0.5 * dx_B), comp_mask=0b11),
         Dirichlet(lo=(-BIG, 0.9 - 0.5 * dx_B), hi=(BIG, BIG), comp_mask=0b10, vel=(0.0, v_top, 0.0)),
     ]
     coarse = DomainSpec("inclusion_coarse", gB, pB, (0.0, 0.0), dirB,
                         newton_tol=newton_tol, cg_rtol=cg_rtol)
     # fine domain
-    nS = int(round(0.4 / dx_S)) + 1
-    gS = Grid(2, (0.3, 0.3), dx_S, (nS, nS))
+    # fine grid: the square [0.3, 0.7]^2, widened when the disk needs it
+    half = max(0.2, float(np.ceil((r_fine + 4 * dx_S) / dx_S - 1e-9)) * dx_S)
+    nS = int(round(2 * half / dx_S)) + 1
+    gS = Grid(2, (0.5 - half, 0.5 - half), dx_S, (nS, nS))
     ncS = nS - 1
     xS = sample_lattice(gS.origin, dx_S, (0, 0), (ncS, ncS), ppc_1d,
                         lambda x: _r2(x, c) < r_fine ** 2)
     sS = dx_S / ppc_1d
     flS = np.where(_r2(xS, c) >= (r_fine - sS) ** 2, FLAG_BOUNDARY, 0).astype(np.uint8)
-    Es = np.where(_r2(xS, c) < r_inc ** 2, E_inc, E)
-    pS = make_particles(xS, dx_S, ppc_1d, rho, Es, nu, flS)
+    inc = _r2(xS, c) < r_inc ** 2
+    Es = np.where(inc, E_inc, E)
+    F0 = np.broadcast_to(np.eye(2), (xS.shape[0], 2, 2)).copy()
+    F0[inc] *= (1.0 - eigenstrain)
+    pS = make_particles(xS, dx_S, ppc_1d, rho, Es, nu, flS, F0=F0)
     fine = DomainSpec("inclusion_fine", gS, pS, (0.0, 0.0), [],
                       newton_tol=newton_tol, cg_rtol=cg_rtol)
     sch = SchwarzSpec(M=M, k_max=50, eps_conv=1e-5,

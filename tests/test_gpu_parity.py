@@ -209,6 +209,26 @@ def test_schwarz_subcycling_ratio(osmpm, M):
     assert rel_disp(xB, rB.p.x, cB.particles.x) <= DISP_TOL
 
 
+def test_schwarz_last_substep_projection_matches_oracle(osmpm):
+    """The alternative Pi source (the fine P2G grid that ends sub-step M)."""
+    cB, cS, sch, dT = W.inclusion(dx_S=0.02, M=2)
+    sch = dataclasses.replace(sch, pi_source=osmpm.OSMPM_PI_LAST_SUBSTEP)
+    B, S, rB, rS, out = _run_schwarz(osmpm, cB, cS, sch, dT, 1)
+    st, ost, _ = out[-1]
+    assert st["converged"] == 1 and ost.converged
+    assert abs(st["schwarz_iters"] - ost.iters) <= 1
+    assert rel_disp(S.get_particles()[0], rS.p.x, cS.particles.x) <= DISP_TOL
+    assert rel_disp(B.get_particles()[0], rB.p.x, cB.particles.x) <= DISP_TOL
+
+
+def test_schwarz_rejects_unknown_pi_source(osmpm):
+    cB, cS, sch, dT = W.inclusion(dx_S=0.02, M=2)
+    B, S = osmpm.Domain(cB), osmpm.Domain(cS)
+    with pytest.raises(osmpm.OsmpmError) as e:
+        osmpm.osmpm_schwarz_couple(B, S, dT, dataclasses.replace(sch, pi_source=2))
+    assert e.value.status == osmpm.OSMPM_E_INVALID
+
+
 def test_schwarz_no_boundary_nodes_decouples(osmpm):
     cB, cS, sch, dT = W.inclusion(dx_S=0.02, M=2)
     sch = dataclasses.replace(sch, tau_B=np.inf, tau_S=np.inf)

@@ -235,3 +235,35 @@ def test_round_off_weight_nodes_are_inactive():
     ds = O.DomainState.create(spec)
     O.step(ds, 0.01)
     np.testing.assert_allclose(ds.p.v[:, 1], -9.81 * 0.01, rtol=1e-12)
+
+
+def _free_problem(spec, dt):
+    gf = O.p2g(spec.particles, spec.grid, mass_eps=spec.mass_eps)
+    mask, vel = O.dirichlet_nodes(spec.grid, [], dt)
+    return O.make_problem(spec.particles, spec.grid, gf, dt, spec.gravity, mask, vel)
+
+
+def test_initial_guess_takes_the_lower_energy_start():
+    """Rigid translation: x_tilde = x^n + dt v^n has zero inertia and no
+    strain, so it is the start.  A uniform stretching rate v = c (x - x_c)
+    over a step far above the elastic period: x_tilde stretches the block by
+    1 + c dt = 6, whose stored energy V E O(1) far exceeds the kinetic term
+    m |v|^2 / 2 it saves, so the start is x^n (u = 0 on the free DOFs)."""
+    spec = W.block(2, n_cells=(4, 3), dx=0.1, E=1e5)
+    spec.particles.v[:] = np.array([0.3, -0.2])
+    pr = _free_problem(spec, 0.01)
+    u = O.initial_guess(pr)
+    a = pr.gf.active
+    np.testing.assert_allclose(u[a], np.broadcast_to(0.01 * np.array([0.3, -0.2]), u[a].shape),
+                               atol=1e-15)
+    spec = W.block(2, n_cells=(4, 3), dx=0.1, E=1e5)
+    xc = spec.particles.x.mean(axis=0)
+    spec.particles.v[:] = 0.5 * (spec.particles.x - xc)
+    pr = _free_problem(spec, 10.0)
+    u_tilde = np.where(pr.gf.active[:, None], pr.dt * pr.gf.vn, 0.0)
+    assert O.energy_change(pr, np.zeros_like(u_tilde), u_tilde, 1.0) > 0.0
+    np.testing.assert_array_equal(O.initial_guess(pr), 0.0)
+    # the same field over a short step: x_tilde is the start again
+    pr = _free_problem(spec, 1e-3)
+    u = O.initial_guess(pr)
+    np.testing.assert_allclose(u[a], (pr.dt * pr.gf.vn)[a], rtol=0, atol=0)

@@ -134,3 +134,57 @@ def test_schwarz_residuals_decay_geometrically():
     assert st.r_B <= sch.eps_conv and st.r_S <= sch.eps_conv
     ratios = h[4:, 0] / h[3:-1, 0]
     assert np.all(ratios < 0.9)
+
+
+def test_substep_average_of_free_fall_is_mid_step_velocity():
+    """Backward Euler on a stress-free block under gravity g gives the uniform
+    grid velocity v^(m) = m g dt after sub-step m (E_h is minimised by the
+    uniform u = dt v + dt^2 g, where F = I and the stress vanishes).  Over a
+    coarse step of M = 2 sub-steps the fine motion is dT * 1.5 g dt, so the
+    step-averaged velocity that feeds Pi is 1.5 g dt on every active node,
+    not the 2 g dt of the last sub-step."""
+    g = np.array([0.0, -9.81])
+    spec = W.block(2, n_cells=(10, 8), dx=0.1, E=1e5, gravity=tuple(g))
+    ds = O.DomainState.create(spec)
+    dt, M = 0.01, 2
+    grids, vels = [], []
+    x0 = ds.p.x.copy()
+    for m in range(1, M + 1):
+        gf = O.p2g(ds.p, spec.grid, mass_eps=spec.mass_eps)
+        u = O.solve_domain(ds, gf, dt)
+        v = u / dt
+        np.testing.assert_allclose(v[gf.active], np.broadcast_to(m * g * dt, v[gf.active].shape),
+                                   atol=1e-9)
+        grids.append(gf)
+        vels.append(v)
+        ds.p = O.g2p(ds.p, spec.grid, u, dt)
+    avg = O.substep_average(grids, vels)
+    m1 = np.where(grids[0].active, grids[0].m, 0.0)
+    m2 = np.where(grids[1].active, grids[1].m, 0.0)
+    # mass and momentum are the means over the two sub-steps
+    np.testing.assert_allclose(avg.m, 0.5 * (m1 + m2), rtol=1e-14)
+    np.testing.assert_allclose(avg.mv, 0.5 * (m1[:, None] * vels[0] + m2[:, None] * vels[1]),
+                               rtol=1e-13, atol=1e-18)
+    np.testing.assert_array_equal(avg.active, grids[0].active | grids[1].active)
+    # interior nodes: two particles per cell along each axis make the nodal
+    # mass invariant under the fall (partition of unity on each half-lattice),
+    # so the average is exactly the mid-step velocity 1.5 g dt
+    inner = grids[0].active & grids[1].active & (np.abs(m1 - m2) <= 1e-12 * np.maximum(m1, m2))
+    assert inner.sum() >= 20
+    np.testing.assert_allclose(avg.vn[inner], np.broadcast_to(1.5 * g * dt, avg.vn[inner].shape),
+                               atol=1e-12)
+    # edge nodes: a convex combination of g dt and 2 g dt
+    vy = avg.vn[avg.active, 1]
+    assert np.all(vy <= g[1] * dt + 1e-12) and np.all(vy >= 2 * g[1] * dt - 1e-12)
+    # the particles moved by dT times the mid-step velocity
+    np.testing.assert_allclose(ds.p.x - x0, np.broadcast_to(M * dt * 1.5 * g * dt, x0.shape), atol=1e-12)
+
+
+def test_substep_average_with_one_substep_is_the_solved_grid():
+    spec = W.perturb(W.block(2, n_cells=(5, 4), dx=0.1, E=1e5, gravity=(0.0, -9.81)), 7)
+    ds = O.DomainState.create(spec)
+    gf = O.p2g(ds.p, spec.grid, mass_eps=spec.mass_eps)
+    u = O.solve_domain(ds, gf, 0.01)
+    avg = O.substep_average([gf], [u / 0.01])
+    np.testing.assert_array_equal(avg.active, gf.active)
+    np.testing.assert_allclose(avg.vn[gf.active], (u / 0.01)[gf.active], rtol=1e-13, atol=1e-15)
