@@ -51,7 +51,7 @@ WORKLOAD = "inclusion_osmpm_2d_fp64_dxB0.05_dxS0.005_M2"
 # Schwarz iterations of one global step of this workload, averaged over the
 # first three global steps of an FP64 oracle run (used to scale the oracle's
 # bounded sample, which runs a fixed number of Schwarz iterations).
-ORACLE_SCHWARZ_ITERS_PER_STEP = 17.0
+ORACLE_SCHWARZ_ITERS_PER_STEP = 12.0
 ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
 # FP64 flops of one Hessian-vector product per particle: gather G (2 d^2 3^d),

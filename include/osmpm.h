@@ -215,6 +215,48 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
                                         int32_t n_threads, osmpm_stats* stats,
                                         osmpm_status* status);
 
+/* Reverse mode, recording.  enable = 1 discards any earlier record and
+ * makes every later osmpm_step of dom keep, in device memory from the
+ * domain's allocator, its input particle state (x, v, B, F), its converged
+ * grid displacement u* and its free-DOF mask (about 12 doubles per particle
+ * and 2-3 per grid node and step, in 2D); enable = 0 stops and frees the
+ * record.  A coupled step (osmpm_schwarz_couple) or osmpm_set_particles on a
+ * recording domain interrupts the record, and osmpm_adjoint then refuses it.
+ * Errors: OSMPM_E_UNSUPPORTED for a mixed-precision domain. */
+osmpm_status osmpm_record(osmpm_domain* dom, int32_t enable);
+
+/* Outputs of osmpm_adjoint: device arrays of the caller, in particle-id
+ * order, particle-major (entry (p, a) at p*dim + a; (p, a, b) at
+ * (p*dim + a)*dim + b).  dJ_dE is required; the adjoints of the state at the
+ * start of the record may be NULL. */
+typedef struct osmpm_adjoint_out {
+  double* dJ_dE;    /* n: dJ / dE_p (Young's modulus of particle p) */
+  double* dJ_dx0;   /* n*dim or NULL */
+  double* dJ_dv0;   /* n*dim or NULL */
+  double* dJ_dB0;   /* n*dim*dim or NULL */
+  double* dJ_dF0;   /* n*dim*dim or NULL */
+} osmpm_adjoint_out;
+
+/* Reverse-mode gradient of an objective J of the particle positions after
+ * the recorded steps (dJ_dx: device, n*dim, id order, particle-major) with
+ * respect to every particle's Young's modulus, through the recorded
+ * backward-Euler steps (Sec. 2.2).  Per step, last to first: the transposed
+ * G2P, F update and advection (Eqs. g2p_v, g2p_B, F_update, advection), one
+ * adjoint PCG K lam = u_bar on the free DOFs with the step's own symmetric
+ * Hessian-vector product (the implicit function theorem at the converged
+ * Newton solve, Sec. 2.2.5; stopped at cg_rtol |u_bar|), the lam-weighted
+ * derivatives of the Newton residual (Eq. grid_residual) with respect to
+ * F_p, the moduli, x_p, the nodal mass and velocity, and the transposed APIC
+ * P2G (Eq. p2g_transfer).  The active node set and the Dirichlet DOFs of each
+ * step are held fixed.  The domain's state is unchanged and the record kept
+ * (several objectives may be differentiated).  fine must be NULL (single
+ * domain); coarse is the recorded domain.  stats: cg_iters and solves of the
+ * adjoint PCGs.  Errors: OSMPM_E_INVALID (null arguments, no or interrupted
+ * record), OSMPM_E_UNSUPPORTED (fine != NULL, mixed precision),
+ * OSMPM_E_NONFINITE, OSMPM_E_CUDA, OSMPM_E_TIMEOUT. */
+osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const double* dJ_dx,
+                           const osmpm_adjoint_out* out, osmpm_stats* stats);
+
 /* Particle count and dimension of a domain. */
 osmpm_status osmpm_get_info(const osmpm_domain* dom, int64_t* n_particles, int32_t* dim);
 

@@ -20,7 +20,7 @@ STAMP = os.path.join(BUILD, "host_arch.txt")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["osmpm_host.cu", "kernels_d2.cu", "kernels_d3.cu", "kernels_d2f.cu", "kernels_d3f.cu",
-           "sort.cu", "noalloc.cu"]
+           "sort.cu", "noalloc.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-diag-suppress=550",

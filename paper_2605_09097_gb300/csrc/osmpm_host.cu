@@ -144,6 +144,17 @@ struct osmpm_domain {
   // point); each PCG grid uses at most 1/pcg_share of the device
   int pcg_share = 1;
 
+  // reverse-mode tape (osmpm_record / osmpm_adjoint): per recorded step its
+  // input particle state, the converged grid displacement and the DOF mask
+  struct TapeStep {
+    void* mem = nullptr;
+    size_t bytes = 0;
+    double dt = 0.0;
+  };
+  bool recording = false, tape_broken = false;
+  std::vector<TapeStep> tape;
+  double* adj = nullptr;  // adjoint work arrays, allocated on first use
+
   // optional CUDA-event timing of the PCG launches (osmpm_set_profiling)
   bool time_hvp = false;
   std::vector<cudaEvent_t> ev;  // one start/stop pair
@@ -180,7 +191,38 @@ osmpm_status dalloc_n(osmpm_domain* d, int64_t count, T** out) {
   return OSMPM_OK;
 }
 
+// Device memory outside the domain's block list (the tape, freed with it).
+osmpm_status raw_alloc(osmpm_domain* d, size_t bytes, void** out) {
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (d->have_alloc) {
+    p = d->alloc.alloc(bytes, d->alloc.ctx, (void*)d->stream);
+    if (!p) return fail(OSMPM_E_NOMEM, "allocator returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMallocAsync(&p, bytes, d->stream);
+    if (e != cudaSuccess) return fail(OSMPM_E_NOMEM, "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  *out = p;
+  return OSMPM_OK;
+}
+
+void raw_free(osmpm_domain* d, void* p, size_t bytes) {
+  if (!p) return;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (d->have_alloc)
+    d->alloc.free(p, bytes, d->alloc.ctx, (void*)d->stream);
+  else
+    cudaFreeAsync(p, d->stream);
+}
+
+void clear_tape(osmpm_domain* d) {
+  for (auto& t : d->tape) raw_free(d, t.mem, t.bytes);
+  d->tape.clear();
+  d->tape_broken = false;
+}
+
 void free_all(osmpm_domain* d) {
+  clear_tape(d);
   for (auto& b : d->blocks) {
     if (d->have_alloc)
       d->alloc.free(b.first, b.second, d->alloc.ctx, (void*)d->stream);
@@ -399,6 +441,8 @@ cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
 // Newton forcing bound: PCG tolerance eta |r0| with eta <= kEtaMax.
 constexpr double kEtaMax = 1e-3;
 
+osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st);
+
 osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, SolveStats& st) {
   const int64_t nn = d->geo.nn;
   const int D = d->dim;
@@ -408,8 +452,16 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, SolveStats
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
                              d->desc.cg_rtol, kEtaMax, first ? 1 : 0, d->desc.cg_max, d->grad,
                              d->diag, d->cx, d->cr, d->cz, d->cp, d->S, d->partials, d->stream));
-  // whole PCG in one cooperative launch: s[1], w[0..2], p and the barrier
-  // counter start at zero; x = 0 and r[0] = -g come from grad_finish
+  return run_pcg(d, dt, true, st);
+}
+
+// The whole PCG in one cooperative launch on a prepared system (x = 0, r[0],
+// the inverted diagonal and the controls in place): s[1], w[0..2], p and the
+// barrier counter start at zero.  With `newton` also reduces max |x| for the
+// Newton stop test.
+osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st) {
+  const int64_t nn = d->geo.nn;
+  const int D = d->dim;
   const size_t vb = sizeof(double) * D * nn;
   CUDA_TRY(cudaMemsetAsync(d->cp1, 0, vb, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->cq, 0, vb, d->stream));
@@ -422,7 +474,7 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, SolveStats
   cudaError_t le = cudaSuccess;
   DISPATCH(d, (le = launch_pcg<K, R>(d, dt, work, timed)));
   if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(le));
-  DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
+  if (newton) DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
   OSMPM_TRY(sync_scalars(d));
   OSMPM_TRY(check_err(d));
   st.cg += d->S_host->cg_iter;
@@ -581,6 +633,47 @@ osmpm_status probe_setup(osmpm_domain* d, double dt, const double* u_host) {
   OSMPM_TRY(upload_grid_vec(d, u_host, d->u));
   OSMPM_TRY(sync_scalars(d));
   return check_err(d);
+}
+
+// Tape slot layout: x, v, B, F (sorted order, component-major), u, DOF mask.
+struct TapeLayout {
+  size_t x, v, B, F, u, mask, bytes;
+  explicit TapeLayout(const osmpm_domain* d) {
+    const size_t D = d->dim, n = (size_t)d->n, nn = (size_t)d->geo.nn;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    x = 0;
+    v = x + up(8 * D * n);
+    B = v + up(8 * D * n);
+    F = B + up(8 * D * D * n);
+    u = F + up(8 * D * D * n);
+    mask = u + up(8 * D * nn);
+    bytes = mask + up(nn);
+  }
+};
+
+osmpm_status tape_begin(osmpm_domain* d, osmpm_domain::TapeStep& slot) {
+  const TapeLayout L(d);
+  const size_t D = d->dim, n = (size_t)d->n;
+  OSMPM_TRY(raw_alloc(d, L.bytes, &slot.mem));
+  slot.bytes = L.bytes;
+  char* b = (char*)slot.mem;
+  CUDA_TRY(cudaMemcpyAsync(b + L.x, d->P.x, 8 * D * n, cudaMemcpyDeviceToDevice, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(b + L.v, d->P.v, 8 * D * n, cudaMemcpyDeviceToDevice, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(b + L.B, d->P.B, 8 * D * D * n, cudaMemcpyDeviceToDevice, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(b + L.F, d->P.F, 8 * D * D * n, cudaMemcpyDeviceToDevice, d->stream));
+  return OSMPM_OK;
+}
+
+osmpm_status tape_end(osmpm_domain* d, osmpm_domain::TapeStep& slot, double dt) {
+  const TapeLayout L(d);
+  const size_t D = d->dim, nn = (size_t)d->geo.nn;
+  char* b = (char*)slot.mem;
+  CUDA_TRY(cudaMemcpyAsync(b + L.u, d->u, 8 * D * nn, cudaMemcpyDeviceToDevice, d->stream));
+  CUDA_TRY(cudaMemcpyAsync(b + L.mask, d->dofmask, nn, cudaMemcpyDeviceToDevice, d->stream));
+  slot.dt = dt;
+  d->tape.push_back(slot);
+  slot.mem = nullptr;
+  return OSMPM_OK;
 }
 
 }  // namespace
@@ -772,17 +865,30 @@ osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
   OSMPM_TRY(check_domain(d));
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(OSMPM_E_INVALID, "dt must be > 0");
   SolveStats st;
+  osmpm_domain::TapeStep slot{};
+  if (d->recording) OSMPM_TRY(tape_begin(d, slot));
+  auto drop = [&](osmpm_status e) {
+    raw_free(d, slot.mem, slot.bytes);
+    return e;
+  };
+#define T_TRY(expr)                       \
+  do {                                    \
+    osmpm_status t_ = (expr);             \
+    if (t_ != OSMPM_OK) return drop(t_);  \
+  } while (0)
   CUDA_TRY(cudaMemsetAsync(d->err, 0, sizeof(int), d->stream));
-  OSMPM_TRY(run_p2g(d, false));
-  OSMPM_TRY(sync_scalars(d));
-  OSMPM_TRY(check_err(d));
-  OSMPM_TRY(prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, nullptr));
-  OSMPM_TRY(cold_start(d, dt));
+  T_TRY(run_p2g(d, false));
+  T_TRY(sync_scalars(d));
+  T_TRY(check_err(d));
+  T_TRY(prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, nullptr));
+  T_TRY(cold_start(d, dt));
   osmpm_status s = newton_solve(d, dt, st);
   if (s != OSMPM_OK) {
     fill_stats(stats, st, 0, 0, 0.0, 0.0);
-    return s;
+    return drop(s);
   }
+  if (slot.mem) T_TRY(tape_end(d, slot, dt));
+#undef T_TRY
   DISPATCH(d, K::g2p(P_, d->geo, d->u, dt, d->stream));
   CUDA_TRY(cudaStreamSynchronize(d->stream));
   CUDA_TRY(cudaGetLastError());
@@ -811,6 +917,9 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   const int M = sd->M;
   const double dt = dT / M;
   const int D = B->dim;
+  // a coupled step is not recorded: a tape that it interrupts is unusable
+  if (B->recording) B->tape_broken = true;
+  if (S->recording) S->tape_broken = true;
   const GridGeo &gB = B->geo, &gS = S->geo;
   cudaStream_t s = B->stream;
   SolveStats st;
@@ -960,6 +1069,115 @@ osmpm_status osmpm_get_counters(const osmpm_domain* d, osmpm_counters* out) {
   return OSMPM_OK;
 }
 
+osmpm_status osmpm_record(osmpm_domain* d, int32_t enable) {
+  OSMPM_TRY(check_domain(d));
+  if (enable && d->prec != 0)
+    return fail(OSMPM_E_UNSUPPORTED, "reverse mode needs a precision 0 (FP64) domain");
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  clear_tape(d);
+  d->recording = enable != 0;
+  return OSMPM_OK;
+}
+
+#define ADJ(d, call)                     \
+  do {                                   \
+    if ((d)->dim == 2) {                 \
+      using AK = AdjointKernels<2>;      \
+      call;                              \
+    } else {                             \
+      using AK = AdjointKernels<3>;      \
+      call;                              \
+    }                                    \
+  } while (0)
+
+osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const double* dJ_dx,
+                           const osmpm_adjoint_out* out, osmpm_stats* stats) {
+  OSMPM_TRY(check_domain(coarse));
+  if (fine) return fail(OSMPM_E_UNSUPPORTED, "the coupled (Schwarz) adjoint is not built");
+  osmpm_domain* d = coarse;
+  if (!dJ_dx || !out || !out->dJ_dE) return fail(OSMPM_E_INVALID, "null dJ_dx or dJ_dE");
+  if (d->prec != 0) return fail(OSMPM_E_UNSUPPORTED, "reverse mode needs a precision 0 (FP64) domain");
+  if (d->tape_broken)
+    return fail(OSMPM_E_INVALID, "the tape was interrupted (a coupled step or set_particles while recording)");
+  if (d->tape.empty()) return fail(OSMPM_E_INVALID, "nothing recorded (osmpm_record, then osmpm_step)");
+  const int D = d->dim, DD = D * D;
+  const int64_t n = d->n, nn = d->geo.nn;
+  cudaStream_t s = d->stream;
+  if (!d->adj) OSMPM_TRY(dalloc_n(d, (int64_t)(2 * (2 * D + 2 * DD) + 1) * n + (2 * D + 1) * nn, &d->adj));
+  double* xb = d->adj;
+  double* vb = xb + D * n;
+  double* Bb = vb + D * n;
+  double* Fb = Bb + DD * n;
+  double* xb2 = Fb + DD * n;
+  double* vb2 = xb2 + D * n;
+  double* Bb2 = vb2 + D * n;
+  double* Fb2 = Bb2 + DD * n;
+  double* Eb = Fb2 + DD * n;
+  double* ubar = Eb + n;
+  double* qbar = ubar + D * nn;
+  double* mbar = qbar + D * nn;
+  SolveStats st;
+  CUDA_TRY(cudaMemsetAsync(d->err, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(vb, 0, sizeof(double) * (D + 2 * DD) * n, s));
+  CUDA_TRY(cudaMemsetAsync(Eb, 0, sizeof(double) * n, s));
+  ADJ(d, AK::from_ids(n, D, d->P.id, dJ_dx, xb, s));
+  // the state after the last recorded step comes back at the end
+  OSMPM_TRY(snapshot(d, false));
+  const TapeLayout TL(d);
+  osmpm_status status = OSMPM_OK;
+  for (size_t k = d->tape.size(); k-- > 0 && status == OSMPM_OK;) {
+    const auto& t = d->tape[k];
+    const char* b = (const char*)t.mem;
+    const double dt = t.dt;
+    CUDA_TRY(cudaMemcpyAsync(d->P.x, b + TL.x, 8 * D * n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d->P.v, b + TL.v, 8 * D * n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d->P.B, b + TL.B, 8 * DD * n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d->P.F, b + TL.F, 8 * DD * n, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d->u, b + TL.u, 8 * D * nn, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(d->dofmask, b + TL.mask, nn, cudaMemcpyDeviceToDevice, s));
+    // the step's grid (m, v^n) and stencil cache
+    status = run_p2g(d, false);
+    if (status != OSMPM_OK) break;
+    // 1. transposed G2P, F update and advection
+    CUDA_TRY(cudaMemsetAsync(ubar, 0, sizeof(double) * D * nn, s));
+    ADJ(d, AK::g2p(n, d->P.x, (const double*)d->P.F, d->geo, d->u, dt, xb, vb, Bb, Fb, ubar, xb2, Fb2, s));
+    // 2. K lam = u_bar with the Hessian at the converged u (implicit function theorem)
+    CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, s));
+    CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, s));
+    DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, s));
+    ADJ(d, AK::rhs(d->geo, d->m, d->dofmask, dt, d->desc.cg_rtol, d->desc.cg_max, ubar, d->diag,
+                   d->cx, d->cr, d->cz, d->cp, d->S, d->partials, s));
+    status = run_pcg(d, dt, false, st);
+    if (status != OSMPM_OK) break;
+    st.solves++;
+    // 3. -lam . dg/dz for the particle and node inputs of the solve
+    ADJ(d, AK::solve(n, d->P.x, (const double*)d->P.F, d->P.mu, d->P.lam, d->P.vol0, d->geo, d->u,
+                     d->cx, xb2, Fb2, Eb, d->err, s));
+    ADJ(d, AK::nodes(d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt, qbar, mbar, s));
+    // 4. transposed P2G
+    ADJ(d, AK::p2g(n, d->P.x, (const double*)d->P.v, (const double*)d->P.B, d->P.mass, d->geo, qbar,
+                   mbar, vb2, Bb2, xb2, s));
+    std::swap(xb, xb2);
+    std::swap(vb, vb2);
+    std::swap(Bb, Bb2);
+    std::swap(Fb, Fb2);
+  }
+  const osmpm_status restored = snapshot(d, true);
+  if (status != OSMPM_OK) return status;
+  OSMPM_TRY(restored);
+  ADJ(d, AK::to_ids(n, 1, d->P.id, Eb, out->dJ_dE, s));
+  if (out->dJ_dx0) ADJ(d, AK::to_ids(n, D, d->P.id, xb, out->dJ_dx0, s));
+  if (out->dJ_dv0) ADJ(d, AK::to_ids(n, D, d->P.id, vb, out->dJ_dv0, s));
+  if (out->dJ_dB0) ADJ(d, AK::to_ids(n, DD, d->P.id, Bb, out->dJ_dB0, s));
+  if (out->dJ_dF0) ADJ(d, AK::to_ids(n, DD, d->P.id, Fb, out->dJ_dF0, s));
+  OSMPM_TRY(sync_scalars(d));
+  OSMPM_TRY(check_err(d));
+  CUDA_TRY(cudaGetLastError());
+  fill_stats(stats, st, 0, 1, 0.0, 0.0);
+  return OSMPM_OK;
+}
+#undef ADJ
+
 osmpm_status osmpm_check_wait_timeout(void* cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   void* mem = nullptr;
@@ -1063,6 +1281,7 @@ osmpm_status osmpm_set_particles(osmpm_domain* d, const double* x, const double*
   const int64_t n = d->n;
   if (!finite_all(x, D * n) || !finite_all(v, D * n) || !finite_all(B, D * D * n) || !finite_all(F, D * D * n))
     return fail(OSMPM_E_NONFINITE, "non-finite particle input");
+  if (d->recording) d->tape_broken = true;  // the recorded steps no longer lead here
   // materials and ids back to id order in A, then the new kinematic state
   DISPATCH(d, K::scatter_by_id(P_, A_, d->stream));
   OSMPM_TRY(upload_state(d, x, v, B, F));

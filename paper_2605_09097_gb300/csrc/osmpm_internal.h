@@ -39,6 +39,32 @@ struct PrepArgs {
   uint8_t* physmask;    // 1 where a physical rule fixes a component (written), may be null
 };
 
+// Launchers of the reverse-mode kernels (FP64 only; osmpm_adjoint.cuh).
+template <int D>
+struct AdjointKernels {
+  static void g2p(int64_t n, const double* x, const double* F, const GridGeo& g, const double* u,
+                  double dt, const double* xb, const double* vb, const double* Bb,
+                  const double* Fb, double* ubar, double* xb_out, double* Fb_out, cudaStream_t s);
+  static void rhs(const GridGeo& g, const double* m, const uint8_t* dofmask, double dt,
+                  double cg_rtol, int cg_max, const double* ubar, double* diag, double* x,
+                  double* r, double* z, double* p, DevScalars* S, double* partials,
+                  cudaStream_t s);
+  static void solve(int64_t n, const double* x, const double* F, const double* mu,
+                    const double* lam, const double* vol0, const GridGeo& g, const double* u,
+                    const double* lamg, double* xb, double* Fb, double* Eb, int* err,
+                    cudaStream_t s);
+  static void nodes(const GridGeo& g, const double* m, const double* vn, const double* u,
+                    const double* lamg, const double* gravity, double dt, double* qbar,
+                    double* mbar, cudaStream_t s);
+  static void p2g(int64_t n, const double* x, const double* v, const double* B,
+                  const double* mass, const GridGeo& g, const double* qbar, const double* mbar,
+                  double* vb_out, double* Bb_out, double* xb, cudaStream_t s);
+  static void from_ids(int64_t n, int w, const uint32_t* id, const double* src, double* dst,
+                       cudaStream_t s);
+  static void to_ids(int64_t n, int w, const uint32_t* id, const double* src, double* dst,
+                     cudaStream_t s);
+};
+
 template <int D, typename R>
 struct Kernels {
   static void morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,

@@ -115,6 +115,11 @@ class osmpm_noalloc_particles(Structure):
                 ("mu", c_void_p), ("lam", c_void_p)]
 
 
+class osmpm_adjoint_out(Structure):
+    _fields_ = [("dJ_dE", c_void_p), ("dJ_dx0", c_void_p), ("dJ_dv0", c_void_p),
+                ("dJ_dB0", c_void_p), ("dJ_dF0", c_void_p)]
+
+
 _DP = POINTER(c_double)
 _sig = {
     "osmpm_create_domain": (c_int32, [POINTER(osmpm_domain_desc), POINTER(osmpm_particles_in),
@@ -138,6 +143,9 @@ _sig = {
     "osmpm_set_profiling": (c_int32, [c_void_p, c_int32]),
     "osmpm_get_counters": (c_int32, [c_void_p, POINTER(osmpm_counters)]),
     "osmpm_check_wait_timeout": (c_int32, [c_void_p]),
+    "osmpm_record": (c_int32, [c_void_p, c_int32]),
+    "osmpm_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(osmpm_adjoint_out),
+                                POINTER(osmpm_stats)]),
     "osmpm_energy_change_noalloc": (c_int32, [POINTER(osmpm_noalloc_grid),
                                               POINTER(osmpm_noalloc_particles), c_double,
                                               c_double, c_void_p, c_void_p]),
@@ -255,6 +263,7 @@ class Domain:
                  device: int = 0):
         p = spec.particles
         self.spec = spec
+        self.device = device
         self.dim = spec.grid.dim
         self.n = p.n
         self._arrays = [np.ascontiguousarray(a, dtype=np.float64) for a in
@@ -298,6 +307,33 @@ class Domain:
         st = osmpm_stats()
         _check(_lib.osmpm_step(self.h, dt, ctypes.byref(st)), "osmpm_step")
         return st.as_dict()
+
+    def record(self, enable: bool = True) -> None:
+        _check(_lib.osmpm_record(self.h, 1 if enable else 0), "osmpm_record")
+
+    def adjoint(self, dJ_dx, initial_state: bool = False):
+        """dJ/dE for dJ_dx = dJ/dx after the recorded steps (a CUDA float64
+        tensor (n, dim), id order).  Returns (dJ_dE, adjoints of the recorded
+        start state as a dict of tensors when ``initial_state``, stats)."""
+        import torch
+        n, d = self.n, self.dim
+        if dJ_dx.dtype != torch.float64 or not dJ_dx.is_cuda or tuple(dJ_dx.shape) != (n, d):
+            raise ValueError("dJ_dx must be a CUDA float64 tensor of shape (n, dim)")
+        g = dJ_dx.contiguous()
+        torch.cuda.synchronize(g.device)
+        dE = torch.empty(n, dtype=torch.float64, device=g.device)
+        out = osmpm_adjoint_out()
+        out.dJ_dE = dE.data_ptr()
+        state = {}
+        if initial_state:
+            shapes = {"x": (n, d), "v": (n, d), "B": (n, d, d), "F": (n, d, d)}
+            for k, shp in shapes.items():
+                state[k] = torch.empty(shp, dtype=torch.float64, device=g.device)
+                setattr(out, f"dJ_d{k}0", state[k].data_ptr())
+        st = osmpm_stats()
+        _check(_lib.osmpm_adjoint(self.h, None, c_void_p(g.data_ptr()), ctypes.byref(out),
+                                  ctypes.byref(st)), "osmpm_adjoint")
+        return dE, state, st.as_dict()
 
     def get_particles(self):
         n, d = self.n, self.dim
@@ -388,6 +424,56 @@ def osmpm_energy_change_noalloc(grid: osmpm_noalloc_grid, parts: osmpm_noalloc_p
 def osmpm_check_wait_timeout(stream: int) -> int:
     """Runs the bounded-wait diagnostic; returns the status code."""
     return _lib.osmpm_check_wait_timeout(c_void_p(stream))
+
+
+def osmpm_record(dom: Domain, enable: bool = True) -> None:
+    dom.record(enable)
+
+
+def osmpm_adjoint(coarse: Domain, fine: Optional[Domain], dJ_dx, initial_state: bool = False):
+    """Reverse-mode gradient through the steps recorded on ``coarse``
+    (single domain: ``fine`` must be None)."""
+    if fine is not None:
+        _check(_lib.osmpm_adjoint(coarse.h, fine.h, None, None, None), "osmpm_adjoint")
+    return coarse.adjoint(dJ_dx, initial_state)
+
+
+def _trajectory_function():
+    import torch
+
+    class Trajectory(torch.autograd.Function):
+        """x_final = steps(E): n_steps backward-Euler steps of a domain built
+        from ``spec`` with per-particle Young's moduli E (a float64 tensor in
+        id order); backward is one osmpm_adjoint over the recorded steps."""
+
+        @staticmethod
+        def forward(ctx, E, spec, n_steps, dt):
+            import dataclasses
+            p = spec.particles.copy()
+            p.E = E.detach().to("cpu", torch.float64).numpy().copy()
+            dom = Domain(dataclasses.replace(spec, particles=p))
+            dom.record(True)
+            for _ in range(n_steps):
+                dom.step(dt)
+            x = dom.get_particles()[0]
+            ctx.dom = dom
+            ctx.E_device = E.device
+            return torch.from_numpy(x).to(E.device)
+
+        @staticmethod
+        def backward(ctx, gx):
+            dom = ctx.dom
+            dE, _, _ = dom.adjoint(gx.to(f"cuda:{dom.device}", torch.float64).contiguous())
+            dom.close()
+            return dE.to(ctx.E_device), None, None, None
+
+    return Trajectory
+
+
+def trajectory(E, spec, n_steps: int, dt: float):
+    """Differentiable final positions (n, dim) after n_steps steps of dt with
+    Young's moduli E: torch.autograd.Function backed by osmpm_adjoint."""
+    return _trajectory_function().apply(E, spec, n_steps, dt)
 
 
 def launch_count() -> int:

@@ -1,0 +1,195 @@
+"""The CUDA reverse mode (osmpm_record / osmpm_adjoint) against the oracle's
+adjoint and against central differences of the CUDA forward steps."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import adjoint as AD
+from oracle import osmpm_oracle as O
+from paper_2605_09097_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osmpm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_09097_gb300 import build
+    build.build()
+    from paper_2605_09097_gb300 import osmpm as m
+    return m
+
+
+def _spec(dim, seed, tight=True):
+    """A perturbed block with varying moduli, gravity and a clamped face."""
+    rng = np.random.default_rng(seed)
+    n_cells = (6, 4, 3)[:dim]
+    g = (0.0, -9.81, 0.0)[:dim]
+    spec = W.perturb(W.block(dim, n_cells=n_cells, dx=0.1, E=1e5, gravity=g), seed,
+                     v_scale=0.2, B_scale=0.01, F_scale=0.02)
+    spec.particles.E = spec.particles.E * (1.0 + 0.5 * rng.random(spec.particles.E.shape))
+    clamp = W.Dirichlet(lo=(-W.BIG,) * dim, hi=(0.05,) + (W.BIG,) * (dim - 1),
+                        comp_mask=(1 << dim) - 1)
+    spec = dataclasses.replace(spec, dirichlet=[clamp])
+    if tight:
+        spec = dataclasses.replace(spec, newton_tol=1e-12, cg_rtol=1e-12, cg_max=100000)
+    return spec, rng
+
+
+def _gpu_gradient(osmpm, spec, dt, n_steps, c, initial_state=False):
+    import torch
+    dom = osmpm.Domain(spec)
+    dom.record(True)
+    for _ in range(n_steps):
+        dom.step(dt)
+    x = dom.get_particles()[0]
+    g = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+    dE, state, st = dom.adjoint(g, initial_state)
+    out = {k: v.cpu().numpy() for k, v in state.items()}
+    return x, dE.cpu().numpy(), out, st, dom
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adjoint_matches_oracle(osmpm, dim):
+    spec, rng = _spec(dim, 21 + dim)
+    dt, n_steps = 0.01, 3
+    n = spec.particles.x.shape[0]
+    c = rng.standard_normal((n, dim))
+    x, dE, st0, st, _ = _gpu_gradient(osmpm, spec, dt, n_steps, c, initial_state=True)
+    op, oE, obar = AD.trajectory_gradient(spec, dt, n_steps, c, newton_tol=1e-13)
+    assert _rel(x, op.x) <= 1e-10
+    assert st["solves"] == n_steps and st["cg_iters"] > 0
+    assert _rel(dE, oE) <= 1e-7
+    assert _rel(st0["x"], obar.x) <= 1e-7
+    assert _rel(st0["v"], obar.v) <= 1e-7
+    assert _rel(st0["B"], obar.B) <= 1e-7
+    assert _rel(st0["F"], obar.F) <= 1e-7
+
+
+def test_adjoint_matches_central_differences_of_the_cuda_path(osmpm):
+    spec, rng = _spec(2, 5)
+    dt, n_steps = 0.01, 2
+    n = spec.particles.x.shape[0]
+    c = rng.standard_normal((n, 2))
+    _, dE, _, _, _ = _gpu_gradient(osmpm, spec, dt, n_steps, c)
+
+    def J(E):
+        p = spec.particles.copy()
+        p.E = E
+        dom = osmpm.Domain(dataclasses.replace(spec, particles=p))
+        for _ in range(n_steps):
+            dom.step(dt)
+        return float(np.sum(c * dom.get_particles()[0]))
+
+    for p in rng.choice(n, 4, replace=False):
+        h = 1e-4 * spec.particles.E[p]
+        Ep, Em = spec.particles.E.copy(), spec.particles.E.copy()
+        Ep[p] += h
+        Em[p] -= h
+        fd = (J(Ep) - J(Em)) / (2 * h)
+        np.testing.assert_allclose(dE[p], fd, rtol=1e-5, atol=1e-6 * np.abs(dE).max())
+
+
+def test_recording_leaves_the_forward_unchanged(osmpm):
+    """Recording copies state only.  (Two runs of the forward agree to
+    round-off, not bit for bit: the scatters sum with atomics.)"""
+    spec, _ = _spec(2, 9, tight=False)
+    a, b = osmpm.Domain(spec), osmpm.Domain(spec)
+    b.record(True)
+    for _ in range(3):
+        sa = a.step(0.01)
+        sb = b.step(0.01)
+        assert sa["newton_iters"] == sb["newton_iters"]
+    np.testing.assert_allclose(a.get_particles()[0], b.get_particles()[0], rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(a.get_particles()[3], b.get_particles()[3], rtol=1e-12, atol=1e-14)
+
+
+def test_adjoint_keeps_the_state_and_the_record(osmpm):
+    """Two objectives in a row from one record; the state is untouched."""
+    import torch
+    spec, rng = _spec(2, 13)
+    n = spec.particles.x.shape[0]
+    dom = osmpm.Domain(spec)
+    dom.record(True)
+    dom.step(0.01)
+    dom.step(0.01)
+    before = dom.get_particles()
+    c1 = torch.from_numpy(rng.standard_normal((n, 2))).cuda()
+    c2 = torch.from_numpy(rng.standard_normal((n, 2))).cuda()
+    g1 = dom.adjoint(c1)[0].cpu().numpy()
+    g2 = dom.adjoint(c2)[0].cpu().numpy()
+    g12 = dom.adjoint(c1 + c2)[0].cpu().numpy()
+    after = dom.get_particles()
+    for u, v in zip(before, after):
+        np.testing.assert_array_equal(u, v)
+    # linear in dJ/dx
+    np.testing.assert_allclose(g12, g1 + g2, rtol=1e-7, atol=1e-9 * np.abs(g12).max())
+
+
+def test_autograd_function_gives_the_adjoint(osmpm):
+    import torch
+    spec, rng = _spec(2, 17)
+    n = spec.particles.x.shape[0]
+    dt, n_steps = 0.01, 2
+    c = rng.standard_normal((n, 2))
+    E = torch.tensor(spec.particles.E, dtype=torch.float64, device="cuda", requires_grad=True)
+    x = osmpm.trajectory(E, spec, n_steps, dt)
+    J = (x * torch.from_numpy(c).cuda()).sum()
+    J.backward()
+    _, dE, _, _, _ = _gpu_gradient(osmpm, spec, dt, n_steps, c)
+    # two forward runs agree to round-off (atomic scatters), not bit for bit
+    np.testing.assert_allclose(E.grad.cpu().numpy(), dE, rtol=1e-9, atol=1e-12 * np.abs(dE).max())
+
+
+def test_cantilever_tip_gradient_matches_oracle(osmpm):
+    """The 2560-particle cantilever under gravity, 6 steps of 0.05 s (inside
+    the first swing, period about 1.9 s): gradient of the mean tip deflection
+    with respect to every particle's modulus."""
+    spec = dataclasses.replace(W.cantilever(), newton_tol=1e-10, cg_rtol=1e-12, cg_max=100000)
+    x0 = spec.particles.x
+    n = x0.shape[0]
+    tip = x0[:, 0] > 0.98
+    c = np.zeros((n, 2))
+    c[tip, 1] = -1.0 / tip.sum()
+    dt, n_steps = 0.05, 6
+    _, dE, _, st, _ = _gpu_gradient(osmpm, spec, dt, n_steps, c)
+    _, oE, _ = AD.trajectory_gradient(spec, dt, n_steps, c, newton_tol=1e-11)
+    assert _rel(dE, oE) <= 1e-6
+    # a stiffer beam deflects less: the total sensitivity is negative
+    assert np.sum(dE * spec.particles.E) < 0
+
+
+def test_adjoint_errors(osmpm):
+    import torch
+    spec, _ = _spec(2, 3, tight=False)
+    n = spec.particles.x.shape[0]
+    g = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
+    dom = osmpm.Domain(spec)
+    with pytest.raises(osmpm.OsmpmError) as e:
+        dom.adjoint(g)                                  # nothing recorded
+    assert e.value.status == osmpm.OSMPM_E_INVALID
+    dom.record(True)
+    dom.step(0.01)
+    x, v, B, F = dom.get_particles()
+    dom.set_particles(x, v, B, F)                       # interrupts the record
+    with pytest.raises(osmpm.OsmpmError) as e:
+        dom.adjoint(g)
+    assert e.value.status == osmpm.OSMPM_E_INVALID
+    dom.record(True)                                    # a fresh record works again
+    dom.step(0.01)
+    dom.adjoint(g)
+    other = osmpm.Domain(spec)
+    with pytest.raises(osmpm.OsmpmError) as e:
+        osmpm.osmpm_adjoint(dom, other, g)              # coupled adjoint not built
+    assert e.value.status == osmpm.OSMPM_E_UNSUPPORTED
+    mixed = osmpm.Domain(dataclasses.replace(spec, precision=1))
+    with pytest.raises(osmpm.OsmpmError) as e:
+        mixed.record(True)
+    assert e.value.status == osmpm.OSMPM_E_UNSUPPORTED
