@@ -224,6 +224,7 @@ def run_ours(args, rank, local, world):
         cS_ = S.counters()
         B.set_profiling(False)
         S.set_profiling(False)
+        adj = adjoint_cost(osmpm, stream) if rank == 0 else None
 
         # end to end through the public API with host buffers
         e2e = None
@@ -291,10 +292,56 @@ def run_ours(args, rank, local, world):
                      "flops_per_particle_iter": HVP_FLOPS_PER_PARTICLE[2]},
         "clocks": clk,
         "e2e": e2e,
+        "adjoint": adj,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(ORACLE_SAMPLE_ITERS)
     return out
+
+
+ADJ_STEPS, ADJ_DT = 20, 1e-3
+
+
+def adjoint_cost(osmpm, stream):
+    """Reverse-mode cost per forward step on the single-domain cantilever
+    (2560 particles, FP64): CUDA-event times of ADJ_STEPS plain steps, of the
+    same steps while recording, and of one osmpm_adjoint over the record
+    (J = mean tip deflection)."""
+    import torch
+    spec = W.cantilever()
+    x0 = spec.particles.x
+    tip = x0[:, 0] > 0.98
+    c = np.zeros_like(x0)
+    c[tip, 1] = -1.0 / tip.sum()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), r
+
+    def steps(dom):
+        for _ in range(ADJ_STEPS):
+            dom.step(ADJ_DT)
+
+    plain = osmpm.Domain(spec, stream=stream.cuda_stream)
+    ms_plain, _ = timed(lambda: steps(plain))
+    rec = osmpm.Domain(spec, stream=stream.cuda_stream)
+    rec.record(True)
+    ms_rec, _ = timed(lambda: steps(rec))
+    g = torch.from_numpy(c).cuda()
+    ms_adj, (_, _, st) = timed(lambda: rec.adjoint(g))
+    rec.record(False)
+    return {"workload": f"cantilever_2d_fp64 ({x0.shape[0]} particles), {ADJ_STEPS} steps of "
+                        f"{ADJ_DT:g} s, J = mean tip deflection",
+            "forward_ms_per_step": ms_plain / ADJ_STEPS,
+            "recording_ms_per_step": ms_rec / ADJ_STEPS,
+            "adjoint_ms_per_step": ms_adj / ADJ_STEPS,
+            "adjoint_over_forward": ms_adj / ms_plain,
+            "adjoint_cg_iters": st["cg_iters"]}
 
 
 # ----------------------------------------------------------------------------

@@ -85,7 +85,9 @@ typedef struct osmpm_domain_desc {
   int32_t cg_max;           /* PCG iteration cap per Newton iteration */
   int32_t ls_max;           /* line search tries alpha = 1, 1/2, ..., 2^-ls_max */
   double mass_eps;          /* active nodes (the set N of Sec. 3.2.1): m_i > mass_eps >= 0 */
-  int32_t reserved[8];      /* must be zero */
+  double cg_eta_max;        /* inexact Newton: PCG stops at eta |r_0|, eta = |g_k|/|g_0|
+                               clamped to [cg_rtol, cg_eta_max]; 0 means 1e-3; < 1 */
+  int32_t reserved[6];      /* must be zero */
 } osmpm_domain_desc;
 
 /* Initial particle state, host arrays in id order (layouts above).  flags

@@ -438,7 +438,8 @@ cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
   return cudaSuccess;
 }
 
-// Newton forcing bound: PCG tolerance eta |r0| with eta <= kEtaMax.
+// Newton forcing bound: PCG tolerance eta |r0| with eta <= cg_eta_max
+// (default kEtaMax).
 constexpr double kEtaMax = 1e-3;
 
 osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st);
@@ -450,7 +451,8 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, SolveStats
   CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
   DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
-                             d->desc.cg_rtol, kEtaMax, first ? 1 : 0, d->desc.cg_max, d->grad,
+                             d->desc.cg_rtol, d->desc.cg_eta_max > 0.0 ? d->desc.cg_eta_max : kEtaMax,
+                             first ? 1 : 0, d->desc.cg_max, d->grad,
                              d->diag, d->cx, d->cr, d->cz, d->cp, d->S, d->partials, d->stream));
   return run_pcg(d, dt, true, st);
 }
@@ -469,7 +471,9 @@ osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st) {
   CUDA_TRY(cudaMemsetAsync(d->cw2, 0, vb, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->cpp, 0, vb, d->stream));
   CUDA_TRY(cudaMemsetAsync(&d->S->bar_count, 0, sizeof(unsigned), d->stream));
-  const int64_t work = std::max<int64_t>(d->n, D * nn);
+  // threads: one per DOF, and LPP lanes per particle (GP particles per warp)
+  const int GP = 32 / (D == 2 ? 3 : 9);
+  const int64_t work = std::max<int64_t>((d->n + GP - 1) / GP * 32, D * nn);
   const bool timed = d->time_hvp && !d->ev.empty();
   cudaError_t le = cudaSuccess;
   DISPATCH(d, (le = launch_pcg<K, R>(d, dt, work, timed)));
@@ -693,8 +697,10 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   if (desc->dim != 2 && desc->dim != 3) return fail(OSMPM_E_INVALID, "dim must be 2 or 3");
   if (desc->precision != 0 && desc->precision != 1)
     return fail(OSMPM_E_INVALID, "precision must be 0 (FP64) or 1 (mixed)");
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 6; ++i)
     if (desc->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
+  if (!(desc->cg_eta_max >= 0.0 && desc->cg_eta_max < 1.0))
+    return fail(OSMPM_E_INVALID, "cg_eta_max must be in [0, 1)");
   if (!(desc->dx > 0.0) || !std::isfinite(desc->dx)) return fail(OSMPM_E_INVALID, "dx must be > 0");
   int64_t nn = 1;
   for (int a = 0; a < desc->dim; ++a) {

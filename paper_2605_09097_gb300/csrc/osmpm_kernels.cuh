@@ -1155,7 +1155,10 @@ void Kernels<D, R>::pcg_shape(int64_t work, int share, int* blocks, int* threads
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&i.sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&i.per_sm256, k_pcg<D, R>, 256, 0);
+    int one = 1, many = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&one, k_pcg<D, R, true>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&many, k_pcg<D, R, false>, 256, 0);
+    i.per_sm256 = one < many ? one : many;
     if (i.per_sm256 < 1) i.per_sm256 = 1;
     if (i.sms < 1) i.sms = 1;
     return i;
@@ -1179,7 +1182,14 @@ cudaError_t Kernels<D, R>::pcg(const PcgArgsT<R>& a, int blocks, int threads, cu
   PcgArgsT<R> copy = a;
   void* args[] = {(void*)&copy};
   g_launch_count += 1;
-  return cudaLaunchCooperativeKernel((const void*)k_pcg<D, R>, dim3(blocks), dim3(threads), args, 0, s);
+  // the single-pass variant when every thread owns at most one DOF and every
+  // lane at most one particle
+  const int64_t ndof = a.g.nn * D;
+  const int64_t chunk = (ndof + blocks - 1) / blocks;
+  const int64_t groups = (a.P.n + HvpGroup<D>::GP - 1) / HvpGroup<D>::GP;
+  const bool one = chunk <= threads && groups <= (int64_t)blocks * threads / 32;
+  const void* fn = one ? (const void*)k_pcg<D, R, true> : (const void*)k_pcg<D, R, false>;
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
 }
 
 template <int D, typename R>

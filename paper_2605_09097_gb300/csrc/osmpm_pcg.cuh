@@ -7,7 +7,8 @@
 //   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s.
 // Phase k (after barrier k) does the owner updates above and, in the same
 // phase, the particle Hessian-vector product w_{k+1} = A u_{k+1}: each
-// particle gathers u_{k+1} at its stencil as (r_k - alpha (w_k + beta
+// particle (a group of lanes, one per stencil row) gathers u_{k+1} at its
+// stencil as (r_k - alpha (w_k + beta
 // s_{k-1})) D^-1 from buffers that were complete at barrier k (r and s
 // double-buffered, w triple-buffered), and delta_{k+1} = u.Au is the
 // particle quadratic form sum_p G:LG plus sum m/dt^2 u^2, so it does not
@@ -100,118 +101,307 @@ __device__ __forceinline__ int64_t stencil_offset(const GridGeo& g, int k) {
   return D == 2 ? ox + oy * g.res[0] : ox + (oy + oz * g.res[1]) * (int64_t)g.res[0];
 }
 
-// Particle Hessian-vector product in arithmetic type R: gathers u at the
-// stencil through `ufun(j)` (j = flat DOF index), scatters (L G) grad N_i
-// into w on the free DOFs and returns the quadratic form G : L G.
-template <int D, typename R, class UF>
-__device__ __forceinline__ double particle_hvp(const PcgArgsT<R>& a, int64_t pi, UF ufun, double* w) {
+// Particle Hessian-vector product in arithmetic type R, spread over a group
+// of LPP lanes per particle: lane q owns the stencil row of nodes
+// k = 3q .. 3q+2 (x fastest).  Each lane gathers u at its nodes through
+// `ufun(j)` (j = flat DOF index) into a partial G = sum u grad N^T; the
+// group sums the partials in lane order (every lane gets the same G), lane q
+// forms the rows i = q, q + LPP, ... of Y = L G, the rows are broadcast, and
+// each lane scatters (Y grad N_k) onto the free DOFs of its nodes.  Returns
+// this lane's share of the quadratic form G : L G (its rows).  All lanes of
+// the warp must call it together (it shuffles); lanes with valid = false
+// take part without loading or writing.
+template <int D>
+struct HvpGroup {
+  static constexpr int LPP = (D == 2) ? 3 : 9;  // lanes per particle (stencil rows)
+  static constexpr int GP = 32 / LPP;           // particles per warp
+};
+
+// One lane's share of a particle: the nodes of its stencil row, their grad N
+// and its rows i = q, q + LPP, ... of the particle's Hessian block L.
+template <int D, typename R>
+struct LaneData {
+  static constexpr int DD = D * D;
+  static constexpr int ROWS = (DD + HvpGroup<D>::LPP - 1) / HvpGroup<D>::LPP;
+  int64_t node[3];
+  R dN[3][D];
+  R L[ROWS][DD];
+};
+
+template <int D, typename R>
+__device__ __forceinline__ void load_lane(const PcgArgsT<R>& a, int64_t pi, bool valid, int q,
+                                          LaneData<D, R>& ld) {
   constexpr int DD = D * D;
   constexpr int K = (D == 2) ? 9 : 27;
-  const GridGeo& g = a.g;
+  constexpr int LPP = HvpGroup<D>::LPP;
+  if (!valid) return;
   const int64_t base = a.sbase[pi];
-  R dN[K][D];
 #pragma unroll
-  for (int k = 0; k < K; ++k)
+  for (int j = 0; j < 3; ++j) {
+    const int k = 3 * q + j;
+    ld.node[j] = base + stencil_offset<D>(a.g, k);
 #pragma unroll
-    for (int c = 0; c < D; ++c) dN[k][c] = a.sdn[(int64_t)(c * K + k) * a.P.n + pi];
+    for (int c = 0; c < D; ++c) ld.dN[j][c] = a.sdn[(int64_t)(c * K + k) * a.P.n + pi];
+  }
+#pragma unroll
+  for (int r = 0; r < LaneData<D, R>::ROWS; ++r) {
+    const int i = q + r * LPP;
+#pragma unroll
+    for (int j = 0; j < DD; ++j)
+      ld.L[r][j] = i < DD ? a.L[(int64_t)Sym<D>::idx(i, j) * a.P.n + pi] : R(0);
+  }
+}
+
+template <int D, typename R, class UF>
+__device__ __forceinline__ double group_hvp_lane(const PcgArgsT<R>& a, const LaneData<D, R>& ld,
+                                                 bool valid, int q, int leader, UF ufun, double* w) {
+  constexpr int DD = D * D;
+  constexpr int LPP = HvpGroup<D>::LPP;
+  const GridGeo& g = a.g;
   R G[DD];
 #pragma unroll
   for (int e = 0; e < DD; ++e) G[e] = R(0);
+  if (valid) {
+    R uv[3][D];
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int64_t node = base + stencil_offset<D>(g, k);
+    for (int j = 0; j < 3; ++j)
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      const R uv = (R)ufun(c * g.nn + node);
+      for (int c = 0; c < D; ++c) uv[j][c] = (R)ufun(c * g.nn + ld.node[j]);
 #pragma unroll
-      for (int b = 0; b < D; ++b) G[c * D + b] += uv * dN[k][b];
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int b = 0; b < D; ++b) G[c * D + b] += uv[j][c] * ld.dN[j][b];
+  }
+  // the group's G, summed in lane order
+#pragma unroll
+  for (int e = 0; e < DD; ++e) {
+    R t = __shfl_sync(kFull, G[e], leader);
+#pragma unroll
+    for (int l = 1; l < LPP; ++l) t += __shfl_sync(kFull, G[e], leader + l);
+    G[e] = t;
+  }
+  // this lane's rows of Y = L G, then every row from its owner lane
+  R Ymine[DD];
+  double qf = 0.0;
+#pragma unroll
+  for (int i = 0; i < DD; ++i) Ymine[i] = R(0);
+  if (valid) {
+#pragma unroll
+    for (int r = 0; r < LaneData<D, R>::ROWS; ++r) {
+      const int i = q + r * LPP;
+      if (i < DD) {
+        R t = R(0);
+#pragma unroll
+        for (int j = 0; j < DD; ++j) t += ld.L[r][j] * G[j];
+        // i depends on the lane: select with static indices (keeps G and
+        // Ymine in registers)
+        R Gi = R(0);
+#pragma unroll
+        for (int ii = 0; ii < DD; ++ii)
+          if (ii == i) {
+            Gi = G[ii];
+            Ymine[ii] = t;
+          }
+        qf += (double)Gi * (double)t;
+      }
     }
   }
   R Y[DD];
 #pragma unroll
-  for (int i = 0; i < DD; ++i) {
-    R t = R(0);
+  for (int i = 0; i < DD; ++i) Y[i] = __shfl_sync(kFull, Ymine[i], leader + i % LPP);
+  if (valid) {
 #pragma unroll
-    for (int j = 0; j < DD; ++j) t += a.L[(int64_t)Sym<D>::idx(i, j) * a.P.n + pi] * G[j];
-    Y[i] = t;
-  }
-  double qf = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      const unsigned fm = a.dofmask[ld.node[j]];
+      if (!fm) continue;
 #pragma unroll
-  for (int i = 0; i < DD; ++i) qf += (double)G[i] * (double)Y[i];
+      for (int c = 0; c < D; ++c) {
+        if (!((fm >> c) & 1u)) continue;
+        R f = R(0);
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int64_t node = base + stencil_offset<D>(g, k);
-    const unsigned fm = a.dofmask[node];
-    if (!fm) continue;
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      if (!((fm >> c) & 1u)) continue;
-      R f = R(0);
-#pragma unroll
-      for (int b = 0; b < D; ++b) f += Y[c * D + b] * dN[k][b];
-      atomicAdd(&w[c * g.nn + node], (double)f);
+        for (int b = 0; b < D; ++b) f += Y[c * D + b] * ld.dN[j][b];
+        atomicAdd(&w[c * g.nn + ld.node[j]], (double)f);
+      }
     }
   }
   return qf;
 }
 
-template <int D, typename R>
+template <int D, typename R, class UF>
+__device__ __forceinline__ double group_hvp(const PcgArgsT<R>& a, int64_t pi, bool valid, int q,
+                                            int leader, UF ufun, double* w) {
+  LaneData<D, R> ld;
+  load_lane<D, R>(a, pi, valid, q, ld);
+  return group_hvp_lane<D, R>(a, ld, valid, q, leader, ufun, w);
+}
+
+// FP64 instructions are scarce on this part (one warp-wide FP64 instruction
+// per SMSP every ~64 clocks), so the per-iteration control avoids
+// redundant FP64 work: warp 0 alone sums the block partials after each
+// barrier, thread 0 alone evaluates alpha, beta and the stopping tests and
+// hands them to the block through shared memory, and the DOFs are dealt to
+// the blocks in equal contiguous chunks.
+
+// Sum of one row of NV values over the block into thread 0 (warp sums, then
+// warp 0 over at most kThreads/32 warp totals).
+template <int NV>
+__device__ __forceinline__ void pcg_block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(kFull, v[k], off);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][warp] = v[k];
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      v[k] = lane < nw ? sh[k][lane] : 0.0;
+#pragma unroll
+      for (int off = kThreads / 64; off > 0; off >>= 1) v[k] += __shfl_down_sync(kFull, v[k], off);
+    }
+  }
+}
+
+// Warp 0: the NV totals of the grid's partial rows (lane-strided over the
+// blocks, then a warp sum; the order depends only on the launch shape).
+// Result in lane 0 of warp 0.
+template <int NV>
+__device__ __forceinline__ void pcg_grid_totals(const double* partials, double (&out)[NV]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = 0.0;
+  for (unsigned b = lane; b < gridDim.x; b += 32)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] += __ldcg(&partials[k * gridDim.x + b]);
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) out[k] += __shfl_down_sync(kFull, out[k], off);
+}
+
+// ONE: the launch covers the problem in a single pass (every thread owns at
+// most one DOF, every lane at most one particle); then each lane keeps its
+// particle's stencil, grad N and Hessian rows in registers for the whole
+// solve, and each DOF owner its inverse diagonal, m/dt^2, p and x, so an
+// iteration reads only r, s and w.
+template <int D, typename R, bool ONE>
 __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
   const GridGeo& g = a.g;
   const int64_t ndof = g.nn * D;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   DevScalars* S = a.S;
-  const int max_it = S->cg_max;
-  const double tol2 = S->tol2;
   const double* idiag = a.diag;  // inverse Jacobi diagonal
   __shared__ unsigned bar_target;  // this block's running barrier goal (count starts at 0)
+  __shared__ double sh_alpha, sh_beta;
+  __shared__ int sh_stop;          // 0 go on, 1 stop
   if (threadIdx.x == 0) bar_target = 0u;
+  // DOFs: block b owns the contiguous chunk [b c, (b+1) c)
+  const int64_t chunk = (ndof + gridDim.x - 1) / gridDim.x;
+  const int64_t d_lo = (int64_t)blockIdx.x * chunk;
+  const int64_t d_hi = d_lo + chunk < ndof ? d_lo + chunk : ndof;
+  // particle work: groups of LPP lanes, GP particles per warp (blockDim is a
+  // multiple of 32); the loops over particles run warp-uniformly
+  constexpr int LPP = HvpGroup<D>::LPP, GP = HvpGroup<D>::GP;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / LPP;
+  const int q = lane - grp * LPP;
+  const int leader = grp * LPP;
+  const bool in_group = grp < GP;
+  const int64_t warp0 = (tid >> 5) * GP;
+  const int64_t wstride = (stride >> 5) * GP;
+  // single-pass residents
+  const int64_t my_idx = d_lo + threadIdx.x;
+  bool my_free = false;
+  double my_id = 0.0, my_md = 0.0, my_p = 0.0, my_x = 0.0;
+  const int64_t my_pi = warp0 + grp;
+  const bool my_valid = in_group && my_pi < a.P.n;
+  LaneData<D, R> ld;
+  if constexpr (ONE) {
+    if (my_idx < d_hi) {
+      const int c = (int)(my_idx / g.nn);
+      const int64_t i = my_idx - (int64_t)c * g.nn;
+      my_free = (a.dofmask[i] >> c) & 1u;
+      if (my_free) {
+        my_id = idiag[my_idx];
+        my_md = a.m[i] * a.inv_dt2;
+      }
+    }
+    load_lane<D, R>(a, my_pi, my_valid, q, ld);
+  }
+  // scalar state, held by thread 0 of every block (all blocks see the same
+  // totals, so they take the same decisions)
   int it = 0, neg = 0;
-  double sums[3];
+  double gamma = 0.0, delta = 0.0, gamma_old = 1.0, alpha_old = 1.0;
+  const int max_it = S->cg_max;
+  const double tol2 = S->tol2;
 
   // ---- phase 0: w_0 = A u_0, gamma_0 = r0.u0, delta_0 = u0.w0
   {
     double acc[3] = {0.0, 0.0, 0.0};
     const double* r0 = a.r[0];
-    for (int64_t idx = tid; idx < ndof; idx += stride) {
-      const int c = (int)(idx / g.nn);
-      const int64_t i = idx - (int64_t)c * g.nn;
-      if ((a.dofmask[i] >> c) & 1u) {
-        const double ri = r0[idx];
-        const double ui = ri * idiag[idx];
+    auto u0 = [=](int64_t j) { return __ldcg(&r0[j]) * idiag[j]; };
+    if constexpr (ONE) {
+      if (my_free) {
+        const double ri = r0[my_idx];
+        const double ui = ri * my_id;
+        const double mu = my_md * ui;
         acc[0] += ri * ui;
-        acc[2] += a.m[i] * a.inv_dt2 * ui * ui;
-        atomicAdd(&a.w[0][idx], a.m[i] * a.inv_dt2 * ui);
+        acc[2] += mu * ui;
+        atomicAdd(&a.w[0][my_idx], mu);
       }
-    }
-    for (int64_t pi = tid; pi < a.P.n; pi += stride)
-      acc[2] += particle_hvp<D, R>(a, pi, [&](int64_t j) { return __ldcg(&r0[j]) * idiag[j]; }, a.w[0]);
-    publish_partials<3>(acc, a.partials, 0);
-    if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
-    sum_partials<3>(a.partials, sums);
-  }
-  double gamma = sums[0], delta = sums[2];
-  double alpha_old = 1.0, gamma_old = 1.0;
-  int done = (gamma == 0.0) || (S->cg_done != 0);
-  for (; it < max_it && !done; ++it) {
-    double beta, alpha;
-    if (it == 0) {
-      beta = 0.0;
-      if (!(delta > 0.0)) {
-        neg = 1;
-        break;
-      }
-      alpha = gamma / delta;
+      acc[2] += group_hvp_lane<D, R>(a, ld, my_valid, q, leader, u0, a.w[0]);
     } else {
-      beta = gamma / gamma_old;
-      const double den = delta - beta * gamma / alpha_old;
-      if (!(den > 0.0)) {
-        neg = 1;
-        break;
+      for (int64_t idx = d_lo + threadIdx.x; idx < d_hi; idx += blockDim.x) {
+        const int c = (int)(idx / g.nn);
+        const int64_t i = idx - (int64_t)c * g.nn;
+        if ((a.dofmask[i] >> c) & 1u) {
+          const double ri = r0[idx];
+          const double ui = ri * idiag[idx];
+          const double mu = a.m[i] * a.inv_dt2 * ui;
+          acc[0] += ri * ui;
+          acc[2] += mu * ui;
+          atomicAdd(&a.w[0][idx], mu);
+        }
       }
-      alpha = gamma / den;
+      for (int64_t b0 = warp0; b0 < a.P.n; b0 += wstride) {
+        const int64_t pi = b0 + grp;
+        acc[2] += group_hvp<D, R>(a, pi, in_group && pi < a.P.n, q, leader, u0, a.w[0]);
+      }
     }
+    pcg_block_sum<3>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a.partials[k * gridDim.x + blockIdx.x] = acc[k];
+    if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
+    if (threadIdx.x < 32) {
+      double tot[3];
+      pcg_grid_totals<3>(a.partials, tot);
+      if (threadIdx.x == 0) {
+        gamma = tot[0];
+        delta = tot[2];
+        int stop = (gamma == 0.0) || (S->cg_done != 0) || max_it <= 0;
+        if (!stop && !(delta > 0.0)) {
+          neg = 1;
+          stop = 1;
+        }
+        sh_alpha = stop ? 0.0 : gamma / delta;
+        sh_beta = 0.0;
+        sh_stop = stop;
+      }
+    }
+    __syncthreads();
+  }
+  while (!sh_stop) {
+    const double alpha = sh_alpha, beta = sh_beta;
     const double* rk = a.r[it & 1];
     double* rn = a.r[(it + 1) & 1];
     double* sk = a.s[it & 1];
@@ -220,52 +410,98 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
     double* wn = a.w[(it + 1) % 3];
     double* wz = a.w[(it + 2) % 3];
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t idx = tid; idx < ndof; idx += stride) {
-      const int c = (int)(idx / g.nn);
-      const int64_t i = idx - (int64_t)c * g.nn;
-      if ((a.dofmask[i] >> c) & 1u) {
-        const double id = idiag[idx];
-        const double rki = __ldcg(&rk[idx]);
-        const double ski = __ldcg(&wk[idx]) + beta * __ldcg(&sp[idx]);
-        sk[idx] = ski;
-        const double pk = rki * id + beta * a.p[idx];
-        a.p[idx] = pk;
-        a.x[idx] += alpha * pk;
+    auto uk = [=](int64_t j) {
+      return (__ldcg(&rk[j]) - alpha * (__ldcg(&wk[j]) + beta * __ldcg(&sp[j]))) * idiag[j];
+    };
+    if constexpr (ONE) {
+      if (my_free) {
+        const double rki = __ldcg(&rk[my_idx]);
+        const double ski = __ldcg(&wk[my_idx]) + beta * __ldcg(&sp[my_idx]);
+        sk[my_idx] = ski;
+        my_p = rki * my_id + beta * my_p;
+        my_x += alpha * my_p;
         const double rni = rki - alpha * ski;
-        rn[idx] = rni;
-        const double ui = rni * id;
+        rn[my_idx] = rni;
+        const double ui = rni * my_id;
+        const double mu = my_md * ui;
         acc[0] += rni * ui;
         acc[1] += rni * rni;
-        const double md = a.m[i] * a.inv_dt2;
-        acc[2] += md * ui * ui;
-        atomicAdd(&wn[idx], md * ui);
+        acc[2] += mu * ui;
+        atomicAdd(&wn[my_idx], mu);
       }
-      wz[idx] = 0.0;
+      if (my_idx < d_hi) wz[my_idx] = 0.0;
+      acc[2] += group_hvp_lane<D, R>(a, ld, my_valid, q, leader, uk, wn);
+    } else {
+      for (int64_t idx = d_lo + threadIdx.x; idx < d_hi; idx += blockDim.x) {
+        const int c = (int)(idx / g.nn);
+        const int64_t i = idx - (int64_t)c * g.nn;
+        if ((a.dofmask[i] >> c) & 1u) {
+          const double id = idiag[idx];
+          const double rki = __ldcg(&rk[idx]);
+          const double ski = __ldcg(&wk[idx]) + beta * __ldcg(&sp[idx]);
+          sk[idx] = ski;
+          const double pk = rki * id + beta * a.p[idx];
+          a.p[idx] = pk;
+          a.x[idx] += alpha * pk;
+          const double rni = rki - alpha * ski;
+          rn[idx] = rni;
+          const double ui = rni * id;
+          const double mu = a.m[i] * a.inv_dt2 * ui;
+          acc[0] += rni * ui;
+          acc[1] += rni * rni;
+          acc[2] += mu * ui;
+          atomicAdd(&wn[idx], mu);
+        }
+        wz[idx] = 0.0;
+      }
+      for (int64_t b0 = warp0; b0 < a.P.n; b0 += wstride) {
+        const int64_t pi = b0 + grp;
+        acc[2] += group_hvp<D, R>(a, pi, in_group && pi < a.P.n, q, leader, uk, wn);
+      }
     }
-    for (int64_t pi = tid; pi < a.P.n; pi += stride)
-      acc[2] += particle_hvp<D, R>(
-          a, pi,
-          [&](int64_t j) {
-            return (__ldcg(&rk[j]) - alpha * (__ldcg(&wk[j]) + beta * __ldcg(&sp[j]))) * idiag[j];
-          },
-          wn);
-    publish_partials<3>(acc, a.partials, 0);
+    pcg_block_sum<3>(acc);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a.partials[k * gridDim.x + blockIdx.x] = acc[k];
     if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
-    sum_partials<3>(a.partials, sums);
-    gamma_old = gamma;
-    alpha_old = alpha;
-    gamma = sums[0];
-    delta = sums[2];
-    if (sums[1] <= tol2) {
-      done = 1;
-      ++it;
-      break;
+    ++it;
+    if (threadIdx.x < 32) {
+      double tot[3];
+      pcg_grid_totals<3>(a.partials, tot);
+      if (threadIdx.x == 0) {
+        gamma_old = gamma;
+        alpha_old = alpha;
+        gamma = tot[0];
+        delta = tot[2];
+        int stop = tot[1] <= tol2 || it >= max_it;
+        double an = 0.0, bn = 0.0;
+        if (!stop) {
+          bn = gamma / gamma_old;
+          const double den = delta - bn * gamma / alpha_old;
+          if (!(den > 0.0)) {
+            neg = 1;
+            stop = 1;
+          } else {
+            an = gamma / den;
+          }
+        }
+        sh_alpha = an;
+        sh_beta = bn;
+        sh_stop = stop;
+      }
     }
+    __syncthreads();
   }
-  if (neg && it == 0) {
-    // no direction yet: take the preconditioned steepest descent u_0
-    const double* r0 = a.r[0];
-    for (int64_t idx = tid; idx < ndof; idx += stride) {
+  // thread 0 of each block knows whether the first direction failed
+  __shared__ int sh_fallback;
+  if (threadIdx.x == 0) sh_fallback = (neg && it == 0);
+  __syncthreads();
+  const double* r0 = a.r[0];
+  if constexpr (ONE) {
+    // no direction yet: the preconditioned steepest descent u_0
+    if (my_free) a.x[my_idx] = sh_fallback ? r0[my_idx] * my_id : my_x;
+  } else if (sh_fallback) {
+    for (int64_t idx = d_lo + threadIdx.x; idx < d_hi; idx += blockDim.x) {
       const int c = (int)(idx / g.nn);
       const int64_t i = idx - (int64_t)c * g.nn;
       if ((a.dofmask[i] >> c) & 1u) a.x[idx] = r0[idx] * idiag[idx];

@@ -62,7 +62,7 @@ class osmpm_domain_desc(Structure):
                 ("dx", c_double), ("res", c_int32 * 3), ("gravity", c_double * 3),
                 ("newton_tol", c_double), ("newton_max", c_int32), ("cg_rtol", c_double),
                 ("cg_max", c_int32), ("ls_max", c_int32), ("mass_eps", c_double),
-                ("reserved", c_int32 * 8)]
+                ("cg_eta_max", c_double), ("reserved", c_int32 * 6)]
 
 
 class osmpm_particles_in(Structure):
@@ -225,6 +225,7 @@ def make_desc(spec) -> osmpm_domain_desc:
     d.cg_max = spec.cg_max
     d.ls_max = spec.ls_max
     d.mass_eps = spec.mass_eps
+    d.cg_eta_max = getattr(spec, "cg_eta_max", 0.0)
     return d
 
 

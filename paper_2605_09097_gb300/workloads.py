@@ -96,6 +96,7 @@ class DomainSpec:
     # nodes with m_i <= mass_eps carry no DOF; None -> 1e-10 x mean particle mass
     mass_eps: Optional[float] = None
     precision: int = 0            # 0: FP64; 1: mixed (FP32 particle state and HVP)
+    cg_eta_max: float = 0.0       # inexact-Newton forcing cap (0: the library default 1e-3)
 
     def __post_init__(self):
         if self.mass_eps is None:
@@ -250,6 +251,26 @@ def inclusion(dx_S: float = 0.005, M: int = 2, dx_B: float = 0.05,
                       tau_S=rho * dx_S ** 2 / ppc_1d ** 2,
                       eps_tol=1e-12 * rho * dx_S ** 2)
     return coarse, fine, sch, dT
+
+
+def inclusion_single(dx: float = 0.005, r_inc: float = 0.05, E_inc: float = 1e6,
+                     E: float = 1e6, nu: float = 0.3, rho: float = 1000.0,
+                     eigenstrain: float = 0.01, ppc_1d: int = 2, newton_tol: float = 1e-8,
+                     cg_rtol: float = 1e-6) -> DomainSpec:
+    """The single-domain reference of Sec. 4.3: the traction-free matrix
+    [0.1,0.9]^2 with the inclusion r < r_inc (F0 = (1 - eigenstrain) I,
+    modulus E_inc) on one grid [0,1]^2 at dx."""
+    c = (0.5, 0.5)
+    n = int(round(1.0 / dx)) + 1
+    g = Grid(2, (0.0, 0.0), dx, (n, n))
+    lo, hi = int(round(0.1 / dx)), int(round(0.9 / dx))
+    x = sample_lattice(g.origin, dx, (lo, lo), (hi, hi), ppc_1d, _box((0.1, 0.1), (0.9, 0.9)))
+    inc = _r2(x, c) < r_inc ** 2
+    F0 = np.broadcast_to(np.eye(2), (x.shape[0], 2, 2)).copy()
+    F0[inc] *= (1.0 - eigenstrain)
+    p = make_particles(x, dx, ppc_1d, rho, np.where(inc, E_inc, E), nu, F0=F0)
+    return DomainSpec("inclusion_single", g, p, (0.0, 0.0), [], newton_tol=newton_tol,
+                      cg_rtol=cg_rtol)
 
 
 def hertz(dx_c: float = 1.0 / 64, ratio: int = 4, M: int = 4, E_block: float = 1e6,
