@@ -54,6 +54,10 @@ WORKLOAD = "inclusion_osmpm_2d_fp64_dxB0.05_dxS0.005_M2"
 ORACLE_SCHWARZ_ITERS_PER_STEP = 12.0
 ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
+# launch, from the ncu capture of the current kernel (the k_pcg profile
+# summary of this workload); None whenever the kernel changes
+PCG_TRAFFIC_BYTES = 3.04e6 + 0.09e6
 # FP64 flops of one Hessian-vector product per particle: gather G (2 d^2 3^d),
 # Y = L G (2 d^4), G:Y (2 d^2), scatter (2 d^2 3^d); an FMA counts 2.
 HVP_FLOPS_PER_PARTICLE = {2: 184, 3: 1152}
@@ -285,7 +289,9 @@ def run_ours(args, rank, local, world):
         "gpu_launches": int(launches),
         "roofline": {"kernel": "k_pcg (persistent PCG)", "bound": "alu", "achieved": achieved,
                      "peak": fp64_peak, "unit": "GFLOP/s", "frac": achieved / fp64_peak,
-                     "traffic": None, "peak_source": "nominal FP64 1.25 TFLOP/s (GB300)",
+                     "traffic": PCG_TRAFFIC_BYTES,
+                     "traffic_source": "ncu, one fine-domain launch (dram read + write bytes)",
+                     "peak_source": "nominal FP64 1.25 TFLOP/s (GB300)",
                      "launches": pcg_n, "avg_launch_us": 1e3 * pcg_ms / max(pcg_n, 1),
                      "pcg_iters": cB_["pcg_iters"] + cS_["pcg_iters"],
                      "us_per_pcg_iter": 1e3 * pcg_ms / max(cB_["pcg_iters"] + cS_["pcg_iters"], 1),
