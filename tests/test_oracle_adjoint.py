@@ -85,3 +85,69 @@ def test_stencil_hessian_matches_differences_of_gradients():
     # symmetric, and the Hessians of a partition of unity sum to zero
     np.testing.assert_allclose(H, H.transpose(0, 1, 3, 2), atol=0)
     np.testing.assert_allclose(H.sum(axis=1), 0.0, atol=1e-10 / grid.dx ** 2)
+
+
+def _coupled_case():
+    """A small coupled inclusion (coarse 0.1, fine 0.05, M = 2) with seeded
+    particle velocities, so that every term of the coupled step is live."""
+    cB, cS, sch, dT = W.inclusion(dx_S=0.05, dx_B=0.1, M=2, E_inc=4e6)
+    rng = np.random.default_rng(3)
+    out = []
+    for spec in (cB, cS):
+        p = spec.particles.copy()
+        p.v = 0.01 * rng.standard_normal(p.v.shape)
+        p.E = p.E * (1.0 + 0.2 * rng.random(p.E.shape))
+        out.append(dataclasses.replace(spec, particles=p))
+    return out[0], out[1], sch, dT, rng
+
+
+def test_recorded_coupled_step_is_schwarz_step():
+    cB, cS, sch, dT, _ = _coupled_case()
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    B2, S2 = O.DomainState.create(cB), O.DomainState.create(cS)
+    rec = AD.record_schwarz_step(B, S, dT, sch)
+    st = O.SchwarzStats()
+    O.schwarz_step(B2, S2, dT, sch, st)
+    assert len(rec.iters) == st.iters
+    np.testing.assert_array_equal(B.p.x, B2.p.x)
+    np.testing.assert_array_equal(S.p.F, S2.p.F)
+
+
+def test_coupled_adjoint_matches_central_differences():
+    """Alg. 1 differentiated through the iterations it ran: dJ/dE and the
+    start-state adjoints of both particle sets against central differences
+    (which run the same number of Schwarz iterations)."""
+    cB, cS, sch, dT, rng = _coupled_case()
+    nB, nS = cB.particles.n, cS.particles.n
+    cb, cs = rng.standard_normal((nB, 2)), rng.standard_normal((nS, 2))
+
+    def J(specB, specS):
+        B, S = O.DomainState.create(specB), O.DomainState.create(specS)
+        r = AD.record_schwarz_step(B, S, dT, sch, 1e-11)
+        return float(np.sum(cb * B.p.x) + np.sum(cs * S.p.x)), len(r.iters)
+
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    rec = AD.record_schwarz_step(B, S, dT, sch, 1e-11)
+    z = lambda n: (np.zeros((n, 2)), np.zeros((n, 2, 2)), np.zeros((n, 2, 2)))
+    vb, Bb, Fb = z(nB)
+    vs, Bs, Fs = z(nS)
+    B0b, S0b, EB, ES = AD.schwarz_adjoint(rec, AD.StateBar(cb, vb, Bb, Fb), AD.StateBar(cs, vs, Bs, Fs))
+    assert len(rec.iters) >= 3 and rec.sets.recvB.sum() > 0 and rec.sets.recvS.sum() > 0
+    for which, spec, E_ad, bar in (("B", cB, EB, B0b), ("S", cS, ES, S0b)):
+        n = spec.particles.n
+        cases = [("E", E_ad, None), ("x", bar.x, 1e-7), ("v", bar.v, 1e-6), ("B", bar.B, 1e-6),
+                 ("F", bar.F, 1e-6)]
+        for field, adj, h in cases:
+            p = int(rng.integers(0, n))
+            idx = (p,) + tuple(rng.integers(0, 2, size=adj.ndim - 1))
+            hh = 1e-4 * spec.particles.E[p] if field == "E" else h
+            vals = []
+            for sgn in (1.0, -1.0):
+                q = spec.particles.copy()
+                getattr(q, field)[idx] += sgn * hh
+                s2 = dataclasses.replace(spec, particles=q)
+                vals.append(J(s2, cS) if which == "B" else J(cB, s2))
+            assert vals[0][1] == vals[1][1] == len(rec.iters)
+            fd = (vals[0][0] - vals[1][0]) / (2 * hh)
+            np.testing.assert_allclose(adj[idx], fd, rtol=1e-4, atol=1e-5 * np.abs(adj).max(),
+                                       err_msg=f"{which} {field}{idx}")
