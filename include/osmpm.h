@@ -222,9 +222,14 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
  * domain's allocator, its input particle state (x, v, B, F), its converged
  * grid displacement u* and its free-DOF mask (about 12 doubles per particle
  * and 2-3 per grid node and step, in 2D); enable = 0 stops and frees the
- * record.  A coupled step (osmpm_schwarz_couple) or osmpm_set_particles on a
- * recording domain interrupts the record, and osmpm_adjoint then refuses it.
- * Errors: OSMPM_E_UNSUPPORTED for a mixed-precision domain. */
+ * record.  When both domains of osmpm_schwarz_couple record, the coupled
+ * step is recorded on the coarse domain instead (its start states, every
+ * coarse solve and fine sub-step it ran, the projection sums).  A record
+ * holds single-domain steps or coupled steps of one pair, not both;
+ * mixing them, osmpm_set_particles, a mixed-precision domain or the
+ * last-sub-step projection interrupts it, and osmpm_adjoint refuses an
+ * interrupted record.  Errors: OSMPM_E_UNSUPPORTED for a mixed-precision
+ * domain. */
 osmpm_status osmpm_record(osmpm_domain* dom, int32_t enable);
 
 /* Outputs of osmpm_adjoint: device arrays of the caller, in particle-id
@@ -250,12 +255,26 @@ typedef struct osmpm_adjoint_out {
  * derivatives of the Newton residual (Eq. grid_residual) with respect to
  * F_p, the moduli, x_p, the nodal mass and velocity, and the transposed APIC
  * P2G (Eq. p2g_transfer).  The active node set and the Dirichlet DOFs of each
- * step are held fixed.  The domain's state is unchanged and the record kept
- * (several objectives may be differentiated).  fine must be NULL (single
- * domain); coarse is the recorded domain.  stats: cg_iters and solves of the
- * adjoint PCGs.  Errors: OSMPM_E_INVALID (null arguments, no or interrupted
- * record), OSMPM_E_UNSUPPORTED (fine != NULL, mixed precision),
- * OSMPM_E_NONFINITE, OSMPM_E_CUDA, OSMPM_E_TIMEOUT. */
+ * step are held fixed.  The domains' states are unchanged and the record kept
+ * (several objectives may be differentiated).
+ *
+ * fine == NULL: coarse is a domain whose osmpm_step calls were recorded.
+ * fine != NULL: the pair's recorded osmpm_schwarz_couple steps (both domains
+ * recording, step-average projection), differentiated through the Schwarz
+ * iterations each step ran (their number and the receiver sets held fixed):
+ * per step the post-convergence coarse G2P, then for every iteration from
+ * the last to the first the fine sub-steps in reverse (including the adjoint
+ * of their receiver data, u_bar_D - (K lam)_D, through T_m), the transposed
+ * I_{B->S} into the coarse solve of that iteration, its adjoint, and its
+ * receiver data back through the transposed Pi_{S->B} (Eqs. interp_BtoS,
+ * spatial_projection, temporal_interp).  Then every array holds the coarse
+ * particles' entries followed by the fine ones: dJ_dx has (n_coarse +
+ * n_fine) * dim entries, dJ_dE n_coarse + n_fine, and so on.
+ *
+ * stats: cg_iters and solves of the adjoint PCGs.  Errors: OSMPM_E_INVALID
+ * (null arguments, no or interrupted record, a single-domain call on a
+ * coupled record), OSMPM_E_UNSUPPORTED (mixed precision), OSMPM_E_NONFINITE,
+ * OSMPM_E_CUDA, OSMPM_E_TIMEOUT. */
 osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const double* dJ_dx,
                            const osmpm_adjoint_out* out, osmpm_stats* stats);
 

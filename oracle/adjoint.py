@@ -290,8 +290,11 @@ def _problem(ds: O.DomainState, gf: O.GridFields, dt: float, extra_mask, extra_v
 
 
 def record_schwarz_step(B: O.DomainState, S: O.DomainState, dT: float, sch,
-                        newton_tol: Optional[float] = None) -> SchwarzRecord:
-    """``O.schwarz_step`` (step-average Pi) that keeps what its adjoint needs."""
+                        newton_tol: Optional[float] = None,
+                        n_iters: Optional[int] = None) -> SchwarzRecord:
+    """``O.schwarz_step`` (step-average Pi) that keeps what its adjoint needs.
+    With ``n_iters`` it runs exactly that many Schwarz iterations instead of
+    stopping at convergence (to unroll the same iterations as another run)."""
     if sch.pi_source != 0:
         raise NotImplementedError("the adjoint follows the step-average projection")
     M = sch.M
@@ -307,7 +310,7 @@ def record_schwarz_step(B: O.DomainState, S: O.DomainState, dT: float, sch,
     vGS = O.interp_B2S(gB, gS, gfB.vn, sets.recvS)
     vSn = vGS.copy()
     iters: List[SchwarzIter] = []
-    for k in range(sch.k_max + 1):
+    for k in range(sch.k_max + 1 if n_iters is None else n_iters):
         prB = _problem(B, gfB, dT, sets.recvB, vGB)
         uB = O.newton(prB, tolB, B.spec.newton_max, B.spec.ls_max)
         vB_new = np.where(gfB.active[:, None], uB / dT, 0.0)
@@ -329,7 +332,7 @@ def record_schwarz_step(B: O.DomainState, S: O.DomainState, dT: float, sch,
         rB = O.rel_change(vGB_new, vGB, sets.recvB)
         rS = O.rel_change(vSnp1, vGS, sets.recvS)
         vGB, vGS = vGB_new, vSnp1
-        if k >= 1 and rB <= sch.eps_conv and rS <= sch.eps_conv:
+        if n_iters is None and k >= 1 and rB <= sch.eps_conv and rS <= sch.eps_conv:
             break
     B.p = O.g2p(B.p, gB, uB, dT)
     return SchwarzRecord(B0, snap, gfB, gfS, sets, iters, M, dT, sch.eps_tol)

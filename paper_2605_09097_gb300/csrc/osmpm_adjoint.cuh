@@ -205,12 +205,15 @@ __global__ void k_adj_rhs(GridGeo g, const double* m, const uint8_t* dofmask, do
 // -lam . dg/dz for the particle inputs of g: F_p, mu_p, lam_p and x_p (the
 // last through grad N in F_p(u) and in the internal force).  E_bar gets
 // (mu_bar mu + lam_bar lam) / E, both moduli being proportional to E.
+// With klam, also scatters (K lam)_i = sum_p V Y F^T grad N_i onto the fixed
+// DOFs (the adjoint of prescribed displacements needs u_bar_D - (K lam)_D).
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_adj_solve(int64_t n, const double* x, const double* F,
                                                         const double* mu, const double* lamb,
                                                         const double* vol0, GridGeo g,
                                                         const double* u, const double* lam,
-                                                        double* xb, double* Fb, double* Eb,
+                                                        const uint8_t* dofmask, double* xb,
+                                                        double* Fb, double* Eb, double* klam,
                                                         int* err) {
   constexpr int DD = D * D;
   constexpr int K = (D == 2) ? 9 : 27;
@@ -317,6 +320,25 @@ __global__ void __launch_bounds__(kThreads) k_adj_solve(int64_t n, const double*
       for (int b = 0; b < D; ++b) v += H[a * D + b] * t[b];
       xacc[a] += v;
     }
+    if (klam) {
+      const unsigned fm = dofmask[node];
+      double ftn[D];  // F^T grad N_k
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < D; ++b) v += Fp[b * D + e] * dN[b];
+        ftn[e] = v;
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        if ((fm >> c) & 1u) continue;
+        double v = 0.0;
+#pragma unroll
+        for (int e = 0; e < D; ++e) v += Y[c * D + e] * ftn[e];
+        atomicAdd(&klam[(int64_t)c * g.nn + node], V * v);
+      }
+    }
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) xb[(int64_t)a * n + p] -= V * xacc[a];
@@ -325,30 +347,27 @@ __global__ void __launch_bounds__(kThreads) k_adj_solve(int64_t n, const double*
 // Nodal part: -lam . dg/dz for z = v_i (m_i/dt lam_i) and m_i
 // (-lam_i . ((u_i - dt v_i)/dt^2 - g)), then through v_i = q_i / m_i:
 // q_bar = v_bar / m, m_bar -= v_bar . v / m.  lam vanishes off the free DOFs.
+// Adds to qbar and mbar; mextra (may be null) is a further adjoint of m_i.
 template <int D>
 __global__ void k_adj_nodes(GridGeo g, const double* m, const double* vn, const double* u,
                             const double* lam, double gx, double gy, double gz, double dt,
-                            double* qbar, double* mbar) {
+                            const double* mextra, double* qbar, double* mbar) {
   const double gv[3] = {gx, gy, gz};
   for (int64_t i = gtid(); i < g.nn; i += gstride()) {
     const double mi = m[i];
-    double mb = 0.0;
-    if (mi > g.mass_eps) {
+    if (!(mi > g.mass_eps)) continue;
+    double mb = mextra ? mextra[i] : 0.0;
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        const int64_t idx = (int64_t)a * g.nn + i;
-        const double l = lam[idx];
-        const double vi = vn[idx];
-        const double vba = mi / dt * l;
-        mb -= l * ((u[idx] - dt * vi) / (dt * dt) - gv[a]);
-        mb -= vba * vi / mi;
-        qbar[idx] = vba / mi;
-      }
-    } else {
-#pragma unroll
-      for (int a = 0; a < D; ++a) qbar[(int64_t)a * g.nn + i] = 0.0;
+    for (int a = 0; a < D; ++a) {
+      const int64_t idx = (int64_t)a * g.nn + i;
+      const double l = lam[idx];
+      const double vi = vn[idx];
+      const double vba = mi / dt * l;
+      mb -= l * ((u[idx] - dt * vi) / (dt * dt) - gv[a]);
+      mb -= vba * vi / mi;
+      qbar[idx] += vba / mi;
     }
-    mbar[i] = mb;
+    mbar[i] += mb;
   }
 }
 
@@ -413,6 +432,184 @@ __global__ void __launch_bounds__(kThreads) k_adj_p2g(int64_t n, const double* x
   }
 #pragma unroll
   for (int e = 0; e < DD; ++e) Bb_out[(int64_t)e * n + p] = Bb[e];
+}
+
+// ---------------------------------------------------------------------------
+// Coupled step (Alg. 1) in reverse
+// ---------------------------------------------------------------------------
+
+// Adjoint of the prescribed velocities on receiver nodes: with u_D = s v on
+// an active receiver, v0bar += s0 (u_bar - K lam) and (if v1bar) v1bar +=
+// s1 (u_bar - K lam) (the two end values of the temporal interpolation).
+template <int D>
+__global__ void k_adj_bc(GridGeo g, const uint8_t* recv, const double* m, const double* ubar,
+                         const double* klam, double s0, double s1, double* v0bar, double* v1bar) {
+  for (int64_t j = gtid(); j < g.nn; j += gstride()) {
+    if (!recv[j] || !(m[j] > g.mass_eps)) continue;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int64_t idx = (int64_t)a * g.nn + j;
+      const double ud = ubar[idx] - klam[idx];
+      v0bar[idx] += s0 * ud;
+      if (v1bar) v1bar[idx] += s1 * ud;
+    }
+  }
+}
+
+// Transposed I_{B->S} (Eq. interp_BtoS): each fine receiver scatters
+// N_I(x_j) vbar_j onto its coarse support.
+template <int D>
+__global__ void k_adj_interp(GridGeo gB, GridGeo gS, const uint8_t* recvS, const double* vbar,
+                             double* out) {
+  for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
+    if (!recvS[j]) continue;
+    double xs[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xs[a] = node_pos(gS, j, a);
+    Stencil<D> s;
+    make_stencil<D>(xs, gB, s);
+    for (int k = 0; k < Pow3<D>::K; ++k) {
+      double N, dN[D];
+      const int64_t node = stencil_node<D>(s, gB, k, N, dN);
+#pragma unroll
+      for (int a = 0; a < D; ++a) atomicAdd(&out[(int64_t)a * gB.nn + node], N * vbar[(int64_t)a * gS.nn + j]);
+    }
+  }
+}
+
+// Transposed Pi_{S->B} (Eq. spatial_projection), coarse part: with
+// Pi_I = num_I / (den_I + eps) on the receivers, nbar = vbar / (den + eps)
+// and dbar = -vbar . num / (den + eps)^2.
+template <int D>
+__global__ void k_adj_proj_coarse(GridGeo gB, const uint8_t* recvB, const double* num,
+                                  const double* den, double eps, const double* vbar,
+                                  double* nbar, double* dbar) {
+  for (int64_t I = gtid(); I < gB.nn; I += gstride()) {
+    double db = 0.0;
+    const bool r = recvB[I];
+    const double dd = den[I] + eps;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int64_t idx = (int64_t)a * gB.nn + I;
+      const double vb = r ? vbar[idx] : 0.0;
+      nbar[idx] = vb / dd;
+      db -= vb * num[idx];
+    }
+    dbar[I] = r ? db / (dd * dd) : 0.0;
+  }
+}
+
+// Fine part: G_j = sum_I N_I(x_j) nbar_I and H_j = sum_I N_I(x_j) dbar_I
+// over the coarse support inside the coarse box (the weights of the forward
+// scatter without the fine mass).
+template <int D>
+__global__ void k_adj_proj_fine(GridGeo gB, GridGeo gS, const double* nbar, const double* dbar,
+                                double* G, double* H) {
+  for (int64_t j = gtid(); j < gS.nn; j += gstride()) {
+    double xs[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) xs[a] = node_pos(gS, j, a);
+    int base[D];
+    double w[D][3];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const double t = __dmul_rn(__dsub_rn(xs[a], gB.o[a]), gB.inv_dx);
+      const double b = floor(__dsub_rn(t, 0.5));
+      base[a] = (int)b;
+      const double fx = t - b;
+      const double e0 = 1.5 - fx, e1 = fx - 1.0, e2 = fx - 0.5;
+      w[a][0] = 0.5 * e0 * e0;
+      w[a][1] = 0.75 - e1 * e1;
+      w[a][2] = 0.5 * e2 * e2;
+    }
+    double g[D], h = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) g[a] = 0.0;
+    for (int k = 0; k < Pow3<D>::K; ++k) {
+      const int off[3] = {k % 3, (k / 3) % 3, k / 9};
+      bool in = true;
+      int64_t node = 0, stride = 1;
+      double N = 1.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int c = base[a] + off[a];
+        in = in && c >= 0 && c < gB.res[a];
+        node += (int64_t)c * stride;
+        stride *= gB.res[a];
+        N *= w[a][off[a]];
+      }
+      if (!in) continue;
+      h += N * dbar[node];
+#pragma unroll
+      for (int a = 0; a < D; ++a) g[a] += N * nbar[(int64_t)a * gB.nn + node];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) G[(int64_t)a * gS.nn + j] = g[a];
+    H[j] = h;
+  }
+}
+
+// A fine sub-step's share of the step-averaged projection: its solved grid
+// (m_j, u_j / dt) entered the sums as m_j u_j / dt and m_j, so
+// u_bar_j += m_j / dt G_j and the mass adjoint m_extra_j = u_j / dt . G_j + H_j
+// on the sub-step's active nodes.
+template <int D>
+__global__ void k_adj_inject(GridGeo g, const double* m, const double* u, double dt,
+                             const double* G, const double* H, double* ubar, double* mextra) {
+  for (int64_t j = gtid(); j < g.nn; j += gstride()) {
+    double mx = 0.0;
+    const double mj = m[j];
+    if (mj > g.mass_eps) {
+      mx = H[j];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int64_t idx = (int64_t)a * g.nn + j;
+        ubar[idx] += mj / dt * G[idx];
+        mx += u[idx] / dt * G[idx];
+      }
+    }
+    mextra[j] = mx;
+  }
+}
+
+// Adjoints of a P2G grid's momentum and mass (qbar += G, mbar += H) and of
+// its velocity v = q / m (qbar += vbar / m, mbar -= vbar . v / m), on the
+// active nodes; either source may be null.
+template <int D>
+__global__ void k_adj_grid_acc(GridGeo g, const double* m, const double* vn, const double* G,
+                               const double* H, const double* vbar, double* qbar, double* mbar) {
+  for (int64_t j = gtid(); j < g.nn; j += gstride()) {
+    const double mj = m[j];
+    if (!(mj > g.mass_eps)) continue;
+    double mb = H ? H[j] : 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int64_t idx = (int64_t)a * g.nn + j;
+      double qb = G ? G[idx] : 0.0;
+      if (vbar) {
+        qb += vbar[idx] / mj;
+        mb -= vbar[idx] * vn[idx] / mj;
+      }
+      qbar[idx] += qb;
+    }
+    mbar[j] += mb;
+  }
+}
+
+// out += scale * v on the active nodes (D components).
+template <int D>
+__global__ void k_adj_axpy_active(GridGeo g, const double* m, double scale, const double* v,
+                                  double* out) {
+  for (int64_t idx = gtid(); idx < g.nn * D; idx += gstride()) {
+    const int64_t j = idx % g.nn;
+    if (m[j] > g.mass_eps) out[idx] += scale * v[idx];
+  }
+}
+
+// dst += src over cnt doubles.
+template <int D>
+__global__ void k_adj_add(int64_t cnt, const double* src, double* dst) {
+  for (int64_t t = gtid(); t < cnt; t += gstride()) dst[t] += src[t];
 }
 
 // Layout changes between the caller's id-ordered, particle-major arrays and

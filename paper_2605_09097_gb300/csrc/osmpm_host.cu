@@ -154,6 +154,19 @@ struct osmpm_domain {
   bool recording = false, tape_broken = false;
   std::vector<TapeStep> tape;
   double* adj = nullptr;  // adjoint work arrays, allocated on first use
+  // coupled steps recorded on the coarse domain: per step a head block (both
+  // start states, receiver masks, the k = 0 projection sums) and one block
+  // per Schwarz iteration (see CoupledLayout)
+  struct CoupledStep {
+    TapeStep head;
+    std::vector<TapeStep> iters;
+    int M = 1;
+    double dT = 0.0, eps_tol = 0.0;
+  };
+  std::vector<CoupledStep> ctape;
+  osmpm_domain* partner = nullptr;  // the other domain of the recorded coupled steps
+  int tape_kind = 0;                // 0 empty, 1 single-domain steps, 2 coupled (coarse), 3 coupled (fine)
+  double* cadj = nullptr;           // coupled-adjoint work arrays
 
   // optional CUDA-event timing of the PCG launches (osmpm_set_profiling)
   bool time_hvp = false;
@@ -218,6 +231,13 @@ void raw_free(osmpm_domain* d, void* p, size_t bytes) {
 void clear_tape(osmpm_domain* d) {
   for (auto& t : d->tape) raw_free(d, t.mem, t.bytes);
   d->tape.clear();
+  for (auto& c : d->ctape) {
+    raw_free(d, c.head.mem, c.head.bytes);
+    for (auto& t : c.iters) raw_free(d, t.mem, t.bytes);
+  }
+  d->ctape.clear();
+  d->partner = nullptr;
+  d->tape_kind = 0;
   d->tape_broken = false;
 }
 
@@ -680,6 +700,68 @@ osmpm_status tape_end(osmpm_domain* d, osmpm_domain::TapeStep& slot, double dt) 
   return OSMPM_OK;
 }
 
+// Coupled-step record layout (coarse domain B, fine domain S, M sub-steps).
+// Head: both start states (x, v, B, F contiguous), the receiver masks and
+// the k = 0 projection sums.  Per iteration: the coarse solution and DOF
+// mask, per sub-step the fine state entering it (from the second sub-step
+// on), its solution and DOF mask, and the iteration's projection sums.
+struct CoupledLayout {
+  size_t stB, stS, recvB, recvS, N0, D0, head_bytes;
+  size_t uB, maskB, N, Dn, iter_bytes;
+  std::vector<size_t> state, uS, maskS;
+  CoupledLayout(const osmpm_domain* B, const osmpm_domain* S, int M) {
+    const size_t D = B->dim, DD = D * D, nB = (size_t)B->n, nS = (size_t)S->n;
+    const size_t nnB = (size_t)B->geo.nn, nnS = (size_t)S->geo.nn;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      const size_t r = o;
+      o += (bytes + 255) & ~size_t(255);
+      return r;
+    };
+    stB = take(8 * (2 * D + 2 * DD) * nB);
+    stS = take(8 * (2 * D + 2 * DD) * nS);
+    recvB = take(nnB);
+    recvS = take(nnS);
+    N0 = take(8 * D * nnB);
+    D0 = take(8 * nnB);
+    head_bytes = o;
+    o = 0;
+    uB = take(8 * D * nnB);
+    maskB = take(nnB);
+    state.assign(M, 0);
+    uS.assign(M, 0);
+    maskS.assign(M, 0);
+    for (int m = 0; m < M; ++m) {
+      if (m > 0) state[m] = take(8 * (2 * D + 2 * DD) * nS);
+      uS[m] = take(8 * D * nnS);
+      maskS[m] = take(nnS);
+    }
+    N = take(8 * D * nnB);
+    Dn = take(8 * nnB);
+    iter_bytes = o;
+  }
+};
+
+// Copies of an FP64 particle state (x, v, B, F) to and from a contiguous block.
+osmpm_status save_state(osmpm_domain* d, char* b) {
+  const size_t D = d->dim, n = (size_t)d->n;
+  const size_t off[4] = {0, 8 * D * n, 16 * D * n, 8 * (2 * D + D * D) * n};
+  const size_t len[4] = {8 * D * n, 8 * D * n, 8 * D * D * n, 8 * D * D * n};
+  void* src[4] = {d->P.x, d->P.v, d->P.B, d->P.F};
+  for (int i = 0; i < 4; ++i)
+    CUDA_TRY(cudaMemcpyAsync(b + off[i], src[i], len[i], cudaMemcpyDeviceToDevice, d->stream));
+  return OSMPM_OK;
+}
+osmpm_status load_state(osmpm_domain* d, const char* b) {
+  const size_t D = d->dim, n = (size_t)d->n;
+  const size_t off[4] = {0, 8 * D * n, 16 * D * n, 8 * (2 * D + D * D) * n};
+  const size_t len[4] = {8 * D * n, 8 * D * n, 8 * D * D * n, 8 * D * D * n};
+  void* dst[4] = {d->P.x, d->P.v, d->P.B, d->P.F};
+  for (int i = 0; i < 4; ++i)
+    CUDA_TRY(cudaMemcpyAsync(dst[i], b + off[i], len[i], cudaMemcpyDeviceToDevice, d->stream));
+  return OSMPM_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -872,7 +954,11 @@ osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(OSMPM_E_INVALID, "dt must be > 0");
   SolveStats st;
   osmpm_domain::TapeStep slot{};
-  if (d->recording) OSMPM_TRY(tape_begin(d, slot));
+  if (d->recording) {
+    if (d->tape_kind != 0 && d->tape_kind != 1) d->tape_broken = true;
+    d->tape_kind = 1;
+    if (!d->tape_broken) OSMPM_TRY(tape_begin(d, slot));
+  }
   auto drop = [&](osmpm_status e) {
     raw_free(d, slot.mem, slot.bytes);
     return e;
@@ -923,13 +1009,35 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   const int M = sd->M;
   const double dt = dT / M;
   const int D = B->dim;
-  // a coupled step is not recorded: a tape that it interrupts is unusable
-  if (B->recording) B->tape_broken = true;
-  if (S->recording) S->tape_broken = true;
+  // reverse-mode record of this step, kept on the coarse domain (needs both
+  // domains recording in FP64, the step-average projection and a record of
+  // coupled steps of this pair only; anything else interrupts the record)
+  const bool want_rec = B->recording || S->recording;
+  const bool rec = want_rec && B->recording && S->recording && !B->tape_broken &&
+                   !S->tape_broken && sd->pi_source == OSMPM_PI_STEP_AVERAGE && B->prec == 0 &&
+                   S->prec == 0 && (B->tape_kind == 0 || (B->tape_kind == 2 && B->partner == S)) &&
+                   (S->tape_kind == 0 || (S->tape_kind == 3 && S->partner == B));
+  if (want_rec && !rec) {
+    if (B->recording) B->tape_broken = true;
+    if (S->recording) S->tape_broken = true;
+  }
+  osmpm_domain::CoupledStep cs{};
+  const CoupledLayout CL(B, S, sd->M);
+  auto drop_rec = [&]() {
+    raw_free(B, cs.head.mem, cs.head.bytes);
+    for (auto& t : cs.iters) raw_free(B, t.mem, t.bytes);
+    cs.head.mem = nullptr;
+    cs.iters.clear();
+    if (rec) {
+      B->tape_broken = true;
+      S->tape_broken = true;
+    }
+  };
   const GridGeo &gB = B->geo, &gS = S->geo;
   cudaStream_t s = B->stream;
   SolveStats st;
   auto bail = [&](osmpm_status e) {
+    drop_rec();
     snapshot(S, true);  // the fine particles go back to t_n
     cudaStreamSynchronize(s);
     fill_stats(stats, st, 0, 0, 0.0, 0.0);
@@ -969,6 +1077,20 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   DISPATCH(B, K::proj_finish(gB, B->recv, B->proj_num, B->proj_den, sd->eps_tol, B->bc0, s));
   DISPATCH(B, K::interp(gB, gS, B->vn, S->recv, S->bc0, s));
   CUDA_TRY(cudaMemcpyAsync(S->bc_prev, S->bc0, sizeof(double) * D * gS.nn, cudaMemcpyDeviceToDevice, s));
+  if (rec) {
+    S_TRY(raw_alloc(B, CL.head_bytes, &cs.head.mem));
+    cs.head.bytes = CL.head_bytes;
+    cs.M = M;
+    cs.dT = dT;
+    cs.eps_tol = sd->eps_tol;
+    char* h = (char*)cs.head.mem;
+    S_TRY(save_state(B, h + CL.stB));
+    S_TRY(save_state(S, h + CL.stS));
+    CUDA_TRY(cudaMemcpyAsync(h + CL.recvB, B->recv, gB.nn, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h + CL.recvS, S->recv, gS.nn, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h + CL.N0, B->proj_num, 8 * D * gB.nn, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(h + CL.D0, B->proj_den, 8 * gB.nn, cudaMemcpyDeviceToDevice, s));
+  }
 
   // Newton warm starts for the re-solves of iterations k >= 1: the coarse
   // solve from its previous solution, fine sub-step m from the previous
@@ -987,6 +1109,16 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
       S_TRY(cold_start(B, dT));
     S_TRY(newton_solve(B, dT, st));
     CUDA_TRY(cudaMemcpyAsync(keep_slot(B, 0), B->u, bytesB, cudaMemcpyDeviceToDevice, s));
+    char* ib = nullptr;
+    if (rec) {
+      osmpm_domain::TapeStep it{};
+      S_TRY(raw_alloc(B, CL.iter_bytes, &it.mem));
+      it.bytes = CL.iter_bytes;
+      cs.iters.push_back(it);
+      ib = (char*)it.mem;
+      CUDA_TRY(cudaMemcpyAsync(ib + CL.uB, B->u, bytesB, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(ib + CL.maskB, B->dofmask, gB.nn, cudaMemcpyDeviceToDevice, s));
+    }
     DISPATCH(B, K::vel_from_u(gB, B->m, B->u, dT, B->vtmp, s));
     // 2. fine: restore, P2G, endpoint data I(v_B^n), I(v_B^(k+1)), sub-cycle
     S_TRY(snapshot(S, true));
@@ -1002,8 +1134,13 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
         DISPATCH(S, K::warm_start(gS, S->dofmask, keep_slot(S, m - 1), S->u, s));
       else
         S_TRY(cold_start(S, dt));
+      if (ib && m > 1) S_TRY(save_state(S, ib + CL.state[m - 1]));
       S_TRY(newton_solve(S, dt, st));
       CUDA_TRY(cudaMemcpyAsync(keep_slot(S, m - 1), S->u, bytesS, cudaMemcpyDeviceToDevice, s));
+      if (ib) {
+        CUDA_TRY(cudaMemcpyAsync(ib + CL.uS[m - 1], S->u, bytesS, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(ib + CL.maskS[m - 1], S->dofmask, gS.nn, cudaMemcpyDeviceToDevice, s));
+      }
       if (pi_avg) {
         DISPATCH(S, K::vel_from_u(gS, S->m, S->u, dt, S->vtmp, s));
         DISPATCH(B, K::proj_scatter(gB, gS, S->m, S->vtmp, B->proj_num, B->proj_den, s));
@@ -1018,6 +1155,10 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
     // Pi = avg num / (avg den + eps_tol).  Last sub-step: Pi of the P2G grid.
     if (!pi_avg)
       DISPATCH(B, K::proj_scatter(gB, gS, S->m, S->vn, B->proj_num, B->proj_den, s));
+    if (ib) {
+      CUDA_TRY(cudaMemcpyAsync(ib + CL.N, B->proj_num, 8 * D * gB.nn, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(ib + CL.Dn, B->proj_den, 8 * gB.nn, cudaMemcpyDeviceToDevice, s));
+    }
     DISPATCH(B, K::proj_finish(gB, B->recv, B->proj_num, B->proj_den,
                                pi_avg ? sd->eps_tol * M : sd->eps_tol, B->bc1, s));
     DISPATCH(B, K::rel_change(gB, B->bc1, B->bc0, B->recv, 0, B->S, B->partials, s));
@@ -1039,6 +1180,13 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   const int iters = converged ? k + 1 : sd->k_max + 1;
   // 4. post-convergence coarse update (Sec. 3.5)
   DISPATCH(B, K::g2p(P_, gB, B->u, dT, s));
+  if (rec) {
+    B->ctape.push_back(cs);
+    B->tape_kind = 2;
+    B->partner = S;
+    S->tape_kind = 3;
+    S->partner = B;
+  }
   CUDA_TRY(cudaStreamSynchronize(s));
   CUDA_TRY(cudaGetLastError());
 #undef S_TRY
@@ -1096,11 +1244,251 @@ osmpm_status osmpm_record(osmpm_domain* d, int32_t enable) {
     }                                    \
   } while (0)
 
+// Reverse of the recorded coupled steps (Alg. 1 differentiated through the
+// iterations it ran).  Per step, last to first: the post-convergence coarse
+// G2P; then for k = K .. 0 the fine sub-steps of iteration k in reverse
+// (each a single-domain step adjoint, plus the adjoint of its receiver data
+// through T_m and, for k < K, the share of the next coarse solve's
+// projection adjoint), the transposed I_{B->S} into coarse solve k, that
+// solve's adjoint, and its receiver data back through the transposed
+// Pi_{S->B} (into fine iteration k-1, or for k = 0 into the fine P2G at
+// t_n); finally v_S^n = I(v_B^n) and the coarse P2G at t_n.
+static osmpm_status coupled_adjoint(osmpm_domain* B, osmpm_domain* S, const double* dJ_dx,
+                                    const osmpm_adjoint_out* out, osmpm_stats* stats) {
+  if (B->dim != S->dim || B->stream != S->stream)
+    return fail(OSMPM_E_INVALID, "coarse and fine must share dim and stream");
+  if (B->prec != 0 || S->prec != 0)
+    return fail(OSMPM_E_UNSUPPORTED, "reverse mode needs precision 0 (FP64) domains");
+  if (B->tape_broken || S->tape_broken)
+    return fail(OSMPM_E_INVALID, "the record was interrupted");
+  if (B->ctape.empty() || B->tape_kind != 2 || B->partner != S || S->partner != B)
+    return fail(OSMPM_E_INVALID, "no coupled steps of this pair recorded");
+  const int D = B->dim, DD = D * D;
+  const int64_t nB = B->n, nS = S->n, nnB = B->geo.nn, nnS = S->geo.nn;
+  const GridGeo &gB = B->geo, &gS = S->geo;
+  cudaStream_t s = B->stream;
+  for (osmpm_domain* d : {B, S}) {
+    if (!d->adj)
+      OSMPM_TRY(dalloc_n(d, (int64_t)(2 * (2 * D + 2 * DD) + 1) * d->n + (2 * D + 1) * d->geo.nn, &d->adj));
+    if (!d->cadj) OSMPM_TRY(dalloc_n(d, (int64_t)(2 * D + 2 * DD) * d->n + (4 * D + 3) * d->geo.nn, &d->cadj));
+  }
+  struct Bufs {
+    double *x, *v, *B, *F, *x2, *v2, *B2, *F2, *E, *ubar, *qbar, *mbar;
+    double *ax, *av, *aB, *aF, *klam, *g1, *g2, *g3, *h1, *h2;
+  };
+  auto carve = [&](osmpm_domain* d) {
+    Bufs b{};
+    const int64_t n = d->n, nn = d->geo.nn;
+    b.x = d->adj;
+    b.v = b.x + D * n;
+    b.B = b.v + D * n;
+    b.F = b.B + DD * n;
+    b.x2 = b.F + DD * n;
+    b.v2 = b.x2 + D * n;
+    b.B2 = b.v2 + D * n;
+    b.F2 = b.B2 + DD * n;
+    b.E = b.F2 + DD * n;
+    b.ubar = b.E + n;
+    b.qbar = b.ubar + D * nn;
+    b.mbar = b.qbar + D * nn;
+    b.ax = d->cadj;
+    b.av = b.ax + D * n;
+    b.aB = b.av + D * n;
+    b.aF = b.aB + DD * n;
+    b.klam = b.aF + DD * n;
+    b.g1 = b.klam + D * nn;
+    b.g2 = b.g1 + D * nn;
+    b.g3 = b.g2 + D * nn;
+    b.h1 = b.g3 + D * nn;
+    b.h2 = b.h1 + nn;
+    return b;
+  };
+  Bufs bb = carve(B), sb = carve(S);
+  // coarse: g1 = v_GammaB bar, g2 = v_B bar, g3 = Pi's nbar, h1 = dbar
+  // fine:   g1 = v_S^n bar, g2 = v_S^{n+1} bar, g3 = G, h1 = H, h2 = m_extra
+  const size_t stateB = sizeof(double) * (2 * D + 2 * DD) * nB;
+  const size_t stateS = sizeof(double) * (2 * D + 2 * DD) * nS;
+  const size_t gvB = sizeof(double) * D * nnB, gvS = sizeof(double) * D * nnS;
+  SolveStats st;
+  CUDA_TRY(cudaMemsetAsync(B->err, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(S->err, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemsetAsync(bb.v, 0, sizeof(double) * (D + 2 * DD) * nB, s));
+  CUDA_TRY(cudaMemsetAsync(sb.v, 0, sizeof(double) * (D + 2 * DD) * nS, s));
+  CUDA_TRY(cudaMemsetAsync(bb.E, 0, sizeof(double) * nB, s));
+  CUDA_TRY(cudaMemsetAsync(sb.E, 0, sizeof(double) * nS, s));
+  ADJ(B, AK::from_ids(nB, D, B->P.id, dJ_dx, bb.x, s));
+  ADJ(S, AK::from_ids(nS, D, S->P.id, dJ_dx + (int64_t)D * nB, sb.x, s));
+  OSMPM_TRY(snapshot(B, false));
+  OSMPM_TRY(snapshot(S, false));
+  osmpm_status status = OSMPM_OK;
+  // one solve's adjoint on domain d with u, dofmask in place and u_bar in
+  // its ubar: lam in d->cx, particle terms into (xacc, Facc, E), K lam on
+  // the fixed DOFs into klam
+  auto solve_adj = [&](osmpm_domain* d, Bufs& b, double dt, double* xacc, double* Facc) {
+    const int64_t nn = d->geo.nn;
+    CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, s));
+    CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, s));
+    DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, s));
+    ADJ(d, AK::rhs(d->geo, d->m, d->dofmask, dt, d->desc.cg_rtol, d->desc.cg_max, b.ubar, d->diag,
+                   d->cx, d->cr, d->cz, d->cp, d->S, d->partials, s));
+    OSMPM_TRY(run_pcg(d, dt, false, st));
+    st.solves++;
+    CUDA_TRY(cudaMemsetAsync(b.klam, 0, sizeof(double) * D * nn, s));
+    ADJ(d, AK::solve(d->n, d->P.x, (const double*)d->P.F, d->P.mu, d->P.lam, d->P.vol0, d->geo,
+                     d->u, d->cx, d->dofmask, xacc, Facc, b.E, b.klam, d->err, s));
+    return OSMPM_OK;
+  };
+  for (size_t step = B->ctape.size(); step-- > 0 && status == OSMPM_OK;) {
+    const auto& cst = B->ctape[step];
+    const int M = cst.M;
+    const CoupledLayout CL(B, S, M);
+    const char* h = (const char*)cst.head.mem;
+    const int Kit = (int)cst.iters.size() - 1;
+    const double dT = cst.dT, dt = dT / M;
+    const uint8_t* recvB = (const uint8_t*)(h + CL.recvB);
+    const uint8_t* recvS = (const uint8_t*)(h + CL.recvS);
+    // accumulators of the start-state adjoints and of the coarse P2G at t_n
+    CUDA_TRY(cudaMemsetAsync(bb.ax, 0, stateB, s));
+    CUDA_TRY(cudaMemsetAsync(sb.ax, 0, stateS, s));
+    CUDA_TRY(cudaMemsetAsync(bb.qbar, 0, sizeof(double) * (D + 1) * nnB, s));
+    CUDA_TRY(cudaMemsetAsync(sb.g1, 0, gvS, s));
+    // coarse state and grid at t_n (shared by every coarse solve)
+    OSMPM_TRY(load_state(B, h + CL.stB));
+    OSMPM_TRY(run_p2g(B, false));
+    // post-convergence coarse G2P with u_B^(K)
+    {
+      const char* ik = (const char*)cst.iters[Kit].mem;
+      CUDA_TRY(cudaMemcpyAsync(B->u, ik + CL.uB, gvB, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemsetAsync(bb.ubar, 0, gvB, s));
+      ADJ(B, AK::g2p(nB, B->P.x, (const double*)B->P.F, gB, B->u, dT, bb.x, bb.v, bb.B, bb.F, bb.ubar,
+                     bb.x2, bb.F2, s));
+      ADJ(B, AK::add(D * nB, bb.x2, bb.ax, s));
+      ADJ(B, AK::add(DD * nB, bb.F2, bb.aF, s));
+    }
+    bool pending = false;  // G, H of the projection adjoint wait for fine iteration k
+    for (int k = Kit; k >= 0 && status == OSMPM_OK; --k) {
+      const char* ik = (const char*)cst.iters[k].mem;
+      // ---- fine iteration k, sub-steps in reverse
+      double *cx = sb.x, *cv = sb.v, *cB = sb.B, *cF = sb.F;
+      double *nx = sb.x2, *nv = sb.v2, *nB_ = sb.B2, *nF = sb.F2;
+      if (k < Kit) CUDA_TRY(cudaMemsetAsync(sb.x, 0, stateS, s));  // (x, v, B, F contiguous)
+      CUDA_TRY(cudaMemsetAsync(sb.g2, 0, gvS, s));
+      for (int m = M - 1; m >= 0; --m) {
+        OSMPM_TRY(load_state(S, m == 0 ? h + CL.stS : ik + CL.state[m]));
+        status = run_p2g(S, false);
+        if (status != OSMPM_OK) break;
+        CUDA_TRY(cudaMemcpyAsync(S->u, ik + CL.uS[m], gvS, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(S->dofmask, ik + CL.maskS[m], nnS, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(cudaMemsetAsync(sb.ubar, 0, gvS, s));
+        if (pending) ADJ(S, AK::inject(gS, S->m, S->u, dt, sb.g3, sb.h1, sb.ubar, sb.h2, s));
+        ADJ(S, AK::g2p(nS, S->P.x, (const double*)S->P.F, gS, S->u, dt, cx, cv, cB, cF, sb.ubar, nx,
+                       nF, s));
+        status = solve_adj(S, sb, dt, nx, nF);
+        if (status != OSMPM_OK) break;
+        const double a = (double)(m + 1) / (double)M;
+        ADJ(S, AK::bc(gS, recvS, S->m, sb.ubar, sb.klam, (1.0 - a) * dt, a * dt, sb.g1, sb.g2, s));
+        CUDA_TRY(cudaMemsetAsync(sb.qbar, 0, sizeof(double) * (D + 1) * nnS, s));
+        ADJ(S, AK::nodes(gS, S->m, S->vn, S->u, S->cx, S->desc.gravity, dt, pending ? sb.h2 : nullptr,
+                         sb.qbar, sb.mbar, s));
+        ADJ(S, AK::p2g(nS, S->P.x, (const double*)S->P.v, (const double*)S->P.B, S->P.mass, gS,
+                       sb.qbar, sb.mbar, nv, nB_, nx, s));
+        std::swap(cx, nx);
+        std::swap(cv, nv);
+        std::swap(cB, nB_);
+        std::swap(cF, nF);
+      }
+      if (status != OSMPM_OK) break;
+      // the snapshot fed this iteration
+      ADJ(S, AK::add(D * nS, cx, sb.ax, s));
+      ADJ(S, AK::add(D * nS, cv, sb.av, s));
+      ADJ(S, AK::add(DD * nS, cB, sb.aB, s));
+      ADJ(S, AK::add(DD * nS, cF, sb.aF, s));
+      if (cx != sb.x) {  // keep the incoming-adjoint slots where the next pass expects them
+        CUDA_TRY(cudaMemsetAsync(sb.x, 0, stateS, s));
+      }
+      // ---- v_S^{n+1} = I(v_B^(k+1)), v_B^(k+1) = u_B^(k) / dT (active coarse nodes)
+      CUDA_TRY(cudaMemsetAsync(bb.g2, 0, gvB, s));
+      ADJ(B, AK::interp_t(gB, gS, recvS, sb.g2, bb.g2, s));
+      if (k < Kit) CUDA_TRY(cudaMemsetAsync(bb.ubar, 0, gvB, s));
+      ADJ(B, AK::axpy_active(gB, B->m, 1.0 / dT, bb.g2, bb.ubar, s));
+      // ---- coarse solve k
+      CUDA_TRY(cudaMemcpyAsync(B->u, ik + CL.uB, gvB, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(B->dofmask, ik + CL.maskB, nnB, cudaMemcpyDeviceToDevice, s));
+      status = solve_adj(B, bb, dT, bb.ax, bb.aF);
+      if (status != OSMPM_OK) break;
+      ADJ(B, AK::nodes(gB, B->m, B->vn, B->u, B->cx, B->desc.gravity, dT, nullptr, bb.qbar, bb.mbar, s));
+      CUDA_TRY(cudaMemsetAsync(bb.g1, 0, gvB, s));
+      ADJ(B, AK::bc(gB, recvB, B->m, bb.ubar, bb.klam, dT, 0.0, bb.g1, nullptr, s));
+      // ---- transposed Pi: of fine iteration k-1's step average, or of the fine P2G at t_n
+      const double* num = k >= 1 ? (const double*)((const char*)cst.iters[k - 1].mem + CL.N)
+                                 : (const double*)(h + CL.N0);
+      const double* den = k >= 1 ? (const double*)((const char*)cst.iters[k - 1].mem + CL.Dn)
+                                 : (const double*)(h + CL.D0);
+      const double eps = k >= 1 ? cst.eps_tol * M : cst.eps_tol;
+      ADJ(B, AK::proj_coarse(gB, recvB, num, den, eps, bb.g1, bb.g3, bb.h1, s));
+      ADJ(B, AK::proj_fine(gB, gS, bb.g3, bb.h1, sb.g3, sb.h1, s));
+      pending = k >= 1;
+      if (k == 0) {
+        OSMPM_TRY(load_state(S, h + CL.stS));
+        status = run_p2g(S, false);
+        if (status != OSMPM_OK) break;
+        CUDA_TRY(cudaMemsetAsync(sb.qbar, 0, sizeof(double) * (D + 1) * nnS, s));
+        ADJ(S, AK::grid_acc(gS, S->m, S->vn, sb.g3, sb.h1, nullptr, sb.qbar, sb.mbar, s));
+        CUDA_TRY(cudaMemsetAsync(sb.x2, 0, sizeof(double) * D * nS, s));
+        ADJ(S, AK::p2g(nS, S->P.x, (const double*)S->P.v, (const double*)S->P.B, S->P.mass, gS, sb.qbar,
+                       sb.mbar, sb.v2, sb.B2, sb.x2, s));
+        ADJ(S, AK::add(D * nS, sb.x2, sb.ax, s));
+        ADJ(S, AK::add(D * nS, sb.v2, sb.av, s));
+        ADJ(S, AK::add(DD * nS, sb.B2, sb.aB, s));
+      }
+    }
+    if (status != OSMPM_OK) break;
+    // ---- v_S^n = I(v_B^n), then the coarse P2G at t_n
+    CUDA_TRY(cudaMemsetAsync(bb.g2, 0, gvB, s));
+    ADJ(B, AK::interp_t(gB, gS, recvS, sb.g1, bb.g2, s));
+    ADJ(B, AK::grid_acc(gB, B->m, B->vn, nullptr, nullptr, bb.g2, bb.qbar, bb.mbar, s));
+    CUDA_TRY(cudaMemsetAsync(bb.x2, 0, sizeof(double) * D * nB, s));
+    ADJ(B, AK::p2g(nB, B->P.x, (const double*)B->P.v, (const double*)B->P.B, B->P.mass, gB, bb.qbar,
+                   bb.mbar, bb.v2, bb.B2, bb.x2, s));
+    ADJ(B, AK::add(D * nB, bb.x2, bb.ax, s));
+    ADJ(B, AK::add(D * nB, bb.v2, bb.av, s));
+    ADJ(B, AK::add(DD * nB, bb.B2, bb.aB, s));
+    // the start-state adjoints feed the earlier step
+    CUDA_TRY(cudaMemcpyAsync(bb.x, bb.ax, stateB, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(sb.x, sb.ax, stateS, cudaMemcpyDeviceToDevice, s));
+  }
+  const osmpm_status rB = snapshot(B, true), rS = snapshot(S, true);
+  if (status != OSMPM_OK) return status;
+  OSMPM_TRY(rB);
+  OSMPM_TRY(rS);
+  ADJ(B, AK::to_ids(nB, 1, B->P.id, bb.E, out->dJ_dE, s));
+  ADJ(S, AK::to_ids(nS, 1, S->P.id, sb.E, out->dJ_dE + nB, s));
+  struct O4 {
+    double* dst;
+    double *srcB, *srcS;
+    int w;
+  } o4[4] = {{out->dJ_dx0, bb.x, sb.x, D}, {out->dJ_dv0, bb.v, sb.v, D},
+             {out->dJ_dB0, bb.B, sb.B, DD}, {out->dJ_dF0, bb.F, sb.F, DD}};
+  for (auto& o : o4) {
+    if (!o.dst) continue;
+    ADJ(B, AK::to_ids(nB, o.w, B->P.id, o.srcB, o.dst, s));
+    ADJ(S, AK::to_ids(nS, o.w, S->P.id, o.srcS, o.dst + (int64_t)o.w * nB, s));
+  }
+  OSMPM_TRY(sync_scalars(B));
+  OSMPM_TRY(check_err(B));
+  OSMPM_TRY(check_err(S));
+  CUDA_TRY(cudaGetLastError());
+  fill_stats(stats, st, 0, 1, 0.0, 0.0);
+  return OSMPM_OK;
+}
+
 osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const double* dJ_dx,
                            const osmpm_adjoint_out* out, osmpm_stats* stats) {
   OSMPM_TRY(check_domain(coarse));
-  if (fine) return fail(OSMPM_E_UNSUPPORTED, "the coupled (Schwarz) adjoint is not built");
+  if (!dJ_dx || !out || !out->dJ_dE) return fail(OSMPM_E_INVALID, "null dJ_dx or dJ_dE");
+  if (fine) return coupled_adjoint(coarse, fine, dJ_dx, out, stats);
   osmpm_domain* d = coarse;
+  if (d->tape_kind > 1) return fail(OSMPM_E_INVALID, "the record holds coupled steps: pass both domains");
   if (!dJ_dx || !out || !out->dJ_dE) return fail(OSMPM_E_INVALID, "null dJ_dx or dJ_dE");
   if (d->prec != 0) return fail(OSMPM_E_UNSUPPORTED, "reverse mode needs a precision 0 (FP64) domain");
   if (d->tape_broken)
@@ -1158,8 +1546,9 @@ osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const doubl
     st.solves++;
     // 3. -lam . dg/dz for the particle and node inputs of the solve
     ADJ(d, AK::solve(n, d->P.x, (const double*)d->P.F, d->P.mu, d->P.lam, d->P.vol0, d->geo, d->u,
-                     d->cx, xb2, Fb2, Eb, d->err, s));
-    ADJ(d, AK::nodes(d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt, qbar, mbar, s));
+                     d->cx, d->dofmask, xb2, Fb2, Eb, nullptr, d->err, s));
+    CUDA_TRY(cudaMemsetAsync(qbar, 0, sizeof(double) * (D + 1) * nn, s));
+    ADJ(d, AK::nodes(d->geo, d->m, d->vn, d->u, d->cx, d->desc.gravity, dt, nullptr, qbar, mbar, s));
     // 4. transposed P2G
     ADJ(d, AK::p2g(n, d->P.x, (const double*)d->P.v, (const double*)d->P.B, d->P.mass, d->geo, qbar,
                    mbar, vb2, Bb2, xb2, s));

@@ -51,11 +51,30 @@ struct AdjointKernels {
                   cudaStream_t s);
   static void solve(int64_t n, const double* x, const double* F, const double* mu,
                     const double* lam, const double* vol0, const GridGeo& g, const double* u,
-                    const double* lamg, double* xb, double* Fb, double* Eb, int* err,
-                    cudaStream_t s);
+                    const double* lamg, const uint8_t* dofmask, double* xb, double* Fb,
+                    double* Eb, double* klam, int* err, cudaStream_t s);
   static void nodes(const GridGeo& g, const double* m, const double* vn, const double* u,
-                    const double* lamg, const double* gravity, double dt, double* qbar,
-                    double* mbar, cudaStream_t s);
+                    const double* lamg, const double* gravity, double dt, const double* mextra,
+                    double* qbar, double* mbar, cudaStream_t s);
+  // coupled step in reverse
+  static void bc(const GridGeo& g, const uint8_t* recv, const double* m, const double* ubar,
+                 const double* klam, double s0, double s1, double* v0bar, double* v1bar,
+                 cudaStream_t s);
+  static void interp_t(const GridGeo& gB, const GridGeo& gS, const uint8_t* recvS,
+                       const double* vbar, double* out, cudaStream_t s);
+  static void proj_coarse(const GridGeo& gB, const uint8_t* recvB, const double* num,
+                          const double* den, double eps, const double* vbar, double* nbar,
+                          double* dbar, cudaStream_t s);
+  static void proj_fine(const GridGeo& gB, const GridGeo& gS, const double* nbar,
+                        const double* dbar, double* G, double* H, cudaStream_t s);
+  static void inject(const GridGeo& g, const double* m, const double* u, double dt, const double* G,
+                     const double* H, double* ubar, double* mextra, cudaStream_t s);
+  static void grid_acc(const GridGeo& g, const double* m, const double* vn, const double* G,
+                       const double* H, const double* vbar, double* qbar, double* mbar,
+                       cudaStream_t s);
+  static void axpy_active(const GridGeo& g, const double* m, double scale, const double* v,
+                          double* out, cudaStream_t s);
+  static void add(int64_t cnt, const double* src, double* dst, cudaStream_t s);
   static void p2g(int64_t n, const double* x, const double* v, const double* B,
                   const double* mass, const GridGeo& g, const double* qbar, const double* mbar,
                   double* vb_out, double* Bb_out, double* xb, cudaStream_t s);

@@ -432,11 +432,31 @@ def osmpm_record(dom: Domain, enable: bool = True) -> None:
 
 
 def osmpm_adjoint(coarse: Domain, fine: Optional[Domain], dJ_dx, initial_state: bool = False):
-    """Reverse-mode gradient through the steps recorded on ``coarse``
-    (single domain: ``fine`` must be None)."""
-    if fine is not None:
-        _check(_lib.osmpm_adjoint(coarse.h, fine.h, None, None, None), "osmpm_adjoint")
-    return coarse.adjoint(dJ_dx, initial_state)
+    """Reverse-mode gradient through the steps recorded on ``coarse`` (fine
+    None) or through the pair's recorded coupled steps.  In the coupled case
+    dJ_dx is a CUDA float64 tensor (n_coarse + n_fine, dim), coarse rows
+    first, and every output has the same order."""
+    if fine is None:
+        return coarse.adjoint(dJ_dx, initial_state)
+    import torch
+    n, d = coarse.n + fine.n, coarse.dim
+    if dJ_dx.dtype != torch.float64 or not dJ_dx.is_cuda or tuple(dJ_dx.shape) != (n, d):
+        raise ValueError("dJ_dx must be a CUDA float64 tensor of shape (n_coarse + n_fine, dim)")
+    g = dJ_dx.contiguous()
+    torch.cuda.synchronize(g.device)
+    dE = torch.empty(n, dtype=torch.float64, device=g.device)
+    out = osmpm_adjoint_out()
+    out.dJ_dE = dE.data_ptr()
+    state = {}
+    if initial_state:
+        shapes = {"x": (n, d), "v": (n, d), "B": (n, d, d), "F": (n, d, d)}
+        for k, shp in shapes.items():
+            state[k] = torch.empty(shp, dtype=torch.float64, device=g.device)
+            setattr(out, f"dJ_d{k}0", state[k].data_ptr())
+    st = osmpm_stats()
+    _check(_lib.osmpm_adjoint(coarse.h, fine.h, c_void_p(g.data_ptr()), ctypes.byref(out),
+                              ctypes.byref(st)), "osmpm_adjoint")
+    return dE, state, st.as_dict()
 
 
 def _trajectory_function():

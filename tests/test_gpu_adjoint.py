@@ -186,10 +186,120 @@ def test_adjoint_errors(osmpm):
     dom.step(0.01)
     dom.adjoint(g)
     other = osmpm.Domain(spec)
+    g2 = torch.zeros((2 * n, 2), dtype=torch.float64, device="cuda")
     with pytest.raises(osmpm.OsmpmError) as e:
-        osmpm.osmpm_adjoint(dom, other, g)              # coupled adjoint not built
-    assert e.value.status == osmpm.OSMPM_E_UNSUPPORTED
+        osmpm.osmpm_adjoint(dom, other, g2)             # no coupled steps of this pair
+    assert e.value.status == osmpm.OSMPM_E_INVALID
     mixed = osmpm.Domain(dataclasses.replace(spec, precision=1))
     with pytest.raises(osmpm.OsmpmError) as e:
         mixed.record(True)
     assert e.value.status == osmpm.OSMPM_E_UNSUPPORTED
+
+
+# ----------------------------------------------------------------------------
+# coupled steps (Alg. 1) in reverse
+# ----------------------------------------------------------------------------
+def _coupled(tight=True):
+    """The small coupled inclusion (coarse 0.1, fine 0.05, M = 2) with seeded
+    velocities and moduli, as in the oracle's coupled-adjoint pins."""
+    cB, cS, sch, dT = W.inclusion(dx_S=0.05, dx_B=0.1, M=2, E_inc=4e6)
+    rng = np.random.default_rng(3)
+    out = []
+    for spec in (cB, cS):
+        p = spec.particles.copy()
+        p.v = 0.01 * rng.standard_normal(p.v.shape)
+        p.E = p.E * (1.0 + 0.2 * rng.random(p.E.shape))
+        spec = dataclasses.replace(spec, particles=p)
+        if tight:
+            spec = dataclasses.replace(spec, newton_tol=1e-11, cg_rtol=1e-12, cg_max=100000)
+        out.append(spec)
+    return out[0], out[1], sch, dT, rng
+
+
+def _coupled_gpu(osmpm, cB, cS, sch, dT, c, n_steps, initial_state=False):
+    import torch
+    B, S = osmpm.Domain(cB), osmpm.Domain(cS)
+    B.record(True)
+    S.record(True)
+    iters = []
+    for _ in range(n_steps):
+        iters.append(osmpm.osmpm_schwarz_couple(B, S, dT, sch)["schwarz_iters"])
+    g = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+    dE, state, st = osmpm.osmpm_adjoint(B, S, g, initial_state)
+    return iters, dE.cpu().numpy(), {k: v.cpu().numpy() for k, v in state.items()}, st, (B, S)
+
+
+def _coupled_oracle(cB, cS, sch, dT, c, iters):
+    nB = cB.particles.n
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    recs = [AD.record_schwarz_step(B, S, dT, sch, 1e-12, k) for k in iters]
+    z = lambda p: AD.StateBar.zeros_like(p)
+    barB, barS = z(B.p), z(S.p)
+    barB.x = c[:nB].copy()
+    barS.x = c[nB:].copy()
+    EB = np.zeros(nB)
+    ES = np.zeros(cS.particles.n)
+    for rec in reversed(recs):
+        barB, barS, eb, es = AD.schwarz_adjoint(rec, barB, barS)
+        EB += eb
+        ES += es
+    return np.concatenate([EB, ES]), barB, barS, (B, S)
+
+
+@pytest.mark.parametrize("n_steps", [1, 2])
+def test_coupled_adjoint_matches_oracle(osmpm, n_steps):
+    cB, cS, sch, dT, rng = _coupled()
+    n = cB.particles.n + cS.particles.n
+    c = rng.standard_normal((n, 2))
+    iters, dE, st0, st, (B, S) = _coupled_gpu(osmpm, cB, cS, sch, dT, c, n_steps, True)
+    oE, barB, barS, (oB, oS) = _coupled_oracle(cB, cS, sch, dT, c, iters)
+    # the same unrolled iterations give the same forward ...
+    assert _rel(B.get_particles()[0], oB.p.x) <= 1e-9
+    assert _rel(S.get_particles()[0], oS.p.x) <= 1e-9
+    assert st["solves"] == sum(k * (1 + sch.M) for k in iters)
+    # ... and the same gradients
+    assert _rel(dE, oE) <= 1e-6
+    assert _rel(st0["x"], np.concatenate([barB.x, barS.x])) <= 1e-6
+    assert _rel(st0["v"], np.concatenate([barB.v, barS.v])) <= 1e-6
+    assert _rel(st0["B"], np.concatenate([barB.B, barS.B])) <= 1e-6
+    assert _rel(st0["F"], np.concatenate([barB.F, barS.F])) <= 1e-6
+
+
+def test_coupled_adjoint_matches_central_differences_of_the_cuda_path(osmpm):
+    cB, cS, sch, dT, rng = _coupled()
+    nB, nS = cB.particles.n, cS.particles.n
+    c = rng.standard_normal((nB + nS, 2))
+    iters, dE, _, _, _ = _coupled_gpu(osmpm, cB, cS, sch, dT, c, 1)
+
+    def J(specB, specS):
+        B, S = osmpm.Domain(specB), osmpm.Domain(specS)
+        it = osmpm.osmpm_schwarz_couple(B, S, dT, sch)["schwarz_iters"]
+        x = np.concatenate([B.get_particles()[0], S.get_particles()[0]])
+        return float(np.sum(c * x)), it
+
+    for which, spec, off in (("B", cB, 0), ("S", cS, nB)):
+        for p in rng.choice(spec.particles.n, 2, replace=False):
+            h = 1e-4 * spec.particles.E[p]
+            vals = []
+            for sgn in (1.0, -1.0):
+                q = spec.particles.copy()
+                q.E[p] += sgn * h
+                s2 = dataclasses.replace(spec, particles=q)
+                vals.append(J(s2, cS) if which == "B" else J(cB, s2))
+            assert vals[0][1] == vals[1][1] == iters[0]
+            fd = (vals[0][0] - vals[1][0]) / (2 * h)
+            np.testing.assert_allclose(dE[off + p], fd, rtol=1e-4, atol=1e-5 * np.abs(dE).max())
+
+
+def test_coupled_record_is_interrupted_by_a_single_step(osmpm):
+    import torch
+    cB, cS, sch, dT, _ = _coupled(tight=False)
+    B, S = osmpm.Domain(cB), osmpm.Domain(cS)
+    B.record(True)
+    S.record(True)
+    osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+    B.step(dT)                                          # not part of a coupled record
+    g = torch.zeros((cB.particles.n + cS.particles.n, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(osmpm.OsmpmError) as e:
+        osmpm.osmpm_adjoint(B, S, g)
+    assert e.value.status == osmpm.OSMPM_E_INVALID
