@@ -454,6 +454,51 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_fold(args, rank, local, world):
+    """The 3D folding plate (mixed precision): coarse plate at 0.02, fine
+    hinge band at 0.005 (128k particles) or, with --scaled, a band [0.2, 0.8]
+    at 0.0025 (3.07M particles), M = 4.  Times --steps coupled steps after
+    --warmup with CUDA events on the domains' stream; the per-kernel HBM
+    fractions of this configuration come from ncu (profiles)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2605_09097_gb300 import build
+    build.build()
+    from paper_2605_09097_gb300 import osmpm
+    kw = dict(dx_f=0.0025, band=(0.2, 0.8)) if args.scaled else {}
+    cB, cS, sch, dT = W.fold3d(**kw)
+    units = cB.particles.n + sch.M * cS.particles.n
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        B = osmpm.Domain(cB, stream=stream.cuda_stream)
+        S = osmpm.Domain(cS, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+        torch.cuda.synchronize()
+        B.set_profiling(True)
+        S.set_profiling(True)
+        stats, ms = [], 0.0
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stats.append(osmpm.osmpm_schwarz_couple(B, S, dT, sch))
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        cS_ = S.counters()
+    return {"metric": METRIC, "value": units * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
+            "data": "synthetic",
+            "config": {"workload": "fold3d_mixed" + ("_scaled" if args.scaled else ""),
+                       "particles_coarse": cB.particles.n, "particles_fine": cS.particles.n,
+                       "M": sch.M, "dT": dT, "units_per_step": units,
+                       "schwarz_iters_per_step": [s["schwarz_iters"] for s in stats],
+                       "newton_iters_per_step": [s["newton_iters"] for s in stats],
+                       "cg_iters_per_step": [s["cg_iters"] for s in stats],
+                       "fine_us_per_pcg_iter": 1e3 * cS_["pcg_ms"] / max(cS_["pcg_iters"], 1)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,8 +507,10 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["inclusion", "batched"], default="inclusion",
-                    help="inclusion: the headline FP64 configuration; batched: many instances")
+    ap.add_argument("--workload", choices=["inclusion", "batched", "fold3d"], default="inclusion",
+                    help="inclusion: the headline FP64 configuration; batched: many instances; "
+                         "fold3d: the 3D folding plate (mixed)")
+    ap.add_argument("--scaled", action="store_true", help="fold3d: the 3.07M-particle band")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--threads", type=int, default=16)
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
@@ -473,6 +520,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.workload == "batched":
         out = run_batched(args, rank, local, world)
+    elif args.workload == "fold3d":
+        out = run_fold(args, rank, local, world)
     else:
         out = run_ours(args, rank, local, world)
     if rank == 0 and out is not None:

@@ -87,7 +87,11 @@ typedef struct osmpm_domain_desc {
   double mass_eps;          /* active nodes (the set N of Sec. 3.2.1): m_i > mass_eps >= 0 */
   double cg_eta_max;        /* inexact Newton: PCG stops at eta |r_0|, eta = |g_k|/|g_0|
                                clamped to [cg_rtol, cg_eta_max]; 0 means 1e-3; < 1 */
-  int32_t reserved[6];      /* must be zero */
+  int32_t pcg_mode;         /* 0: automatic (the persistent single-launch PCG when one
+                               co-resident pass covers the problem, else the streaming
+                               PCG of three kernels per iteration); 1: persistent;
+                               2: streaming */
+  int32_t reserved[5];      /* must be zero */
 } osmpm_domain_desc;
 
 /* Initial particle state, host arrays in id order (layouts above).  flags

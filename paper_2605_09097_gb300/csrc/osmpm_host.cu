@@ -422,8 +422,8 @@ struct SolveStats {
 // |r| <= rtol |r0| (device-side control, host polls once per chunk).
 // Launches the persistent PCG kernel with the domain's buffers (x, r[2],
 // s[2], w[3], p) and one block per SM; records the timing events if asked.
-template <class K, class R>
-cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
+template <class R>
+PcgArgsT<R> pcg_args(osmpm_domain* d, double dt) {
   PcgArgsT<R> a{};
   a.P = typed<R>(d->P);
   a.g = d->geo;
@@ -446,6 +446,26 @@ cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
   a.err = d->err;
   a.sbase = d->sbase;
   a.sdn = (const R*)d->sdn;
+  return a;
+}
+
+// Automatic PCG choice: the persistent kernel while its co-resident grid
+// covers the problem in at most kMaxPasses[dim] passes, else the streaming
+// kernels (measured: the register-light 2D persistent kernel stays ahead up
+// to about 1M particles, the 3D one only for small problems).
+constexpr int64_t kMaxPasses2D = 64, kMaxPasses3D = 4;
+
+template <class K, class R>
+bool pcg_persistent_fits(osmpm_domain* d, double dt, int64_t work) {
+  int blocks = 0, threads = 0;
+  K::pcg_shape(work, d->pcg_share, &blocks, &threads);
+  const int64_t passes = K::pcg_passes(pcg_args<R>(d, dt), blocks, threads);
+  return passes <= (d->dim == 2 ? kMaxPasses2D : kMaxPasses3D);
+}
+
+template <class K, class R>
+cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
+  const PcgArgsT<R> a = pcg_args<R>(d, dt);
   int blocks = 0, threads = 0;
   K::pcg_shape(work, d->pcg_share, &blocks, &threads);
   if (timed) {
@@ -456,6 +476,19 @@ cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
   if (le != cudaSuccess) return le;
   if (timed) return cudaEventRecord(d->ev[1], d->stream);
   return cudaSuccess;
+}
+
+// Streaming PCG: the start kernel, then chunks of kStreamChunk iterations
+// (kernels launched after convergence return at once) with a look at the
+// device flags between chunks.
+constexpr int kStreamChunk = 16;
+
+template <class K, class R>
+cudaError_t stream_pcg_chunk(osmpm_domain* d, double dt, bool first) {
+  const PcgArgsT<R> a = pcg_args<R>(d, dt);
+  if (first) K::cgs_start(a, d->stream);
+  for (int i = 0; i < kStreamChunk; ++i) K::cgs_iteration(a, d->stream);
+  return cudaGetLastError();
 }
 
 // Newton forcing bound: PCG tolerance eta |r0| with eta <= cg_eta_max
@@ -495,9 +528,22 @@ osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st) {
   const int GP = 32 / (D == 2 ? 3 : 9);
   const int64_t work = std::max<int64_t>((d->n + GP - 1) / GP * 32, D * nn);
   const bool timed = d->time_hvp && !d->ev.empty();
+  bool streaming = d->desc.pcg_mode == 2;
+  if (d->desc.pcg_mode == 0) DISPATCH(d, (streaming = !pcg_persistent_fits<K, R>(d, dt, work)));
   cudaError_t le = cudaSuccess;
-  DISPATCH(d, (le = launch_pcg<K, R>(d, dt, work, timed)));
-  if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(le));
+  if (!streaming) {
+    DISPATCH(d, (le = launch_pcg<K, R>(d, dt, work, timed)));
+    if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(le));
+  } else {
+    if (timed) CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
+    for (bool first = true;; first = false) {
+      DISPATCH(d, (le = stream_pcg_chunk<K, R>(d, dt, first)));
+      if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "streaming PCG launch: %s", cudaGetErrorString(le));
+      OSMPM_TRY(sync_scalars(d));
+      if (d->S_host->cg_done || d->S_host->err) break;
+    }
+    if (timed) CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
+  }
   if (newton) DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
   OSMPM_TRY(sync_scalars(d));
   OSMPM_TRY(check_err(d));
@@ -779,8 +825,9 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   if (desc->dim != 2 && desc->dim != 3) return fail(OSMPM_E_INVALID, "dim must be 2 or 3");
   if (desc->precision != 0 && desc->precision != 1)
     return fail(OSMPM_E_INVALID, "precision must be 0 (FP64) or 1 (mixed)");
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 5; ++i)
     if (desc->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
+  if (desc->pcg_mode < 0 || desc->pcg_mode > 2) return fail(OSMPM_E_INVALID, "pcg_mode must be 0, 1 or 2");
   if (!(desc->cg_eta_max >= 0.0 && desc->cg_eta_max < 1.0))
     return fail(OSMPM_E_INVALID, "cg_eta_max must be in [0, 1)");
   if (!(desc->dx > 0.0) || !std::isfinite(desc->dx)) return fail(OSMPM_E_INVALID, "dx must be > 0");

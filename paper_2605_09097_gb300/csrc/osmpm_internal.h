@@ -126,6 +126,13 @@ struct Kernels {
   // persistent cooperative PCG (whole solve in one launch)
   static void pcg_shape(int64_t work, int share, int* blocks, int* threads);
   static cudaError_t pcg(const PcgArgsT<R>& a, int blocks, int threads, cudaStream_t s);
+  // does one co-resident pass of the persistent PCG cover the problem, and
+  // how many passes does it need?
+  static bool pcg_one_pass(const PcgArgsT<R>& a, int blocks, int threads);
+  static int64_t pcg_passes(const PcgArgsT<R>& a, int blocks, int threads);
+  // streaming PCG: start, then per iteration hvp, alpha, beta
+  static void cgs_start(const PcgArgsT<R>& a, cudaStream_t s);
+  static void cgs_iteration(const PcgArgsT<R>& a, cudaStream_t s);
   static void hvp_only(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
                        const uint8_t* dofmask, const R* L, double dt, double* p, double* q,
                        DevScalars* S, double* partials, cudaStream_t s);

@@ -1184,12 +1184,36 @@ cudaError_t Kernels<D, R>::pcg(const PcgArgsT<R>& a, int blocks, int threads, cu
   g_launch_count += 1;
   // the single-pass variant when every thread owns at most one DOF and every
   // lane at most one particle
+  const bool one = pcg_one_pass(a, blocks, threads);
+  const void* fn = one ? (const void*)k_pcg<D, R, true> : (const void*)k_pcg<D, R, false>;
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
+}
+template <int D, typename R>
+bool Kernels<D, R>::pcg_one_pass(const PcgArgsT<R>& a, int blocks, int threads) {
   const int64_t ndof = a.g.nn * D;
   const int64_t chunk = (ndof + blocks - 1) / blocks;
   const int64_t groups = (a.P.n + HvpGroup<D>::GP - 1) / HvpGroup<D>::GP;
-  const bool one = chunk <= threads && groups <= (int64_t)blocks * threads / 32;
-  const void* fn = one ? (const void*)k_pcg<D, R, true> : (const void*)k_pcg<D, R, false>;
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
+  return chunk <= threads && groups <= (int64_t)blocks * threads / 32;
+}
+template <int D, typename R>
+int64_t Kernels<D, R>::pcg_passes(const PcgArgsT<R>& a, int blocks, int threads) {
+  const int64_t ndof = a.g.nn * D;
+  const int64_t dpass = (ndof + (int64_t)blocks * threads - 1) / ((int64_t)blocks * threads);
+  const int64_t warps = (int64_t)blocks * threads / 32;
+  const int64_t groups = (a.P.n + HvpGroup<D>::GP - 1) / HvpGroup<D>::GP;
+  const int64_t ppass = (groups + warps - 1) / warps;
+  return dpass > ppass ? dpass : ppass;
+}
+template <int D, typename R>
+void Kernels<D, R>::cgs_start(const PcgArgsT<R>& a, cudaStream_t s) {
+  k_cgs_start<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
+}
+template <int D, typename R>
+void Kernels<D, R>::cgs_iteration(const PcgArgsT<R>& a, cudaStream_t s) {
+  const int64_t lanes = (a.P.n + HvpGroup<D>::GP - 1) / HvpGroup<D>::GP * 32;
+  k_cgs_hvp<D, R><<<OSMPM_RB(lanes)>>>(a);
+  k_cgs_alpha<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
+  k_cgs_beta<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
 }
 
 template <int D, typename R>

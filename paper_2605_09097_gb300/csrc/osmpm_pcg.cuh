@@ -515,4 +515,141 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Streaming PCG for problems that one co-resident pass does not cover: the
+// same Jacobi PCG as three small kernels per iteration at full occupancy,
+// the kernel boundaries standing in for the grid barrier.  The scalars stay
+// on the device; a kernel launched after convergence returns at once, so
+// the host enqueues iterations in chunks and looks at the flag between them.
+//   k_cgs_start: q = 0 and the mass part of p.Ap (r, z = D^-1 r, p = z,
+//                x = 0 and r.z come from the gradient kernel); vectors x = a.x,
+//                r = a.r[0], z = a.r[1], p = a.s[0], q = a.w[0]
+//   k_cgs_hvp:   q = K p by the particle gather-scatter (lane groups) and
+//                the particle part p:Kp = sum_p G : L G
+//   k_cgs_alpha: alpha = r.z / p.Ap; x += alpha p; r -= alpha (q + M/dt^2 p);
+//                z = D^-1 r; the last block takes r.z, r.r, beta and the
+//                stopping tests
+//   k_cgs_beta:  p = z + beta p, q = 0, the mass part of the next p.Ap
+// Deterministic: every sum is taken in block order by the last block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t cgs_tid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t cgs_stride() { return (int64_t)gridDim.x * blockDim.x; }
+
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_cgs_start(PcgArgsT<R> a) {
+  const GridGeo& g = a.g;
+  double acc[1] = {0.0};
+  for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
+    const int c = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)c * g.nn;
+    a.w[0][idx] = 0.0;
+    if ((a.dofmask[i] >> c) & 1u) {
+      const double pi = a.s[0][idx];
+      acc[0] += a.m[i] * a.inv_dt2 * pi * pi;
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, a.partials, &a.S->counter, tot) && threadIdx.x == 0) {
+    a.S->pq_diag = tot[0];
+    a.S->cg_iter = 0;
+    a.S->cg_neg = 0;
+    if (a.S->cg_max <= 0) a.S->cg_done = 1;
+  }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_cgs_hvp(PcgArgsT<R> a) {
+  if (__ldcg(&a.S->cg_done)) return;
+  constexpr int LPP = HvpGroup<D>::LPP, GP = HvpGroup<D>::GP;
+  const int64_t tid = cgs_tid(), stride = cgs_stride();
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / LPP;
+  const int q = lane - grp * LPP;
+  const int leader = grp * LPP;
+  const bool in_group = grp < GP;
+  const double* p = a.s[0];
+  double acc[1] = {0.0};
+  for (int64_t b0 = (tid >> 5) * GP; b0 < a.P.n; b0 += (stride >> 5) * GP) {
+    const int64_t pi = b0 + grp;
+    acc[0] += group_hvp<D, R>(a, pi, in_group && pi < a.P.n, q, leader,
+                              [=](int64_t j) { return __ldcg(&p[j]); }, a.w[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, a.partials, &a.S->counter, tot) && threadIdx.x == 0) a.S->pq = tot[0];
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_cgs_alpha(PcgArgsT<R> a) {
+  DevScalars* S = a.S;
+  if (__ldcg(&S->cg_done)) return;
+  const GridGeo& g = a.g;
+  const double pAp = __ldcg(&S->pq) + __ldcg(&S->pq_diag);
+  const double rz = __ldcg(&S->rz);
+  const int it = __ldcg(&S->cg_iter);
+  if (!(pAp > 0.0)) {
+    // negative curvature: stop; with no direction yet take z_0 = D^-1 r_0
+    if (it == 0)
+      for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
+        const int c = (int)(idx / g.nn);
+        const int64_t i = idx - (int64_t)c * g.nn;
+        if ((a.dofmask[i] >> c) & 1u) a.x[idx] = a.s[0][idx];
+      }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->cg_neg = 1;
+      S->cg_done = 1;
+    }
+    return;
+  }
+  const double alpha = rz / pAp;
+  double* r = a.r[0];
+  double* z = a.r[1];
+  double acc[2] = {0.0, 0.0};
+  for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
+    const int c = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)c * g.nn;
+    if ((a.dofmask[i] >> c) & 1u) {
+      const double pi = a.s[0][idx];
+      a.x[idx] += alpha * pi;
+      const double ap = a.w[0][idx] + a.m[i] * a.inv_dt2 * pi;
+      const double ri = r[idx] - alpha * ap;
+      r[idx] = ri;
+      const double zi = ri * a.diag[idx];
+      z[idx] = zi;
+      acc[0] += ri * zi;
+      acc[1] += ri * ri;
+    }
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, a.partials, &S->counter, tot) && threadIdx.x == 0) {
+    const int itn = it + 1;
+    S->cg_iter = itn;
+    S->beta = tot[0] / rz;
+    S->rz = tot[0];
+    S->rr = tot[1];
+    if (tot[1] <= S->tol2 || itn >= S->cg_max) S->cg_done = 1;
+  }
+}
+
+template <int D, typename R>
+__global__ void __launch_bounds__(kThreads) k_cgs_beta(PcgArgsT<R> a) {
+  DevScalars* S = a.S;
+  if (__ldcg(&S->cg_done)) return;
+  const GridGeo& g = a.g;
+  const double beta = __ldcg(&S->beta);
+  const double* z = a.r[1];
+  double acc[1] = {0.0};
+  for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
+    const int c = (int)(idx / g.nn);
+    const int64_t i = idx - (int64_t)c * g.nn;
+    a.w[0][idx] = 0.0;
+    if ((a.dofmask[i] >> c) & 1u) {
+      const double pi = z[idx] + beta * a.s[0][idx];
+      a.s[0][idx] = pi;
+      acc[0] += a.m[i] * a.inv_dt2 * pi * pi;
+    }
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, a.partials, &S->counter, tot) && threadIdx.x == 0) S->pq_diag = tot[0];
+}
+
 }  // namespace osmpm

@@ -62,7 +62,7 @@ class osmpm_domain_desc(Structure):
                 ("dx", c_double), ("res", c_int32 * 3), ("gravity", c_double * 3),
                 ("newton_tol", c_double), ("newton_max", c_int32), ("cg_rtol", c_double),
                 ("cg_max", c_int32), ("ls_max", c_int32), ("mass_eps", c_double),
-                ("cg_eta_max", c_double), ("reserved", c_int32 * 6)]
+                ("cg_eta_max", c_double), ("pcg_mode", c_int32), ("reserved", c_int32 * 5)]
 
 
 class osmpm_particles_in(Structure):
@@ -226,6 +226,7 @@ def make_desc(spec) -> osmpm_domain_desc:
     d.ls_max = spec.ls_max
     d.mass_eps = spec.mass_eps
     d.cg_eta_max = getattr(spec, "cg_eta_max", 0.0)
+    d.pcg_mode = getattr(spec, "pcg_mode", 0)
     return d
 
 

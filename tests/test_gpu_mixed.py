@@ -43,6 +43,18 @@ def test_mixed_cantilever_100_steps(osmpm):
     np.testing.assert_allclose(F, ref.p.F, atol=1e-5)
 
 
+def test_mixed_streaming_pcg(osmpm):
+    """Mixed precision with the streaming PCG forced: 20 cantilever steps."""
+    spec = dataclasses.replace(W.cantilever(), precision=1, pcg_mode=2)
+    dom = osmpm.Domain(spec)
+    ref = O.DomainState.create(W.cantilever())
+    x0 = spec.particles.x.copy()
+    for _ in range(20):
+        dom.step(1e-3)
+        O.step(ref, 1e-3)
+    assert rel_disp(dom.get_particles()[0], ref.p.x, x0) <= MIXED_TOL
+
+
 def test_mixed_state_is_stored_in_fp32(osmpm):
     spec = W.perturb(W.block(2, n_cells=(4, 3), dx=0.1), 3)
     spec = dataclasses.replace(spec, precision=1)

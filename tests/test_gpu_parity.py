@@ -121,9 +121,11 @@ def test_free_flight(osmpm):
     np.testing.assert_allclose(F, np.broadcast_to(np.eye(2), F.shape), atol=1e-14)
 
 
-def test_cantilever_20_steps_matches_oracle(osmpm):
-    """Small configuration: 2D cantilever, 2560 particles, dt = 1e-3, 20 steps."""
-    spec = W.cantilever()
+@pytest.mark.parametrize("pcg_mode", [0, 2])
+def test_cantilever_20_steps_matches_oracle(osmpm, pcg_mode):
+    """Small configuration: 2D cantilever, 2560 particles, dt = 1e-3, 20 steps
+    (the persistent PCG, and the streaming PCG forced)."""
+    spec = dataclasses.replace(W.cantilever(), pcg_mode=pcg_mode)
     dom = osmpm.Domain(spec)
     ref = O.DomainState.create(spec)
     x0 = spec.particles.x.copy()
@@ -136,9 +138,10 @@ def test_cantilever_20_steps_matches_oracle(osmpm):
     np.testing.assert_allclose(v, ref.p.v, atol=1e-6 * np.abs(ref.p.v).max())
 
 
-@pytest.mark.parametrize("dim", [2, 3])
-def test_random_state_steps_match_oracle(osmpm, dim):
+@pytest.mark.parametrize("dim,pcg_mode", [(2, 0), (3, 0), (2, 2), (3, 2)])
+def test_random_state_steps_match_oracle(osmpm, dim, pcg_mode):
     spec = _perturbed(dim, 11, n_cells=(6, 5, 4), dx=0.1, E=1e5, gravity=(0.0, -9.8, 0.0)[:dim])
+    spec.pcg_mode = pcg_mode
     spec.dirichlet = [W.Dirichlet(lo=(-1e30,) * dim, hi=(0.05,) + (1e30,) * (dim - 1),
                                   comp_mask=(1 << dim) - 1)]
     dom = osmpm.Domain(spec)
@@ -207,6 +210,24 @@ def test_schwarz_subcycling_ratio(osmpm, M):
     xB, _, _, _ = B.get_particles()
     assert rel_disp(xS, rS.p.x, cS.particles.x) <= DISP_TOL
     assert rel_disp(xB, rB.p.x, cB.particles.x) <= DISP_TOL
+
+
+def test_schwarz_streaming_pcg_matches_oracle(osmpm):
+    """The coupled step with the streaming PCG forced on both domains."""
+    cB, cS, sch, dT = W.inclusion(dx_S=0.02, M=2)
+    cB = dataclasses.replace(cB, pcg_mode=2)
+    cS = dataclasses.replace(cS, pcg_mode=2)
+    B, S, rB, rS, out = _run_schwarz(osmpm, cB, cS, sch, dT, 1)
+    st, ost, _ = out[-1]
+    assert st["converged"] == 1 and abs(st["schwarz_iters"] - ost.iters) <= 1
+    assert rel_disp(S.get_particles()[0], rS.p.x, cS.particles.x) <= DISP_TOL
+    assert rel_disp(B.get_particles()[0], rB.p.x, cB.particles.x) <= DISP_TOL
+
+
+def test_pcg_mode_validated(osmpm):
+    with pytest.raises(osmpm.OsmpmError) as e:
+        osmpm.Domain(dataclasses.replace(W.cantilever(), pcg_mode=3))
+    assert e.value.status == osmpm.OSMPM_E_INVALID
 
 
 def test_schwarz_last_substep_projection_matches_oracle(osmpm):
