@@ -497,15 +497,21 @@ constexpr double kEtaMax = 1e-3;
 
 osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st);
 
-osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, SolveStats& st) {
+// The confirming Newton step: once the previous step is within
+// kCheckRatio x the tolerance, the next one (expected below it) is solved
+// only to kCheckEta and accepted when max |delta| <= tol / 2.
+constexpr double kCheckRatio = 500.0, kCheckEta = 0.1;
+
+osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check, SolveStats& st) {
   const int64_t nn = d->geo.nn;
   const int D = d->dim;
   CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
   DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
-  DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt,
-                             d->desc.cg_rtol, d->desc.cg_eta_max > 0.0 ? d->desc.cg_eta_max : kEtaMax,
-                             first ? 1 : 0, d->desc.cg_max, d->grad,
+  const double eta_max = d->desc.cg_eta_max > 0.0 ? d->desc.cg_eta_max : kEtaMax;
+  const double rtol = check ? std::max(kCheckEta, d->desc.cg_rtol) : d->desc.cg_rtol;
+  DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt, rtol,
+                             check ? rtol : eta_max, first ? 1 : 0, d->desc.cg_max, d->grad,
                              d->diag, d->cx, d->cr, d->cz, d->cp, d->S, d->partials, d->stream));
   return run_pcg(d, dt, true, st);
 }
@@ -576,13 +582,15 @@ osmpm_status cold_start(osmpm_domain* d, double dt) {
 osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
   st.solves++;
   const double tol = d->desc.newton_tol * dt;
+  double prev_dx = INFINITY;
   for (int it = 0; it < d->desc.newton_max; ++it) {
     st.newton++;
-    OSMPM_TRY(gradient_and_pcg(d, dt, it == 0, st));
+    const bool check = it > 0 && prev_dx <= kCheckRatio * tol;
+    OSMPM_TRY(gradient_and_pcg(d, dt, it == 0, check, st));
     const double dxinf = d->S_host->maxabs;
     st.last_dx = dxinf;
     if (!std::isfinite(dxinf)) return fail(OSMPM_E_NONFINITE, "non-finite Newton step");
-    if (dxinf <= tol) {
+    if (dxinf <= (check ? 0.5 * tol : tol)) {
       DISPATCH(d, K::axpy(d->geo, d->u, d->cx, 1.0, d->stream));
       return OSMPM_OK;
     }
@@ -601,6 +609,7 @@ osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
     }
     if (!ok) return fail(OSMPM_E_LINESEARCH, "no decrease of E_h after %d halvings", d->desc.ls_max);
     DISPATCH(d, K::axpy(d->geo, d->u, d->cx, alpha, d->stream));
+    prev_dx = alpha * dxinf;
   }
   return fail(OSMPM_E_NEWTON_MAXITER, "Newton did not reach %g in %d iterations (last |dx| %g)",
               d->desc.newton_tol, d->desc.newton_max, st.last_dx);

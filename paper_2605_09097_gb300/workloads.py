@@ -345,6 +345,64 @@ def hertz(dx_c: float = 1.0 / 64, ratio: int = 4, M: int = 4, E_block: float = 1
     return coarse, fine, sch, dT
 
 
+def hertz_rigid(dx_c: float = 1.0 / 64, ratio: int = 4, M: int = 4, E: float = 2e5,
+                nu: float = 0.3, rho: float = 1000.0, R: float = 0.5, dT: float = 0.02,
+                indent: float = 0.01, n_steps: int = 10, ppc_1d: int = 2,
+                box_half=(0.25, 0.125), precision: int = 0, newton_tol: float = 1e-8,
+                cg_rtol: float = 1e-6):
+    """The Hertz benchmark of Sec. 4.2: a half-disk cylinder r < R, y < R
+    centred at (0, R) (flat face up, lowest point touching the plane y = 0)
+    pressed onto a rigid frictionless plane.  The plane is the grid nodes
+    with y <= 0, whose y velocity is held at zero (x free); the flat face's
+    nodes move down by ``indent`` over ``n_steps`` global steps of dT.  Fine
+    subdomain: the box [-bx, bx] x [0, by] around the contact at dx_c /
+    ratio; coarse: the cylinder minus that box shrunk by 2 dx_c.  Returns
+    (coarse, fine, schwarz, dT)."""
+    c = np.array([0.0, R])
+    dx_f = dx_c / ratio
+    blo = np.array([-box_half[0], 0.0])
+    bhi = np.array([box_half[0], box_half[1]])
+
+    def cyl(x):
+        return (_r2(x, c) < R * R) & (x[:, 1] < c[1])
+
+    def in_box(x, lo, hi):
+        return np.all((x >= lo) & (x < hi), axis=1)
+
+    hole_lo, hole_hi = blo + np.array([2 * dx_c, -BIG]), bhi - 2 * dx_c
+    m = 3
+    nx = int(round(2 * (R + 0.05) / dx_c))
+    ny = int(round((R + 0.05) / dx_c))
+    gB = Grid(2, (-(R + 0.05) - m * dx_c, -m * dx_c), dx_c, (nx + 2 * m + 1, ny + 2 * m + 1))
+    xB = sample_lattice(gB.origin, dx_c, (m, m), (m + nx, m + ny), ppc_1d,
+                        lambda x: cyl(x) & ~in_box(x, hole_lo, hole_hi))
+    sB = dx_c / ppc_1d
+    flB = np.where(in_box(xB, hole_lo - sB, hole_hi + sB), FLAG_BOUNDARY, 0).astype(np.uint8)
+    pB = make_particles(xB, dx_c, ppc_1d, rho, E, nu, flB)
+    v_push = -indent / (n_steps * dT)
+    plane = lambda dx: Dirichlet(lo=(-BIG, -BIG), hi=(BIG, 0.5 * dx), comp_mask=0b10)
+    top = Dirichlet(lo=(-BIG, R - 0.5 * dx_c), hi=(BIG, BIG), comp_mask=0b11, vel=(0.0, v_push, 0.0))
+    coarse = DomainSpec("hertz_rigid_coarse", gB, pB, (0.0, 0.0), [plane(dx_c), top],
+                        newton_tol=newton_tol, cg_rtol=cg_rtol, precision=precision)
+    mf = 3
+    nfx = int(round((bhi[0] - blo[0]) / dx_f))
+    nfy = int(round((bhi[1] - blo[1]) / dx_f))
+    o = (blo[0] - mf * dx_f, blo[1] - mf * dx_f)
+    gS = Grid(2, o, dx_f, (nfx + 2 * mf + 1, nfy + 2 * mf + 1))
+    xS = sample_lattice(o, dx_f, (mf, mf), (mf + nfx, mf + nfy), ppc_1d,
+                        lambda x: cyl(x) & in_box(x, blo, bhi))
+    sS = dx_f / ppc_1d
+    inner = in_box(xS, blo + np.array([sS, -BIG]), bhi - sS)
+    flS = np.where(~inner, FLAG_BOUNDARY, 0).astype(np.uint8)
+    pS = make_particles(xS, dx_f, ppc_1d, rho, E, nu, flS)
+    fine = DomainSpec("hertz_rigid_fine", gS, pS, (0.0, 0.0), [plane(dx_f)],
+                      newton_tol=newton_tol, cg_rtol=cg_rtol, precision=precision)
+    sch = SchwarzSpec(M=M, k_max=50, eps_conv=1e-5,
+                      tau_B=rho * dx_c ** 2 / ppc_1d ** 2, tau_S=rho * dx_f ** 2 / ppc_1d ** 2,
+                      eps_tol=1e-12 * rho * dx_f ** 2)
+    return coarse, fine, sch, dT
+
+
 def fold3d(dx_c: float = 0.02, dx_f: float = 0.005, band=(0.4, 0.6), M: int = 4,
            size=(1.0, 0.5, 0.02), E: float = 1e6, nu: float = 0.3, rho: float = 1000.0,
            dT: float = 0.01, fold_steps: int = 400, ppc_1d: int = 2, precision: int = 1,
