@@ -168,8 +168,10 @@ typedef struct osmpm_domain osmpm_domain;
 /* Creates a domain: validates the descriptor and particles, copies the
  * particles to the device (allocator, stream), sorts them by the Morton code
  * of their base node (ties keep id order) and computes the Lame parameters
- * mu = E/(2(1+nu)), lam = E nu/((1+nu)(1-2nu)).  Errors: OSMPM_E_INVALID,
- * OSMPM_E_NONFINITE, OSMPM_E_OUT_OF_GRID, OSMPM_E_NOMEM, OSMPM_E_CUDA. */
+ * mu = E/(2(1+nu)), lam = E nu/((1+nu)(1-2nu)).  Errors: OSMPM_E_INVALID
+ * (among others a particle count outside [1, 2^31 - 1], nu outside (-1, 0.5),
+ * a non-positive mass or volume), OSMPM_E_NONFINITE, OSMPM_E_OUT_OF_GRID,
+ * OSMPM_E_NOMEM, OSMPM_E_CUDA. */
 osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc,
                                  const osmpm_particles_in* particles,
                                  const osmpm_allocator* allocator,

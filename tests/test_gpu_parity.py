@@ -335,6 +335,53 @@ def test_single_particle(osmpm):
     np.testing.assert_allclose(dom.get_particles()[0], ref.p.x, atol=1e-15)
 
 
+def _subset(spec, keep):
+    p = spec.particles
+    q = W.Particles(*(np.array(getattr(p, f.name)[keep], copy=True)
+                      for f in dataclasses.fields(p)))
+    return dataclasses.replace(spec, particles=q)
+
+
+@pytest.mark.parametrize("dim,n_keep,pcg_mode", [(2, 67, 0), (2, 67, 2), (3, 61, 0), (3, 61, 2)])
+def test_ragged_particle_counts_match_oracle(osmpm, dim, n_keep, pcg_mode):
+    """Particle counts that fill neither lane groups (3 per particle in 2D,
+    9 in 3D), warps nor blocks, in both PCG engines: a random subset of a
+    perturbed block with gravity and a clamped face."""
+    spec = _perturbed(dim, 13, n_cells=(5, 4, 3), dx=0.1, E=1e5, gravity=(0.0, -9.8, 0.0)[:dim])
+    keep = np.sort(np.random.default_rng(5).choice(spec.particles.n, n_keep, replace=False))
+    spec = _subset(spec, keep)
+    spec.dirichlet = [W.Dirichlet(lo=(-1e30,) * dim, hi=(0.05,) + (1e30,) * (dim - 1),
+                                  comp_mask=(1 << dim) - 1)]
+    spec.pcg_mode = pcg_mode
+    dom = osmpm.Domain(spec)
+    ref = O.DomainState.create(spec)
+    x0 = spec.particles.x.copy()
+    for _ in range(3):
+        dom.step(5e-3)
+        O.step(ref, 5e-3)
+    assert rel_disp(dom.get_particles()[0], ref.p.x, x0) <= DISP_TOL
+
+
+@pytest.mark.parametrize("pcg_mode", [0, 2])
+def test_domain_at_rest_stays_at_rest(osmpm, pcg_mode):
+    """No load, no velocity, F = I: the residual is zero, Newton stops at its
+    first test without a PCG iteration, and the state does not move."""
+    spec = dataclasses.replace(W.block(2, n_cells=(4, 3), dx=0.1), pcg_mode=pcg_mode)
+    dom = osmpm.Domain(spec)
+    st = dom.step(0.01)
+    x, v, B, F = dom.get_particles()
+    np.testing.assert_array_equal(x, spec.particles.x)
+    np.testing.assert_array_equal(v, 0.0)
+    assert st["newton_iters"] == 1 and st["cg_iters"] == 0
+
+
+def test_empty_domain_is_rejected(osmpm):
+    spec = _subset(W.block(2, n_cells=(2, 2), dx=0.1), np.zeros(0, dtype=np.int64))
+    with pytest.raises(osmpm.OsmpmError) as e:
+        osmpm.Domain(spec)
+    assert e.value.status == osmpm.OSMPM_E_INVALID
+
+
 def test_bench_workload_full_size_one_global_step(osmpm):
     """The configuration bench.py times (inclusion, coarse dx 0.05, fine dx
     0.005, M = 2, FP64), one global Schwarz step, every particle compared
