@@ -238,53 +238,49 @@ __device__ __forceinline__ double group_hvp(const PcgArgsT<R>& a, int64_t pi, bo
 }
 
 // FP64 instructions are scarce on this part (one warp-wide FP64 instruction
-// per SMSP every ~64 clocks), so the per-iteration control avoids
-// redundant FP64 work: warp 0 alone sums the block partials after each
-// barrier, thread 0 alone evaluates alpha, beta and the stopping tests and
-// hands them to the block through shared memory, and the DOFs are dealt to
+// per SMSP every ~64 clocks), and every FP64 instruction on the serial path
+// between two grid barriers costs that much latency.  So the per-iteration
+// control avoids redundant and serial FP64 work: the block sums and the
+// grid totals of the three recurrence values run on three warps at once
+// (different SMSPs), thread 0 evaluates beta and the stopping tests while
+// thread 32 evaluates alpha, both handing them to the block through shared
+// memory (the launch has at least 64 threads), and the DOFs are dealt to
 // the blocks in equal contiguous chunks.
 
-// Sum of one row of NV values over the block into thread 0 (warp sums, then
-// warp 0 over at most kThreads/32 warp totals).
+// This block's sums of NV values per thread, stored as its partials
+// (partials[k * gridDim.x + blockIdx.x]): the threads park their values in
+// shared memory, then warp k alone sums value k (lane-strided over the
+// threads, then a warp shuffle).  The order depends only on the block size.
 template <int NV>
-__device__ __forceinline__ void pcg_block_sum(double (&v)[NV]) {
-  __shared__ double sh[NV][kThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ void pcg_block_partials(const double (&v)[NV], double* partials) {
+  __shared__ double sh[NV][kThreads];
 #pragma unroll
-  for (int k = 0; k < NV; ++k)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(kFull, v[k], off);
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
   __syncthreads();
-  if (lane == 0)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int k = warp; k < NV; k += nw) {
+    double t = 0.0;
+    for (unsigned j = lane; j < blockDim.x; j += 32) t += sh[k][j];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) sh[k][warp] = v[k];
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = (int)(blockDim.x >> 5);
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      v[k] = lane < nw ? sh[k][lane] : 0.0;
-#pragma unroll
-      for (int off = kThreads / 64; off > 0; off >>= 1) v[k] += __shfl_down_sync(kFull, v[k], off);
-    }
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(kFull, t, off);
+    if (lane == 0) partials[k * gridDim.x + blockIdx.x] = t;
   }
 }
 
-// Warp 0: the NV totals of the grid's partial rows (lane-strided over the
-// blocks, then a warp sum; the order depends only on the launch shape).
-// Result in lane 0 of warp 0.
+// The NV totals of the grid's partial rows into tot[] (shared): warp k forms
+// total k, lane-strided over the blocks, then a warp shuffle (the order
+// depends only on the launch shape).  The caller synchronises the block
+// before reading tot.
 template <int NV>
-__device__ __forceinline__ void pcg_grid_totals(const double* partials, double (&out)[NV]) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void pcg_grid_totals(const double* partials, double* tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int k = warp; k < NV; k += nw) {
+    double t = 0.0;
+    for (unsigned b = lane; b < gridDim.x; b += 32) t += __ldcg(&partials[k * gridDim.x + b]);
 #pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = 0.0;
-  for (unsigned b = lane; b < gridDim.x; b += 32)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) out[k] += __ldcg(&partials[k * gridDim.x + b]);
-#pragma unroll
-  for (int k = 0; k < NV; ++k)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) out[k] += __shfl_down_sync(kFull, out[k], off);
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(kFull, t, off);
+    if (lane == 0) tot[k] = t;
+  }
 }
 
 // ONE: the launch covers the problem in a single pass (every thread owns at
@@ -302,7 +298,9 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
   const double* idiag = a.diag;  // inverse Jacobi diagonal
   __shared__ unsigned bar_target;  // this block's running barrier goal (count starts at 0)
   __shared__ double sh_alpha, sh_beta;
-  __shared__ int sh_stop;          // 0 go on, 1 stop
+  __shared__ int sh_stop;          // tolerance or iteration cap reached
+  __shared__ int sh_neg;           // the curvature test failed
+  __shared__ double sh_tot[3];     // the grid totals after a barrier
   if (threadIdx.x == 0) bar_target = 0u;
   // DOFs: block b owns the contiguous chunk [b c, (b+1) c)
   const int64_t chunk = (ndof + gridDim.x - 1) / gridDim.x;
@@ -337,10 +335,12 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
     }
     load_lane<D, R>(a, my_pi, my_valid, q, ld);
   }
-  // scalar state, held by thread 0 of every block (all blocks see the same
-  // totals, so they take the same decisions)
+  // scalar state: thread 0 of every block keeps gamma for beta and the
+  // stopping tests, thread 32 its own copy for alpha (all blocks see the
+  // same totals, so they take the same decisions); every thread counts the
+  // iterations and keeps the curvature-failure flag
   int it = 0, neg = 0;
-  double gamma = 0.0, delta = 0.0, gamma_old = 1.0, alpha_old = 1.0;
+  double gamma = 0.0;
   const int max_it = S->cg_max;
   const double tol2 = S->tol2;
 
@@ -377,30 +377,25 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
         acc[2] += group_hvp<D, R>(a, pi, in_group && pi < a.P.n, q, leader, u0, a.w[0]);
       }
     }
-    pcg_block_sum<3>(acc);
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) a.partials[k * gridDim.x + blockIdx.x] = acc[k];
+    pcg_block_partials<3>(acc, a.partials);
     if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
-    if (threadIdx.x < 32) {
-      double tot[3];
-      pcg_grid_totals<3>(a.partials, tot);
-      if (threadIdx.x == 0) {
-        gamma = tot[0];
-        delta = tot[2];
-        int stop = (gamma == 0.0) || (S->cg_done != 0) || max_it <= 0;
-        if (!stop && !(delta > 0.0)) {
-          neg = 1;
-          stop = 1;
-        }
-        sh_alpha = stop ? 0.0 : gamma / delta;
-        sh_beta = 0.0;
-        sh_stop = stop;
-      }
-    }
+    pcg_grid_totals<3>(a.partials, sh_tot);
     __syncthreads();
+    if (threadIdx.x == 0) {
+      const double delta = sh_tot[2];
+      int stop = (sh_tot[0] == 0.0) || (S->cg_done != 0) || max_it <= 0;
+      const int bad = !stop && !(delta > 0.0);
+      sh_alpha = stop || bad ? 0.0 : sh_tot[0] / delta;
+      sh_beta = 0.0;
+      sh_stop = stop;
+      sh_neg = bad;
+    }
+    gamma = sh_tot[0];
+    __syncthreads();
+    neg = sh_neg;
   }
-  while (!sh_stop) {
+  bool halt = sh_stop || sh_neg;
+  while (!halt) {
     const double alpha = sh_alpha, beta = sh_beta;
     const double* rk = a.r[it & 1];
     double* rn = a.r[(it + 1) & 1];
@@ -459,38 +454,33 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
         acc[2] += group_hvp<D, R>(a, pi, in_group && pi < a.P.n, q, leader, uk, wn);
       }
     }
-    pcg_block_sum<3>(acc);
-    if (threadIdx.x == 0)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) a.partials[k * gridDim.x + blockIdx.x] = acc[k];
+    pcg_block_partials<3>(acc, a.partials);
     if (!grid_barrier(&S->bar_count, &bar_target, a.err, gridDim.x)) return;
     ++it;
-    if (threadIdx.x < 32) {
-      double tot[3];
-      pcg_grid_totals<3>(a.partials, tot);
-      if (threadIdx.x == 0) {
-        gamma_old = gamma;
-        alpha_old = alpha;
-        gamma = tot[0];
-        delta = tot[2];
-        int stop = tot[1] <= tol2 || it >= max_it;
-        double an = 0.0, bn = 0.0;
-        if (!stop) {
-          bn = gamma / gamma_old;
-          const double den = delta - bn * gamma / alpha_old;
-          if (!(den > 0.0)) {
-            neg = 1;
-            stop = 1;
-          } else {
-            an = gamma / den;
-          }
-        }
-        sh_alpha = an;
-        sh_beta = bn;
-        sh_stop = stop;
-      }
+    pcg_grid_totals<3>(a.partials, sh_tot);
+    __syncthreads();
+    // beta = gamma / gamma_old, and alpha = gamma / (delta - beta gamma /
+    // alpha_old) as gamma P / Q with P = gamma_old alpha_old > 0 and
+    // Q = delta P - gamma^2 (the sign of the curvature term), so the two
+    // divisions (each a long serial FP64 sequence) run at once on two warps
+    if (threadIdx.x == 0) {
+      const double gamma_old = gamma;
+      gamma = sh_tot[0];
+      const int stop = sh_tot[1] <= tol2 || it >= max_it;
+      sh_beta = stop ? 0.0 : gamma / gamma_old;
+      sh_stop = stop;
+    } else if (threadIdx.x == 32) {
+      const double gamma_new = sh_tot[0];
+      const double P = gamma * alpha;
+      const double Q = fma(sh_tot[2], P, -gamma_new * gamma_new);
+      const int ok = Q > 0.0;
+      sh_alpha = ok ? gamma_new * P / Q : 0.0;
+      sh_neg = !ok;
+      gamma = gamma_new;
     }
     __syncthreads();
+    if (!sh_stop && sh_neg) neg = 1;
+    halt = sh_stop || sh_neg;
   }
   // thread 0 of each block knows whether the first direction failed
   __shared__ int sh_fallback;
