@@ -29,6 +29,7 @@ for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse
+import dataclasses
 import json
 import statistics
 import subprocess
@@ -54,10 +55,11 @@ WORKLOAD = "inclusion_osmpm_2d_fp64_dxB0.05_dxS0.005_M2"
 ORACLE_SCHWARZ_ITERS_PER_STEP = 12.0
 ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
+AUTOTUNE_THREADS = [4, 6, 8, 12, 16]
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
 # launch, from the ncu capture of the current kernel (the k_pcg profile
 # summary of this workload); None whenever the kernel changes
-PCG_TRAFFIC_BYTES = 3.04e6 + 0.09e6
+PCG_TRAFFIC_BYTES = None
 # FP64 flops of one Hessian-vector product per particle: gather G (2 d^2 3^d),
 # Y = L G (2 d^4), G:Y (2 d^2), scatter (2 d^2 3^d); an FMA counts 2.
 HVP_FLOPS_PER_PARTICLE = {2: 184, 3: 1152}
@@ -192,6 +194,8 @@ def run_ours(args, rank, local, world):
     from paper_2605_09097_gb300 import osmpm
 
     cB, cS, sch, dT = workload()
+    cB = dataclasses.replace(cB, launch_mode=args.launch_mode)
+    cS = dataclasses.replace(cS, launch_mode=args.launch_mode)
     units = units_per_step(cB, cS, sch.M)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -282,6 +286,8 @@ def run_ours(args, rank, local, world):
                    "particles_fine": cS.particles.n, "M": sch.M, "dT": dT,
                    "units_per_step": units, "parallelism": f"replicas{world}",
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                   "launch": ("CUDA graph per Newton iteration" if args.launch_mode == 0
+                              else "plain stream launches"),
                    "schwarz_iters_per_step": iters,
                    "newton_iters_per_step": [s["newton_iters"] for s in stats],
                    "cg_iters_per_step": [s["cg_iters"] for s in stats],
@@ -290,7 +296,9 @@ def run_ours(args, rank, local, world):
         "roofline": {"kernel": "k_pcg (persistent PCG)", "bound": "alu", "achieved": achieved,
                      "peak": fp64_peak, "unit": "GFLOP/s", "frac": achieved / fp64_peak,
                      "traffic": PCG_TRAFFIC_BYTES,
-                     "traffic_source": "ncu, one fine-domain launch (dram read + write bytes)",
+                     "traffic_source": ("ncu, one fine-domain launch (dram read + write bytes)"
+                                        if PCG_TRAFFIC_BYTES is not None
+                                        else "not captured for the current kernel"),
                      "peak_source": "nominal FP64 1.25 TFLOP/s (GB300)",
                      "launches": pcg_n, "avg_launch_us": 1e3 * pcg_ms / max(pcg_n, 1),
                      "pcg_iters": cB_["pcg_iters"] + cS_["pcg_iters"],
@@ -357,7 +365,6 @@ def oracle_sample(n_iters):
     """Times the FP64 oracle on the bench workload: the first ``n_iters``
     Schwarz iterations of global step 1.  Returns (seconds, units), units
     scaled by n_iters / ORACLE_SCHWARZ_ITERS_PER_STEP."""
-    import dataclasses
     from oracle import osmpm_oracle as O
     cB, cS, sch, dT = workload()
     sch = dataclasses.replace(sch, k_max=n_iters - 1)
@@ -386,7 +393,6 @@ def run_batched(args, rank, local, world):
     the batched family (uneven fine resolutions), each on its own stream,
     advanced together by osmpm_schwarz_couple_batch (host wall clock around
     each batched step, the device synchronised on both sides)."""
-    import dataclasses
     import torch
     torch.cuda.set_device(local)
     from paper_2605_09097_gb300 import build
@@ -396,15 +402,19 @@ def run_batched(args, rank, local, world):
     prec = 1 if args.precision == "mixed" else 0
     B, S, streams = [], [], []
     for cB, cS, sch, dT in specs:
-        st = torch.cuda.Stream()
+        st = osmpm.create_stream()  # one stream per pair (torch's streams come from a pool of 32)
         streams.append(st)
-        B.append(osmpm.Domain(dataclasses.replace(cB, precision=prec), stream=st.cuda_stream))
-        S.append(osmpm.Domain(dataclasses.replace(cS, precision=prec), stream=st.cuda_stream))
+        B.append(osmpm.Domain(dataclasses.replace(cB, precision=prec), stream=st))
+        S.append(osmpm.Domain(dataclasses.replace(cS, precision=prec), stream=st))
     schs = [s[2] for s in specs]
     dT = specs[0][3]
     units = sum(units_per_step(s[0], s[1], s[2].M) for s in specs)
-    for _ in range(args.warmup):
-        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=args.threads)
+    threads, tuned = args.threads, None
+    if threads == 0:
+        # the launch-shape autotuner's steps stand in for the warm-up
+        threads, tuned = osmpm.osmpm_autotune_batch(B, S, dT, schs, AUTOTUNE_THREADS)
+    for _ in range(args.warmup if tuned is None else 0):
+        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=threads)
     torch.cuda.synchronize()
     barrier(world)
     launches0 = osmpm.launch_count()
@@ -412,22 +422,29 @@ def run_batched(args, rank, local, world):
     clocks.start()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=args.threads)
+        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=threads)
     torch.cuda.synchronize()
     t = max_over_ranks(time.perf_counter() - t0, world)
     clk = clocks.stop()
     value = sum_over_ranks(units * args.steps, world) / t
+    launches = int(osmpm.launch_count() - launches0)
+    for d in B + S:
+        d.close()
+    for st in streams:
+        osmpm.destroy_stream(st)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "warmup": args.warmup if tuned is None else len(AUTOTUNE_THREADS) + 1,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32/f64",
             "data": "synthetic",
             "config": {"workload": f"batched_inclusion_{args.instances}_literal",
-                       "instances": args.instances, "host_threads": args.threads,
+                       "instances": args.instances, "host_threads": threads,
+                       "autotune_us_per_cg_iter": tuned,
                        "particles": sum(s[0].particles.n + s[1].particles.n for s in specs),
                        "units_per_step": units, "precision": args.precision,
                        "timing": "host wall clock around each batched step",
                        "parallelism": f"replicas{world}"},
-            "gpu_launches": int(osmpm.launch_count() - launches0), "clocks": clk}
+            "gpu_launches": launches, "clocks": clk}
 
 
 def run_reference(args, rank, world):
@@ -507,12 +524,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--launch-mode", type=int, choices=[0, 1], default=0,
+                    help="0: each Newton iteration replays a captured CUDA graph; 1: plain launches")
     ap.add_argument("--workload", choices=["inclusion", "batched", "fold3d"], default="inclusion",
                     help="inclusion: the headline FP64 configuration; batched: many instances; "
                          "fold3d: the 3D folding plate (mixed)")
     ap.add_argument("--scaled", action="store_true", help="fold3d: the 3.07M-particle band")
     ap.add_argument("--instances", type=int, default=256)
-    ap.add_argument("--threads", type=int, default=16)
+    ap.add_argument("--threads", type=int, default=0,
+                    help="host threads of the batched workload; 0: chosen by the autotuner")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     args = ap.parse_args()
     rank, local, world = dist_init(args.gpus)

@@ -91,7 +91,15 @@ typedef struct osmpm_domain_desc {
                                co-resident pass covers the problem, else the streaming
                                PCG of three kernels per iteration); 1: persistent;
                                2: streaming */
-  int32_t reserved[5];      /* must be zero */
+  int32_t launch_mode;      /* 0: each Newton iteration's device work (gradient, Jacobi
+                               diagonal, persistent PCG, max |delta|, scalar read-back) is
+                               captured once per (dt, iteration kind, PCG shape) as a CUDA
+                               graph and replayed; 1: plain stream launches.  Streaming PCG
+                               solves, domains on the legacy default stream (which
+                               cannot be captured) and the worker threads of
+                               osmpm_schwarz_couple_batch always launch directly.
+                               Results do not depend on it */
+  int32_t reserved[4];      /* must be zero */
 } osmpm_domain_desc;
 
 /* Initial particle state, host arrays in id order (layouts above).  flags
@@ -213,7 +221,9 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* coarse, osmpm_domain* fine, doub
  * call runs, each pair's persistent PCG grid is limited to 1/n_threads of
  * the device's co-resident capacity, so that the concurrent cooperative
  * grids can all be resident together (their grid barriers never wait on a
- * block another grid keeps out).  Calls that drive domains concurrently
+ * block another grid keeps out).  The worker threads launch directly
+ * (launch_mode 0 graphs are built and replayed only by calls made from the
+ * caller's thread).  Calls that drive domains concurrently
  * from several host threads must go through this entry point.  stats and
  * status (either may be NULL) receive n entries.  Returns OSMPM_OK, or the
  * status of the first failing pair (message names the pair), or
@@ -222,6 +232,32 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
                                         int32_t n, double dT, const osmpm_schwarz_desc* sdesc,
                                         int32_t n_threads, osmpm_stats* stats,
                                         osmpm_status* status);
+
+/* A new non-blocking CUDA stream on the current device, for callers without
+ * a stream factory of their own (every pair of osmpm_schwarz_couple_batch
+ * wants its own stream).  *out receives the cudaStream_t; release it with
+ * osmpm_destroy_stream after the domains that use it are destroyed.  Errors:
+ * OSMPM_E_INVALID (null out), OSMPM_E_CUDA. */
+osmpm_status osmpm_create_stream(void** out);
+osmpm_status osmpm_destroy_stream(void* stream);
+
+/* Launch-shape autotuner of the batched path (not in the paper): picks the
+ * host concurrency of osmpm_schwarz_couple_batch for these pairs, which
+ * also sets each pair's persistent PCG grid (1/n_threads of the device's
+ * co-resident blocks).  It runs one untimed batched step with candidates[0]
+ * and then one timed batched step per candidate (host wall clock, the
+ * device synchronised on both sides); these are real global steps, so the
+ * pairs advance by n_candidates + 1 steps.  A step's cost varies with the
+ * Schwarz, Newton and PCG iterations it needs, so each candidate is scored
+ * by wall time per PCG iteration summed over the pairs; *best receives the
+ * candidate with the lowest score, us_per_cg_iter (may be NULL) the
+ * n_candidates scores in microseconds.  candidates must be >= 1.  Errors:
+ * OSMPM_E_INVALID for bad arguments, else the first failing step's status
+ * (a pair reaching k_max is not a failure). */
+osmpm_status osmpm_autotune_batch(osmpm_domain* const* coarse, osmpm_domain* const* fine,
+                                  int32_t n, double dT, const osmpm_schwarz_desc* sdesc,
+                                  const int32_t* candidates, int32_t n_candidates,
+                                  int32_t* best, double* us_per_cg_iter);
 
 /* Reverse mode, recording.  enable = 1 discards any earlier record and
  * makes every later osmpm_step of dom keep, in device memory from the
@@ -338,7 +374,11 @@ osmpm_status osmpm_probe_energy_change(osmpm_domain* dom, double dt, const doubl
  * persistent PCG launches (one per Newton iteration), their summed
  * duration from CUDA events recorded on the domain's stream around each
  * launch, and the PCG iterations they ran; particles and dofs are the
- * per-iteration work units of the domain (n and n_nodes * dim). */
+ * per-iteration work units of the domain (n and n_nodes * dim);
+ * graph_replays: Newton iterations of the domain that ran as a replay of a
+ * captured CUDA graph (launch_mode 0), graphs: graphs it holds,
+ * graph_error: the cudaError_t of a capture that failed (the domain then
+ * launches directly), 0 if none. */
 typedef struct osmpm_counters {
   int64_t launches;
   int64_t pcg_launches;
@@ -346,7 +386,9 @@ typedef struct osmpm_counters {
   int64_t pcg_iters;
   int64_t particles;
   int64_t dofs;
-  double reserved[2];
+  int64_t graph_replays;
+  int32_t graphs;
+  int32_t graph_error;
 } osmpm_counters;
 
 /* Enables (1) or disables (0) CUDA-event timing of this domain's PCG

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <string>
 #include <thread>
+#include <chrono>
 #include <utility>
 #include <vector>
 
@@ -168,6 +169,21 @@ struct osmpm_domain {
   int tape_kind = 0;                // 0 empty, 1 single-domain steps, 2 coupled (coarse), 3 coupled (fine)
   double* cadj = nullptr;           // coupled-adjoint work arrays
 
+  // CUDA graphs of one Newton iteration's device work (launch_mode 0), one
+  // slot per iteration kind (first | confirming << 1 | timed << 2), each
+  // valid for the dt and PCG launch shape it was captured with
+  struct NewtonGraph {
+    cudaGraphExec_t exec = nullptr;
+    double dt = 0.0;
+    int blocks = 0, threads = 0;
+    int kernels = 0;  // kernel nodes, counted as launches per replay
+  };
+  NewtonGraph ngraph[8];
+  bool graph_off = false;  // capture failed once: plain launches from then on
+  bool graph_hold = false; // set while a batched call drives the domain from a worker thread
+  int graph_error = 0;     // its cudaError_t
+  long long graph_replays = 0;
+
   // optional CUDA-event timing of the PCG launches (osmpm_set_profiling)
   bool time_hvp = false;
   std::vector<cudaEvent_t> ev;  // one start/stop pair
@@ -250,6 +266,10 @@ void free_all(osmpm_domain* d) {
       cudaFreeAsync(b.first, d->stream);
   }
   d->blocks.clear();
+  for (auto& gs : d->ngraph) {
+    if (gs.exec) cudaGraphExecDestroy(gs.exec);
+    gs = osmpm_domain::NewtonGraph{};
+  }
   for (cudaEvent_t e : d->ev) cudaEventDestroy(e);
   d->ev.clear();
   if (d->S_host) cudaFreeHost(d->S_host);
@@ -502,18 +522,219 @@ osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st);
 // only to kCheckEta and accepted when max |delta| <= tol / 2.
 constexpr double kCheckRatio = 500.0, kCheckEta = 0.1;
 
-osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check, SolveStats& st) {
+// Gradient, Jacobi diagonal and the PCG start (x = 0, r[0], inverted
+// diagonal, tolerance and controls) of a Newton iteration.
+void enqueue_gradient(osmpm_domain* d, double dt, bool first, bool check) {
   const int64_t nn = d->geo.nn;
   const int D = d->dim;
-  CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream));
+  cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream);
+  cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream);
   DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
   const double eta_max = d->desc.cg_eta_max > 0.0 ? d->desc.cg_eta_max : kEtaMax;
   const double rtol = check ? std::max(kCheckEta, d->desc.cg_rtol) : d->desc.cg_rtol;
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt, rtol,
                              check ? rtol : eta_max, first ? 1 : 0, d->desc.cg_max, d->grad,
                              d->diag, d->cx, d->cr, d->cz, d->cp, d->S, d->partials, d->stream));
-  return run_pcg(d, dt, true, st);
+}
+
+// PCG launch threads: one per DOF, and LPP lanes per particle (GP particles
+// per warp).
+int64_t pcg_work(const osmpm_domain* d) {
+  const int GP = 32 / (d->dim == 2 ? 3 : 9);
+  return std::max<int64_t>((d->n + GP - 1) / GP * 32, (int64_t)d->dim * d->geo.nn);
+}
+
+bool pcg_streaming(osmpm_domain* d, double dt, int64_t work) {
+  bool streaming = d->desc.pcg_mode == 2;
+  if (d->desc.pcg_mode == 0) DISPATCH(d, (streaming = !pcg_persistent_fits<K, R>(d, dt, work)));
+  return streaming;
+}
+
+// s[1], w[0..2], p and the barrier counter of the persistent PCG to zero.
+void enqueue_pcg_reset(osmpm_domain* d) {
+  const size_t vb = sizeof(double) * d->dim * d->geo.nn;
+  cudaMemsetAsync(d->cp1, 0, vb, d->stream);
+  cudaMemsetAsync(d->cq, 0, vb, d->stream);
+  cudaMemsetAsync(d->cw1, 0, vb, d->stream);
+  cudaMemsetAsync(d->cw2, 0, vb, d->stream);
+  cudaMemsetAsync(d->cpp, 0, vb, d->stream);
+  cudaMemsetAsync(&d->S->bar_count, 0, sizeof(unsigned), d->stream);
+}
+
+// One Newton iteration's device work up to the host's decision: gradient,
+// persistent PCG, max |delta| and the scalars and error word copied to the
+// pinned mirrors.  Enqueue errors come back as the first failing status.
+cudaError_t enqueue_newton_iteration(osmpm_domain* d, double dt, bool first, bool check, bool timed,
+                                     int64_t work) {
+  enqueue_gradient(d, dt, first, check);
+  enqueue_pcg_reset(d);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  DISPATCH(d, (e = launch_pcg<K, R>(d, dt, work, timed)));
+  if (e != cudaSuccess) return e;
+  DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
+  cudaMemcpyAsync(d->S_host, d->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, d->stream);
+  cudaMemcpyAsync(d->err_host, d->err, sizeof(int), cudaMemcpyDeviceToHost, d->stream);
+  return cudaGetLastError();
+}
+
+// Kernel nodes of a graph.
+size_t graph_kernels(cudaGraph_t g) {
+  size_t nodes = 0, nk = 0;
+  if (cudaGraphGetNodes(g, nullptr, &nodes) != cudaSuccess || nodes == 0) return 0;
+  std::vector<cudaGraphNode_t> list(nodes);
+  if (cudaGraphGetNodes(g, list.data(), &nodes) != cudaSuccess) return 0;
+  for (size_t i = 0; i < nodes; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(list[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+  }
+  return nk;
+}
+
+// The persistent PCG as a cooperative kernel node after `dep` (stream
+// capture does not record cooperative launches, graph nodes take them as
+// a launch attribute).
+template <class K, class R>
+cudaError_t add_pcg_node(osmpm_domain* d, double dt, int64_t work, cudaGraph_t g,
+                         cudaGraphNode_t dep, cudaGraphNode_t* out) {
+  PcgArgsT<R> a = pcg_args<R>(d, dt);
+  int blocks = 0, threads = 0;
+  K::pcg_shape(work, d->pcg_share, &blocks, &threads);
+  void* args[] = {(void*)&a};
+  cudaKernelNodeParams kp = {};
+  kp.func = const_cast<void*>(K::pcg_kernel(a, blocks, threads));
+  kp.gridDim = dim3(blocks);
+  kp.blockDim = dim3(threads);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  cudaError_t e = cudaGraphAddKernelNode(out, g, &dep, 1, &kp);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttributeValue v = {};
+  v.cooperative = 1;
+  return cudaGraphKernelNodeSetAttribute(*out, cudaLaunchAttributeCooperative, &v);
+}
+
+// Stream work enqueued by `body`, captured (thread-local mode, so domains
+// driven by other host threads are not affected) into a new graph.
+template <class F>
+cudaError_t capture(osmpm_domain* d, F&& body, cudaGraph_t* out) {
+  *out = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(d->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  body();
+  const cudaError_t eb = cudaGetLastError();
+  e = cudaStreamEndCapture(d->stream, out);
+  return e != cudaSuccess ? e : eb;
+}
+
+// The graph of one Newton iteration for this key, built on first use: the
+// captured gradient and PCG set-up, the cooperative PCG node (between event
+// records when timed), then the captured max |delta| and scalar read-back.
+// nullptr when graphs are off, the domain runs on the legacy default stream
+// or building failed; the caller then enqueues the same work directly.
+cudaGraphExec_t newton_graph(osmpm_domain* d, double dt, bool first, bool check, bool timed,
+                             int64_t work, int* kernels) {
+  // the legacy default stream cannot be captured: plain launches there
+  if (d->desc.launch_mode != 0 || d->graph_off || d->graph_hold || d->stream == nullptr ||
+      d->stream == cudaStreamLegacy)
+    return nullptr;
+  int blocks = 0, threads = 0;
+  DISPATCH(d, K::pcg_shape(work, d->pcg_share, &blocks, &threads));
+  osmpm_domain::NewtonGraph& slot = d->ngraph[(first ? 1 : 0) | (check ? 2 : 0) | (timed ? 4 : 0)];
+  if (slot.exec && slot.dt == dt && slot.blocks == blocks && slot.threads == threads) {
+    *kernels = slot.kernels;
+    return slot.exec;
+  }
+  if (slot.exec) cudaGraphExecDestroy(slot.exec);
+  slot = osmpm_domain::NewtonGraph{};
+  cudaGraph_t ga = nullptr, gb = nullptr, top = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  size_t nk = 0;
+  cudaError_t e = capture(d, [&] {
+    enqueue_gradient(d, dt, first, check);
+    enqueue_pcg_reset(d);
+  }, &ga);
+  if (e == cudaSuccess)
+    e = capture(d, [&] {
+      DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
+      cudaMemcpyAsync(d->S_host, d->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, d->stream);
+      cudaMemcpyAsync(d->err_host, d->err, sizeof(int), cudaMemcpyDeviceToHost, d->stream);
+    }, &gb);
+  // the launchers counted the captured kernels; replays count them instead
+  const size_t captured = (ga ? graph_kernels(ga) : 0) + (gb ? graph_kernels(gb) : 0);
+  g_launch_count -= (long long)captured;
+  if (e == cudaSuccess) e = cudaGraphCreate(&top, 0);
+  cudaGraphNode_t prev = nullptr, node = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&prev, top, nullptr, 0, ga);
+  if (e == cudaSuccess && timed) {
+    e = cudaGraphAddEventRecordNode(&node, top, &prev, 1, d->ev[0]);
+    prev = node;
+  }
+  if (e == cudaSuccess) {
+    DISPATCH(d, (e = add_pcg_node<K, R>(d, dt, work, top, prev, &node)));
+    prev = node;
+  }
+  if (e == cudaSuccess && timed) {
+    e = cudaGraphAddEventRecordNode(&node, top, &prev, 1, d->ev[1]);
+    prev = node;
+  }
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&node, top, &prev, 1, gb);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, top, 0);
+  nk = captured + 1;
+  if (ga) cudaGraphDestroy(ga);
+  if (gb) cudaGraphDestroy(gb);
+  if (top) cudaGraphDestroy(top);
+  if (e != cudaSuccess || !exec) {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();  // a failed capture or build leaves no sticky error
+    d->graph_off = true;
+    d->graph_error = e != cudaSuccess ? (int)e : -1;
+    return nullptr;
+  }
+  slot.exec = exec;
+  slot.dt = dt;
+  slot.blocks = blocks;
+  slot.threads = threads;
+  slot.kernels = (int)nk;
+  *kernels = slot.kernels;
+  return exec;
+}
+
+osmpm_status pcg_finish(osmpm_domain* d, bool timed, SolveStats& st) {
+  OSMPM_TRY(check_err(d));
+  st.cg += d->S_host->cg_iter;
+  if (timed) {
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]));
+    d->pcg_ms += ms;
+    d->pcg_launches += 1;
+    d->pcg_iters += d->S_host->cg_iter;
+  }
+  return OSMPM_OK;
+}
+
+osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check, SolveStats& st) {
+  const int64_t work = pcg_work(d);
+  const bool timed = d->time_hvp && !d->ev.empty();
+  if (pcg_streaming(d, dt, work)) {
+    enqueue_gradient(d, dt, first, check);
+    CUDA_TRY(cudaGetLastError());
+    return run_pcg(d, dt, true, st);
+  }
+  int kernels = 0;
+  const cudaGraphExec_t g = newton_graph(d, dt, first, check, timed, work, &kernels);
+  if (g) {
+    CUDA_TRY(cudaGraphLaunch(g, d->stream));
+    g_launch_count += kernels;
+    d->graph_replays += 1;
+  } else {
+    const cudaError_t e = enqueue_newton_iteration(d, dt, first, check, timed, work);
+    if (e != cudaSuccess) return fail(OSMPM_E_CUDA, "Newton iteration launch: %s", cudaGetErrorString(e));
+  }
+  CUDA_TRY(cudaStreamSynchronize(d->stream));
+  CUDA_TRY(cudaGetLastError());
+  return pcg_finish(d, timed, st);
 }
 
 // The whole PCG in one cooperative launch on a prepared system (x = 0, r[0],
@@ -521,23 +742,12 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check
 // barrier counter start at zero.  With `newton` also reduces max |x| for the
 // Newton stop test.
 osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st) {
-  const int64_t nn = d->geo.nn;
-  const int D = d->dim;
-  const size_t vb = sizeof(double) * D * nn;
-  CUDA_TRY(cudaMemsetAsync(d->cp1, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cq, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cw1, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cw2, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(d->cpp, 0, vb, d->stream));
-  CUDA_TRY(cudaMemsetAsync(&d->S->bar_count, 0, sizeof(unsigned), d->stream));
-  // threads: one per DOF, and LPP lanes per particle (GP particles per warp)
-  const int GP = 32 / (D == 2 ? 3 : 9);
-  const int64_t work = std::max<int64_t>((d->n + GP - 1) / GP * 32, D * nn);
+  enqueue_pcg_reset(d);
+  CUDA_TRY(cudaGetLastError());
+  const int64_t work = pcg_work(d);
   const bool timed = d->time_hvp && !d->ev.empty();
-  bool streaming = d->desc.pcg_mode == 2;
-  if (d->desc.pcg_mode == 0) DISPATCH(d, (streaming = !pcg_persistent_fits<K, R>(d, dt, work)));
   cudaError_t le = cudaSuccess;
-  if (!streaming) {
+  if (!pcg_streaming(d, dt, work)) {
     DISPATCH(d, (le = launch_pcg<K, R>(d, dt, work, timed)));
     if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(le));
   } else {
@@ -552,16 +762,7 @@ osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st) {
   }
   if (newton) DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
   OSMPM_TRY(sync_scalars(d));
-  OSMPM_TRY(check_err(d));
-  st.cg += d->S_host->cg_iter;
-  if (timed) {
-    float ms = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&ms, d->ev[0], d->ev[1]));
-    d->pcg_ms += ms;
-    d->pcg_launches += 1;
-    d->pcg_iters += d->S_host->cg_iter;
-  }
-  return OSMPM_OK;
+  return pcg_finish(d, timed, st);
 }
 
 // Newton's method with backtracking line search (Sec. 2.2.5) on the
@@ -834,9 +1035,11 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   if (desc->dim != 2 && desc->dim != 3) return fail(OSMPM_E_INVALID, "dim must be 2 or 3");
   if (desc->precision != 0 && desc->precision != 1)
     return fail(OSMPM_E_INVALID, "precision must be 0 (FP64) or 1 (mixed)");
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < 4; ++i)
     if (desc->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
   if (desc->pcg_mode < 0 || desc->pcg_mode > 2) return fail(OSMPM_E_INVALID, "pcg_mode must be 0, 1 or 2");
+  if (desc->launch_mode != 0 && desc->launch_mode != 1)
+    return fail(OSMPM_E_INVALID, "launch_mode must be 0 (graphs) or 1 (plain launches)");
   if (!(desc->cg_eta_max >= 0.0 && desc->cg_eta_max < 1.0))
     return fail(OSMPM_E_INVALID, "cg_eta_max must be in [0, 1)");
   if (!(desc->dx > 0.0) || !std::isfinite(desc->dx)) return fail(OSMPM_E_INVALID, "dx must be > 0");
@@ -1275,6 +1478,9 @@ osmpm_status osmpm_get_counters(const osmpm_domain* d, osmpm_counters* out) {
     out->pcg_iters = d->pcg_iters;
     out->particles = d->n;
     out->dofs = d->geo.nn * d->dim;
+    out->graph_replays = d->graph_replays;
+    out->graph_error = d->graph_error;
+    for (const auto& gs : d->ngraph) out->graphs += gs.exec ? 1 : 0;
   }
   return OSMPM_OK;
 }
@@ -1665,6 +1871,10 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
   std::vector<osmpm_status> st((size_t)n, OSMPM_OK);
   std::vector<std::string> msg((size_t)n);
   for (int32_t i = 0; i < n; ++i) coarse[i]->pcg_share = fine[i]->pcg_share = threads;
+  // the worker threads launch directly: no graph capture from concurrent
+  // host threads (a capture records whatever reaches its stream, and pairs
+  // may share a stream)
+  for (int32_t i = 0; i < n; ++i) coarse[i]->graph_hold = fine[i]->graph_hold = true;
   std::atomic<int32_t> next{0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1683,7 +1893,10 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
   for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
   worker();
   for (auto& t : pool) t.join();
-  for (int32_t i = 0; i < n; ++i) coarse[i]->pcg_share = fine[i]->pcg_share = 1;
+  for (int32_t i = 0; i < n; ++i) {
+    coarse[i]->pcg_share = fine[i]->pcg_share = 1;
+    coarse[i]->graph_hold = fine[i]->graph_hold = false;
+  }
   osmpm_status worst = OSMPM_OK;
   int32_t first_bad = -1;
   for (int32_t i = 0; i < n; ++i) {
@@ -1696,6 +1909,58 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
   }
   if (first_bad >= 0) return fail(worst, "pair %d: %s", first_bad, msg[(size_t)first_bad].c_str());
   if (worst != OSMPM_OK) return fail(worst, "at least one pair hit k_max");
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_create_stream(void** out) {
+  if (!out) return fail(OSMPM_E_INVALID, "null out");
+  cudaStream_t s = nullptr;
+  CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  *out = (void*)s;
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_destroy_stream(void* stream) {
+  if (!stream) return OSMPM_OK;
+  CUDA_TRY(cudaStreamDestroy((cudaStream_t)stream));
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_autotune_batch(osmpm_domain* const* coarse, osmpm_domain* const* fine, int32_t n,
+                                  double dT, const osmpm_schwarz_desc* sdesc,
+                                  const int32_t* candidates, int32_t n_candidates, int32_t* best,
+                                  double* us_per_cg_iter) {
+  if (!candidates || n_candidates < 1 || !best || n < 1)
+    return fail(OSMPM_E_INVALID, "need n >= 1 pairs, candidates and best");
+  for (int32_t c = 0; c < n_candidates; ++c)
+    if (candidates[c] < 1) return fail(OSMPM_E_INVALID, "candidate %d is < 1", c);
+  std::vector<osmpm_stats> stats((size_t)n);
+  auto step = [&](int32_t threads, double* seconds, int64_t* cg) -> osmpm_status {
+    CUDA_TRY(cudaDeviceSynchronize());
+    const auto t0 = std::chrono::steady_clock::now();
+    const osmpm_status st = osmpm_schwarz_couple_batch(coarse, fine, n, dT, sdesc, threads,
+                                                       stats.data(), nullptr);
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (st != OSMPM_OK && st != OSMPM_W_SCHWARZ_MAXITER) return st;
+    *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *cg = 0;
+    for (const auto& x : stats) *cg += x.cg_iters;
+    return OSMPM_OK;
+  };
+  double sec = 0.0;
+  int64_t cg = 0;
+  OSMPM_TRY(step(candidates[0], &sec, &cg));  // warm-up: first-use allocations and graph captures
+  double best_score = INFINITY;
+  *best = candidates[0];
+  for (int32_t c = 0; c < n_candidates; ++c) {
+    OSMPM_TRY(step(candidates[c], &sec, &cg));
+    const double score = 1e6 * sec / (double)std::max<int64_t>(cg, 1);
+    if (us_per_cg_iter) us_per_cg_iter[c] = score;
+    if (score < best_score) {
+      best_score = score;
+      *best = candidates[c];
+    }
+  }
   return OSMPM_OK;
 }
 

@@ -126,6 +126,8 @@ struct Kernels {
   // persistent cooperative PCG (whole solve in one launch)
   static void pcg_shape(int64_t work, int share, int* blocks, int* threads);
   static cudaError_t pcg(const PcgArgsT<R>& a, int blocks, int threads, cudaStream_t s);
+  // the k_pcg variant pcg() launches for this shape (for a graph kernel node)
+  static const void* pcg_kernel(const PcgArgsT<R>& a, int blocks, int threads);
   // does one co-resident pass of the persistent PCG cover the problem, and
   // how many passes does it need?
   static bool pcg_one_pass(const PcgArgsT<R>& a, int blocks, int threads);

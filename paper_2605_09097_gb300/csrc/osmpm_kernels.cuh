@@ -1184,9 +1184,13 @@ cudaError_t Kernels<D, R>::pcg(const PcgArgsT<R>& a, int blocks, int threads, cu
   g_launch_count += 1;
   // the single-pass variant when every thread owns at most one DOF and every
   // lane at most one particle
-  const bool one = pcg_one_pass(a, blocks, threads);
-  const void* fn = one ? (const void*)k_pcg<D, R, true> : (const void*)k_pcg<D, R, false>;
-  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), args, 0, s);
+  return cudaLaunchCooperativeKernel(pcg_kernel(a, blocks, threads), dim3(blocks), dim3(threads),
+                                     args, 0, s);
+}
+template <int D, typename R>
+const void* Kernels<D, R>::pcg_kernel(const PcgArgsT<R>& a, int blocks, int threads) {
+  return pcg_one_pass(a, blocks, threads) ? (const void*)k_pcg<D, R, true>
+                                          : (const void*)k_pcg<D, R, false>;
 }
 template <int D, typename R>
 bool Kernels<D, R>::pcg_one_pass(const PcgArgsT<R>& a, int blocks, int threads) {

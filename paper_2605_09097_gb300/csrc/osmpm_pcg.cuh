@@ -104,7 +104,8 @@ __device__ __forceinline__ int64_t stencil_offset(const GridGeo& g, int k) {
 // Particle Hessian-vector product in arithmetic type R, spread over a group
 // of LPP lanes per particle: lane q owns the stencil row of nodes
 // k = 3q .. 3q+2 (x fastest).  Each lane gathers u at its nodes through
-// `ufun(j)` (j = flat DOF index) into a partial G = sum u grad N^T; the
+// `ufun(f, j, c)` (f = flat DOF index of component c at the lane's node j)
+// into a partial G = sum u grad N^T; the
 // group sums the partials in lane order (every lane gets the same G), lane q
 // forms the rows i = q, q + LPP, ... of Y = L G, the rows are broadcast, and
 // each lane scatters (Y grad N_k) onto the free DOFs of its nodes.  Returns
@@ -166,7 +167,7 @@ __device__ __forceinline__ double group_hvp_lane(const PcgArgsT<R>& a, const Lan
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-      for (int c = 0; c < D; ++c) uv[j][c] = (R)ufun(c * g.nn + ld.node[j]);
+      for (int c = 0; c < D; ++c) uv[j][c] = (R)ufun(c * g.nn + ld.node[j], j, c);
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -283,6 +284,27 @@ __device__ __forceinline__ void pcg_grid_totals(const double* partials, double* 
   }
 }
 
+// Block-local node table of the single-pass variant: the distinct nodes of
+// the block's particle stencils (open addressing on the node index, bounded
+// probes).  Each iteration then forms u_{k+1} once per table node into
+// shared memory and the gathers read it there, instead of every (particle,
+// stencil node) pair forming it again from three L2 loads (a node sits in
+// the stencils of ~9 x particles-per-cell particles).  A block whose nodes do
+// not fit keeps the L2 gather.
+constexpr int kLocNodes = 512;  // table slots, a power of two; local ids < 1024
+
+struct LocTable {
+  unsigned long long key[kLocNodes];  // node index, or kLocEmpty
+  int id[kLocNodes];                  // dense local id of the slot's node
+  long long node[kLocNodes];          // dense local id -> node index
+  int count, over;
+};
+constexpr unsigned long long kLocEmpty = ~0ull;
+
+__device__ __forceinline__ unsigned loc_hash(unsigned long long key) {
+  return (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 55) & (kLocNodes - 1);
+}
+
 // ONE: the launch covers the problem in a single pass (every thread owns at
 // most one DOF, every lane at most one particle); then each lane keeps its
 // particle's stencil, grad N and Hessian rows in registers for the whole
@@ -323,6 +345,26 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
   const int64_t my_pi = warp0 + grp;
   const bool my_valid = in_group && my_pi < a.P.n;
   LaneData<D, R> ld;
+  __shared__ LocTable loc;
+  __shared__ double loc_u[D * kLocNodes];  // u at the table's nodes, component-major
+  bool loc_ok = false;
+  unsigned my_slots = 0u;  // local ids of the lane's 3 nodes, 10 bits each
+  // u for the gathers: from the table when the block has one, else from L2
+  auto loc_gather = [&](auto ufun) {
+    return [&, ufun](int64_t f, int j, int c) {
+      return loc_ok ? loc_u[c * kLocNodes + ((my_slots >> (10 * j)) & 1023u)] : ufun(f, j, c);
+    };
+  };
+  auto loc_fill = [&](auto ufun) {
+    if (loc_ok) {
+      const int nl = loc.count;
+      for (int t = threadIdx.x; t < nl * D; t += blockDim.x) {
+        const int c = t / nl, i = t - c * nl;
+        loc_u[c * kLocNodes + i] = ufun(c * g.nn + loc.node[i], 0, c);
+      }
+    }
+    __syncthreads();
+  };
   if constexpr (ONE) {
     if (my_idx < d_hi) {
       const int c = (int)(my_idx / g.nn);
@@ -334,6 +376,44 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
       }
     }
     load_lane<D, R>(a, my_pi, my_valid, q, ld);
+    for (int i = threadIdx.x; i < kLocNodes; i += blockDim.x) loc.key[i] = kLocEmpty;
+    if (threadIdx.x == 0) {
+      loc.count = 0;
+      loc.over = 0;
+    }
+    __syncthreads();
+    if (my_valid)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const unsigned long long key = (unsigned long long)ld.node[j];
+        unsigned h = loc_hash(key);
+        bool done = false;
+        for (int probe = 0; probe < kLocNodes && !done; ++probe, h = (h + 1) & (kLocNodes - 1)) {
+          const unsigned long long prev = atomicCAS(&loc.key[h], kLocEmpty, key);
+          if (prev == kLocEmpty) {
+            const int id = atomicAdd(&loc.count, 1);
+            loc.node[id] = (long long)key;
+            loc.id[h] = id;
+            done = true;
+          } else if (prev == key) {
+            done = true;
+          }
+        }
+        if (!done) loc.over = 1;
+      }
+    __syncthreads();
+    loc_ok = loc.over == 0;
+    if (my_valid && loc_ok)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const unsigned long long key = (unsigned long long)ld.node[j];
+        unsigned h = loc_hash(key);
+        for (int probe = 0; probe < kLocNodes; ++probe, h = (h + 1) & (kLocNodes - 1))
+          if (loc.key[h] == key) {
+            my_slots |= (unsigned)loc.id[h] << (10 * j);
+            break;
+          }
+      }
   }
   // scalar state: thread 0 of every block keeps gamma for beta and the
   // stopping tests, thread 32 its own copy for alpha (all blocks see the
@@ -348,7 +428,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
   {
     double acc[3] = {0.0, 0.0, 0.0};
     const double* r0 = a.r[0];
-    auto u0 = [=](int64_t j) { return __ldcg(&r0[j]) * idiag[j]; };
+    auto u0 = [=](int64_t f, int, int) { return __ldcg(&r0[f]) * idiag[f]; };
     if constexpr (ONE) {
       if (my_free) {
         const double ri = r0[my_idx];
@@ -358,7 +438,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
         acc[2] += mu * ui;
         atomicAdd(&a.w[0][my_idx], mu);
       }
-      acc[2] += group_hvp_lane<D, R>(a, ld, my_valid, q, leader, u0, a.w[0]);
+      loc_fill(u0);
+      acc[2] += group_hvp_lane<D, R>(a, ld, my_valid, q, leader, loc_gather(u0), a.w[0]);
     } else {
       for (int64_t idx = d_lo + threadIdx.x; idx < d_hi; idx += blockDim.x) {
         const int c = (int)(idx / g.nn);
@@ -405,8 +486,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
     double* wn = a.w[(it + 1) % 3];
     double* wz = a.w[(it + 2) % 3];
     double acc[3] = {0.0, 0.0, 0.0};
-    auto uk = [=](int64_t j) {
-      return (__ldcg(&rk[j]) - alpha * (__ldcg(&wk[j]) + beta * __ldcg(&sp[j]))) * idiag[j];
+    auto uk = [=](int64_t f, int, int) {
+      return (__ldcg(&rk[f]) - alpha * (__ldcg(&wk[f]) + beta * __ldcg(&sp[f]))) * idiag[f];
     };
     if constexpr (ONE) {
       if (my_free) {
@@ -425,7 +506,8 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
         atomicAdd(&wn[my_idx], mu);
       }
       if (my_idx < d_hi) wz[my_idx] = 0.0;
-      acc[2] += group_hvp_lane<D, R>(a, ld, my_valid, q, leader, uk, wn);
+      loc_fill(uk);
+      acc[2] += group_hvp_lane<D, R>(a, ld, my_valid, q, leader, loc_gather(uk), wn);
     } else {
       for (int64_t idx = d_lo + threadIdx.x; idx < d_hi; idx += blockDim.x) {
         const int c = (int)(idx / g.nn);
@@ -562,7 +644,7 @@ __global__ void __launch_bounds__(kThreads) k_cgs_hvp(PcgArgsT<R> a) {
   for (int64_t b0 = (tid >> 5) * GP; b0 < a.P.n; b0 += (stride >> 5) * GP) {
     const int64_t pi = b0 + grp;
     acc[0] += group_hvp<D, R>(a, pi, in_group && pi < a.P.n, q, leader,
-                              [=](int64_t j) { return __ldcg(&p[j]); }, a.w[0]);
+                              [=](int64_t f, int, int) { return __ldcg(&p[f]); }, a.w[0]);
   }
   double tot[1];
   if (grid_sum<1>(acc, a.partials, &a.S->counter, tot) && threadIdx.x == 0) a.S->pq = tot[0];

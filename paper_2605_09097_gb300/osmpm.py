@@ -62,7 +62,8 @@ class osmpm_domain_desc(Structure):
                 ("dx", c_double), ("res", c_int32 * 3), ("gravity", c_double * 3),
                 ("newton_tol", c_double), ("newton_max", c_int32), ("cg_rtol", c_double),
                 ("cg_max", c_int32), ("ls_max", c_int32), ("mass_eps", c_double),
-                ("cg_eta_max", c_double), ("pcg_mode", c_int32), ("reserved", c_int32 * 5)]
+                ("cg_eta_max", c_double), ("pcg_mode", c_int32), ("launch_mode", c_int32),
+                ("reserved", c_int32 * 4)]
 
 
 class osmpm_particles_in(Structure):
@@ -98,7 +99,7 @@ class osmpm_stats(Structure):
 class osmpm_counters(Structure):
     _fields_ = [("launches", c_int64), ("pcg_launches", c_int64), ("pcg_ms", c_double),
                 ("pcg_iters", c_int64), ("particles", c_int64), ("dofs", c_int64),
-                ("reserved", c_double * 2)]
+                ("graph_replays", c_int64), ("graphs", c_int32), ("graph_error", c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -132,6 +133,11 @@ _sig = {
     "osmpm_schwarz_couple_batch": (c_int32, [POINTER(c_void_p), POINTER(c_void_p), c_int32, c_double,
                                              POINTER(osmpm_schwarz_desc), c_int32,
                                              POINTER(osmpm_stats), POINTER(c_int32)]),
+    "osmpm_create_stream": (c_int32, [POINTER(c_void_p)]),
+    "osmpm_destroy_stream": (c_int32, [c_void_p]),
+    "osmpm_autotune_batch": (c_int32, [POINTER(c_void_p), POINTER(c_void_p), c_int32, c_double,
+                                       POINTER(osmpm_schwarz_desc), POINTER(c_int32), c_int32,
+                                       POINTER(c_int32), _DP]),
     "osmpm_get_info": (c_int32, [c_void_p, POINTER(c_int64), POINTER(c_int32)]),
     "osmpm_get_particles": (c_int32, [c_void_p, _DP, _DP, _DP, _DP]),
     "osmpm_set_particles": (c_int32, [c_void_p, _DP, _DP, _DP, _DP]),
@@ -227,6 +233,7 @@ def make_desc(spec) -> osmpm_domain_desc:
     d.mass_eps = spec.mass_eps
     d.cg_eta_max = getattr(spec, "cg_eta_max", 0.0)
     d.pcg_mode = getattr(spec, "pcg_mode", 0)
+    d.launch_mode = getattr(spec, "launch_mode", 0)
     return d
 
 
@@ -518,6 +525,37 @@ def osmpm_schwarz_couple_batch(coarse: List[Domain], fine: List[Domain], dT: flo
     _check(_lib.osmpm_schwarz_couple_batch(cs, fs, n, dT, sd, n_threads, st, status),
            "osmpm_schwarz_couple_batch", warn_ok=True)
     return [s.as_dict() for s in st], list(status)
+
+
+def create_stream() -> int:
+    """A new non-blocking CUDA stream made by the library (a distinct stream
+    per pair of osmpm_schwarz_couple_batch; torch.cuda.Stream() hands out
+    streams from a fixed pool).  Release with destroy_stream."""
+    h = c_void_p()
+    _check(_lib.osmpm_create_stream(ctypes.byref(h)), "osmpm_create_stream")
+    return int(h.value)
+
+
+def destroy_stream(stream: int) -> None:
+    _check(_lib.osmpm_destroy_stream(c_void_p(stream)), "osmpm_destroy_stream")
+
+
+def osmpm_autotune_batch(coarse: List[Domain], fine: List[Domain], dT: float, schs, candidates):
+    """Host concurrency for osmpm_schwarz_couple_batch on these pairs, chosen
+    by timing one batched step per candidate (the pairs advance by
+    len(candidates) + 1 global steps).  Returns (best, {candidate: wall
+    microseconds per PCG iteration})."""
+    n = len(coarse)
+    cs = (c_void_p * n)(*[d.h.value for d in coarse])
+    fs = (c_void_p * n)(*[d.h.value for d in fine])
+    sd = (osmpm_schwarz_desc * n)(*[make_schwarz_desc(s) for s in schs])
+    cand = (c_int32 * len(candidates))(*candidates)
+    best = c_int32(0)
+    score = np.zeros(len(candidates), dtype=np.float64)
+    _check(_lib.osmpm_autotune_batch(cs, fs, n, dT, sd, cand, len(candidates), ctypes.byref(best),
+                                     score.ctypes.data_as(_DP)),
+           "osmpm_autotune_batch", warn_ok=True)
+    return int(best.value), {int(c): float(v) for c, v in zip(candidates, score)}
 
 
 def osmpm_get_particles(dom: Domain):

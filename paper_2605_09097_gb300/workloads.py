@@ -98,6 +98,7 @@ class DomainSpec:
     precision: int = 0            # 0: FP64; 1: mixed (FP32 particle state and HVP)
     cg_eta_max: float = 0.0       # inexact-Newton forcing cap (0: the library default 1e-3)
     pcg_mode: int = 0             # 0 automatic, 1 persistent PCG, 2 streaming PCG
+    launch_mode: int = 0          # 0 CUDA graph per Newton iteration, 1 plain stream launches
 
     def __post_init__(self):
         if self.mass_eps is None:

@@ -93,3 +93,63 @@ def test_batch_many_concurrent_pairs_complete(env):
                                                      n_threads=16)
     assert all(s == osmpm.OSMPM_OK for s in status), status
     assert all(st["converged"] == 1 for st in stats)
+
+
+def test_autotune_picks_a_candidate_and_steps_like_the_batch(env):
+    """The autotuner's steps are ordinary batched steps: after it, each pair
+    is where len(candidates) + 1 batched steps put it (any thread count
+    gives each pair its own result), and the pick is the fastest candidate
+    per PCG iteration."""
+    torch, osmpm = env
+    specs = [W.inclusion_instance(i) for i in range(4)]
+    B, S, _ = _pairs(torch, osmpm, specs)
+    B1, S1, _ = _pairs(torch, osmpm, specs)
+    dT = specs[0][3]
+    schs = [s[2] for s in specs]
+    cands = [1, 2, 4]
+    best, score = osmpm.osmpm_autotune_batch(B, S, dT, schs, cands)
+    assert best in cands and sorted(score) == cands
+    assert all(np.isfinite(v) and v > 0 for v in score.values())
+    assert score[best] == min(score.values())
+    for _ in range(len(cands) + 1):
+        osmpm.osmpm_schwarz_couple_batch(B1, S1, dT, schs, n_threads=2)
+    for i in range(len(specs)):
+        x0 = specs[i][1].particles.x
+        assert rel_disp(S[i].get_particles()[0], S1[i].get_particles()[0], x0) <= 1e-9
+
+
+def test_autotune_rejects_bad_candidates(env):
+    torch, osmpm = env
+    specs = [W.inclusion_instance(0)]
+    B, S, _ = _pairs(torch, osmpm, specs)
+    with pytest.raises(osmpm.OsmpmError):
+        osmpm.osmpm_autotune_batch(B, S, specs[0][3], [specs[0][2]], [2, 0])
+
+
+def test_batch_pairs_sharing_a_stream_launch_directly(env):
+    """Two pairs on one stream and two on streams of their own: the batch's
+    worker threads launch directly (no graph capture from concurrent host
+    threads), and every pair gets its own result."""
+    torch, osmpm = env
+    specs = [W.inclusion_instance(i) for i in range(4)]
+    s0, s1, s2 = osmpm.create_stream(), osmpm.create_stream(), osmpm.create_stream()
+    streams = [s0, s0, s1, s2]
+    B = [osmpm.Domain(s[0], stream=st) for s, st in zip(specs, streams)]
+    S = [osmpm.Domain(s[1], stream=st) for s, st in zip(specs, streams)]
+    B1, S1, _ = _pairs(torch, osmpm, specs)
+    dT = specs[0][3]
+    schs = [s[2] for s in specs]
+    for _ in range(2):
+        _, status = osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=4)
+        assert all(s == osmpm.OSMPM_OK for s in status)
+        for i in range(len(specs)):
+            osmpm.osmpm_schwarz_couple(B1[i], S1[i], dT, schs[i])
+    for i in range(len(specs)):
+        x0 = specs[i][1].particles.x
+        assert rel_disp(S[i].get_particles()[0], S1[i].get_particles()[0], x0) <= 1e-9
+        c = S[i].counters()
+        assert c["graph_error"] == 0 and c["graph_replays"] == 0 and c["graphs"] == 0, (i, c)
+    for d in B + S:
+        d.close()
+    for st in (s0, s1, s2):
+        osmpm.destroy_stream(st)

@@ -138,6 +138,39 @@ def test_cantilever_20_steps_matches_oracle(osmpm, pcg_mode):
     np.testing.assert_allclose(v, ref.p.v, atol=1e-6 * np.abs(ref.p.v).max())
 
 
+def test_cantilever_graph_replay_matches_plain_launches(osmpm):
+    """launch_mode 0 replays a CUDA graph per Newton iteration (built once
+    per iteration kind) on a created stream; launch_mode 1, and any domain
+    on the legacy default stream, launch the same work directly.  All match
+    the oracle; only the first replays graphs."""
+    import torch
+    ref = O.DomainState.create(W.cantilever())
+    x0 = ref.p.x.copy()
+    for _ in range(20):
+        O.step(ref, 1e-3)
+    stream = torch.cuda.Stream()
+    for mode, st in ((0, stream.cuda_stream), (1, stream.cuda_stream), (0, 0)):
+        dom = osmpm.Domain(dataclasses.replace(W.cantilever(), pcg_mode=1, launch_mode=mode), stream=st)
+        newton = 0
+        for _ in range(20):
+            newton += dom.step(1e-3)["newton_iters"]
+        x, v, B, F = dom.get_particles()
+        assert rel_disp(x, ref.p.x, x0) <= DISP_TOL
+        np.testing.assert_allclose(F, ref.p.F, atol=1e-9)
+        c = dom.counters()
+        assert c["graph_error"] == 0, f"graph build failed: cudaError {c['graph_error']}"
+        if mode == 0 and st != 0:
+            assert c["graph_replays"] == newton
+            assert 1 <= c["graphs"] <= 8
+        else:
+            assert c["graph_replays"] == 0 and c["graphs"] == 0
+
+
+def test_launch_mode_validated(osmpm):
+    with pytest.raises(osmpm.OsmpmError):
+        osmpm.Domain(dataclasses.replace(W.cantilever(), launch_mode=2))
+
+
 @pytest.mark.parametrize("dim,pcg_mode", [(2, 0), (3, 0), (2, 2), (3, 2)])
 def test_random_state_steps_match_oracle(osmpm, dim, pcg_mode):
     spec = _perturbed(dim, 11, n_cells=(6, 5, 4), dx=0.1, E=1e5, gravity=(0.0, -9.8, 0.0)[:dim])
