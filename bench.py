@@ -55,11 +55,11 @@ WORKLOAD = "inclusion_osmpm_2d_fp64_dxB0.05_dxS0.005_M2"
 ORACLE_SCHWARZ_ITERS_PER_STEP = 12.0
 ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
-AUTOTUNE_THREADS = [4, 6, 8, 12, 16]
+AUTOTUNE_THREADS = [8, 12, 16]
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
 # launch, from the ncu capture of the current kernel (the k_pcg profile
 # summary of this workload); None whenever the kernel changes
-PCG_TRAFFIC_BYTES = None
+PCG_TRAFFIC_BYTES = 3.05e6 + 0.06e6
 # FP64 flops of one Hessian-vector product per particle: gather G (2 d^2 3^d),
 # Y = L G (2 d^4), G:Y (2 d^2), scatter (2 d^2 3^d); an FMA counts 2.
 HVP_FLOPS_PER_PARTICLE = {2: 184, 3: 1152}

@@ -218,9 +218,10 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* coarse, osmpm_domain* fine, doub
  * up to n_threads host worker threads (0: 8) driving the pairs
  * concurrently; each pair must own its two domains and should have its own
  * stream, so that kernels of different pairs overlap on the GPU.  While the
- * call runs, each pair's persistent PCG grid is limited to 1/n_threads of
- * the device's co-resident capacity, so that the concurrent cooperative
- * grids can all be resident together (their grid barriers never wait on a
+ * call runs, each pair's persistent PCG grid is limited to 3/4 of
+ * 1/n_threads of the device's co-resident capacity, so that the concurrent
+ * cooperative grids can all be resident together with room to spare for
+ * the other pairs' ordinary kernels (their grid barriers never wait on a
  * block another grid keeps out).  The worker threads launch directly
  * (launch_mode 0 graphs are built and replayed only by calls made from the
  * caller's thread).  Calls that drive domains concurrently

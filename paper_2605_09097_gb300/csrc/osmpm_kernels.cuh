@@ -1146,7 +1146,10 @@ void Kernels<D, R>::pcg_shape(int64_t work, int share, int* blocks, int* threads
   // co-resident capacity (counted in 256-thread blocks): when `share`
   // cooperative grids run concurrently they can then all be resident at
   // once, so none of their grid barriers can wait on a block that another
-  // grid keeps out.
+  // grid keeps out.  Concurrent grids (share > 1) together take at most 3/4
+  // of that capacity, so a block launched late still finds room beside the
+  // other pairs' ordinary kernels (at the full capacity a 256-instance batch
+  // with four concurrent grids let a grid barrier run out its bounded wait).
   struct Info {
     int sms = 0, per_sm256 = 1;
   };
@@ -1165,6 +1168,7 @@ void Kernels<D, R>::pcg_shape(int64_t work, int share, int* blocks, int* threads
   }();
   if (share < 1) share = 1;
   int64_t cap = (int64_t)info.sms * info.per_sm256 / share;
+  if (share > 1) cap = cap * 3 / 4;
   if (cap < 1) cap = 1;
   const int64_t sms_share = info.sms / share > 0 ? info.sms / share : 1;
   int64_t t = (work + sms_share - 1) / sms_share;
