@@ -544,6 +544,8 @@ int64_t pcg_work(const osmpm_domain* d) {
   return std::max<int64_t>((d->n + GP - 1) / GP * 32, (int64_t)d->dim * d->geo.nn);
 }
 
+// Whether this solve takes the streaming PCG (pcg_mode 2, or 0 when the
+// persistent grid would need too many passes) rather than the persistent one.
 bool pcg_streaming(osmpm_domain* d, double dt, int64_t work) {
   bool streaming = d->desc.pcg_mode == 2;
   if (d->desc.pcg_mode == 0) DISPATCH(d, (streaming = !pcg_persistent_fits<K, R>(d, dt, work)));
@@ -701,6 +703,8 @@ cudaGraphExec_t newton_graph(osmpm_domain* d, double dt, bool first, bool check,
   return exec;
 }
 
+// After the scalars reached the pinned mirror: the device error word, the
+// iteration count and, when timed, the PCG launch's event time.
 osmpm_status pcg_finish(osmpm_domain* d, bool timed, SolveStats& st) {
   OSMPM_TRY(check_err(d));
   st.cg += d->S_host->cg_iter;
@@ -714,6 +718,9 @@ osmpm_status pcg_finish(osmpm_domain* d, bool timed, SolveStats& st) {
   return OSMPM_OK;
 }
 
+// One Newton iteration's gradient and PCG solve, up to the host's look at
+// max |delta|: a replayed graph where launch_mode 0 allows one, else the
+// same work launched directly; the streaming PCG always launches directly.
 osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check, SolveStats& st) {
   const int64_t work = pcg_work(d);
   const bool timed = d->time_hvp && !d->ev.empty();
