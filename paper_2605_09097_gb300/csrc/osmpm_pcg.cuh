@@ -8,14 +8,15 @@
 // Phase k (after barrier k) does the owner updates above and, in the same
 // phase, the particle Hessian-vector product w_{k+1} = A u_{k+1}: each
 // particle (a group of lanes, one per stencil row) gathers u_{k+1} at its
-// stencil as (r_k - alpha (w_k + beta
-// s_{k-1})) D^-1 from buffers that were complete at barrier k (r and s
-// double-buffered, w triple-buffered), and delta_{k+1} = u.Au is the
-// particle quadratic form sum_p G:LG plus sum m/dt^2 u^2, so it does not
-// wait for the scatter.  Every block sums the partials itself, in block
-// order, so all blocks take the same branch and the result is
-// deterministic.  Arrays that other blocks write during the launch are
-// read with __ldcg (L2, not the non-coherent L1).
+// stencil as (r_k - alpha (w_k + beta s_{k-1})) D^-1 from buffers that were
+// complete at barrier k (r and s double-buffered, w triple-buffered; the
+// single-pass variant forms it once per node of a block-local table), and
+// delta_{k+1} = u.Au is the particle quadratic form sum_p G:LG plus
+// sum m/dt^2 u^2, so it does not wait for the scatter.  Every block sums
+// the partials itself, in an order fixed by the launch shape, so all
+// blocks take the same branch (the scatter's FP64 atomics still let the
+// last bits of a solve vary between runs).  Arrays that other blocks write
+// during the launch are read with __ldcg (L2, not the non-coherent L1).
 #pragma once
 
 #include "osmpm_device.cuh"
