@@ -267,3 +267,31 @@ def test_initial_guess_takes_the_lower_energy_start():
     pr = _free_problem(spec, 1e-3)
     u = O.initial_guess(pr)
     np.testing.assert_allclose(u[a], (pr.dt * pr.gf.vn)[a], rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_cauchy_stress_from_the_energy(d):
+    """sigma = (d psi / d F) F^T / J, with d psi / d F taken by central
+    differences of psi (pinned above), not through pk1; symmetric (balance
+    of angular momentum), and -p I under a pure volume change with
+    p = -(lam ln J + mu (s^2 - 1)) / J for F = s I."""
+    F = _rand_F(4, d, 0.15, 11 + d)
+    mu, lam = np.full(4, 3.0e5), np.full(4, 7.0e5)
+    h = 1e-6
+    P = np.zeros_like(F)
+    for a in range(d):
+        for b in range(d):
+            E = np.zeros((d, d))
+            E[a, b] = h
+            P[:, a, b] = (O.psi(F + E, mu, lam) - O.psi(F - E, mu, lam)) / (2 * h)
+    J = np.linalg.det(F)
+    sig_fd = np.einsum("pab,pcb->pac", P, F) / J[:, None, None]
+    sig = O.cauchy_stress(F, mu, lam)
+    np.testing.assert_allclose(sig, sig_fd, rtol=0, atol=1e-6 * np.abs(sig).max())
+    np.testing.assert_allclose(sig, np.swapaxes(sig, 1, 2), atol=1e-9 * np.abs(sig).max())
+    s = 1.02
+    Fs = np.broadcast_to(s * np.eye(d), (1, d, d)).copy()
+    Js = s ** d
+    p = -(7.0e5 * np.log(Js) + 3.0e5 * (s * s - 1.0)) / Js
+    np.testing.assert_allclose(O.cauchy_stress(Fs, mu[:1], lam[:1])[0], -p * np.eye(d),
+                               rtol=1e-12, atol=1e-9 * abs(p))

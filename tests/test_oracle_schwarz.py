@@ -188,3 +188,56 @@ def test_substep_average_with_one_substep_is_the_solved_grid():
     avg = O.substep_average([gf], [u / 0.01])
     np.testing.assert_array_equal(avg.active, gf.active)
     np.testing.assert_allclose(avg.vn[gf.active], (u / 0.01)[gf.active], rtol=1e-13, atol=1e-15)
+
+
+def _brute_boundary_mass(p, grid):
+    """Boundary-particle mass per node by a loop over particles and their
+    3^d stencil nodes, B-spline weights from the 1D definition."""
+    def w1(r):
+        r = abs(r)
+        return 0.75 - r * r if r < 0.5 else (0.5 * (1.5 - r) ** 2 if r < 1.5 else 0.0)
+    d = grid.dim
+    res = np.asarray(grid.res)
+    bm = np.zeros(int(np.prod(res)))
+    for q in np.nonzero(p.flags & 1)[0]:
+        t = (p.x[q] - np.asarray(grid.origin[:d])) / grid.dx
+        base = np.floor(t - 0.5).astype(int)
+        for off in np.ndindex(*(3,) * d):
+            node = base + np.array(off)
+            w = np.prod([w1(t[a] - node[a]) for a in range(d)])
+            flat = node[0] + res[0] * (node[1] + (res[1] * node[2] if d == 3 else 0))
+            bm[flat] += p.mass[q] * w
+    return bm
+
+
+def test_interface_sets_follow_the_definitions():
+    """Gamma (Eq. boundary_grid_set) holds the active nodes that carry more
+    than tau of boundary-particle mass (checked against a brute-force
+    boundary mass); after arbitration (Eq. overlap_donor) no coincident pair
+    receives on both sides; receivers lie where the outer particle layers
+    are (fine: around r = 0.15; coarse: around the hole r = 0.1, inside the
+    fine region) and never on nodes with a physical Dirichlet rule."""
+    cB, cS, sch, dT = _inclusion_small()
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    gfB = O.p2g(B.p, cB.grid, boundary_mass=True, mass_eps=cB.mass_eps)
+    gfS = O.p2g(S.p, cS.grid, boundary_mass=True, mass_eps=cS.mass_eps)
+    for gf, st, tau in ((gfB, B, sch.tau_B), (gfS, S, sch.tau_S)):
+        bm = _brute_boundary_mass(st.p, st.spec.grid)
+        np.testing.assert_allclose(gf.bm, bm, rtol=1e-12, atol=1e-15 * bm.max())
+        assert np.array_equal(O.boundary_sets(gf, tau), gf.active & (bm > tau))
+    sets = O.interface_sets(B, S, gfB, gfS, sch, dT)
+    assert sets.recvB.any() and sets.recvS.any()
+    assert not (sets.recvB & ~sets.gammaB).any() and not (sets.recvS & ~sets.gammaS).any()
+    j = O.coincident_fine_node(cB.grid, cS.grid)
+    pair = (j >= 0) & sets.recvB
+    assert not sets.recvS[j[pair]].any()
+    xS = O.node_positions(cS.grid)
+    rS = np.hypot(xS[sets.recvS, 0] - 0.5, xS[sets.recvS, 1] - 0.5)
+    reach = 1.5 * np.sqrt(2) * cS.grid.dx
+    assert rS.min() >= 0.15 - cS.grid.dx / 2 - reach and rS.max() <= 0.15 + reach
+    xB = O.node_positions(cB.grid)
+    rB = np.hypot(xB[sets.recvB, 0] - 0.5, xB[sets.recvB, 1] - 0.5)
+    assert rB.max() <= 0.125 + 1.5 * np.sqrt(2) * cB.grid.dx
+    assert rB.max() <= 0.15 + 1.5 * np.sqrt(2) * cS.grid.dx   # fed by the fine projection
+    mB, _ = O.dirichlet_nodes(cB.grid, cB.dirichlet, dT)
+    assert not (sets.recvB & mB.any(axis=1)).any()
