@@ -241,3 +241,25 @@ def test_interface_sets_follow_the_definitions():
     assert rB.max() <= 0.15 + 1.5 * np.sqrt(2) * cS.grid.dx   # fed by the fine projection
     mB, _ = O.dirichlet_nodes(cB.grid, cB.dirichlet, dT)
     assert not (sets.recvB & mB.any(axis=1)).any()
+
+
+def test_particles_advance_once_per_global_step():
+    """Sec. 3.5: after convergence the fine particles keep the state of the
+    last iteration's sub-steps (they are not reset to the snapshot), and the
+    coarse particles take one G2P with the last coarse solve.  Under the top
+    edge's 1e-3 downward displacement per step, the fine particles have
+    moved downward (a reset would leave them at rest), and no coarse particle
+    moves by more than the prescribed 1e-3 (a G2P per Schwarz iteration
+    would move the top rows by about k times as much)."""
+    cB, cS, sch, dT = _inclusion_small()
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    st = O.SchwarzStats()
+    O.schwarz_step(B, S, dT, sch, st)
+    assert st.converged and st.iters >= 2
+    dS = S.p.x - cS.particles.x
+    dB = B.p.x - cB.particles.x
+    upper = cS.particles.x[:, 1] > 0.55
+    assert dS[upper, 1].mean() < -1e-6
+    assert np.abs(dB).max() <= 1e-3 * (1 + 1e-9)
+    top = cB.particles.x[:, 1] > 0.85
+    assert dB[top, 1].mean() < -0.5e-3
