@@ -295,3 +295,19 @@ def test_cauchy_stress_from_the_energy(d):
     p = -(7.0e5 * np.log(Js) + 3.0e5 * (s * s - 1.0)) / Js
     np.testing.assert_allclose(O.cauchy_stress(Fs, mu[:1], lam[:1])[0], -p * np.eye(d),
                                rtol=1e-12, atol=1e-9 * abs(p))
+
+
+def test_newton_reports_a_failed_line_search(monkeypatch):
+    """A line search that finds no decrease within its halving cap is an
+    error (LineSearchFailed), not a silently accepted step: forced by
+    reporting every trial step as an energy increase."""
+    spec = W.cantilever()
+    gf = O.p2g(spec.particles, spec.grid, mass_eps=spec.mass_eps)
+    mask, vel = O.dirichlet_nodes(spec.grid, spec.dirichlet, 1e-3)
+    pr = O.make_problem(spec.particles, spec.grid, gf, 1e-3, spec.gravity, mask, vel)
+    calls = []
+    monkeypatch.setattr(O, "energy_change", lambda *a: calls.append(a[3]) or 1.0)
+    with pytest.raises(O.LineSearchFailed):
+        O.newton(pr, spec.newton_tol, spec.newton_max, 3)
+    # the cold start compares x_tilde with x^n once, then alpha = 1 and three halvings
+    assert calls == [1.0, 1.0, 0.5, 0.25, 0.125]
