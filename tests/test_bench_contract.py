@@ -28,3 +28,21 @@ def test_reference_arm_json_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_clock_rows_summary():
+    """The clocks object of the bench line: median SM clock under load, the
+    maximum clock, and every throttle reason seen active (a run with a
+    hardware or thermal slowdown is rejected; sw_power_cap is noted)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = ["0, 2070, 2070, 850.10, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, 1950, 2070, 1390.52, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 1120.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+            "garbage"]
+    c = bench.parse_clock_rows(rows)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 4}
+    hot = bench.parse_clock_rows(["0, 1500, 2070, 1300, 0x48, Active, Not Active, Active, Not Active"])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
+    assert bench.parse_clock_rows([]) is None
