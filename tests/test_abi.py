@@ -138,3 +138,17 @@ def test_batch_and_stream_argument_checks_run_on_the_host():
     assert st == osmpm.OSMPM_E_INVALID
     c = osmpm.osmpm_counters()
     assert lib.osmpm_get_counters(None, ctypes.byref(c)) == osmpm.OSMPM_OK and c.launches >= 0
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """On a host without a CUDA device the product path fails loudly: a
+    valid domain cannot be created (the library's first device allocation
+    fails), and nothing falls back to a CPU computation."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2605_09097_gb300 import osmpm
+    from paper_2605_09097_gb300 import workloads as W
+    with pytest.raises(osmpm.OsmpmError) as e:
+        osmpm.Domain(W.cantilever(), stream=0, use_torch_allocator=False)
+    assert e.value.status in (osmpm.OSMPM_E_CUDA, osmpm.OSMPM_E_NOMEM)
