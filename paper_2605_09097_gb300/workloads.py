@@ -404,6 +404,36 @@ def hertz_rigid(dx_c: float = 1.0 / 64, ratio: int = 4, M: int = 4, E: float = 2
     return coarse, fine, sch, dT
 
 
+def hertz_rigid_single(dx: float = 1.0 / 64, E: float = 2e5, nu: float = 0.3,
+                       rho: float = 1000.0, R: float = 0.5, dt: float = 0.02,
+                       indent: float = 0.01, n_steps: int = 10, ppc_1d: int = 2,
+                       newton_tol: float = 1e-8):
+    """The cylinder of the Sec. 4.2 benchmark on one grid at dx: the
+    half-disk r < R, y < R centred at (0, R), lowest point on the plane
+    y = 0; its flat face's nodes move down by ``indent`` over ``n_steps``
+    steps of dt (that rule is the spec's only Dirichlet entry, so a caller
+    can stop the push by zeroing its velocity).  The plane itself is not a Dirichlet rule here:
+    the grid nodes with y <= dx/2 are the candidates of a unilateral
+    contact (``plane_nodes``).  Returns (spec, plane_nodes)."""
+    c = np.array([0.0, R])
+
+    def cyl(x):
+        return (_r2(x, c) < R * R) & (x[:, 1] < c[1])
+
+    m = 3
+    nh = int(np.ceil((R + 0.05) / dx))   # a node at x = 0: grid and lattice symmetric about the contact
+    ny = int(round((R + 0.05) / dx))
+    g = Grid(2, (-(nh + m) * dx, -m * dx), dx, (2 * (nh + m) + 1, ny + 2 * m + 1))
+    x = sample_lattice(g.origin, dx, (m, m), (m + 2 * nh, m + ny), ppc_1d, cyl)
+    p = make_particles(x, dx, ppc_1d, rho, E, nu)
+    v_push = -indent / (n_steps * dt)
+    top = Dirichlet(lo=(-BIG, R - 0.5 * dx), hi=(BIG, BIG), comp_mask=0b11, vel=(0.0, v_push, 0.0))
+    spec = DomainSpec("hertz_rigid_single", g, p, (0.0, 0.0), [top], newton_tol=newton_tol)
+    iy = np.arange(g.res[0] * g.res[1]) // g.res[0]
+    plane_nodes = g.origin[1] + iy * dx <= 0.5 * dx
+    return spec, plane_nodes
+
+
 def fold3d(dx_c: float = 0.02, dx_f: float = 0.005, band=(0.4, 0.6), M: int = 4,
            size=(1.0, 0.5, 0.02), E: float = 1e6, nu: float = 0.3, rho: float = 1000.0,
            dT: float = 0.01, fold_steps: int = 400, ppc_1d: int = 2, precision: int = 1,

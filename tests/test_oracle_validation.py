@@ -63,3 +63,62 @@ def test_oracle_cantilever_matches_elastica(gamma):
     clamp smearing add ~1 %)."""
     w, _ = quasi_static_cantilever_tip(gamma)
     np.testing.assert_allclose(w, A.elastica_tip_deflection(gamma), rtol=0.03)
+
+
+def _settled_hertz_contact(dx, ppc_1d, indent, n_steps=10, dt=0.02, dt_settle=0.2):
+    """The cylinder of Sec. 4.2 pressed onto the rigid plane by its flat
+    face (``indent`` over ``n_steps`` steps), then held and settled: every
+    step a kinetically damped implicit step (v and B zeroed after it), the
+    plane unilateral (oracle.contact), until the particle speed is below
+    1e-6.  Returns (spec, plane nodes, active set, multipliers, last u)."""
+    import dataclasses
+    from oracle import contact as C
+    spec, plane = W.hertz_rigid_single(dx=dx, ppc_1d=ppc_1d, indent=indent, n_steps=n_steps, dt=dt)
+    ds = O.DomainState.create(spec)
+    h = dx / ppc_1d
+    for _ in range(n_steps):
+        C.step_with_plane(ds, dt, plane, h)
+        ds.p.v[:] = 0.0
+        ds.p.B[:] = 0.0
+    ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(spec.dirichlet[0],
+                                                                        vel=(0.0, 0.0, 0.0))])
+    for _ in range(200):
+        gf = O.p2g(ds.p, spec.grid, mass_eps=spec.mass_eps)
+        gap = C.plane_gaps(ds.p, spec.grid, plane, h)
+        u, act, lam = C.solve_with_plane(ds, gf, dt_settle, plane, gap)
+        ds.p = O.g2p(ds.p, spec.grid, u, dt_settle)
+        vmax = np.abs(ds.p.v).max()
+        ds.p.v[:] = 0.0
+        ds.p.B[:] = 0.0
+        if vmax < 1e-6:
+            return spec, plane, gf, gap, act, lam, u
+    raise AssertionError("the contact did not settle")
+
+
+def test_unilateral_plane_contact_gives_the_hertz_pressure():
+    """The oracle's reading of the rigid frictionless plane (a gap-aware
+    Signorini condition on the plane nodes' normal motion, oracle.contact)
+    satisfies the Signorini conditions at the settled state, and its
+    contact pressure (plane multipliers summed per node column / dx) follows
+    the Hertz semi-ellipse p_max sqrt(1 - (x/b)^2) with b and p_max from
+    the transmitted load: half-width within two node spacings, relative L2
+    error below 0.2 at dx = 1/32 with 16 particles per cell."""
+    dx = 1.0 / 32
+    spec, plane, gf, gap, act, lam, u = _settled_hertz_contact(dx, 4, 0.03)
+    cand = plane & gf.active & np.isfinite(gap)
+    # Signorini: lambda >= 0 where held, no penetration where free
+    assert (lam[act] >= 0.0).all()
+    assert (u[cand & ~act, 1] >= -gap[cand & ~act] - 1e-12).all()
+    g = spec.grid
+    ix = np.arange(g.res[0] * g.res[1]) % g.res[0]
+    p = np.bincount(ix, weights=np.where(plane, lam, 0.0), minlength=g.res[0]) / dx
+    xc = g.origin[0] + np.arange(g.res[0]) * dx
+    F = p.sum() * dx
+    b, pmax = A.hertz_line_contact(F, 0.5, 2e5, 0.3)
+    edge = np.abs(xc[p > 0]).max()
+    assert abs(edge - b) <= 2 * dx
+    ph = pmax * np.sqrt(np.clip(1.0 - (xc / b) ** 2, 0.0, None))
+    sel = np.abs(xc) <= 1.5 * b
+    err = np.linalg.norm(p[sel] - ph[sel]) / np.linalg.norm(ph[sel])
+    assert err < 0.2, err
+    np.testing.assert_allclose(p, p[::-1], rtol=1e-6, atol=1e-9 * pmax)   # symmetric about x = 0
