@@ -76,12 +76,17 @@ def _settled_hertz_contact(dx, ppc_1d, indent, n_steps=10, dt=0.02, dt_settle=0.
     spec, plane = W.hertz_rigid_single(dx=dx, ppc_1d=ppc_1d, indent=indent, n_steps=n_steps, dt=dt)
     ds = O.DomainState.create(spec)
     h = dx / ppc_1d
-    for _ in range(n_steps):
+    push = spec.dirichlet[0]
+    for k in range(n_steps):
+        # the pushed rows follow the flat face down (a fixed box would lose
+        # the face once the indent passes a grid spacing)
+        lo = (push.lo[0], push.lo[1] - k * indent / n_steps)
+        ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(push, lo=lo)])
         C.step_with_plane(ds, dt, plane, h)
         ds.p.v[:] = 0.0
         ds.p.B[:] = 0.0
-    ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(spec.dirichlet[0],
-                                                                        vel=(0.0, 0.0, 0.0))])
+    lo = (push.lo[0], push.lo[1] - indent)
+    ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(push, lo=lo, vel=(0.0, 0.0, 0.0))])
     for _ in range(200):
         gf = O.p2g(ds.p, spec.grid, mass_eps=spec.mass_eps)
         gap = C.plane_gaps(ds.p, spec.grid, plane, h)
