@@ -31,7 +31,7 @@ from tests.test_oracle_validation import _settled_hertz_contact  # noqa: E402
 
 def run(dx: float, ppc: int = 4, indent: float = 0.03) -> dict:
     t0 = time.time()
-    spec, plane, gf, gap, act, lam, u = _settled_hertz_contact(dx, ppc, indent)
+    spec, plane, gf, gap, act, lam, u, ds = _settled_hertz_contact(dx, ppc, indent)
     g = spec.grid
     ix = np.arange(g.res[0] * g.res[1]) % g.res[0]
     p = np.bincount(ix, weights=np.where(plane, lam, 0.0), minlength=g.res[0]) / dx

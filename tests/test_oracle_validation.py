@@ -70,7 +70,8 @@ def _settled_hertz_contact(dx, ppc_1d, indent, n_steps=10, dt=0.02, dt_settle=0.
     face (``indent`` over ``n_steps`` steps), then held and settled: every
     step a kinetically damped implicit step (v and B zeroed after it), the
     plane unilateral (oracle.contact), until the particle speed is below
-    1e-6.  Returns (spec, plane nodes, active set, multipliers, last u)."""
+    1e-6.  Returns (spec, plane nodes, grid fields, gaps, active set,
+    multipliers, last u, settled domain state)."""
     import dataclasses
     from oracle import contact as C
     spec, plane = W.hertz_rigid_single(dx=dx, ppc_1d=ppc_1d, indent=indent, n_steps=n_steps, dt=dt)
@@ -96,7 +97,7 @@ def _settled_hertz_contact(dx, ppc_1d, indent, n_steps=10, dt=0.02, dt_settle=0.
         ds.p.v[:] = 0.0
         ds.p.B[:] = 0.0
         if vmax < 1e-6:
-            return spec, plane, gf, gap, act, lam, u
+            return spec, plane, gf, gap, act, lam, u, ds
     raise AssertionError("the contact did not settle")
 
 
@@ -109,7 +110,7 @@ def test_unilateral_plane_contact_gives_the_hertz_pressure():
     the transmitted load: half-width within two node spacings, relative L2
     error below 0.2 at dx = 1/32 with 16 particles per cell."""
     dx = 1.0 / 32
-    spec, plane, gf, gap, act, lam, u = _settled_hertz_contact(dx, 4, 0.03)
+    spec, plane, gf, gap, act, lam, u, _ = _settled_hertz_contact(dx, 4, 0.03)
     cand = plane & gf.active & np.isfinite(gap)
     # Signorini: lambda >= 0 where held, no penetration where free
     assert (lam[act] >= 0.0).all()
