@@ -526,6 +526,49 @@ def run_fold(args, rank, local, world):
                        "fine_us_per_pcg_iter": 1e3 * cS_["pcg_ms"] / max(cS_["pcg_iters"], 1)}}
 
 
+def run_fold_solve(args, rank, local, world):
+    """Single-domain implicit steps of the fine band of the scaled 3D fold
+    (3.07M particles at dx 0.0025, mixed precision, streaming PCG) with
+    seeded velocities, B and F: the configuration of the tiled
+    Hessian-vector product.  CUDA events around each step on the domain's
+    stream; the library's PCG events give the time per PCG iteration."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2605_09097_gb300 import build
+    build.build()
+    from paper_2605_09097_gb300 import osmpm
+    _, cS, sch, dT = W.fold3d(dx_f=0.0025, band=(0.2, 0.8))
+    spec = W.perturb(cS, 7, v_scale=0.05)
+    spec = dataclasses.replace(spec, hvp_mode=args.hvp_mode)
+    dt = dT / sch.M
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dom = osmpm.Domain(spec, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            dom.step(dt)
+        torch.cuda.synchronize()
+        dom.set_profiling(True)
+        stats, ms = [], 0.0
+        for _ in range(args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            stats.append(dom.step(dt))
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        c = dom.counters()
+    n = spec.particles.n
+    return {"metric": METRIC, "value": n * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
+            "data": "synthetic",
+            "config": {"workload": "fold3d_scaled_fine_band_single_domain_mixed", "particles": n,
+                       "hvp_mode": args.hvp_mode, "dt": dt,
+                       "newton_iters_per_step": [s["newton_iters"] for s in stats],
+                       "cg_iters_per_step": [s["cg_iters"] for s in stats],
+                       "us_per_pcg_iter": 1e3 * c["pcg_ms"] / max(c["pcg_iters"], 1)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -536,7 +579,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--launch-mode", type=int, choices=[0, 1], default=0,
                     help="0: each Newton iteration replays a captured CUDA graph; 1: plain launches")
-    ap.add_argument("--workload", choices=["inclusion", "batched", "fold3d"], default="inclusion",
+    ap.add_argument("--hvp-mode", type=int, choices=[0, 1, 2], default=0,
+                    help="fold3d_solve: Hessian-vector product of the streaming PCG")
+    ap.add_argument("--workload", choices=["inclusion", "batched", "fold3d", "fold3d_solve"],
+                    default="inclusion",
                     help="inclusion: the headline FP64 configuration; batched: many instances; "
                          "fold3d: the 3D folding plate (mixed)")
     ap.add_argument("--scaled", action="store_true", help="fold3d: the 3.07M-particle band")
@@ -552,6 +598,8 @@ def main():
         out = run_batched(args, rank, local, world)
     elif args.workload == "fold3d":
         out = run_fold(args, rank, local, world)
+    elif args.workload == "fold3d_solve":
+        out = run_fold_solve(args, rank, local, world)
     else:
         out = run_ours(args, rank, local, world)
     if rank == 0 and out is not None:

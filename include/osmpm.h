@@ -99,7 +99,16 @@ typedef struct osmpm_domain_desc {
                                cannot be captured) and the worker threads of
                                osmpm_schwarz_couple_batch always launch directly.
                                Results do not depend on it */
-  int32_t reserved[4];      /* must be zero */
+  int32_t hvp_mode;         /* Hessian-vector product of the streaming PCG in mixed
+                               precision: 0 automatic (= 2); 1: lane groups over the
+                               stencil gradients cached at P2G and the Hessian blocks
+                               cached by the gradient kernel; 2: block tiles - each block
+                               stages the grid nodes its Morton-sorted particles touch in
+                               shared memory (gathers and a shared scatter, one global
+                               atomic per tile node and component) and recomputes the
+                               particle Hessian from the Newton iterate.  FP64 domains
+                               always use 1 */
+  int32_t reserved[3];      /* must be zero */
 } osmpm_domain_desc;
 
 /* Initial particle state, host arrays in id order (layouts above).  flags
@@ -168,7 +177,9 @@ typedef struct osmpm_stats {
   int32_t converged;        /* Schwarz converged (1) or hit k_max (0) */
   double r_B, r_S;          /* last interface residuals */
   double last_dx_inf;       /* max |delta x_hat| of the last Newton iteration */
-  double reserved[6];
+  int32_t contact_sets;     /* active sets of the rigid-plane contact (0 without a plane) */
+  int32_t pad;
+  double reserved[5];
 } osmpm_stats;
 
 typedef struct osmpm_domain osmpm_domain;
@@ -192,6 +203,31 @@ osmpm_status osmpm_destroy_domain(osmpm_domain* dom);
 /* Replaces the domain's physical Dirichlet rules (n_rules may be 0). */
 osmpm_status osmpm_set_dirichlet(osmpm_domain* dom, const osmpm_dirichlet* rules,
                                  int32_t n_rules);
+
+/* Rigid frictionless plane y = level under a 2D domain (the rigid plane of
+ * Sec. 4.2; the paper gives no contact treatment).  Reading: a unilateral,
+ * gap-aware Signorini condition on the normal motion of the candidate grid
+ * nodes (y_i <= cand_hi, active, no physical rule on y, some particle within
+ * `spacing` of the node's column in x): over one step u_iy >= -gap_i, where
+ * gap_i = max(0, (lowest such particle's y - spacing/2) - level); the
+ * tangential motion stays free.  osmpm_step then solves the contact by a
+ * primal-dual active set: Newton with u_iy = -gap_i held on the active
+ * nodes, multipliers lambda_i = dE_h/du_iy (the plane's force on node i)
+ * from the gradient with every active DOF free, release of held nodes with
+ * lambda_i < 0 and holding of free candidates with u_iy < -gap_i, until the
+ * set stops changing (at most max_sets solves; 0 means 50; then
+ * OSMPM_E_NEWTON_MAXITER).  The first set holds the nodes whose gap is
+ * closed.  enabled = 0 removes the plane.  Errors: OSMPM_E_UNSUPPORTED in
+ * 3D; osmpm_schwarz_couple refuses a domain with a plane.  The reverse mode
+ * holds the last active set fixed, like the Dirichlet DOFs. */
+typedef struct osmpm_plane {
+  int32_t enabled;
+  int32_t max_sets;
+  double level;      /* the plane y = level; the body lies above it */
+  double cand_hi;    /* candidate nodes: y_i <= cand_hi */
+  double spacing;    /* particle spacing: column width and gap offset */
+} osmpm_plane;
+osmpm_status osmpm_set_plane(osmpm_domain* dom, const osmpm_plane* plane);
 
 /* One backward-Euler MPM step of a single domain (Sec. 2.2): P2G (Eq.
  * p2g_transfer), Newton with line search on E_h (Eq. discrete_energy,
@@ -271,8 +307,20 @@ osmpm_status osmpm_autotune_batch(osmpm_domain* const* coarse, osmpm_domain* con
  * holds single-domain steps or coupled steps of one pair, not both;
  * mixing them, osmpm_set_particles, a mixed-precision domain or the
  * last-sub-step projection interrupts it, and osmpm_adjoint refuses an
- * interrupted record.  Errors: OSMPM_E_UNSUPPORTED for a mixed-precision
- * domain. */
+ * interrupted record.
+ *
+ * Step checkpointing: enable = K >= 2 records only the particle state at
+ * the start of every K-th step (for coupled steps both domains', on the
+ * coarse domain, whose K counts) and every step's controls (dt or dT, the
+ * Schwarz descriptor, the Dirichlet rule sets in force).  osmpm_adjoint then
+ * works through the record one segment of K steps at a time, last segment
+ * first: it re-runs the segment's steps from its checkpoint with the full
+ * record, reverses them and frees that record.  Memory: the N/K checkpoints
+ * plus one segment's full record, for about one extra forward pass.  The
+ * re-run steps repeat the recorded ones up to the rounding order of the
+ * atomic sums (the gradient is that of the re-run trajectory).
+ * Errors: OSMPM_E_UNSUPPORTED for a mixed-precision domain (the adjoint
+ * differentiates the FP64 trajectory); OSMPM_E_INVALID for enable < 0. */
 osmpm_status osmpm_record(osmpm_domain* dom, int32_t enable);
 
 /* Outputs of osmpm_adjoint: device arrays of the caller, in particle-id
@@ -351,7 +399,10 @@ enum {
   OSMPM_FIELD_U = 2,
   OSMPM_FIELD_BMASS = 3,
   OSMPM_FIELD_RECEIVER = 4,
-  OSMPM_FIELD_BC = 5
+  OSMPM_FIELD_BC = 5,
+  OSMPM_FIELD_PLANE_FORCE = 6,   /* rigid plane: multiplier lambda_i per node (0 if not held) */
+  OSMPM_FIELD_PLANE_GAP = 7,     /* rigid plane: gap_i per node (+inf off the candidates) */
+  OSMPM_FIELD_PLANE_ACTIVE = 8   /* rigid plane: 1.0 on the held nodes of the last step */
 };
 osmpm_status osmpm_get_grid(const osmpm_domain* dom, int32_t field, double* out);
 
@@ -361,7 +412,10 @@ osmpm_status osmpm_get_grid(const osmpm_domain* dom, int32_t field, double* out)
  * on inactive nodes are ignored (read) or 0 (written).
  *  osmpm_probe_gradient: dE_h/du (Eq. grid_residual with the energy-
  *    consistent internal force) at u = x_hat - x^n, all active DOFs.
- *  osmpm_probe_hvp: (M/dt^2 + K(u)) d, all active DOFs.
+ *  osmpm_probe_hvp: (M/dt^2 + K(u)) d, all active DOFs.  With pcg_mode 2
+ *    the particle part comes from the streaming PCG's own product (lane
+ *    groups or, in mixed precision, block tiles per hvp_mode); otherwise
+ *    from a one-thread-per-particle product over the cached Hessian blocks.
  *  osmpm_probe_energy_change: E_h(u + alpha d) - E_h(u), +inf if a trial
  *    inverts an element. */
 osmpm_status osmpm_probe_gradient(osmpm_domain* dom, double dt, const double* u, double* grad);
@@ -423,14 +477,17 @@ osmpm_status osmpm_get_counters(const osmpm_domain* dom, osmpm_counters* out);
  *    component-major (vn[a*n_nodes + i]); m has one value per node.
  *  - mu, lam are the Lame parameters E/(2(1+nu)), E nu/((1+nu)(1-2nu)).
  *  - The result (one double, +inf if a trial inverts an element) is
- *    written to the device pointer dE on the given stream; the call does
- *    not synchronise.
+ *    written to the device pointer dE on the given stream.  The call then
+ *    waits for that stream: a particle whose B-spline support leaves the
+ *    grid box makes dE NaN and the call return OSMPM_E_OUT_OF_GRID.
  *  - Size limit: max(n_particles, n_nodes * dim) <= 1,048,576; larger
  *    problems are rejected with OSMPM_E_INVALID before any device work.
  *  - The first call on each device looks up the scratch array's device
  *    address (cudaGetSymbolAddress with that device current); make that
- *    first call before any stream capture.  All calls share the scratch:
- *    calls that overlap on the GPU (other streams, other threads) race.
+ *    first call before any stream capture.  The address is kept for the
+ *    life of the process (a cudaDeviceReset would make it stale).  All
+ *    calls share the scratch, which keeps the last call's contents: calls
+ *    that overlap on the GPU (other streams, other threads) race.
  * ------------------------------------------------------------------------- */
 typedef struct osmpm_noalloc_grid {
   int32_t dim;

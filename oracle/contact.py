@@ -75,3 +75,42 @@ def step_with_plane(ds: O.DomainState, dt: float, plane_nodes: np.ndarray, spaci
     u, act, lam = solve_with_plane(ds, gf, dt, plane_nodes, gap, stats=stats)
     ds.p = O.g2p(ds.p, ds.spec.grid, u, dt)
     return act, lam
+
+
+def settle_hertz(dx: float, ppc_1d: int, indent: float, n_steps: int = 10, dt: float = 0.02,
+                 dt_settle: float = 0.2, max_settle: int = 200):
+    """The cylinder of Sec. 4.2 (``workloads.hertz_rigid_single``) pressed
+    onto the rigid plane y = 0 by its flat face (``indent`` over ``n_steps``
+    steps of dt, the pushed node rows following the face down), then held
+    and settled with steps of dt_settle.  Every step is kinetically damped
+    (v and B zeroed after it) and solves the unilateral contact
+    (``step_with_plane``) with the plane candidates of the workload and the
+    particle spacing dx/ppc_1d; settling stops at the first step after which
+    the largest particle speed is below 1e-6.  Returns (spec, plane nodes,
+    grid fields, gaps, active set, multipliers, last u, settled state,
+    settle steps)."""
+    import dataclasses
+    from paper_2605_09097_gb300 import workloads as W
+    spec, plane = W.hertz_rigid_single(dx=dx, ppc_1d=ppc_1d, indent=indent, n_steps=n_steps, dt=dt)
+    ds = O.DomainState.create(spec)
+    h = dx / ppc_1d
+    push = spec.dirichlet[0]
+    for k in range(n_steps):
+        lo = (push.lo[0], push.lo[1] - k * indent / n_steps)
+        ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(push, lo=lo)])
+        step_with_plane(ds, dt, plane, h)
+        ds.p.v[:] = 0.0
+        ds.p.B[:] = 0.0
+    lo = (push.lo[0], push.lo[1] - indent)
+    ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(push, lo=lo, vel=(0.0, 0.0, 0.0))])
+    for k in range(max_settle):
+        gf = O.p2g(ds.p, spec.grid, mass_eps=spec.mass_eps)
+        gap = plane_gaps(ds.p, spec.grid, plane, h)
+        u, act, lam = solve_with_plane(ds, gf, dt_settle, plane, gap)
+        ds.p = O.g2p(ds.p, spec.grid, u, dt_settle)
+        vmax = np.abs(ds.p.v).max()
+        ds.p.v[:] = 0.0
+        ds.p.B[:] = 0.0
+        if vmax < 1e-6:
+            return spec, plane, gf, gap, act, lam, u, ds, k + 1
+    raise O.OracleError("the contact did not settle")

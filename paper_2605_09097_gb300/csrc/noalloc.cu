@@ -14,9 +14,15 @@
 // array's name as a device address: the first call on each device looks
 // the address up with cudaGetSymbolAddress while that device is current
 // and reuses it afterwards.  All calls share the array, which keeps the
-// last call's contents: every call clears the counter that must start at
-// zero, and calls that overlap on the GPU (on different streams, or from
-// several threads) race on it.
+// last call's contents: every call clears the counter and the error word
+// that must start at zero, and calls that overlap on the GPU (on different
+// streams, or from several threads) race on it.  The cached address assumes
+// the device's primary context lives as long as the process: after a
+// cudaDeviceReset the address would be stale.
+//
+// The call waits for its stream before it returns, so that it can report a
+// particle outside the grid box (OSMPM_E_OUT_OF_GRID) instead of a silently
+// wrong sum.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -104,8 +110,9 @@ extern "C" osmpm_status osmpm_energy_change_noalloc(const osmpm_noalloc_grid* gr
   DevScalars* S = (DevScalars*)scratch;
   double* partials = scratch + kNoallocHeader;
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  // the grid reduction's arrival counter must start at zero
+  // the grid reduction's arrival counter and the error word start at zero
   cudaError_t e = cudaMemsetAsync(&S->counter, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&S->err, 0, sizeof(int), s);
   if (e != cudaSuccess) return set_error(OSMPM_E_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   PartPtrs P{};
   P.n = parts->n;
@@ -125,5 +132,13 @@ extern "C" osmpm_status osmpm_energy_change_noalloc(const osmpm_noalloc_grid* gr
   if (e != cudaSuccess) return set_error(OSMPM_E_CUDA, "launch: %s", cudaGetErrorString(e));
   e = cudaMemcpyAsync(dE, &S->dE, sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return set_error(OSMPM_E_CUDA, "cudaMemcpyAsync: %s", cudaGetErrorString(e));
+  // the kernel flags a particle whose support leaves the grid box (its sum
+  // is then NaN); reading the flag makes the call wait for the stream
+  int err = 0;
+  e = cudaMemcpyAsync(&err, &S->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_error(OSMPM_E_CUDA, "error word read-back: %s", cudaGetErrorString(e));
+  if (err & kErrOutOfGrid)
+    return set_error(OSMPM_E_OUT_OF_GRID, "a particle's B-spline support leaves the grid box");
   return OSMPM_OK;
 }

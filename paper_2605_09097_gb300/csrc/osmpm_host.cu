@@ -168,6 +168,20 @@ struct osmpm_domain {
   osmpm_domain* partner = nullptr;  // the other domain of the recorded coupled steps
   int tape_kind = 0;                // 0 empty, 1 single-domain steps, 2 coupled (coarse), 3 coupled (fine)
   double* cadj = nullptr;           // coupled-adjoint work arrays
+  // checkpointed record (osmpm_record with every >= 2): instead of the full
+  // per-step record, the particle state at the start of every ckpt_every-th
+  // recorded step (for coupled steps both domains', kept on the coarse
+  // domain) and the controls of every recorded step; osmpm_adjoint re-runs
+  // one segment of steps at a time with the full record and reverses it
+  int ckpt_every = 1;
+  bool replaying = false;           // osmpm_adjoint re-running a segment
+  struct StepCtl {
+    double dt = 0.0;                               // dt (single) or dT (coupled)
+    osmpm_schwarz_desc sd{};                       // coupled steps
+    std::vector<osmpm_dirichlet> rules, rules_fine;  // the rule sets in force
+  };
+  std::vector<StepCtl> ctl;
+  std::vector<TapeStep> ckpts;      // one per segment: the state at its first step
 
   // CUDA graphs of one Newton iteration's device work (launch_mode 0), one
   // slot per iteration kind (first | confirming << 1 | timed << 2), each
@@ -183,6 +197,17 @@ struct osmpm_domain {
   bool graph_hold = false; // set while a batched call drives the domain from a worker thread
   int graph_error = 0;     // its cudaError_t
   long long graph_replays = 0;
+
+  // rigid-plane contact (osmpm_set_plane): gaps, prescribed y velocities of
+  // held nodes, multipliers per node, candidates, the active set
+  osmpm_plane plane{};
+  bool plane_on = false;
+  bool hold_in_prep = false;  // prep applies the active set as Dirichlet data
+  double *plane_gap = nullptr, *plane_hold_v = nullptr, *plane_lam = nullptr;
+  unsigned long long* plane_colmin = nullptr;
+  uint8_t *plane_cand = nullptr, *plane_act = nullptr, *mask_all = nullptr;
+  int* plane_changes = nullptr;
+  int contact_sets = 0;
 
   // optional CUDA-event timing of the PCG launches (osmpm_set_profiling)
   bool time_hvp = false;
@@ -252,9 +277,21 @@ void clear_tape(osmpm_domain* d) {
     for (auto& t : c.iters) raw_free(d, t.mem, t.bytes);
   }
   d->ctape.clear();
+  for (auto& c : d->ckpts) raw_free(d, c.mem, c.bytes);
+  d->ckpts.clear();
+  d->ctl.clear();
   d->partner = nullptr;
   d->tape_kind = 0;
   d->tape_broken = false;
+}
+
+// Frees a coupled record's per-step blocks, keeping the checkpoints.
+void clear_ctape(osmpm_domain* d) {
+  for (auto& c : d->ctape) {
+    raw_free(d, c.head.mem, c.head.bytes);
+    for (auto& t : c.iters) raw_free(d, t.mem, t.bytes);
+  }
+  d->ctape.clear();
 }
 
 void free_all(osmpm_domain* d) {
@@ -429,12 +466,15 @@ osmpm_status prep(osmpm_domain* d, double dt, bool with_rules, const uint8_t* re
   a.a_m = a_m;
   a.bc_applied = d->bc_applied;
   a.physmask = physmask;
+  a.hold = d->hold_in_prep ? d->plane_act : nullptr;
+  a.hold_v = d->plane_hold_v;
   DISPATCH(d, K::grid_prep(d->geo, d->m, d->vn, a, dt, d->dofmask, d->u, d->stream));
   return OSMPM_OK;
 }
 
 struct SolveStats {
   int newton = 0, cg = 0, ls = 0, solves = 0;
+  int contact_sets = 0;
   double last_dx = 0.0;
 };
 
@@ -466,6 +506,7 @@ PcgArgsT<R> pcg_args(osmpm_domain* d, double dt) {
   a.err = d->err;
   a.sbase = d->sbase;
   a.sdn = (const R*)d->sdn;
+  a.u = d->u;
   return a;
 }
 
@@ -507,7 +548,7 @@ template <class K, class R>
 cudaError_t stream_pcg_chunk(osmpm_domain* d, double dt, bool first) {
   const PcgArgsT<R> a = pcg_args<R>(d, dt);
   if (first) K::cgs_start(a, d->stream);
-  for (int i = 0; i < kStreamChunk; ++i) K::cgs_iteration(a, d->stream);
+  for (int i = 0; i < kStreamChunk; ++i) K::cgs_iteration(a, d->desc.hvp_mode, d->stream);
   return cudaGetLastError();
 }
 
@@ -823,6 +864,50 @@ osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
               d->desc.newton_tol, d->desc.newton_max, st.last_dx);
 }
 
+// One implicit solve with the rigid plane (the primal-dual active set of
+// the unilateral contact, osmpm_contact.cuh): gaps and the initial active
+// set from the prepared grid, then solve with the held nodes' y prescribed,
+// multipliers from the full gradient, update the set, until it no longer
+// changes.  u holds the last solve.
+osmpm_status contact_solve(osmpm_domain* d, double dt, SolveStats& st) {
+  cudaStream_t s = d->stream;
+  const int D = d->dim;
+  const int64_t nn = d->geo.nn;
+  OSMPM_TRY(prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, d->physmask));
+  CUDA_TRY(cudaMemsetAsync(d->plane_colmin, 0xFF, sizeof(unsigned long long) * d->geo.res[0], s));
+  DISPATCH(d, K::plane_colmin(P_, d->geo, d->plane.spacing, d->plane_colmin, s));
+  DISPATCH(d, K::plane_init(d->geo, d->m, d->physmask, d->plane_colmin, d->plane.level,
+                            d->plane.cand_hi, d->plane.spacing, dt, d->plane_gap, d->plane_hold_v,
+                            d->plane_cand, d->plane_act, s));
+  const int max_sets = d->plane.max_sets > 0 ? d->plane.max_sets : 50;
+  for (int set = 0; set < max_sets; ++set) {
+    d->hold_in_prep = true;
+    const osmpm_status e = prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, nullptr);
+    d->hold_in_prep = false;
+    OSMPM_TRY(e);
+    OSMPM_TRY(cold_start(d, dt));
+    OSMPM_TRY(newton_solve(d, dt, st));
+    // lambda = dE_h/du_y on the held nodes: the gradient with every active DOF free
+    CUDA_TRY(cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, s));
+    CUDA_TRY(cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, s));
+    DISPATCH(d, K::mask_all(d->geo, d->m, d->mask_all, s));
+    DISPATCH(d, K::grad(P_, d->geo, d->u, d->mask_all, d->grad, d->diag, L_, d->err, s));
+    DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->mask_all, d->desc.gravity, dt,
+                               d->desc.cg_rtol, d->desc.cg_rtol, 1, d->desc.cg_max, d->grad,
+                               d->diag, d->cx, d->cr, d->cz, d->cp, d->S, d->partials, s));
+    CUDA_TRY(cudaMemsetAsync(d->plane_changes, 0, sizeof(int), s));
+    DISPATCH(d, K::plane_update(d->geo, d->plane_cand, d->grad, d->u, d->plane_gap, d->plane_act,
+                                d->plane_lam, d->plane_changes, s));
+    int changes = 0;
+    CUDA_TRY(cudaMemcpyAsync(&changes, d->plane_changes, sizeof(int), cudaMemcpyDeviceToHost, s));
+    OSMPM_TRY(sync_scalars(d));
+    OSMPM_TRY(check_err(d));
+    st.contact_sets = set + 1;
+    if (changes == 0) return OSMPM_OK;
+  }
+  return fail(OSMPM_E_NEWTON_MAXITER, "the contact active set did not settle in %d sets", max_sets);
+}
+
 void fill_stats(osmpm_stats* out, const SolveStats& st, int schwarz_iters, int converged, double rB,
                 double rS) {
   if (!out) return;
@@ -836,6 +921,7 @@ void fill_stats(osmpm_stats* out, const SolveStats& st, int schwarz_iters, int c
   out->r_B = rB;
   out->r_S = rS;
   out->last_dx_inf = st.last_dx;
+  out->contact_sets = st.contact_sets;
 }
 
 osmpm_status ensure_keep(osmpm_domain* d, int slots) {
@@ -1042,9 +1128,10 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   if (desc->dim != 2 && desc->dim != 3) return fail(OSMPM_E_INVALID, "dim must be 2 or 3");
   if (desc->precision != 0 && desc->precision != 1)
     return fail(OSMPM_E_INVALID, "precision must be 0 (FP64) or 1 (mixed)");
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 3; ++i)
     if (desc->reserved[i] != 0) return fail(OSMPM_E_INVALID, "reserved fields must be zero");
   if (desc->pcg_mode < 0 || desc->pcg_mode > 2) return fail(OSMPM_E_INVALID, "pcg_mode must be 0, 1 or 2");
+  if (desc->hvp_mode < 0 || desc->hvp_mode > 2) return fail(OSMPM_E_INVALID, "hvp_mode must be 0, 1 or 2");
   if (desc->launch_mode != 0 && desc->launch_mode != 1)
     return fail(OSMPM_E_INVALID, "launch_mode must be 0 (graphs) or 1 (plain launches)");
   if (!(desc->cg_eta_max >= 0.0 && desc->cg_eta_max < 1.0))
@@ -1215,18 +1302,73 @@ osmpm_status osmpm_set_dirichlet(osmpm_domain* d, const osmpm_dirichlet* rules, 
   return OSMPM_OK;
 }
 
+osmpm_status osmpm_set_plane(osmpm_domain* d, const osmpm_plane* plane) {
+  OSMPM_TRY(check_domain(d));
+  if (!plane) return fail(OSMPM_E_INVALID, "null plane");
+  if (!plane->enabled) {
+    d->plane_on = false;
+    return OSMPM_OK;
+  }
+  if (d->dim != 2) return fail(OSMPM_E_UNSUPPORTED, "the rigid plane is two-dimensional");
+  if (!std::isfinite(plane->level) || !std::isfinite(plane->cand_hi) || !(plane->spacing > 0.0) ||
+      !std::isfinite(plane->spacing) || plane->max_sets < 0)
+    return fail(OSMPM_E_INVALID, "plane: finite level and cand_hi, spacing > 0, max_sets >= 0");
+  const int64_t nn = d->geo.nn;
+  if (!d->plane_gap) {
+    OSMPM_TRY(dalloc_n(d, nn, &d->plane_gap));
+    OSMPM_TRY(dalloc_n(d, nn, &d->plane_hold_v));
+    OSMPM_TRY(dalloc_n(d, nn, &d->plane_lam));
+    OSMPM_TRY(dalloc_n(d, (int64_t)d->geo.res[0], &d->plane_colmin));
+    OSMPM_TRY(dalloc_n(d, nn, &d->plane_cand));
+    OSMPM_TRY(dalloc_n(d, nn, &d->plane_act));
+    OSMPM_TRY(dalloc_n(d, nn, &d->mask_all));
+    OSMPM_TRY(dalloc_n(d, 1, &d->plane_changes));
+    CUDA_TRY(cudaMemsetAsync(d->plane_lam, 0, sizeof(double) * nn, d->stream));
+    CUDA_TRY(cudaMemsetAsync(d->plane_gap, 0, sizeof(double) * nn, d->stream));
+    CUDA_TRY(cudaMemsetAsync(d->plane_act, 0, nn, d->stream));
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+  }
+  d->plane = *plane;
+  d->plane_on = true;
+  return OSMPM_OK;
+}
+
 osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
   OSMPM_TRY(check_domain(d));
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(OSMPM_E_INVALID, "dt must be > 0");
   SolveStats st;
   osmpm_domain::TapeStep slot{};
+  bool ck_new = false, ck_ctl = false;  // a checkpoint / step controls pushed by this call
   if (d->recording) {
     if (d->tape_kind != 0 && d->tape_kind != 1) d->tape_broken = true;
     d->tape_kind = 1;
-    if (!d->tape_broken) OSMPM_TRY(tape_begin(d, slot));
+    if (!d->tape_broken && (d->ckpt_every <= 1 || d->replaying)) {
+      OSMPM_TRY(tape_begin(d, slot));
+    } else if (!d->tape_broken) {
+      // checkpointed record: the state at the start of every ckpt_every-th
+      // step, and every step's controls
+      if (d->ctl.size() % (size_t)d->ckpt_every == 0) {
+        osmpm_domain::TapeStep c{};
+        c.bytes = sizeof(double) * (2 * d->dim + 2 * d->dim * d->dim) * (size_t)d->n;
+        OSMPM_TRY(raw_alloc(d, c.bytes, &c.mem));
+        d->ckpts.push_back(c);
+        ck_new = true;
+        OSMPM_TRY(save_state(d, (char*)c.mem));
+      }
+      osmpm_domain::StepCtl c;
+      c.dt = dt;
+      c.rules = d->rules;
+      d->ctl.push_back(std::move(c));
+      ck_ctl = true;
+    }
   }
   auto drop = [&](osmpm_status e) {
     raw_free(d, slot.mem, slot.bytes);
+    if (ck_ctl) d->ctl.pop_back();
+    if (ck_new) {
+      raw_free(d, d->ckpts.back().mem, d->ckpts.back().bytes);
+      d->ckpts.pop_back();
+    }
     return e;
   };
 #define T_TRY(expr)                       \
@@ -1238,9 +1380,14 @@ osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
   T_TRY(run_p2g(d, false));
   T_TRY(sync_scalars(d));
   T_TRY(check_err(d));
-  T_TRY(prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, nullptr));
-  T_TRY(cold_start(d, dt));
-  osmpm_status s = newton_solve(d, dt, st);
+  osmpm_status s = OSMPM_OK;
+  if (d->plane_on) {
+    s = contact_solve(d, dt, st);
+  } else {
+    T_TRY(prep(d, dt, true, nullptr, nullptr, nullptr, 0.0, nullptr));
+    T_TRY(cold_start(d, dt));
+    s = newton_solve(d, dt, st);
+  }
   if (s != OSMPM_OK) {
     fill_stats(stats, st, 0, 0, 0.0, 0.0);
     return drop(s);
@@ -1263,6 +1410,8 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   if (B->dim != S->dim) return fail(OSMPM_E_INVALID, "domains differ in dim");
   if (B->stream != S->stream) return fail(OSMPM_E_INVALID, "domains must share one stream");
   if (B->prec != S->prec) return fail(OSMPM_E_INVALID, "domains differ in precision");
+  if (B->plane_on || S->plane_on)
+    return fail(OSMPM_E_UNSUPPORTED, "the rigid-plane contact serves osmpm_step only");
   if (!(B->geo.dx >= S->geo.dx)) return fail(OSMPM_E_INVALID, "coarse dx must be >= fine dx");
   if (sd->M < 1 || sd->k_max < 0 || !(sd->eps_conv > 0.0) || !(sd->eps_tol >= 0.0) ||
       std::isnan(sd->tau_B) || std::isnan(sd->tau_S) ||
@@ -1287,13 +1436,25 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
     if (B->recording) B->tape_broken = true;
     if (S->recording) S->tape_broken = true;
   }
+  // checkpointed record (the coarse domain's interval): controls of every
+  // step, both start states at every ckpt_every-th; the full record while
+  // osmpm_adjoint re-runs a segment
+  const bool ck = rec && B->ckpt_every > 1 && !B->replaying;
+  const bool rec_full = rec && !ck;
   osmpm_domain::CoupledStep cs{};
   const CoupledLayout CL(B, S, sd->M);
+  bool ck_new = false, ck_ctl = false;
   auto drop_rec = [&]() {
     raw_free(B, cs.head.mem, cs.head.bytes);
     for (auto& t : cs.iters) raw_free(B, t.mem, t.bytes);
     cs.head.mem = nullptr;
     cs.iters.clear();
+    if (ck_ctl) B->ctl.pop_back();
+    if (ck_new) {
+      raw_free(B, B->ckpts.back().mem, B->ckpts.back().bytes);
+      B->ckpts.pop_back();
+    }
+    ck_ctl = ck_new = false;
     if (rec) {
       B->tape_broken = true;
       S->tape_broken = true;
@@ -1320,12 +1481,32 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   CUDA_TRY(cudaMemsetAsync(B->err, 0, sizeof(int), s));
   CUDA_TRY(cudaMemsetAsync(S->err, 0, sizeof(int), s));
   OSMPM_TRY(snapshot(S, false));
-  OSMPM_TRY(run_p2g(B, true));
-  OSMPM_TRY(run_p2g(S, true));
-  OSMPM_TRY(sync_scalars(B));
-  OSMPM_TRY(check_err(B));
-  OSMPM_TRY(sync_scalars(S));
-  OSMPM_TRY(check_err(S));
+  if (ck) {
+    if (B->ctl.size() % (size_t)B->ckpt_every == 0) {
+      const size_t sb = sizeof(double) * (2 * D + 2 * D * D) * (size_t)B->n;
+      const size_t ss = sizeof(double) * (2 * D + 2 * D * D) * (size_t)S->n;
+      osmpm_domain::TapeStep c{};
+      c.bytes = sb + ss;
+      S_TRY(raw_alloc(B, c.bytes, &c.mem));
+      B->ckpts.push_back(c);
+      ck_new = true;
+      S_TRY(save_state(B, (char*)c.mem));
+      S_TRY(save_state(S, (char*)c.mem + sb));
+    }
+    osmpm_domain::StepCtl c;
+    c.dt = dT;
+    c.sd = *sd;
+    c.rules = B->rules;
+    c.rules_fine = S->rules;
+    B->ctl.push_back(std::move(c));
+    ck_ctl = true;
+  }
+  S_TRY(run_p2g(B, true));
+  S_TRY(run_p2g(S, true));
+  S_TRY(sync_scalars(B));
+  S_TRY(check_err(B));
+  S_TRY(sync_scalars(S));
+  S_TRY(check_err(S));
   // physical Dirichlet masks of both grids
   S_TRY(prep(B, dT, true, nullptr, nullptr, nullptr, 0.0, B->physmask));
   S_TRY(prep(S, dt, true, nullptr, nullptr, nullptr, 0.0, S->physmask));
@@ -1343,7 +1524,7 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   DISPATCH(B, K::proj_finish(gB, B->recv, B->proj_num, B->proj_den, sd->eps_tol, B->bc0, s));
   DISPATCH(B, K::interp(gB, gS, B->vn, S->recv, S->bc0, s));
   CUDA_TRY(cudaMemcpyAsync(S->bc_prev, S->bc0, sizeof(double) * D * gS.nn, cudaMemcpyDeviceToDevice, s));
-  if (rec) {
+  if (rec_full) {
     S_TRY(raw_alloc(B, CL.head_bytes, &cs.head.mem));
     cs.head.bytes = CL.head_bytes;
     cs.M = M;
@@ -1376,7 +1557,7 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
     S_TRY(newton_solve(B, dT, st));
     CUDA_TRY(cudaMemcpyAsync(keep_slot(B, 0), B->u, bytesB, cudaMemcpyDeviceToDevice, s));
     char* ib = nullptr;
-    if (rec) {
+    if (rec_full) {
       osmpm_domain::TapeStep it{};
       S_TRY(raw_alloc(B, CL.iter_bytes, &it.mem));
       it.bytes = CL.iter_bytes;
@@ -1447,7 +1628,7 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   // 4. post-convergence coarse update (Sec. 3.5)
   DISPATCH(B, K::g2p(P_, gB, B->u, dT, s));
   if (rec) {
-    B->ctape.push_back(cs);
+    if (rec_full) B->ctape.push_back(cs);
     B->tape_kind = 2;
     B->partner = S;
     S->tape_kind = 3;
@@ -1494,11 +1675,13 @@ osmpm_status osmpm_get_counters(const osmpm_domain* d, osmpm_counters* out) {
 
 osmpm_status osmpm_record(osmpm_domain* d, int32_t enable) {
   OSMPM_TRY(check_domain(d));
+  if (enable < 0) return fail(OSMPM_E_INVALID, "enable must be >= 0");
   if (enable && d->prec != 0)
     return fail(OSMPM_E_UNSUPPORTED, "reverse mode needs a precision 0 (FP64) domain");
   CUDA_TRY(cudaStreamSynchronize(d->stream));
   clear_tape(d);
   d->recording = enable != 0;
+  d->ckpt_every = enable > 1 ? enable : 1;
   return OSMPM_OK;
 }
 
@@ -1530,8 +1713,10 @@ static osmpm_status coupled_adjoint(osmpm_domain* B, osmpm_domain* S, const doub
     return fail(OSMPM_E_UNSUPPORTED, "reverse mode needs precision 0 (FP64) domains");
   if (B->tape_broken || S->tape_broken)
     return fail(OSMPM_E_INVALID, "the record was interrupted");
-  if (B->ctape.empty() || B->tape_kind != 2 || B->partner != S || S->partner != B)
+  if ((B->ctape.empty() && B->ctl.empty()) || B->tape_kind != 2 || B->partner != S ||
+      S->partner != B)
     return fail(OSMPM_E_INVALID, "no coupled steps of this pair recorded");
+  const bool ck = !B->ctl.empty();  // checkpointed record: re-run each segment
   const int D = B->dim, DD = D * D;
   const int64_t nB = B->n, nS = S->n, nnB = B->geo.nn, nnS = S->geo.nn;
   const GridGeo &gB = B->geo, &gS = S->geo;
@@ -1587,8 +1772,12 @@ static osmpm_status coupled_adjoint(osmpm_domain* B, osmpm_domain* S, const doub
   CUDA_TRY(cudaMemsetAsync(sb.E, 0, sizeof(double) * nS, s));
   ADJ(B, AK::from_ids(nB, D, B->P.id, dJ_dx, bb.x, s));
   ADJ(S, AK::from_ids(nS, D, S->P.id, dJ_dx + (int64_t)D * nB, sb.x, s));
-  OSMPM_TRY(snapshot(B, false));
-  OSMPM_TRY(snapshot(S, false));
+  // the states after the last recorded step, kept aside (a re-run segment
+  // moves the particles and uses the fine snapshot)
+  void* keep = nullptr;
+  OSMPM_TRY(raw_alloc(B, stateB + stateS, &keep));
+  OSMPM_TRY(save_state(B, (char*)keep));
+  OSMPM_TRY(save_state(S, (char*)keep + stateB));
   osmpm_status status = OSMPM_OK;
   // one solve's adjoint on domain d with u, dofmask in place and u_bar in
   // its ubar: lam in d->cx, particle terms into (xacc, Facc, E), K lam on
@@ -1607,6 +1796,8 @@ static osmpm_status coupled_adjoint(osmpm_domain* B, osmpm_domain* S, const doub
                      d->u, d->cx, d->dofmask, xacc, Facc, b.E, b.klam, d->err, s));
     return OSMPM_OK;
   };
+  // the recorded steps of B->ctape, last to first
+  auto reverse_record = [&]() -> osmpm_status {
   for (size_t step = B->ctape.size(); step-- > 0 && status == OSMPM_OK;) {
     const auto& cst = B->ctape[step];
     const int M = cst.M;
@@ -1726,7 +1917,40 @@ static osmpm_status coupled_adjoint(osmpm_domain* B, osmpm_domain* S, const doub
     CUDA_TRY(cudaMemcpyAsync(bb.x, bb.ax, stateB, cudaMemcpyDeviceToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(sb.x, sb.ax, stateS, cudaMemcpyDeviceToDevice, s));
   }
-  const osmpm_status rB = snapshot(B, true), rS = snapshot(S, true);
+  return status;
+  };
+  if (!ck) {
+    status = reverse_record();
+  } else {
+    // segments last to first: from the segment's checkpoint, re-run its
+    // steps with the full record (the recorded controls and rule sets), then
+    // reverse them
+    const std::vector<osmpm_dirichlet> rulesB = B->rules, rulesS = S->rules;
+    B->replaying = S->replaying = true;
+    const size_t every = (size_t)B->ckpt_every, nsteps = B->ctl.size();
+    for (size_t seg = B->ckpts.size(); seg-- > 0 && status == OSMPM_OK;) {
+      const char* c = (const char*)B->ckpts[seg].mem;
+      status = load_state(B, c);
+      if (status == OSMPM_OK) status = load_state(S, c + stateB);
+      for (size_t j = seg * every; j < std::min(nsteps, (seg + 1) * every) && status == OSMPM_OK;
+           ++j) {
+        const auto& cj = B->ctl[j];
+        B->rules = cj.rules;
+        S->rules = cj.rules_fine;
+        const osmpm_status f = osmpm_schwarz_couple(B, S, cj.dt, &cj.sd, nullptr);
+        if (f != OSMPM_OK && f != OSMPM_W_SCHWARZ_MAXITER) status = f;
+      }
+      if (status == OSMPM_OK) status = reverse_record();
+      clear_ctape(B);
+    }
+    B->replaying = S->replaying = false;
+    B->rules = rulesB;
+    S->rules = rulesS;
+  }
+  const osmpm_status rB = load_state(B, (const char*)keep);
+  const osmpm_status rS = load_state(S, (const char*)keep + stateB);
+  cudaStreamSynchronize(s);
+  raw_free(B, keep, stateB + stateS);
   if (status != OSMPM_OK) return status;
   OSMPM_TRY(rB);
   OSMPM_TRY(rS);
@@ -1762,7 +1986,9 @@ osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const doubl
   if (d->prec != 0) return fail(OSMPM_E_UNSUPPORTED, "reverse mode needs a precision 0 (FP64) domain");
   if (d->tape_broken)
     return fail(OSMPM_E_INVALID, "the tape was interrupted (a coupled step or set_particles while recording)");
-  if (d->tape.empty()) return fail(OSMPM_E_INVALID, "nothing recorded (osmpm_record, then osmpm_step)");
+  if (d->tape.empty() && d->ctl.empty())
+    return fail(OSMPM_E_INVALID, "nothing recorded (osmpm_record, then osmpm_step)");
+  const bool ck = !d->ctl.empty();  // checkpointed record: re-run each segment
   const int D = d->dim, DD = D * D;
   const int64_t n = d->n, nn = d->geo.nn;
   cudaStream_t s = d->stream;
@@ -1785,9 +2011,14 @@ osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const doubl
   CUDA_TRY(cudaMemsetAsync(Eb, 0, sizeof(double) * n, s));
   ADJ(d, AK::from_ids(n, D, d->P.id, dJ_dx, xb, s));
   // the state after the last recorded step comes back at the end
-  OSMPM_TRY(snapshot(d, false));
+  const size_t state_bytes = sizeof(double) * (2 * D + 2 * DD) * (size_t)n;
+  void* keep = nullptr;
+  OSMPM_TRY(raw_alloc(d, state_bytes, &keep));
+  OSMPM_TRY(save_state(d, (char*)keep));
   const TapeLayout TL(d);
   osmpm_status status = OSMPM_OK;
+  // the recorded steps of d->tape, last to first
+  auto reverse_tape = [&]() -> osmpm_status {
   for (size_t k = d->tape.size(); k-- > 0 && status == OSMPM_OK;) {
     const auto& t = d->tape[k];
     const char* b = (const char*)t.mem;
@@ -1826,7 +2057,33 @@ osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const doubl
     std::swap(Bb, Bb2);
     std::swap(Fb, Fb2);
   }
-  const osmpm_status restored = snapshot(d, true);
+  return status;
+  };
+  if (!ck) {
+    status = reverse_tape();
+  } else {
+    // segments last to first: re-run each from its checkpoint with the full
+    // record (the recorded step sizes and rule sets), then reverse it
+    const std::vector<osmpm_dirichlet> rules0 = d->rules;
+    d->replaying = true;
+    const size_t every = (size_t)d->ckpt_every, nsteps = d->ctl.size();
+    for (size_t seg = d->ckpts.size(); seg-- > 0 && status == OSMPM_OK;) {
+      status = load_state(d, (const char*)d->ckpts[seg].mem);
+      for (size_t j = seg * every; j < std::min(nsteps, (seg + 1) * every) && status == OSMPM_OK;
+           ++j) {
+        d->rules = d->ctl[j].rules;
+        status = osmpm_step(d, d->ctl[j].dt, nullptr);
+      }
+      if (status == OSMPM_OK) status = reverse_tape();
+      for (auto& t : d->tape) raw_free(d, t.mem, t.bytes);
+      d->tape.clear();
+    }
+    d->replaying = false;
+    d->rules = rules0;
+  }
+  const osmpm_status restored = load_state(d, (const char*)keep);
+  cudaStreamSynchronize(s);
+  raw_free(d, keep, state_bytes);
   if (status != OSMPM_OK) return status;
   OSMPM_TRY(restored);
   ADJ(d, AK::to_ids(n, 1, d->P.id, Eb, out->dJ_dE, s));
@@ -2037,6 +2294,18 @@ osmpm_status osmpm_get_grid(const osmpm_domain* dc, int32_t field, double* out) 
       return download_grid_vec(d, d->u, out, D);
     case OSMPM_FIELD_BC:
       return download_grid_vec(d, d->bc_applied, out, D);
+    case OSMPM_FIELD_PLANE_FORCE:
+    case OSMPM_FIELD_PLANE_GAP:
+    case OSMPM_FIELD_PLANE_ACTIVE: {
+      if (!d->plane_gap) return fail(OSMPM_E_INVALID, "no rigid plane was set on this domain");
+      if (field == OSMPM_FIELD_PLANE_FORCE) return download_grid_vec(d, d->plane_lam, out, 1);
+      if (field == OSMPM_FIELD_PLANE_GAP) return download_grid_vec(d, d->plane_gap, out, 1);
+      std::vector<uint8_t> tmp((size_t)nn);
+      CUDA_TRY(cudaMemcpyAsync(tmp.data(), d->plane_act, nn, cudaMemcpyDeviceToHost, d->stream));
+      CUDA_TRY(cudaStreamSynchronize(d->stream));
+      for (int64_t i = 0; i < nn; ++i) out[i] = tmp[(size_t)i] ? 1.0 : 0.0;
+      return OSMPM_OK;
+    }
     case OSMPM_FIELD_RECEIVER: {
       std::vector<uint8_t> tmp((size_t)nn);
       CUDA_TRY(cudaMemcpyAsync(tmp.data(), d->recv, nn, cudaMemcpyDeviceToHost, d->stream));
@@ -2077,8 +2346,16 @@ osmpm_status osmpm_probe_hvp(osmpm_domain* d, double dt, const double* u, const 
   DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
   OSMPM_TRY(upload_grid_vec(d, dv, d->cp));
   DISPATCH(d, K::set_cg_state(d->S, 0, 0, d->stream));
-  DISPATCH(d, K::hvp_only(P_, d->geo, d->m, d->dofmask, L_, dt, d->cp, d->cq, d->S,
-                          d->partials, d->stream));
+  if (d->desc.pcg_mode == 2) {
+    // the streaming PCG's own product (lane groups, or block tiles in mixed
+    // precision): the mass part, then the particle part added to it
+    DISPATCH(d, K::cg_a(d->geo, d->m, d->dofmask, dt, d->cp, d->cp, d->cq, d->S, d->partials,
+                        d->stream));
+    DISPATCH(d, K::cgs_hvp(pcg_args<R>(d, dt), d->desc.hvp_mode, d->stream));
+  } else {
+    DISPATCH(d, K::hvp_only(P_, d->geo, d->m, d->dofmask, L_, dt, d->cp, d->cq, d->S,
+                            d->partials, d->stream));
+  }
   OSMPM_TRY(sync_scalars(d));
   OSMPM_TRY(check_err(d));
   return download_grid_vec(d, d->cq, hd, D);

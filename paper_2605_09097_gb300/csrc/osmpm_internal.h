@@ -36,7 +36,9 @@ struct PrepArgs {
   const double* bc1;    // receiver velocity at the end of the window
   double a_m;           // temporal weight: v = (1 - a_m) bc0 + a_m bc1
   double* bc_applied;   // receiver velocity applied (written), may be null
-  uint8_t* physmask;    // 1 where a physical rule fixes a component (written), may be null
+  uint8_t* physmask;    // the components a physical rule fixes, bit a (written), may be null
+  const uint8_t* hold;  // rigid-plane contact: nodes whose y component is held, or nullptr
+  const double* hold_v; // their prescribed y velocity
 };
 
 // Launchers of the reverse-mode kernels (FP64 only; osmpm_adjoint.cuh).
@@ -134,7 +136,12 @@ struct Kernels {
   static int64_t pcg_passes(const PcgArgsT<R>& a, int blocks, int threads);
   // streaming PCG: start, then per iteration hvp, alpha, beta
   static void cgs_start(const PcgArgsT<R>& a, cudaStream_t s);
-  static void cgs_iteration(const PcgArgsT<R>& a, cudaStream_t s);
+  // hvp_mode (mixed precision only): 1 lane groups over the cached stencil
+  // and Hessian blocks, otherwise block tiles recomputing the Hessian
+  static void cgs_iteration(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s);
+  // the streaming PCG's particle product alone: a.w[0] += K a.s[0] on the
+  // free DOFs, p.Kp into S->pq
+  static void cgs_hvp(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s);
   static void hvp_only(const PartPtrsT<R>& P, const GridGeo& g, const double* m,
                        const uint8_t* dofmask, const R* L, double dt, double* p, double* q,
                        DevScalars* S, double* partials, cudaStream_t s);
@@ -181,6 +188,17 @@ struct Kernels {
                           cudaStream_t s);
   static void set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s);
   static void barrier_timeout_check(unsigned* words, int* err, cudaStream_t s);
+  // rigid-plane contact (2D; osmpm_contact.cuh)
+  static void plane_colmin(const PartPtrsT<R>& P, const GridGeo& g, double spacing,
+                           unsigned long long* colmin, cudaStream_t s);
+  static void plane_init(const GridGeo& g, const double* m, const uint8_t* physmask,
+                         const unsigned long long* colmin, double level, double cand_hi,
+                         double spacing, double dt, double* gap, double* hold_v, uint8_t* cand,
+                         uint8_t* act, cudaStream_t s);
+  static void mask_all(const GridGeo& g, const double* m, uint8_t* mask, cudaStream_t s);
+  static void plane_update(const GridGeo& g, const uint8_t* cand, const double* grad,
+                           const double* u, const double* gap, uint8_t* act, double* lam,
+                           int* changes, cudaStream_t s);
 };
 
 // Records the message returned by osmpm_last_error() and returns st.

@@ -9,6 +9,8 @@
 #include "osmpm_device.cuh"
 #include "osmpm_internal.h"
 #include "osmpm_pcg.cuh"
+#include "osmpm_tile.cuh"
+#include "osmpm_contact.cuh"
 
 namespace osmpm {
 
@@ -294,7 +296,11 @@ __global__ void k_grid_prep(GridGeo g, const double* m, const double* vn, PrepAr
         fixed = all;
       }
     }
-    if (A.physmask) A.physmask[i] = fixed != 0u ? 1 : 0;
+    if (A.physmask) A.physmask[i] = (uint8_t)fixed;
+    if (A.hold && A.hold[i]) {  // rigid-plane contact: the held normal component
+      fixed |= 2u;
+      vel[1] = A.hold_v[i];
+    }
     if (A.recv && A.recv[i] && fixed == 0u) {
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -615,7 +621,8 @@ __global__ void k_maxabs(GridGeo g, const uint8_t* dofmask, const double* x, Dev
 // E_h(u + alpha x) - E_h(u) summed term by term (the line-search test of
 // Sec. 2.2.5): per particle V0 (Psi(F(u + alpha x)) - Psi(F(u))), per node
 // m/(2dt^2) s.(2(u - dt v^n) + s) - s.f_ext with s = alpha x.  +inf when a
-// trial inverts an element.
+// trial inverts an element; NaN, with kErrOutOfGrid in S->err, when a
+// particle's support leaves the grid box.
 template <int D, typename R>
 __global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrsT<R> P, GridGeo g, const double* m,
                                                             const double* vn, const double* u,
@@ -629,7 +636,13 @@ __global__ void __launch_bounds__(kThreads) k_energy_change(PartPtrsT<R> P, Grid
     load_x<D>(P, pi, xp);
     load_F<D>(P, pi, Fn);
     Stencil<D> s;
-    make_stencil<D>(xp, g, s);
+    if (!make_stencil<D>(xp, g, s)) {
+      // a support leaving the grid box has no energy term: the sum becomes
+      // NaN and the scalars' error word says why
+      atomicOr(&S->err, kErrOutOfGrid);
+      acc[0] += NAN;
+      continue;
+    }
     gather_grad<D>(s, g, u, Gu);
     gather_grad<D>(s, g, x, Gs);
     deform<D>(Gu, Fn, F0);
@@ -980,7 +993,10 @@ void Kernels<D, R>::unpack_in(const double* x, const double* v, const double* B,
 template <int D, typename R>
 void Kernels<D, R>::p2g(const PartPtrsT<R>& P, const GridGeo& g, double* m, double* mv, double* bm,
                      int* err, int* sbase, R* sdn, cudaStream_t s) {
-  k_p2g<D, R><<<OSMPM_NB(P.n)>>>(P, g, m, mv, bm, err, sbase, sdn);
+  const int64_t tiles = (P.n + TileCap<D>::THREADS - 1) / TileCap<D>::THREADS;
+  g_launch_count += 1;
+  k_p2g_tile<D, R><<<(int)std::min<int64_t>(std::max<int64_t>(tiles, 1), 4096), TileCap<D>::THREADS,
+                     0, s>>>(P, g, m, mv, bm, err, sbase, sdn);
 }
 template <int D, typename R>
 void Kernels<D, R>::normalize(const GridGeo& g, const double* m, const double* mv, double* vn,
@@ -1217,13 +1233,52 @@ void Kernels<D, R>::cgs_start(const PcgArgsT<R>& a, cudaStream_t s) {
   k_cgs_start<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
 }
 template <int D, typename R>
-void Kernels<D, R>::cgs_iteration(const PcgArgsT<R>& a, cudaStream_t s) {
-  const int64_t lanes = (a.P.n + HvpGroup<D>::GP - 1) / HvpGroup<D>::GP * 32;
-  k_cgs_hvp<D, R><<<OSMPM_RB(lanes)>>>(a);
+void Kernels<D, R>::cgs_iteration(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s) {
+  cgs_hvp(a, hvp_mode, s);
   k_cgs_alpha<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
   k_cgs_beta<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
 }
+template <int D, typename R>
+void Kernels<D, R>::cgs_hvp(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s) {
+  bool tiled = false;
+  if constexpr (std::is_same<R, float>::value) {
+    if (hvp_mode != 1) {
+      const int64_t tiles = (a.P.n + TileCap<D>::THREADS - 1) / TileCap<D>::THREADS;
+      const int blocks = (int)std::min<int64_t>(std::max<int64_t>(tiles, 1), kRedBlocksMax);
+      g_launch_count += 1;
+      k_cgs_hvp_tile<D><<<blocks, TileCap<D>::THREADS, 0, s>>>(a);
+      tiled = true;
+    }
+  }
+  if (!tiled) {
+    const int64_t lanes = (a.P.n + HvpGroup<D>::GP - 1) / HvpGroup<D>::GP * 32;
+    k_cgs_hvp<D, R><<<OSMPM_RB(lanes)>>>(a);
+  }
+}
 
+template <int D, typename R>
+void Kernels<D, R>::plane_colmin(const PartPtrsT<R>& P, const GridGeo& g, double spacing,
+                                 unsigned long long* colmin, cudaStream_t s) {
+  k_plane_colmin<D, R><<<OSMPM_NB(P.n)>>>(P, g, spacing, colmin);
+}
+template <int D, typename R>
+void Kernels<D, R>::plane_init(const GridGeo& g, const double* m, const uint8_t* physmask,
+                               const unsigned long long* colmin, double level, double cand_hi,
+                               double spacing, double dt, double* gap, double* hold_v,
+                               uint8_t* cand, uint8_t* act, cudaStream_t s) {
+  k_plane_init<D, R><<<OSMPM_RB(g.nn)>>>(g, m, physmask, colmin, level, cand_hi, spacing, dt, gap,
+                                         hold_v, cand, act);
+}
+template <int D, typename R>
+void Kernels<D, R>::mask_all(const GridGeo& g, const double* m, uint8_t* mask, cudaStream_t s) {
+  k_mask_all<D, R><<<OSMPM_RB(g.nn)>>>(g, m, mask);
+}
+template <int D, typename R>
+void Kernels<D, R>::plane_update(const GridGeo& g, const uint8_t* cand, const double* grad,
+                                 const double* u, const double* gap, uint8_t* act, double* lam,
+                                 int* changes, cudaStream_t s) {
+  k_plane_update<D, R><<<OSMPM_RB(g.nn)>>>(g, cand, grad, u, gap, act, lam, changes);
+}
 template <int D, typename R>
 void Kernels<D, R>::barrier_timeout_check(unsigned* words, int* err, cudaStream_t s) {
   g_launch_count += 1;

@@ -1,0 +1,624 @@
+// Block-tiled particle kernels: each block takes a run of Morton-sorted
+// particles, finds the bounding box of their stencils (a few hundred grid
+// nodes) and stages that box of the grid in shared memory.  Gathers then read
+// shared memory, and the scatter accumulates into a shared tile that is
+// flushed with one global atomic per (tile node, component) instead of one
+// per (particle, stencil node, component).  A block whose box is larger than
+// the tile capacity (a Morton run that jumps across a high-level boundary)
+// works on global memory directly, with the same arithmetic.
+//
+// Included by osmpm_kernels.cuh.
+#pragma once
+
+#include <climits>
+
+#include "osmpm_device.cuh"
+
+namespace osmpm {
+
+// Shared tile capacity in nodes, per dimension.
+template <int D>
+struct TileCap {
+  static constexpr int NODES = 1024;
+  static constexpr int THREADS = (D == 2) ? 256 : 128;  // one particle per thread
+};
+
+// Geometry of one block's tile: the box [lo, lo + ext) of grid nodes.
+template <int D>
+struct TileBox {
+  int lo[3];
+  int ext[3];
+  int nodes;  // ext product, or 0 when the box exceeds the capacity
+};
+
+// Flat index of a tile-local node (x fastest).
+template <int D>
+__device__ __forceinline__ int tile_local(const TileBox<D>& t, int i0, int i1, int i2) {
+  if constexpr (D == 2) return i0 + t.ext[0] * i1;
+  return i0 + t.ext[0] * (i1 + t.ext[1] * i2);
+}
+
+// Global flat node index of tile-local node `l`.
+template <int D>
+__device__ __forceinline__ int64_t tile_global(const TileBox<D>& t, const GridGeo& g, int l) {
+  const int i0 = l % t.ext[0];
+  const int r = l / t.ext[0];
+  if constexpr (D == 2) return (int64_t)(t.lo[0] + i0) + (int64_t)g.res[0] * (t.lo[1] + r);
+  const int i1 = r % t.ext[1];
+  const int i2 = r / t.ext[1];
+  return (int64_t)(t.lo[0] + i0) +
+         (int64_t)g.res[0] * ((int64_t)(t.lo[1] + i1) + (int64_t)g.res[1] * (t.lo[2] + i2));
+}
+
+// The block's tile box from its particles' base nodes (valid lanes only);
+// every thread gets the same box in `out` (shared).  nodes = 0 when the box
+// needs more than `cap` nodes or the block has no valid particle.
+template <int D>
+__device__ __forceinline__ void tile_box(const int (&base)[D], bool valid, int cap,
+                                         TileBox<D>& out) {
+  __shared__ int smin[3][32], smax[3][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    int mn = valid ? base[a] : INT_MAX;
+    int mx = valid ? base[a] : INT_MIN;
+    mn = __reduce_min_sync(kFull, mn);
+    mx = __reduce_max_sync(kFull, mx);
+    if (lane == 0) {
+      smin[a][warp] = mn;
+      smax[a][warp] = mx;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long nodes = 1;
+    bool any = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      int mn = INT_MAX, mx = INT_MIN;
+      for (int w = 0; w < nw; ++w) {
+        mn = min(mn, smin[a][w]);
+        mx = max(mx, smax[a][w]);
+      }
+      any = any && (mx >= mn);
+      out.lo[a] = mn;
+      out.ext[a] = any ? mx - mn + 3 : 0;
+      nodes *= any ? (long long)(mx - mn + 3) : 0ll;
+    }
+    for (int a = D; a < 3; ++a) {
+      out.lo[a] = 0;
+      out.ext[a] = 1;
+    }
+    out.nodes = (any && nodes <= cap) ? (int)nodes : 0;
+  }
+  __syncthreads();
+}
+
+// Quadratic B-spline weights of one particle in FP32 (the stencil base in
+// FP64, exactly as make_stencil forms it), and its base node.  Returns false
+// when the support leaves the grid box.
+template <int D>
+__device__ __forceinline__ bool stencil_f32(const double* xp, const GridGeo& g, int (&base)[D],
+                                            float (&w)[D][3], float (&dw)[D][3]) {
+  bool ok = true;
+  const float inv_dx = (float)g.inv_dx;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const double t = __dmul_rn(__dsub_rn(xp[a], g.o[a]), g.inv_dx);
+    const double b = floor(__dsub_rn(t, 0.5));
+    ok = ok && (b >= 0.0) && (b + 2.0 < (double)g.res[a]);
+    base[a] = ok ? (int)b : 0;
+    const float fx = (float)(t - b);
+    const float e0 = 1.5f - fx, e1 = fx - 1.0f, e2 = fx - 0.5f;
+    w[a][0] = 0.5f * e0 * e0;
+    w[a][1] = 0.75f - e1 * e1;
+    w[a][2] = 0.5f * e2 * e2;
+    dw[a][0] = -e0 * inv_dx;
+    dw[a][1] = -2.0f * e1 * inv_dx;
+    dw[a][2] = e2 * inv_dx;
+  }
+  return ok;
+}
+
+// grad N of stencil node k (offsets x fastest) from the 1D weights.
+template <int D>
+__device__ __forceinline__ void grad_n_f32(const float (&w)[D][3], const float (&dw)[D][3], int k,
+                                           float (&dN)[D]) {
+  const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+  if constexpr (D == 2) {
+    dN[0] = dw[0][o0] * w[1][o1];
+    dN[1] = w[0][o0] * dw[1][o1];
+  } else {
+    dN[0] = dw[0][o0] * w[1][o1] * w[2][o2];
+    dN[1] = w[0][o0] * dw[1][o1] * w[2][o2];
+    dN[2] = w[0][o0] * w[1][o1] * dw[2][o2];
+  }
+}
+
+// The neo-Hookean Hessian applied to one particle in FP32, recomputed from
+// the current Newton iterate: F_hat = (I + G_u) F^n, dF = G_d F^n and
+// Y = V0 dP[F_hat; dF] F^nT with
+//   dP[dF] = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
+// (the same operator as the cached block L(G) = V0 dP[G F^n] F^nT of the
+// gradient kernel).  Returns G_d : Y, the particle's share of d.Kd.
+template <int D>
+__device__ __forceinline__ float hessian_apply_f32(const float (&Gu)[D * D], const float (&Gd)[D * D],
+                                                   const float (&Fn)[D * D], float mu, float lam,
+                                                   float V0, float (&Y)[D * D]) {
+  constexpr int DD = D * D;
+  float Fh[DD], dF[DD];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      float t = Fn[a * D + b], s = 0.0f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        t = fmaf(Gu[a * D + c], Fn[c * D + b], t);
+        s = fmaf(Gd[a * D + c], Fn[c * D + b], s);
+      }
+      Fh[a * D + b] = t;
+      dF[a * D + b] = s;
+    }
+  // J - 1 expanded in H = F_hat - I (no cancellation near J = 1), F^-T
+  float H[DD];
+#pragma unroll
+  for (int i = 0; i < DD; ++i) H[i] = Fh[i] - ((i % (D + 1)) == 0 ? 1.0f : 0.0f);
+  float jm1;
+  float A[DD];  // F^-T
+  if constexpr (D == 2) {
+    jm1 = (H[0] + H[3]) + (H[0] * H[3] - H[1] * H[2]);
+    const float rJ = 1.0f / (1.0f + jm1);
+    A[0] = Fh[3] * rJ;
+    A[1] = -Fh[2] * rJ;
+    A[2] = -Fh[1] * rJ;
+    A[3] = Fh[0] * rJ;
+  } else {
+    const float trH = H[0] + H[4] + H[8];
+    const float m2 = (H[0] * H[4] - H[1] * H[3]) + (H[0] * H[8] - H[2] * H[6]) +
+                     (H[4] * H[8] - H[5] * H[7]);
+    const float dH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                     H[2] * (H[3] * H[7] - H[4] * H[6]);
+    jm1 = trH + m2 + dH;
+    const float rJ = 1.0f / (1.0f + jm1);
+    A[0] = (Fh[4] * Fh[8] - Fh[5] * Fh[7]) * rJ;
+    A[1] = (Fh[5] * Fh[6] - Fh[3] * Fh[8]) * rJ;
+    A[2] = (Fh[3] * Fh[7] - Fh[4] * Fh[6]) * rJ;
+    A[3] = (Fh[2] * Fh[7] - Fh[1] * Fh[8]) * rJ;
+    A[4] = (Fh[0] * Fh[8] - Fh[2] * Fh[6]) * rJ;
+    A[5] = (Fh[1] * Fh[6] - Fh[0] * Fh[7]) * rJ;
+    A[6] = (Fh[1] * Fh[5] - Fh[2] * Fh[4]) * rJ;
+    A[7] = (Fh[2] * Fh[3] - Fh[0] * Fh[5]) * rJ;
+    A[8] = (Fh[0] * Fh[4] - Fh[1] * Fh[3]) * rJ;
+  }
+  const float lnJ = log1pf(jm1);
+  float tr = 0.0f;
+#pragma unroll
+  for (int i = 0; i < DD; ++i) tr = fmaf(A[i], dF[i], tr);
+  const float c1 = mu - lam * lnJ, c2 = lam * tr;
+  // B = dF^T A, then (A dF^T A)_ac = sum_e A_ae B_ec
+  float Bm[DD];
+#pragma unroll
+  for (int e = 0; e < D; ++e)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float t = 0.0f;
+#pragma unroll
+      for (int f = 0; f < D; ++f) t = fmaf(dF[f * D + e], A[f * D + c], t);
+      Bm[e * D + c] = t;
+    }
+  float dP[DD];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float t = 0.0f;
+#pragma unroll
+      for (int e = 0; e < D; ++e) t = fmaf(A[a * D + e], Bm[e * D + c], t);
+      dP[a * D + c] = mu * dF[a * D + c] + c1 * t + c2 * A[a * D + c];
+    }
+  float qf = 0.0f;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      float t = 0.0f;
+#pragma unroll
+      for (int b = 0; b < D; ++b) t = fmaf(dP[a * D + b], Fn[c * D + b], t);
+      Y[a * D + c] = V0 * t;
+      qf = fmaf(Gd[a * D + c], Y[a * D + c], qf);
+    }
+  return qf;
+}
+
+// Reduce-scatter over an aligned group of L lanes (L a power of two, NV a
+// multiple of L): afterwards lane r of the group holds, in v[0 .. NV/L), the
+// group's sums of the values r NV/L .. (r + 1) NV/L - 1.  Recursive halving:
+// at distance h a lane keeps the half of its current segment selected by
+// (r & h), sends the other half to lane r ^ h and adds what it receives.
+template <int L, int NV>
+__device__ __forceinline__ void group_reduce_scatter(float (&v)[NV], int r) {
+  static_assert(NV % L == 0, "NV must be a multiple of L");
+#pragma unroll
+  for (int h = L / 2, seg = NV; h >= 1; h >>= 1, seg >>= 1) {
+    const bool upper = (r & h) != 0;
+#pragma unroll
+    for (int i = 0; i < seg / 2; ++i) {
+      const float send = upper ? v[i] : v[i + seg / 2];
+      const float keep = upper ? v[i + seg / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, h);
+    }
+  }
+}
+
+// Streaming-PCG Hessian-vector product, mixed precision, block tiles:
+// q = K p on the free DOFs (q = a.w[0], zeroed by the start and beta
+// kernels; p = a.s[0]) and p:Kp = sum_p G:Y into S->pq.  The particle
+// Hessian is recomputed from the Newton iterate a.u (no cached blocks or
+// stencils): per particle it reads x, F^n, V0, mu, lam.  Blocks loop over
+// the particle tiles (grid stride), so the launch may be smaller than the
+// tile count.
+template <int D>
+__global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<float> a) {
+  if (__ldcg(&a.S->cg_done)) return;
+  constexpr int DD = D * D;
+  constexpr int K = (D == 2) ? 9 : 27;
+  constexpr int CAP = TileCap<D>::NODES;
+  __shared__ float su[D][CAP];   // Newton iterate u
+  __shared__ float sd[D][CAP];   // direction p
+  __shared__ float sq[D][CAP];   // K p accumulators
+  __shared__ TileBox<D> box;
+  constexpr int GL = 1 << D;                 // particles per full cell (2 per axis)
+  constexpr int KC = 9;                      // stencil nodes per scatter chunk
+  constexpr int NVP = ((KC * D + GL - 1) / GL) * GL;
+  const GridGeo& g = a.g;
+  const int64_t n = a.P.n;
+  const double* pv = a.s[0];
+  double* q = a.w[0];
+  const int lane = threadIdx.x & 31, gr = lane & (GL - 1);
+  double acc[1] = {0.0};
+  const int64_t tiles = (n + blockDim.x - 1) / blockDim.x;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t pi = t * blockDim.x + threadIdx.x;
+    const bool in = pi < n;
+    double xp[D];
+    int base[D];
+    float w[D][3], dw[D][3];
+    bool valid = false;
+    if (in) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) xp[c] = a.P.x[c * n + pi];
+      valid = stencil_f32<D>(xp, g, base, w, dw);
+    } else {
+#pragma unroll
+      for (int c = 0; c < D; ++c) base[c] = 0;
+    }
+    tile_box<D>(base, valid, CAP, box);
+    const bool tiled = box.nodes > 0;
+    // a warp whose lanes form aligned groups of GL = 2^D particles with one
+    // stencil base per group (full cells of 2^D particles, Morton-sorted)
+    // scatters through the group reduce-scatter
+    bool grouped = false;
+    if (tiled) {
+      int key = -1 - lane;
+      if (valid) key = tile_local<D>(box, base[0] - box.lo[0], base[1] - box.lo[1],
+                                     base[D - 1] - box.lo[D - 1]);
+      const unsigned run = __match_any_sync(kFull, key);
+      const unsigned mine = ((1u << GL) - 1u) << (lane & ~(GL - 1));
+      grouped = __all_sync(kFull, valid && run == mine);
+    }
+    if (tiled) {
+      for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
+        const int64_t gi = tile_global<D>(box, g, l);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          su[c][l] = (float)__ldg(&a.u[c * g.nn + gi]);
+          sd[c][l] = (float)__ldcg(&pv[c * g.nn + gi]);
+          sq[c][l] = 0.0f;
+        }
+      }
+      __syncthreads();
+    }
+    if (valid) {
+      // local index of the stencil base inside the tile (when tiled)
+      const int lb = tiled ? tile_local<D>(box, base[0] - box.lo[0], base[1] - box.lo[1],
+                                           base[D - 1] - box.lo[D - 1])
+                           : 0;
+      int64_t gb = base[0];
+      {
+        int64_t stride = g.res[0];
+#pragma unroll
+        for (int c = 1; c < D; ++c) {
+          gb += (int64_t)base[c] * stride;
+          stride *= g.res[c];
+        }
+      }
+      float Gu[DD], Gd[DD];
+#pragma unroll
+      for (int e = 0; e < DD; ++e) {
+        Gu[e] = 0.0f;
+        Gd[e] = 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+        float dN[D];
+        grad_n_f32<D>(w, dw, k, dN);
+        float uk[D], dk[D];
+        if (tiled) {
+          const int l = lb + tile_local<D>(box, o0, o1, o2);
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            uk[c] = su[c][l];
+            dk[c] = sd[c][l];
+          }
+        } else {
+          const int64_t gi =
+              gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
+                           : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            uk[c] = (float)__ldg(&a.u[c * g.nn + gi]);
+            dk[c] = (float)__ldcg(&pv[c * g.nn + gi]);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int b = 0; b < D; ++b) {
+            Gu[c * D + b] = fmaf(uk[c], dN[b], Gu[c * D + b]);
+            Gd[c * D + b] = fmaf(dk[c], dN[b], Gd[c * D + b]);
+          }
+      }
+      float Fn[DD];
+#pragma unroll
+      for (int e = 0; e < DD; ++e) Fn[e] = a.P.F[e * n + pi];
+      float Y[DD];
+      const float qf = hessian_apply_f32<D>(Gu, Gd, Fn, (float)a.P.mu[pi], (float)a.P.lam[pi],
+                                            (float)a.P.vol0[pi], Y);
+      acc[0] += (double)qf;
+      if (grouped) {
+        // the lanes of one cell share their 3^D target nodes: reduce-scatter
+        // each chunk of KC nodes (one stencil layer) over the group, then
+        // every lane adds its share of the chunk's sums to the tile
+#pragma unroll
+        for (int o2c = 0; o2c < 3; ++o2c) {
+          float v[NVP];
+#pragma unroll
+          for (int j = 0; j < NVP; ++j) v[j] = 0.0f;
+#pragma unroll
+          for (int kk = 0; kk < KC; ++kk) {
+            const int k = (D == 2 ? 0 : 9 * o2c) + kk;
+            float dN[D];
+            grad_n_f32<D>(w, dw, k, dN);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+              float s = 0.0f;
+#pragma unroll
+              for (int b = 0; b < D; ++b) s = fmaf(Y[c * D + b], dN[b], s);
+              v[kk * D + c] = s;
+            }
+          }
+          group_reduce_scatter<GL, NVP>(v, gr);
+#pragma unroll
+          for (int j = 0; j < NVP / GL; ++j) {
+            const int idx = gr * (NVP / GL) + j;  // value index within the chunk
+            if (idx < KC * D) {
+              const int kk = idx / D, c = idx - kk * D;
+              const int k = (D == 2 ? 0 : 9 * o2c) + kk;
+              atomicAdd(&sq[c][lb + tile_local<D>(box, k % 3, (k / 3) % 3, k / 9)], v[j]);
+            }
+          }
+          if (D == 2) break;  // one chunk holds the whole 2D stencil
+        }
+      } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+        float dN[D];
+        grad_n_f32<D>(w, dw, k, dN);
+        float f[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          float s = 0.0f;
+#pragma unroll
+          for (int b = 0; b < D; ++b) s = fmaf(Y[c * D + b], dN[b], s);
+          f[c] = s;
+        }
+        if (tiled) {
+          const int l = lb + tile_local<D>(box, o0, o1, o2);
+#pragma unroll
+          for (int c = 0; c < D; ++c) atomicAdd(&sq[c][l], f[c]);
+        } else {
+          const int64_t gi =
+              gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
+                           : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
+          const unsigned fm = a.dofmask[gi];
+#pragma unroll
+          for (int c = 0; c < D; ++c)
+            if ((fm >> c) & 1u) atomicAdd(&q[c * g.nn + gi], (double)f[c]);
+        }
+      }
+      }
+    }
+    if (tiled) {
+      __syncthreads();
+      for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
+        const int64_t gi = tile_global<D>(box, g, l);
+        const unsigned fm = a.dofmask[gi];
+        if (!fm) continue;
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+          if (((fm >> c) & 1u) && sq[c][l] != 0.0f) atomicAdd(&q[c * g.nn + gi], (double)sq[c][l]);
+      }
+    }
+    __syncthreads();  // the tile arrays are reused by the next tile
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, a.partials, &a.S->counter, tot) && threadIdx.x == 0) a.S->pq = tot[0];
+}
+
+// Warp-aggregated add into a shared tile: lanes whose particles share a
+// stencil base (a run of equal keys, contiguous in Morton order) target the
+// same node for every stencil offset, so each run is summed with shuffles
+// and its first lane adds the run's total.  `first` and `last` bound the
+// lane's run; `steps` = ceil(log2(longest run in the warp)).  Every lane of
+// the warp calls it (shuffles); lanes with `active` false add nothing.
+template <int NV>
+__device__ __forceinline__ void warp_run_add(double (&v)[NV], int lane, int first, int last,
+                                             int steps, bool active, double* const (&dst)[NV]) {
+  for (int s = 0, off = 1; s < steps; ++s, off <<= 1) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      const double t = __shfl_down_sync(kFull, v[c], off);
+      if (lane + off <= last) v[c] += t;
+    }
+  }
+  if (active && lane == first)
+#pragma unroll
+    for (int c = 0; c < NV; ++c)
+      if (v[c] != 0.0) atomicAdd(dst[c], v[c]);
+}
+
+// APIC particle-to-grid transfer (Eq. p2g_transfer, Eq. p2g_substep), with
+// bm != nullptr also the boundary-particle mass of Eq. boundary_grid_set,
+// block-tiled: each block accumulates m, mv (and bm) of its Morton run of
+// particles in a shared node tile (warp-aggregated over runs of particles
+// that share a stencil base), then flushes each tile node with one global
+// atomic per field.  Same per-particle arithmetic as the one-thread-per-
+// particle transfer; with sbase/sdn also caches each particle's stencil.
+template <int D, typename R>
+__global__ void __launch_bounds__(TileCap<D>::THREADS)
+    k_p2g_tile(PartPtrsT<R> P, GridGeo g, double* m, double* mv, double* bm, int* err,
+               int* sbase, R* sdn) {
+  constexpr int K = (D == 2) ? 9 : 27;
+  constexpr int NV = D + 2;           // m, mv (D), bm
+  constexpr int CAP = (D == 2) ? 1024 : 768;
+  __shared__ double acc[NV][CAP];
+  __shared__ TileBox<D> box;
+  const int64_t n = P.n;
+  const int lane = threadIdx.x & 31;
+  const double Dinv = 4.0 * g.inv_dx * g.inv_dx;  // D_p^-1 of the quadratic B-spline
+  const int64_t tiles = (n + blockDim.x - 1) / blockDim.x;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t p = t * blockDim.x + threadIdx.x;
+    double xp[D];
+    Stencil<D> s;
+    bool valid = false;
+    if (p < n) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) xp[a] = P.x[a * n + p];
+      valid = make_stencil<D>(xp, g, s);
+      if (!valid) atomicOr(err, kErrOutOfGrid);
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a) s.base[a] = 0;
+    }
+    tile_box<D>(s.base, valid, CAP, box);
+    const bool tiled = box.nodes > 0;
+    if (tiled) {
+      for (int l = threadIdx.x; l < box.nodes; l += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < NV; ++c) acc[c][l] = 0.0;
+      __syncthreads();
+    }
+    double vp[D], Bp[D * D], mp = 0.0;
+    bool isb = false;
+    int lb = 0;
+    if (valid) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) vp[a] = (double)P.v[a * n + p];
+#pragma unroll
+      for (int e = 0; e < D * D; ++e) Bp[e] = (double)P.B[e * n + p];
+      mp = P.mass[p];
+      isb = (bm != nullptr) && (P.flags[p] & 1u);
+      if (sbase) {
+        int64_t b = 0, stride = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          b += (int64_t)s.base[a] * stride;
+          stride *= g.res[a];
+        }
+        sbase[p] = (int)b;
+      }
+      if (tiled)
+        lb = tile_local<D>(box, s.base[0] - box.lo[0], s.base[1] - box.lo[1],
+                           s.base[D - 1] - box.lo[D - 1]);
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a) vp[a] = 0.0;
+#pragma unroll
+      for (int e = 0; e < D * D; ++e) Bp[e] = 0.0;
+    }
+    // runs of lanes with the same stencil base (tile-local base index; an
+    // invalid lane forms a run of its own)
+    const int key = (tiled && valid) ? lb : -1 - lane;
+    const unsigned run = __match_any_sync(kFull, key);
+    const int first = __ffs(run) - 1, last = 31 - __clz(run);
+    const bool contiguous = (run >> first) == ((1u << (last - first)) << 1) - 1u;
+    const bool warp_ok = __all_sync(kFull, contiguous);
+    int longest = __reduce_max_sync(kFull, (unsigned)(last - first + 1));
+    int steps = 0;
+    while ((1 << steps) < longest) ++steps;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double N = 0.0, dN[D];
+      int64_t node = 0;
+      double vals[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) vals[c] = 0.0;
+      if (valid) {
+        node = stencil_node<D>(s, g, k, N, dN);
+        if (sdn)
+#pragma unroll
+          for (int a = 0; a < D; ++a) sdn[(int64_t)(a * K + k) * n + p] = (R)dN[a];
+        double r[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) r[a] = stencil_node_pos<D>(s, g, k, a) - xp[a];
+        const double wm = mp * N;
+        vals[0] = wm;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          double va = 0.0;
+#pragma unroll
+          for (int b = 0; b < D; ++b) va += Bp[a * D + b] * r[b];
+          vals[1 + a] = wm * (vp[a] + Dinv * va);
+        }
+        vals[D + 1] = isb ? wm : 0.0;
+      }
+      if (tiled) {
+        const int l = valid ? lb + tile_local<D>(box, k % 3, (k / 3) % 3, k / 9) : 0;
+        double* dst[NV];
+#pragma unroll
+        for (int c = 0; c < NV; ++c) dst[c] = &acc[c][l];
+        if (warp_ok) {
+          warp_run_add<NV>(vals, lane, first, last, steps, valid, dst);
+        } else if (valid) {
+#pragma unroll
+          for (int c = 0; c < NV; ++c)
+            if (vals[c] != 0.0) atomicAdd(dst[c], vals[c]);
+        }
+      } else if (valid) {
+        atomicAdd(&m[node], vals[0]);
+#pragma unroll
+        for (int a = 0; a < D; ++a) atomicAdd(&mv[a * g.nn + node], vals[1 + a]);
+        if (isb) atomicAdd(&bm[node], vals[D + 1]);
+      }
+    }
+    if (tiled) {
+      __syncthreads();
+      for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
+        if (acc[0][l] == 0.0) continue;  // no particle reached this node
+        const int64_t gi = tile_global<D>(box, g, l);
+        atomicAdd(&m[gi], acc[0][l]);
+#pragma unroll
+        for (int a = 0; a < D; ++a) atomicAdd(&mv[a * g.nn + gi], acc[1 + a][l]);
+        if (bm && acc[D + 1][l] != 0.0) atomicAdd(&bm[gi], acc[D + 1][l]);
+      }
+    }
+    __syncthreads();  // the tile is reused by the next run of particles
+  }
+}
+
+}  // namespace osmpm

@@ -89,6 +89,7 @@ struct PcgArgsT {
   int* err;
   const int* sbase;     // per particle: flat index of the stencil's base node
   const R* sdn;         // per particle: grad N of the 3^D stencil nodes, [(c*K + k)*n + p]
+  const double* u;      // the Newton iterate (the tiled product recomputes the Hessian)
 };
 
 }  // namespace osmpm

@@ -48,6 +48,9 @@ OSMPM_FIELD_U = 2
 OSMPM_FIELD_BMASS = 3
 OSMPM_FIELD_RECEIVER = 4
 OSMPM_FIELD_BC = 5
+OSMPM_FIELD_PLANE_FORCE = 6
+OSMPM_FIELD_PLANE_GAP = 7
+OSMPM_FIELD_PLANE_ACTIVE = 8
 
 _ALLOC = CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
 _FREE = CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
@@ -63,7 +66,7 @@ class osmpm_domain_desc(Structure):
                 ("newton_tol", c_double), ("newton_max", c_int32), ("cg_rtol", c_double),
                 ("cg_max", c_int32), ("ls_max", c_int32), ("mass_eps", c_double),
                 ("cg_eta_max", c_double), ("pcg_mode", c_int32), ("launch_mode", c_int32),
-                ("reserved", c_int32 * 4)]
+                ("hvp_mode", c_int32), ("reserved", c_int32 * 3)]
 
 
 class osmpm_particles_in(Structure):
@@ -90,10 +93,10 @@ class osmpm_stats(Structure):
     _fields_ = [("newton_iters", c_int32), ("cg_iters", c_int32), ("ls_halvings", c_int32),
                 ("schwarz_iters", c_int32), ("solves", c_int32), ("converged", c_int32),
                 ("r_B", c_double), ("r_S", c_double), ("last_dx_inf", c_double),
-                ("reserved", c_double * 6)]
+                ("contact_sets", c_int32), ("pad", c_int32), ("reserved", c_double * 5)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "pad")}
 
 
 class osmpm_counters(Structure):
@@ -103,6 +106,11 @@ class osmpm_counters(Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class osmpm_plane(Structure):
+    _fields_ = [("enabled", c_int32), ("max_sets", c_int32), ("level", c_double),
+                ("cand_hi", c_double), ("spacing", c_double)]
 
 
 class osmpm_noalloc_grid(Structure):
@@ -150,6 +158,7 @@ _sig = {
     "osmpm_get_counters": (c_int32, [c_void_p, POINTER(osmpm_counters)]),
     "osmpm_check_wait_timeout": (c_int32, [c_void_p]),
     "osmpm_record": (c_int32, [c_void_p, c_int32]),
+    "osmpm_set_plane": (c_int32, [c_void_p, POINTER(osmpm_plane)]),
     "osmpm_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(osmpm_adjoint_out),
                                 POINTER(osmpm_stats)]),
     "osmpm_energy_change_noalloc": (c_int32, [POINTER(osmpm_noalloc_grid),
@@ -234,6 +243,7 @@ def make_desc(spec) -> osmpm_domain_desc:
     d.cg_eta_max = getattr(spec, "cg_eta_max", 0.0)
     d.pcg_mode = getattr(spec, "pcg_mode", 0)
     d.launch_mode = getattr(spec, "launch_mode", 0)
+    d.hvp_mode = getattr(spec, "hvp_mode", 0)
     return d
 
 
@@ -317,8 +327,19 @@ class Domain:
         _check(_lib.osmpm_step(self.h, dt, ctypes.byref(st)), "osmpm_step")
         return st.as_dict()
 
-    def record(self, enable: bool = True) -> None:
-        _check(_lib.osmpm_record(self.h, 1 if enable else 0), "osmpm_record")
+    def set_plane(self, level: float = 0.0, cand_hi: float = 0.0, spacing: float = 0.0,
+                  enabled: bool = True, max_sets: int = 0) -> None:
+        """Rigid frictionless plane y = level (osmpm_set_plane); enabled
+        False removes it."""
+        pl = osmpm_plane(1 if enabled else 0, int(max_sets), float(level), float(cand_hi),
+                         float(spacing))
+        _check(_lib.osmpm_set_plane(self.h, ctypes.byref(pl)), "osmpm_set_plane")
+
+    def record(self, enable: bool = True, every: int = 1) -> None:
+        """Start (or with enable False stop) recording for the reverse mode;
+        every >= 2 keeps a checkpoint every ``every`` steps and lets the
+        adjoint re-run each segment."""
+        _check(_lib.osmpm_record(self.h, max(1, int(every)) if enable else 0), "osmpm_record")
 
     def adjoint(self, dJ_dx, initial_state: bool = False):
         """dJ/dE for dJ_dx = dJ/dx after the recorded steps (a CUDA float64
@@ -435,8 +456,8 @@ def osmpm_check_wait_timeout(stream: int) -> int:
     return _lib.osmpm_check_wait_timeout(c_void_p(stream))
 
 
-def osmpm_record(dom: Domain, enable: bool = True) -> None:
-    dom.record(enable)
+def osmpm_record(dom: Domain, enable: bool = True, every: int = 1) -> None:
+    dom.record(enable, every)
 
 
 def osmpm_adjoint(coarse: Domain, fine: Optional[Domain], dJ_dx, initial_state: bool = False):

@@ -99,6 +99,7 @@ class DomainSpec:
     cg_eta_max: float = 0.0       # inexact-Newton forcing cap (0: the library default 1e-3)
     pcg_mode: int = 0             # 0 automatic, 1 persistent PCG, 2 streaming PCG
     launch_mode: int = 0          # 0 CUDA graph per Newton iteration, 1 plain stream launches
+    hvp_mode: int = 0             # mixed streaming PCG product: 0 automatic, 1 lane groups, 2 tiles
 
     def __post_init__(self):
         if self.mass_eps is None:
@@ -485,6 +486,18 @@ def fold3d(dx_c: float = 0.02, dx_f: float = 0.005, band=(0.4, 0.6), M: int = 4,
     return coarse, fine, sch, dT
 
 
+def fold3d_small(precision: int = 1, **kw):
+    """A reduced 3D folding plate small enough for the FP64 oracle: plate
+    0.48 x 0.12 x 0.04, coarse dx 0.04, fine band [0.12, 0.36) at dx 0.02,
+    M = 2, the edge rotated 90 degrees over 20 global steps (the same rules
+    and kernels as ``fold3d``: the kind-1 rotation rule, 3D, mixed precision
+    by default).  240 coarse and 1,152 fine particles."""
+    args = dict(dx_c=0.04, dx_f=0.02, band=(0.12, 0.36), size=(0.48, 0.12, 0.04), M=2,
+                fold_steps=20, precision=precision)
+    args.update(kw)
+    return fold3d(**args)
+
+
 def overlap3d(dx_c: float = 0.1, ratio: int = 2, M: int = 2, E: float = 1e5, nu: float = 0.3,
               rho: float = 1000.0, dT: float = 0.02, ppc_1d: int = 2, precision: int = 0):
     """A small clamped 3D bar [0,0.8]x[0,0.2]x[0,0.2] under gravity split in
@@ -580,10 +593,11 @@ def uniform3(seed: int) -> Tuple[float, float, float]:
     return tuple(out)
 
 
-def inclusion_instance(i: int, scaled: bool = False, **kw):
-    """Instance i of the batched inclusion family: r_inc = 0.03 + 0.05 u1,
-    E_inc = 10^(7 + 2 u2), fine dx 0.01 if u3 < 0.5 else 0.005 (literal) or
-    0.0025 / 0.001 (scaled)."""
+def instance_params(i: int, scaled: bool = False):
+    """(r_inc, E_inc, fine dx) of instance i of the batched inclusion family:
+    r_inc = 0.03 + 0.05 u1, E_inc = 10^(7 + 2 u2), fine dx 0.01 if u3 < 0.5
+    else 0.005 (literal) or 0.0025 / 0.001 (scaled), (u1, u2, u3) from
+    SplitMix64 seeded 0x05AD0000 + i."""
     u1, u2, u3 = uniform3(0x05AD0000 + i)
     r_inc = 0.03 + 0.05 * u1
     E_inc = 10.0 ** (7.0 + 2.0 * u2)
@@ -591,7 +605,21 @@ def inclusion_instance(i: int, scaled: bool = False, **kw):
         dx_S = 0.0025 if u3 < 0.5 else 0.001
     else:
         dx_S = 0.01 if u3 < 0.5 else 0.005
+    return r_inc, E_inc, dx_S
+
+
+def inclusion_instance(i: int, scaled: bool = False, **kw):
+    """Instance i of the batched inclusion family (``instance_params``)."""
+    r_inc, E_inc, dx_S = instance_params(i, scaled)
     return inclusion(dx_S=dx_S, M=2, r_inc=r_inc, E_inc=E_inc, **kw)
+
+
+def top_cap(x: np.ndarray, r_inc: float, center=(0.5, 0.5)) -> np.ndarray:
+    """Particles of the inclusion's top cap: inside the inclusion disk and
+    above its centre by more than half its radius (the objective region of
+    the batched family's gradient)."""
+    d = x - np.asarray(center)[None, :]
+    return (np.hypot(d[:, 0], d[:, 1]) < r_inc) & (d[:, 1] > 0.5 * r_inc)
 
 
 def identical_pair(spec: DomainSpec, M: int = 1):

@@ -91,6 +91,7 @@ def _reserved(d):
     (_set("precision", 2), "precision"),
     (_set("pcg_mode", 3), "pcg_mode"),
     (_set("launch_mode", 2), "launch_mode"),
+    (_set("hvp_mode", 3), "hvp_mode"),
     (_set("cg_eta_max", 1.0), "cg_eta_max"),
     (_set("dx", 0.0), "dx"),
     (_set("newton_max", 0), "solver controls"),

@@ -1,8 +1,13 @@
 """3D OS-MPM.  A small clamped bar split into an overlapping coarse and fine
-subdomain is compared with the FP64 oracle particle by particle; the 3D
+subdomain is compared with the FP64 oracle particle by particle; a reduced
+folding plate (the rotation rule, M = 2) is compared with the FP64 oracle's
+stored run in mixed precision and in FP64, with both PCG engines; the 3D
 folding-plate configuration (coarse dx 0.02, fine band dx 0.005, M = 4,
 ~137k particles, mixed precision) runs two global steps and is checked
 through properties that hold at any size."""
+import dataclasses
+import os
+
 import numpy as np
 import pytest
 
@@ -74,3 +79,36 @@ def test_fold3d_full_size_two_steps(osmpm):
     clamp = cB.particles.x[:, 0] < 0.5 * g.dx
     assert np.abs(xB[clamp] - cB.particles.x[clamp]).max() < 1e-3 * g.dx
     assert np.abs(xS - cS.particles.x).max() > 0
+
+
+def _stored_oracle_run(name):
+    """(coarse x, fine x) of a stored FP64 oracle run (written by
+    tests/golden/make_oracle_runs.py, oracle only), id order."""
+    rows = {"c": [], "f": []}
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_runs", name + ".txt")
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                parts = line.split()
+                rows[parts[0]].append([float(v) for v in parts[2:]])
+    return np.asarray(rows["c"]), np.asarray(rows["f"])
+
+
+@pytest.mark.parametrize("precision,pcg_mode,tol", [(1, 1, 1e-4), (1, 2, 1e-4), (0, 1, 1e-6),
+                                                     (0, 2, 1e-6)])
+def test_fold3d_small_matches_oracle(osmpm, precision, pcg_mode, tol):
+    """Reduced folding plate (3D, the kind-1 rotation rule on the coarse
+    edge, M = 2), two global steps: mixed precision (Kernels<3, float>, the
+    arithmetic of the full fold) within rel-L2 1e-4 and FP64 within 1e-6 of
+    the FP64 oracle, with the persistent (1) and the streaming (2) PCG."""
+    cB, cS, sch, dT = W.fold3d_small(precision=precision)
+    cB = dataclasses.replace(cB, pcg_mode=pcg_mode)
+    cS = dataclasses.replace(cS, pcg_mode=pcg_mode)
+    B, S = osmpm.Domain(cB), osmpm.Domain(cS)
+    for _ in range(2):
+        st = osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+        assert st["converged"] == 1
+    xB_ref, xS_ref = _stored_oracle_run("fold3d_small_M2_2steps")
+    assert xB_ref.shape == cB.particles.x.shape and xS_ref.shape == cS.particles.x.shape
+    assert rel_disp(B.get_particles()[0], xB_ref, cB.particles.x) <= tol
+    assert rel_disp(S.get_particles()[0], xS_ref, cS.particles.x) <= tol

@@ -303,3 +303,145 @@ def test_coupled_record_is_interrupted_by_a_single_step(osmpm):
     with pytest.raises(osmpm.OsmpmError) as e:
         osmpm.osmpm_adjoint(B, S, g)
     assert e.value.status == osmpm.OSMPM_E_INVALID
+
+
+# ----------------------------------------------------------------------------
+# step checkpointing (osmpm_record with every >= 2)
+# ----------------------------------------------------------------------------
+def test_checkpointed_record_matches_full_record(osmpm):
+    """Single-domain steps recorded with a checkpoint every 3 steps (7 steps:
+    segments of 3, 3, 1) give the full record's gradients; the forward and
+    the state after the adjoint are unchanged."""
+    import torch
+    spec, rng = _spec(2, 31)
+    dt, n_steps = 0.01, 7
+    n = spec.particles.n
+    g = torch.from_numpy(rng.standard_normal((n, 2))).cuda()
+    res = {}
+    for every in (1, 3):
+        dom = osmpm.Domain(spec)
+        dom.record(True, every=every)
+        for _ in range(n_steps):
+            dom.step(dt)
+        x = dom.get_particles()
+        dE, st0, st = dom.adjoint(g, True)
+        after = dom.get_particles()
+        for a, b in zip(x, after):
+            np.testing.assert_array_equal(a, b)
+        res[every] = (x[0], dE.cpu().numpy(), {k: v.cpu().numpy() for k, v in st0.items()}, st)
+    # two runs of the same steps (FP64 atomics: equal to the last bits)
+    assert _rel(res[3][0], res[1][0]) <= 1e-12
+    assert res[3][3]["solves"] == res[1][3]["solves"] == n_steps
+    assert _rel(res[3][1], res[1][1]) <= 1e-8
+    for k in ("x", "v", "B", "F"):
+        assert _rel(res[3][2][k], res[1][2][k]) <= 1e-8, k
+
+
+def test_checkpointed_coupled_record_matches_full_record_and_oracle(osmpm):
+    """Three coupled steps recorded with a checkpoint every 2 steps: the
+    gradients of the full record (1e-8) and of the oracle unrolled over the
+    same iterations (1e-6)."""
+    import torch
+    cB, cS, sch, dT, rng = _coupled()
+    n = cB.particles.n + cS.particles.n
+    c = rng.standard_normal((n, 2))
+    g = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+    res = {}
+    for every in (1, 2):
+        B, S = osmpm.Domain(cB), osmpm.Domain(cS)
+        B.record(True, every=every)
+        S.record(True, every=every)
+        iters = [osmpm.osmpm_schwarz_couple(B, S, dT, sch)["schwarz_iters"] for _ in range(3)]
+        dE, st0, st = osmpm.osmpm_adjoint(B, S, g, True)
+        res[every] = (iters, dE.cpu().numpy(), {k: v.cpu().numpy() for k, v in st0.items()}, st)
+    assert res[1][0] == res[2][0]
+    assert res[2][3]["solves"] == res[1][3]["solves"]
+    assert _rel(res[2][1], res[1][1]) <= 1e-8
+    for k in ("x", "v", "B", "F"):
+        assert _rel(res[2][2][k], res[1][2][k]) <= 1e-8, k
+    oE, barB, barS, _ = _coupled_oracle(cB, cS, sch, dT, c, res[2][0])
+    assert _rel(res[2][1], oE) <= 1e-6
+    assert _rel(res[2][2]["x"], np.concatenate([barB.x, barS.x])) <= 1e-6
+
+
+def _golden_module():
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_oracle_runs.py")
+    spec = importlib.util.spec_from_file_location("make_oracle_runs", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _stored_gradient(mod):
+    import os
+    rows = {"c": [], "f": []}
+    with open(os.path.join(mod.OUT, mod.ADJ_NAME + ".txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                parts = line.split()
+                rows[parts[0]].append([float(v) for v in parts[2:]])
+    c, f = np.asarray(rows["c"]), np.asarray(rows["f"])
+    return np.concatenate([c[:, 0], f[:, 0]]), c[:, 1:], f[:, 1:]
+
+
+@pytest.mark.slow
+def test_batched_instance_gradient_over_50_checkpointed_steps(osmpm):
+    """Instance 0 of the batched inclusion family, 50 coupled steps of four
+    Schwarz iterations each, recorded with a checkpoint every 10 steps;
+    J = mean y-displacement of the inclusion's top-cap particles.  dJ/dE
+    against the FP64 oracle's adjoint unrolled over the same iterations
+    (stored run, 1e-6), against the full record (1e-8), and against a
+    central difference of the CUDA forward along a random direction of the
+    moduli."""
+    import torch
+    mod = _golden_module()
+    cB, cS, sch, dT, c = mod.adjoint_case()
+    nB = cB.particles.n
+    oE, oxB, oxS = _stored_gradient(mod)
+    g = torch.from_numpy(np.ascontiguousarray(c)).cuda()
+
+    def forward(specB, specS, every=0):
+        B, S = osmpm.Domain(specB), osmpm.Domain(specS)
+        if every:
+            B.record(True, every=every)
+            S.record(True, every=every)
+        for _ in range(mod.ADJ_STEPS):
+            st = osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+            assert st["schwarz_iters"] == mod.ADJ_ITERS
+        return B, S
+
+    res = {}
+    for every in (10, 1):
+        B, S = forward(cB, cS, every)
+        xB, xS = B.get_particles()[0], S.get_particles()[0]
+        dE, _, _ = osmpm.osmpm_adjoint(B, S, g)
+        res[every] = dE.cpu().numpy()
+        assert _rel(xB - cB.particles.x, oxB - cB.particles.x) <= 1e-8
+        assert _rel(xS - cS.particles.x, oxS - cS.particles.x) <= 1e-8
+        B.close()
+        S.close()
+    assert _rel(res[10], oE) <= 1e-6
+    assert _rel(res[10], res[1]) <= 1e-8
+    # directional central difference: E_p (1 + eps w_p), w_p = +-1
+    rng = np.random.default_rng(50)
+    w = rng.choice([-1.0, 1.0], nB + cS.particles.n)
+    eps = 1e-4
+
+    def J(sign):
+        specs = []
+        for spec, ww in ((cB, w[:nB]), (cS, w[nB:])):
+            q = spec.particles.copy()
+            q.E = q.E * (1.0 + sign * eps * ww)
+            specs.append(dataclasses.replace(spec, particles=q))
+        B, S = forward(*specs)
+        val = float(np.sum(c[nB:] * (S.get_particles()[0] - cS.particles.x)))
+        B.close()
+        S.close()
+        return val
+
+    fd = (J(1.0) - J(-1.0)) / (2 * eps)
+    E = np.concatenate([cB.particles.E, cS.particles.E])
+    ad = float(np.sum(res[10] * E * w))
+    np.testing.assert_allclose(ad, fd, rtol=1e-4)

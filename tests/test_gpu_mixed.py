@@ -84,3 +84,33 @@ def test_mixed_and_fp64_domains_do_not_couple(osmpm):
     with pytest.raises(osmpm.OsmpmError) as e:
         osmpm.osmpm_schwarz_couple(B, S, dT, sch)
     assert e.value.status == osmpm.OSMPM_E_INVALID
+
+
+def _stored_oracle_run(name):
+    """(coarse x, fine x) of a stored FP64 oracle run (written by
+    tests/golden/make_oracle_runs.py, oracle only), id order."""
+    import os
+    rows = {"c": [], "f": []}
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_runs", name + ".txt")
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                parts = line.split()
+                rows[parts[0]].append([float(v) for v in parts[2:]])
+    return np.asarray(rows["c"]), np.asarray(rows["f"])
+
+
+def test_mixed_schwarz_inclusion_100_steps(osmpm):
+    """100 coupled mixed-precision steps of the inclusion (fine dx 0.02,
+    M = 2) against the FP64 oracle's 100 steps: both domains' displacement
+    within rel-L2 1e-4."""
+    cB, cS, sch, dT = W.inclusion(dx_S=0.02, M=2)
+    B = osmpm.Domain(dataclasses.replace(cB, precision=1))
+    S = osmpm.Domain(dataclasses.replace(cS, precision=1))
+    for _ in range(100):
+        st = osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+        assert st["converged"] == 1
+    xB_ref, xS_ref = _stored_oracle_run("inclusion_dxS0.02_M2_100steps")
+    assert xB_ref.shape == cB.particles.x.shape and xS_ref.shape == cS.particles.x.shape
+    assert rel_disp(B.get_particles()[0], xB_ref, cB.particles.x) <= MIXED_TOL
+    assert rel_disp(S.get_particles()[0], xS_ref, cS.particles.x) <= MIXED_TOL

@@ -453,3 +453,25 @@ def test_bench_workload_full_size_one_global_step(osmpm):
     assert rel_disp(xB, rB.p.x, cB.particles.x) <= DISP_TOL
     assert rel_disp(xS, rS.p.x, cS.particles.x) <= DISP_TOL
     np.testing.assert_allclose(FS, rS.p.F, atol=1e-8)
+
+
+@pytest.mark.slow
+def test_bench_workload_full_size_five_global_steps(osmpm):
+    """The configuration bench.py times as its FP64 single-instance line
+    (inclusion, coarse dx 0.05, fine dx 0.005, M = 2), five global steps,
+    every particle compared with the oracle after every step (rel-L2 of
+    displacement <= 1e-6: no drift over the steps whose Newton and PCG
+    counts grow), receiver sets of the last step bit for bit."""
+    cB, cS, sch, dT = W.inclusion(dx_S=0.005, M=2)
+    B, S = osmpm.Domain(cB), osmpm.Domain(cS)
+    rB, rS = O.DomainState.create(cB), O.DomainState.create(cS)
+    for k in range(5):
+        st = osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+        ost, so = O.SchwarzStats(), {}
+        O.schwarz_step(rB, rS, dT, sch, ost, so)
+        assert st["converged"] == 1 and ost.converged
+        assert abs(st["schwarz_iters"] - ost.iters) <= 1
+        assert rel_disp(B.get_particles()[0], rB.p.x, cB.particles.x) <= DISP_TOL, k
+        assert rel_disp(S.get_particles()[0], rS.p.x, cS.particles.x) <= DISP_TOL, k
+    np.testing.assert_array_equal(B.get_grid(osmpm.OSMPM_FIELD_RECEIVER) > 0, so["sets"].recvB)
+    np.testing.assert_array_equal(S.get_grid(osmpm.OSMPM_FIELD_RECEIVER) > 0, so["sets"].recvS)

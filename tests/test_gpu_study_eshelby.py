@@ -1,40 +1,44 @@
 """Accuracy against cost of OS-MPM and of the single fine domain on the
 eigenstrain inclusion of Sec. 4.3 (the paper's accuracy-efficiency study,
-here on one GB300).
+on the GPU).
 
 For each stiffness ratio and fine spacing h: the single-domain reference
 runs the traction-free matrix [0.1,0.9]^2 on one grid at h with dt = h
 (dt / h constant, 0.01 s at h = 0.01); OS-MPM runs the fine disk r < 0.15
 at h and the coarse matrix at 2h with M = 2 and dT = 2 dt.  Both relax until
-the largest particle speed of every domain is below 1e-6.  Reported per run:
-steps, summed GPU time of the steps (CUDA events on the domains' stream;
-the settle checks run outside the events), and the relative L2 error of
-sigma_yy against the Eshelby solution over the particles with r < 0.15 (the
-fine region both methods resolve at h).
+the largest particle speed of every domain is below 1e-6.  Recorded per
+run: steps, summed GPU time of the steps (CUDA events on the domains'
+stream; the settle checks run outside the events), and the relative L2
+error of sigma_yy against the Eshelby solution over the particles with
+r < 0.15 (the fine region both methods resolve at h).
 
-  python tests/study_eshelby_error_vs_time.py [--ratios 1,2,5] [--h 0.01,0.005,0.0025]
+Asserted: OS-MPM reproduces the single domain's accuracy (its error within
+6 % of the single domain's, relative) and both errors fall from h to h/2.
+The default sweep is h = 0.01, 0.005 (seconds of GPU time); the environment
+variable OSMPM_STUDY_H selects others, e.g. the full table:
 
-Prints one JSON object per run and a closing summary table.
+  OSMPM_STUDY_H=0.01,0.005,0.0025 python -m pytest -s tests/test_gpu_study_eshelby.py
+
+which prints one JSON line per run and the summary table.
 """
 from __future__ import annotations
 
-import argparse
 import json
 import os
-import sys
-import time
 
 import numpy as np
+import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-sys.path.insert(0, ROOT)
+from oracle import analytic as A
+from oracle import osmpm_oracle as O
+from paper_2605_09097_gb300 import workloads as W
 
-from oracle import analytic as A  # noqa: E402
-from oracle import osmpm_oracle as O  # noqa: E402
-from paper_2605_09097_gb300 import workloads as W  # noqa: E402
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 DELTA, R_INC, E_OUT, NU = 0.01, 0.05, 1e6, 0.3
 MAX_STEPS, V_STOP = 400, 1e-6
+RATIOS = (1.0, 2.0, 5.0)
+H = tuple(float(v) for v in os.environ.get("OSMPM_STUDY_H", "0.01,0.005").split(","))
 
 
 def sigma_yy_error(x, F, E, nu, ratio):
@@ -97,34 +101,39 @@ def run(ratio, h, osmpm, torch, stream):
     return row
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--ratios", default="1,2,5")
-    ap.add_argument("--h", default="0.01,0.005,0.0025")
-    args = ap.parse_args()
+@pytest.fixture(scope="module")
+def env():
     import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
     from paper_2605_09097_gb300 import build
     build.build()
     from paper_2605_09097_gb300 import osmpm
+    return torch, osmpm
+
+
+def test_osmpm_matches_single_fine_domain_accuracy(env):
+    torch, osmpm = env
     stream = torch.cuda.Stream()
     rows = []
-    t0 = time.time()
     with torch.cuda.stream(stream):
-        for ratio in [float(r) for r in args.ratios.split(",")]:
-            for h in [float(v) for v in args.h.split(",")]:
+        for ratio in RATIOS:
+            for h in H:
                 row = run(ratio, h, osmpm, torch, stream)
                 rows.append(row)
                 print(json.dumps(row), flush=True)
-    print(f"\n| E_in/E_out | h | single: particles, steps, GPU s, err | OS-MPM: particles, steps, "
-          f"GPU s, err | speedup |")
+    print("\n| E_in/E_out | h | single: particles, steps, GPU s, err | OS-MPM: particles, steps, "
+          "GPU s, err | speedup |")
     print("|---|---|---|---|---|")
     for r in rows:
         s, o = r["single"], r["osmpm"]
         print(f"| {r['ratio']:g} | {r['h']:g} | {s['particles']}, {s['steps']}, {s['gpu_s']:.3f}, "
               f"{s['err_syy']:.4f} | {o['particles']}, {o['steps']}, {o['gpu_s']:.3f}, "
               f"{o['err_syy']:.4f} | {r['speedup']:.2f} |")
-    print(f"\n(total wall {time.time() - t0:.0f} s)")
-
-
-if __name__ == "__main__":
-    main()
+    for r in rows:
+        assert abs(r["osmpm"]["err_syy"] - r["single"]["err_syy"]) <= 0.06 * r["single"]["err_syy"], r
+    for ratio in RATIOS:
+        seq = [r for r in rows if r["ratio"] == ratio]
+        for a, b in zip(seq, seq[1:]):
+            assert b["single"]["err_syy"] < a["single"]["err_syy"]
+            assert b["osmpm"]["err_syy"] < a["osmpm"]["err_syy"]

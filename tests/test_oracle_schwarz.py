@@ -263,3 +263,68 @@ def test_particles_advance_once_per_global_step():
     assert np.abs(dB).max() <= 1e-3 * (1 + 1e-9)
     top = cB.particles.x[:, 1] > 0.85
     assert dB[top, 1].mean() < -0.5e-3
+
+
+def _brute_coarse_support_active(gB, gS, activeB):
+    """Per fine node, by loops: its position o_S + j dx_S from the integer
+    multi-index, the coarse base node floor((x - o_B)/dx_B - 1/2) per axis,
+    and all 3^d coarse nodes base + {0, 1, 2}^d inside the coarse box and
+    active."""
+    d = gS.dim
+    resB = [int(r) for r in gB.res[:d]]
+    out = np.zeros(int(np.prod(gS.res)), dtype=bool)
+    for flat, j in enumerate(np.ndindex(*reversed([int(r) for r in gS.res[:d]]))):
+        j = j[::-1]  # x fastest
+        x = [gS.origin[a] + j[a] * gS.dx for a in range(d)]
+        base = [int(np.floor((x[a] - gB.origin[a]) / gB.dx - 0.5)) for a in range(d)]
+        ok = True
+        for off in np.ndindex(*(3,) * d):
+            node = [base[a] + off[a] for a in range(d)]
+            if any(node[a] < 0 or node[a] >= resB[a] for a in range(d)):
+                ok = False
+                break
+            I = node[0] + resB[0] * (node[1] + (resB[1] * node[2] if d == 3 else 0))
+            if not activeB[I]:
+                ok = False
+                break
+        out[flat] = ok
+    return out
+
+
+def test_coarse_support_filter_matches_brute_force():
+    """The Gamma_hat_S filter (coarse support of a fine node inside the box
+    and active) against the brute-force loop, on the inclusion's coarse
+    active set and on seeded random active sets over a fine grid that
+    reaches past the coarse box.  The random sets include fine nodes whose
+    only inactive support node lies in the third stencil row of an axis, so
+    a filter that dropped that row (or tested "inside" without "active", or
+    the reverse) would fail."""
+    cB, cS, _, _ = _inclusion_small()
+    gB, gS = cB.grid, cS.grid
+    gfB = O.p2g(cB.particles, gB, mass_eps=cB.mass_eps)
+    got = O.coarse_support_active(gB, gS, gfB.active)
+    want = _brute_coarse_support_active(gB, gS, gfB.active)
+    assert got.any() and (~got).any()
+    np.testing.assert_array_equal(got, want)
+    # a fine grid hanging over the coarse box (origin below it, reaching past it)
+    gS2 = W.Grid(2, (gB.origin[0] - 3.3 * gS.dx, gB.origin[1] + 0.37 * gB.dx), gS.dx,
+                 (int(round(1.2 / gS.dx)), int(round(0.6 / gS.dx))))
+    rng = np.random.default_rng(7)
+    third_row_hits = 0
+    for p_active in (0.97, 0.9):
+        act = rng.random(gB.n_nodes) < p_active
+        got = O.coarse_support_active(gB, gS2, act)
+        want = _brute_coarse_support_active(gB, gS2, act)
+        np.testing.assert_array_equal(got, want)
+        # fine nodes that only the third row of some axis rules out
+        xs = O.node_positions(gS2)
+        t = (xs - np.asarray(gB.origin)[None]) / gB.dx
+        base = np.floor(t - 0.5).astype(int)
+        inside = np.all((base >= 0) & (base + 2 < np.asarray(gB.res)[None]), axis=1)
+        for k in np.nonzero(inside & ~got)[0][:400]:
+            two = True
+            for off in np.ndindex(2, 2):
+                I = (base[k, 0] + off[0]) + gB.res[0] * (base[k, 1] + off[1])
+                two &= bool(act[I])
+            third_row_hits += two
+    assert third_row_hits > 0

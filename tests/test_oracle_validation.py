@@ -66,39 +66,9 @@ def test_oracle_cantilever_matches_elastica(gamma):
 
 
 def _settled_hertz_contact(dx, ppc_1d, indent, n_steps=10, dt=0.02, dt_settle=0.2):
-    """The cylinder of Sec. 4.2 pressed onto the rigid plane by its flat
-    face (``indent`` over ``n_steps`` steps), then held and settled: every
-    step a kinetically damped implicit step (v and B zeroed after it), the
-    plane unilateral (oracle.contact), until the particle speed is below
-    1e-6.  Returns (spec, plane nodes, grid fields, gaps, active set,
-    multipliers, last u, settled domain state)."""
-    import dataclasses
+    """oracle.contact.settle_hertz without its settle-step count."""
     from oracle import contact as C
-    spec, plane = W.hertz_rigid_single(dx=dx, ppc_1d=ppc_1d, indent=indent, n_steps=n_steps, dt=dt)
-    ds = O.DomainState.create(spec)
-    h = dx / ppc_1d
-    push = spec.dirichlet[0]
-    for k in range(n_steps):
-        # the pushed rows follow the flat face down (a fixed box would lose
-        # the face once the indent passes a grid spacing)
-        lo = (push.lo[0], push.lo[1] - k * indent / n_steps)
-        ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(push, lo=lo)])
-        C.step_with_plane(ds, dt, plane, h)
-        ds.p.v[:] = 0.0
-        ds.p.B[:] = 0.0
-    lo = (push.lo[0], push.lo[1] - indent)
-    ds.spec = dataclasses.replace(spec, dirichlet=[dataclasses.replace(push, lo=lo, vel=(0.0, 0.0, 0.0))])
-    for _ in range(200):
-        gf = O.p2g(ds.p, spec.grid, mass_eps=spec.mass_eps)
-        gap = C.plane_gaps(ds.p, spec.grid, plane, h)
-        u, act, lam = C.solve_with_plane(ds, gf, dt_settle, plane, gap)
-        ds.p = O.g2p(ds.p, spec.grid, u, dt_settle)
-        vmax = np.abs(ds.p.v).max()
-        ds.p.v[:] = 0.0
-        ds.p.B[:] = 0.0
-        if vmax < 1e-6:
-            return spec, plane, gf, gap, act, lam, u, ds
-    raise AssertionError("the contact did not settle")
+    return C.settle_hertz(dx, ppc_1d, indent, n_steps, dt, dt_settle)[:8]
 
 
 def test_unilateral_plane_contact_gives_the_hertz_pressure():

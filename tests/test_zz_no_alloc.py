@@ -1,15 +1,15 @@
 """The allocation-free energy change (osmpm_energy_change_noalloc) against
-the library's regular entry point for the same quantity.
+the FP64 oracle's energy change and the library's regular entry point for
+the same quantity.
 
 It serves callers that may not allocate device memory; its scratch is a
 fixed device array, so this test checks two calls in a row (the second call
-must not see the first call's leftovers) and the size limit.  The file is
-named to be collected last."""
-import ctypes
-
+must not see the first call's leftovers), the size limit and a particle
+outside the grid box.  The file is named to be collected last."""
 import numpy as np
 import pytest
 
+from oracle import osmpm_oracle as O
 from paper_2605_09097_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -65,9 +65,12 @@ def test_noalloc_energy_change_matches_entry_point(env, dim):
     u = 1e-4 * rng.standard_normal((nn, dim))
     s = 1e-4 * rng.standard_normal((nn, dim))
     ref = [dom.probe_energy_change(dt, u, s, a) for a in (1.0, 0.5)]
-    m = dom.get_grid(osmpm.OSMPM_FIELD_MASS)
-    vn = dom.get_grid(osmpm.OSMPM_FIELD_VN)
-    grid, parts, keep = _views(torch, osmpm, spec, m, vn, u, s)
+    # the oracle on the same grid fields (its own P2G)
+    gf = O.p2g(spec.particles, spec.grid, mass_eps=spec.mass_eps)
+    mask, vel = O.dirichlet_nodes(spec.grid, [], dt)
+    pr = O.make_problem(spec.particles, spec.grid, gf, dt, spec.gravity, mask, vel)
+    oracle = [O.energy_change(pr, u, s, a) for a in (1.0, 0.5)]
+    grid, parts, keep = _views(torch, osmpm, spec, gf.m, gf.vn, u, s)
     out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     for k, alpha in enumerate((1.0, 0.5)):   # two calls in a row on the shared scratch
@@ -75,7 +78,28 @@ def test_noalloc_energy_change_matches_entry_point(env, dim):
         assert st == osmpm.OSMPM_OK, osmpm.osmpm_last_error()
     torch.cuda.synchronize()
     got = out.cpu().numpy()
+    np.testing.assert_allclose(got, oracle, rtol=RTOL)
     np.testing.assert_allclose(got, ref, rtol=RTOL)
+
+
+def test_noalloc_reports_a_particle_outside_the_grid(env):
+    torch, osmpm = env
+    spec = W.perturb(W.block(2, n_cells=(5, 4), dx=0.1, E=1e5), 3)
+    nn = spec.grid.n_nodes
+    rng = np.random.default_rng(4)
+    u = 1e-4 * rng.standard_normal((nn, 2))
+    gf = O.p2g(spec.particles, spec.grid, mass_eps=spec.mass_eps)
+    grid, parts, keep = _views(torch, osmpm, spec, gf.m, gf.vn, u, u)
+    keep[0][0, 3] = spec.grid.origin[0] + 0.2 * spec.grid.dx   # support starts below node 0
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    st = osmpm.osmpm_energy_change_noalloc(grid, parts, 0.01, 1.0, out.data_ptr(), stream)
+    assert st == osmpm.OSMPM_E_OUT_OF_GRID, osmpm.osmpm_last_error()
+    assert np.isnan(out.item())
+    keep[0][0, 3] = float(spec.particles.x[3, 0])               # back inside: a clean call
+    st = osmpm.osmpm_energy_change_noalloc(grid, parts, 0.01, 1.0, out.data_ptr(), stream)
+    assert st == osmpm.OSMPM_OK, osmpm.osmpm_last_error()
+    assert np.isfinite(out.item())
 
 
 def test_noalloc_rejects_oversized_problem(env):
