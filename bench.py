@@ -56,6 +56,8 @@ ORACLE_SCHWARZ_ITERS_PER_STEP = 12.0
 ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
 AUTOTUNE_THREADS = [8, 12, 16]
+# (host threads, DOFs per DOF tile, PCG iterations per graph replay)
+AUTOTUNE_MULTI = [(32, 2048, 16), (64, 2048, 16), (64, 4096, 8)]
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
 # launch, from the ncu capture of the current kernel (the k_pcg profile
 # summary of this workload); None whenever the kernel changes
@@ -418,19 +420,37 @@ def run_batched(args, rank, local, world):
     dT = specs[0][3]
     units = sum(units_per_step(s[0], s[1], s[2].M) for s in specs)
     threads, tuned = args.threads, None
-    if threads == 0:
-        # the launch-shape autotuner's steps stand in for the warm-up
-        threads, tuned = osmpm.osmpm_autotune_batch(B, S, dT, schs, AUTOTUNE_THREADS)
+    multi = args.batch_mode == "multi"
+    shape = None
+    if multi:
+        if args.threads == 0:
+            shape, scores = osmpm.osmpm_autotune_multi(B, S, dT, schs, AUTOTUNE_MULTI)
+            tuned = {"x".join(map(str, c)): v for c, v in zip(AUTOTUNE_MULTI, scores)}
+        else:
+            shape = (args.threads, 0, 0)
+        threads = shape[0]
+
+        def batched_step():
+            return osmpm.osmpm_schwarz_couple_multi(B, S, dT, schs, *shape)[2]
+    else:
+        if threads == 0:
+            # the launch-shape autotuner's steps stand in for the warm-up
+            threads, tuned = osmpm.osmpm_autotune_batch(B, S, dT, schs, AUTOTUNE_THREADS)
+
+        def batched_step():
+            osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=threads)
+            return None
     for _ in range(args.warmup if tuned is None else 0):
-        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=threads)
+        batched_step()
     torch.cuda.synchronize()
     barrier(world)
     launches0 = osmpm.launch_count()
     clocks = ClockSampler(local)
     clocks.start()
     t0 = time.perf_counter()
+    service = []
     for _ in range(args.steps):
-        osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=threads)
+        service.append(batched_step())
     torch.cuda.synchronize()
     t = max_over_ranks(time.perf_counter() - t0, world)
     clk = clocks.stop()
@@ -447,6 +467,8 @@ def run_batched(args, rank, local, world):
             "data": "synthetic",
             "config": {"workload": f"batched_inclusion_{args.instances}_literal",
                        "instances": args.instances, "host_threads": threads,
+                       "batch_mode": args.batch_mode, "launch_shape": shape,
+                       "pcg_service": service if multi else None,
                        "autotune_us_per_cg_iter": tuned,
                        "particles": sum(s[0].particles.n + s[1].particles.n for s in specs),
                        "units_per_step": units, "precision": args.precision,
@@ -528,18 +550,24 @@ def run_fold(args, rank, local, world):
 
 def run_fold_solve(args, rank, local, world):
     """Single-domain implicit steps of the fine band of the scaled 3D fold
-    (3.07M particles at dx 0.0025, mixed precision, streaming PCG) with
-    seeded velocities, B and F: the configuration of the tiled
-    Hessian-vector product.  CUDA events around each step on the domain's
-    stream; the library's PCG events give the time per PCG iteration."""
+    (3.07M particles at dx 0.0025, mixed precision, streaming PCG), folded
+    on its own: the nodes of its edge x = 0.2 clamped, those of its edge
+    x = 0.8 turned about the fold axis (x = 0.5, z = 0.01, parallel to y) at
+    the fold's rate of 90 degrees per 400 steps of 0.01 s, dt = 0.0025.  The
+    configuration of the tiled Hessian-vector product.  CUDA events around
+    each step on the domain's stream; the library's PCG events give the time
+    per PCG iteration."""
     import torch
     torch.cuda.set_device(local)
     from paper_2605_09097_gb300 import build
     build.build()
     from paper_2605_09097_gb300 import osmpm
-    _, cS, sch, dT = W.fold3d(dx_f=0.0025, band=(0.2, 0.8))
-    spec = W.perturb(cS, 7, v_scale=0.05)
-    spec = dataclasses.replace(spec, hvp_mode=args.hvp_mode)
+    cB, cS, sch, dT = W.fold3d(dx_f=0.0025, band=(0.2, 0.8))
+    h = cS.grid.dx
+    clamp = W.Dirichlet(lo=(-W.BIG, -W.BIG, -W.BIG), hi=(0.2 + 0.5 * h, W.BIG, W.BIG),
+                        comp_mask=0b111)
+    turn = dataclasses.replace(cB.dirichlet[1], lo=(0.8 - 1.5 * h, -W.BIG, -W.BIG))
+    spec = dataclasses.replace(cS, dirichlet=[clamp, turn], hvp_mode=args.hvp_mode)
     dt = dT / sch.M
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -590,6 +618,9 @@ def main():
     ap.add_argument("--threads", type=int, default=0,
                     help="host threads of the batched workload; 0: chosen by the autotuner")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--batch-mode", choices=["threads", "multi"], default="threads",
+                    help="batched: per-pair PCG launches from a host thread pool, or the "
+                         "batched PCG service (mixed precision)")
     args = ap.parse_args()
     rank, local, world = dist_init(args.gpus)
     if args.impl == "reference":

@@ -296,6 +296,58 @@ osmpm_status osmpm_autotune_batch(osmpm_domain* const* coarse, osmpm_domain* con
                                   const int32_t* candidates, int32_t n_candidates,
                                   int32_t* best, double* us_per_cg_iter);
 
+/* Batched OS-MPM with one PCG service (the project's batching line, not a
+ * passage of the paper; mixed-precision domains).  Advances n independent
+ * pairs by one global step each, like osmpm_schwarz_couple_batch (host
+ * threads drive the pairs' Alg. 1 and Newton loops on their own streams),
+ * but no pair launches a PCG of its own: each Newton system goes to a
+ * service thread, which solves every system handed in meanwhile with one
+ * batched Jacobi PCG (the streaming PCG with the block-tiled
+ * Hessian-vector product) over a work list of (pair's domain, particle
+ * tile) and (pair's domain, DOF tile), each system with its own scalars
+ * and stopping test; the iterations run in chunks replayed from a CUDA
+ * graph captured for the batch, with a look at the stop flags after each.
+ * Systems handed in during a batch join the next.  Results per pair are
+ * those of osmpm_schwarz_couple within the solver tolerances.
+ *  - desc: n_threads host threads (0: 32), dof_tile DOFs per DOF tile
+ *    (0: 2048), chunk iterations per graph replay (0: 16).
+ *  - stats / status per pair as for osmpm_schwarz_couple_batch; ms (may be
+ *    NULL) receives the service's counters.
+ * Errors: OSMPM_E_UNSUPPORTED unless every domain is mixed precision (1)
+ * and all share one dimension; OSMPM_E_INVALID for bad arguments. */
+typedef struct osmpm_multi_desc {
+  int32_t n_threads;
+  int32_t dof_tile;
+  int32_t chunk;
+  int32_t reserved;
+} osmpm_multi_desc;
+
+typedef struct osmpm_multi_stats {
+  int64_t batches;     /* batched PCG solves */
+  int64_t instances;   /* Newton systems solved, summed over the batches */
+  int64_t chunks;      /* graph replays (chunks of iterations) */
+  int64_t max_batch;   /* most systems in one batch */
+  int64_t particles;   /* particles of the systems, summed over the batches */
+  int64_t dofs;        /* grid DOFs of the systems, summed over the batches */
+  double device_ms;    /* device time of the batched PCGs (CUDA events) */
+} osmpm_multi_stats;
+
+osmpm_status osmpm_schwarz_couple_multi(osmpm_domain* const* coarse, osmpm_domain* const* fine,
+                                        int32_t n, double dT, const osmpm_schwarz_desc* sdesc,
+                                        const osmpm_multi_desc* desc, osmpm_stats* stats,
+                                        osmpm_status* status, osmpm_multi_stats* ms);
+
+/* Launch-shape autotuner of osmpm_schwarz_couple_multi: runs one untimed
+ * and then one timed multi step per candidate descriptor (host threads, DOF
+ * tile, iterations per graph replay); these are real global steps, so the
+ * pairs advance by n_candidates + 1 steps.  Scored by wall time per PCG
+ * iteration summed over the pairs; *best receives the index of the best
+ * candidate, us_per_cg_iter (may be NULL) the n_candidates scores. */
+osmpm_status osmpm_autotune_multi(osmpm_domain* const* coarse, osmpm_domain* const* fine,
+                                  int32_t n, double dT, const osmpm_schwarz_desc* sdesc,
+                                  const osmpm_multi_desc* candidates, int32_t n_candidates,
+                                  int32_t* best, double* us_per_cg_iter);
+
 /* Reverse mode, recording.  enable = 1 discards any earlier record and
  * makes every later osmpm_step of dom keep, in device memory from the
  * domain's allocator, its input particle state (x, v, B, F), its converged

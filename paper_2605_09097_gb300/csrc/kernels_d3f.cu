@@ -2,3 +2,4 @@
 #include "osmpm_kernels.cuh"
 
 template struct osmpm::Kernels<3, float>;
+template struct osmpm::MultiKernels<3>;

@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <chrono>
@@ -97,6 +99,10 @@ PartPtrsT<R> typed(const PartMem& m) {
   return p;
 }
 
+namespace {
+struct PcgBatcher;
+}
+
 struct osmpm_domain {
   osmpm_domain_desc desc{};
   int dim = 2;
@@ -144,6 +150,10 @@ struct osmpm_domain {
   // cooperative PCG grids that may run at once (set by the batched entry
   // point); each PCG grid uses at most 1/pcg_share of the device
   int pcg_share = 1;
+  // the batched PCG service of osmpm_schwarz_couple_multi (set while a
+  // multi call drives the domain): Newton systems go there instead of to
+  // a PCG launch of their own
+  struct PcgBatcher* batcher = nullptr;
 
   // reverse-mode tape (osmpm_record / osmpm_adjoint): per recorded step its
   // input particle state, the converged grid displacement and the DOF mask
@@ -759,12 +769,255 @@ osmpm_status pcg_finish(osmpm_domain* d, bool timed, SolveStats& st) {
   return OSMPM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batched PCG service (osmpm_schwarz_couple_multi, mixed precision).  The
+// pairs' host threads run Alg. 1 and Newton as in osmpm_schwarz_couple;
+// when a Newton iteration needs its PCG, the thread enqueues the gradient
+// and PCG start on its stream, waits for it and hands the system to this
+// service.  The service thread takes every system handed in meanwhile and
+// runs one batched streaming PCG over all of them (osmpm_multi.cuh): a work
+// list of (instance, particle tile) and (instance, DOF tile), per-instance
+// scalars and stop flags, iterations replayed in chunks from a CUDA graph
+// captured for the batch; systems handed in during a batch join the next.
+// ---------------------------------------------------------------------------
+struct PcgBatcher {
+  int dim = 2;
+  int dof_tile = 2048;  // DOFs per DOF tile
+  int chunk = 16;       // iterations between looks at the stop flags
+  cudaStream_t stream = nullptr;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  struct Req {
+    osmpm_domain* d;
+    double dt;
+    bool done;
+    osmpm_status st;
+  };
+  std::vector<Req*> queue;
+  bool stop = false;
+  std::thread th;
+  // device and pinned host work areas, grown on demand
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  char* host = nullptr;
+  size_t host_bytes = 0;
+  int* pending_host = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::string error;
+  osmpm_multi_stats stats{};
+
+  osmpm_status open(int dim_, int dof_tile_, int chunk_) {
+    dim = dim_;
+    dof_tile = dof_tile_ > 0 ? dof_tile_ : 2048;
+    chunk = chunk_ > 0 ? chunk_ : 16;
+    CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaMallocHost(&pending_host, sizeof(int)));
+    CUDA_TRY(cudaEventCreate(&ev[0]));
+    CUDA_TRY(cudaEventCreate(&ev[1]));
+    int dev_id = 0;
+    cudaGetDevice(&dev_id);
+    th = std::thread([this, dev_id] {
+      cudaSetDevice(dev_id);
+      loop();
+    });
+    return OSMPM_OK;
+  }
+
+  void close() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv_work.notify_all();
+    if (th.joinable()) th.join();
+    if (stream) cudaStreamSynchronize(stream);
+    if (dev) cudaFreeAsync(dev, stream);
+    if (stream) cudaStreamSynchronize(stream);
+    if (host) cudaFreeHost(host);
+    if (pending_host) cudaFreeHost(pending_host);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (stream) cudaStreamDestroy(stream);
+  }
+
+  // Called by a pair's thread with its system prepared on its (synchronised)
+  // stream; returns when the PCG of that system has finished.
+  osmpm_status solve(osmpm_domain* d, double dt) {
+    Req r{d, dt, false, OSMPM_OK};
+    std::unique_lock<std::mutex> lk(mu);
+    queue.push_back(&r);
+    cv_work.notify_one();
+    cv_done.wait(lk, [&] { return r.done; });
+    return r.st;
+  }
+
+  void loop() {
+    for (;;) {
+      std::vector<Req*> batch;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+        if (queue.empty()) return;
+        batch.swap(queue);
+      }
+      const osmpm_status st = run(batch);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        for (Req* r : batch) {
+          r->st = st;
+          r->done = true;
+        }
+      }
+      cv_done.notify_all();
+    }
+  }
+
+  template <class T>
+  static size_t up(size_t b) {
+    return (b + 255) & ~size_t(255);
+  }
+
+  osmpm_status run(const std::vector<Req*>& batch) {
+    const int n = (int)batch.size();
+    const int TP = dim == 2 ? MultiKernels<2>::particle_tile() : MultiKernels<3>::particle_tile();
+    std::vector<PcgArgsT<float>> inst((size_t)n);
+    std::vector<MultiInfo> info((size_t)n);
+    std::vector<MultiTile> pt, dtl;
+    long long particles = 0, dofs = 0;
+    for (int i = 0; i < n; ++i) {
+      osmpm_domain* d = batch[(size_t)i]->d;
+      inst[(size_t)i] = pcg_args<float>(d, batch[(size_t)i]->dt);
+      info[(size_t)i].pt0 = (int)pt.size();
+      for (int64_t p0 = 0; p0 < d->n; p0 += TP)
+        pt.push_back(MultiTile{i, (int)p0, (int)std::min<int64_t>(d->n, p0 + TP)});
+      info[(size_t)i].npt = (int)pt.size() - info[(size_t)i].pt0;
+      info[(size_t)i].dt0 = (int)dtl.size();
+      const int64_t ndof = (int64_t)d->dim * d->geo.nn;
+      for (int64_t q0 = 0; q0 < ndof; q0 += dof_tile)
+        dtl.push_back(MultiTile{i, (int)q0, (int)std::min<int64_t>(ndof, q0 + dof_tile)});
+      info[(size_t)i].ndt = (int)dtl.size() - info[(size_t)i].dt0;
+      particles += d->n;
+      dofs += ndof;
+    }
+    const int stride = (int)std::max(pt.size(), dtl.size());
+    const size_t b_inst = up<char>(sizeof(PcgArgsT<float>) * n), b_info = up<char>(sizeof(MultiInfo) * n);
+    const size_t b_pt = up<char>(sizeof(MultiTile) * pt.size()), b_dt = up<char>(sizeof(MultiTile) * dtl.size());
+    const size_t b_part = up<char>(sizeof(double) * 2 * stride), b_pend = 256;
+    const size_t in_bytes = b_inst + b_info + b_pt + b_dt;
+    const size_t need = in_bytes + b_part + b_pend;
+    if (need > dev_bytes) {
+      if (dev) cudaFreeAsync(dev, stream);
+      dev = nullptr;
+      dev_bytes = 0;
+      const size_t want = need + need / 2;
+      if (cudaMallocAsync(&dev, want, stream) != cudaSuccess) return set_error(OSMPM_E_NOMEM, "batched PCG: device memory");
+      dev_bytes = want;
+    }
+    if (in_bytes > host_bytes) {
+      if (host) {
+        cudaStreamSynchronize(stream);
+        cudaFreeHost(host);
+      }
+      host = nullptr;
+      host_bytes = 0;
+      const size_t want = in_bytes + in_bytes / 2;
+      if (cudaMallocHost(&host, want) != cudaSuccess) return set_error(OSMPM_E_NOMEM, "batched PCG: pinned memory");
+      host_bytes = want;
+    }
+    memcpy(host, inst.data(), sizeof(PcgArgsT<float>) * n);
+    memcpy(host + b_inst, info.data(), sizeof(MultiInfo) * n);
+    memcpy(host + b_inst + b_info, pt.data(), sizeof(MultiTile) * pt.size());
+    memcpy(host + b_inst + b_info + b_pt, dtl.data(), sizeof(MultiTile) * dtl.size());
+    char* dv = (char*)dev;
+    if (cudaMemcpyAsync(dv, host, in_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+      return set_error(OSMPM_E_CUDA, "batched PCG: upload");
+    MultiArgs m{};
+    m.inst = (const PcgArgsT<float>*)dv;
+    m.info = (const MultiInfo*)(dv + b_inst);
+    m.pt = (const MultiTile*)(dv + b_inst + b_info);
+    m.n_pt = (int)pt.size();
+    m.dtl = (const MultiTile*)(dv + b_inst + b_info + b_pt);
+    m.n_dt = (int)dtl.size();
+    m.n_inst = n;
+    m.part = (double*)(dv + in_bytes);
+    m.stride = stride;
+    m.pending = (int*)(dv + in_bytes + b_part);
+    auto launch_chunk = [&] {
+      for (int c = 0; c < chunk; ++c) {
+        if (dim == 2) MultiKernels<2>::iteration(m, stream);
+        else MultiKernels<3>::iteration(m, stream);
+      }
+      if (dim == 2) MultiKernels<2>::pending(m, stream);
+      else MultiKernels<3>::pending(m, stream);
+      cudaMemcpyAsync(pending_host, m.pending, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    };
+    cudaEventRecord(ev[0], stream);
+    if (dim == 2) MultiKernels<2>::start(m, stream);
+    else MultiKernels<3>::start(m, stream);
+    // the chunk as a CUDA graph captured for this batch (its arguments are
+    // fixed for the batch), replayed until every instance stopped
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const long long before = g_launch_count.load();
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      launch_chunk();
+      if (cudaStreamEndCapture(stream, &graph) != cudaSuccess || !graph ||
+          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+    }
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    const long long per_chunk = g_launch_count.load() - before;
+    if (exec) g_launch_count -= per_chunk;  // replays count them
+    int chunks = 0;
+    cudaError_t e = cudaSuccess;
+    const int max_chunks = 1 + (int)((int64_t)batch[0]->d->desc.cg_max / chunk) + 1;
+    for (;;) {
+      if (exec) {
+        e = cudaGraphLaunch(exec, stream);
+        g_launch_count += per_chunk;
+      } else {
+        launch_chunk();
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (e != cudaSuccess) break;
+      ++chunks;
+      if (*pending_host == 0 || chunks > max_chunks) break;
+    }
+    cudaEventRecord(ev[1], stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return set_error(OSMPM_E_CUDA, "batched PCG: %s", cudaGetErrorString(e));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    stats.batches += 1;
+    stats.instances += n;
+    stats.chunks += chunks;
+    stats.device_ms += ms;
+    stats.particles += particles;
+    stats.dofs += dofs;
+    if (n > stats.max_batch) stats.max_batch = n;
+    return OSMPM_OK;
+  }
+};
+
 // One Newton iteration's gradient and PCG solve, up to the host's look at
 // max |delta|: a replayed graph where launch_mode 0 allows one, else the
 // same work launched directly; the streaming PCG always launches directly.
 osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check, SolveStats& st) {
   const int64_t work = pcg_work(d);
   const bool timed = d->time_hvp && !d->ev.empty();
+  if (d->batcher) {
+    // the batched PCG service solves the system with the other pairs' ones
+    enqueue_gradient(d, dt, first, check);
+    CUDA_TRY(cudaStreamSynchronize(d->stream));
+    CUDA_TRY(cudaGetLastError());
+    OSMPM_TRY(d->batcher->solve(d, dt));
+    DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
+    OSMPM_TRY(sync_scalars(d));
+    return pcg_finish(d, false, st);
+  }
   if (pcg_streaming(d, dt, work)) {
     enqueue_gradient(d, dt, first, check);
     CUDA_TRY(cudaGetLastError());
@@ -2173,6 +2426,111 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
   }
   if (first_bad >= 0) return fail(worst, "pair %d: %s", first_bad, msg[(size_t)first_bad].c_str());
   if (worst != OSMPM_OK) return fail(worst, "at least one pair hit k_max");
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_schwarz_couple_multi(osmpm_domain* const* coarse, osmpm_domain* const* fine,
+                                        int32_t n, double dT, const osmpm_schwarz_desc* sdesc,
+                                        const osmpm_multi_desc* desc, osmpm_stats* stats,
+                                        osmpm_status* status, osmpm_multi_stats* ms) {
+  if (n < 0 || !coarse || !fine || !sdesc || !desc)
+    return fail(OSMPM_E_INVALID, "null argument or n < 0");
+  if (desc->n_threads < 0 || desc->dof_tile < 0 || desc->chunk < 0 || desc->reserved != 0)
+    return fail(OSMPM_E_INVALID, "multi descriptor: counts >= 0, reserved 0");
+  if (ms) memset(ms, 0, sizeof(*ms));
+  if (n == 0) return OSMPM_OK;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!coarse[i] || !fine[i]) return fail(OSMPM_E_INVALID, "pair %d: null domain", i);
+    if (coarse[i]->prec != 1 || fine[i]->prec != 1)
+      return fail(OSMPM_E_UNSUPPORTED, "pair %d: the batched PCG serves mixed-precision domains", i);
+    if (coarse[i]->dim != coarse[0]->dim || fine[i]->dim != coarse[0]->dim)
+      return fail(OSMPM_E_UNSUPPORTED, "pair %d: every domain must have the same dimension", i);
+    for (int32_t j = 0; j < i; ++j)
+      if (coarse[i] == coarse[j] || fine[i] == fine[j] || coarse[i] == fine[j] || fine[i] == coarse[j])
+        return fail(OSMPM_E_INVALID, "pairs %d and %d share a domain", j, i);
+  }
+  PcgBatcher b;
+  OSMPM_TRY(b.open(coarse[0]->dim, desc->dof_tile, desc->chunk));
+  int threads = desc->n_threads > 0 ? desc->n_threads : 32;
+  if (threads > n) threads = n;
+  std::vector<osmpm_status> st((size_t)n, OSMPM_OK);
+  std::vector<std::string> msg((size_t)n);
+  for (int32_t i = 0; i < n; ++i) {
+    coarse[i]->batcher = fine[i]->batcher = &b;
+    coarse[i]->graph_hold = fine[i]->graph_hold = true;
+  }
+  std::atomic<int32_t> next{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int32_t i = next.fetch_add(1);
+      if (i >= n) break;
+      osmpm_stats s1;
+      st[(size_t)i] = osmpm_schwarz_couple(coarse[i], fine[i], dT, &sdesc[i], &s1);
+      if (stats) stats[i] = s1;
+      if (st[(size_t)i] != OSMPM_OK) msg[(size_t)i] = g_last_error;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < threads; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& t : pool) t.join();
+  for (int32_t i = 0; i < n; ++i) {
+    coarse[i]->batcher = fine[i]->batcher = nullptr;
+    coarse[i]->graph_hold = fine[i]->graph_hold = false;
+  }
+  if (ms) *ms = b.stats;
+  b.close();
+  osmpm_status worst = OSMPM_OK;
+  int32_t first_bad = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    if (status) status[i] = st[(size_t)i];
+    if (st[(size_t)i] != OSMPM_OK && st[(size_t)i] != OSMPM_W_SCHWARZ_MAXITER && first_bad < 0) {
+      first_bad = i;
+      worst = st[(size_t)i];
+    }
+    if (worst == OSMPM_OK && st[(size_t)i] == OSMPM_W_SCHWARZ_MAXITER) worst = OSMPM_W_SCHWARZ_MAXITER;
+  }
+  if (first_bad >= 0) return fail(worst, "pair %d: %s", first_bad, msg[(size_t)first_bad].c_str());
+  if (worst != OSMPM_OK) return fail(worst, "at least one pair hit k_max");
+  return OSMPM_OK;
+}
+
+osmpm_status osmpm_autotune_multi(osmpm_domain* const* coarse, osmpm_domain* const* fine, int32_t n,
+                                  double dT, const osmpm_schwarz_desc* sdesc,
+                                  const osmpm_multi_desc* candidates, int32_t n_candidates,
+                                  int32_t* best, double* us_per_cg_iter) {
+  if (!candidates || n_candidates < 1 || !best || n < 1)
+    return fail(OSMPM_E_INVALID, "need n >= 1 pairs, candidates and best");
+  std::vector<osmpm_stats> stats((size_t)n);
+  auto step = [&](const osmpm_multi_desc& md, double* seconds, int64_t* cg) -> osmpm_status {
+    CUDA_TRY(cudaDeviceSynchronize());
+    const auto t0 = std::chrono::steady_clock::now();
+    const osmpm_status st = osmpm_schwarz_couple_multi(coarse, fine, n, dT, sdesc, &md, stats.data(),
+                                                       nullptr, nullptr);
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (st != OSMPM_OK && st != OSMPM_W_SCHWARZ_MAXITER) return st;
+    *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *cg = 0;
+    for (const auto& x : stats) *cg += x.cg_iters;
+    return OSMPM_OK;
+  };
+  double sec = 0.0;
+  int64_t cg = 0;
+  OSMPM_TRY(step(candidates[0], &sec, &cg));  // warm-up: first-use allocations
+  double best_score = INFINITY;
+  *best = 0;
+  for (int32_t c = 0; c < n_candidates; ++c) {
+    OSMPM_TRY(step(candidates[c], &sec, &cg));
+    const double score = 1e6 * sec / (double)std::max<int64_t>(cg, 1);
+    if (us_per_cg_iter) us_per_cg_iter[c] = score;
+    if (score < best_score) {
+      best_score = score;
+      *best = c;
+    }
+  }
   return OSMPM_OK;
 }
 

@@ -86,6 +86,17 @@ struct AdjointKernels {
                      cudaStream_t s);
 };
 
+// Launchers of the batched streaming PCG over many domains (mixed
+// precision; osmpm_multi.cuh).
+template <int D>
+struct MultiKernels {
+  static void start(const MultiArgs& m, cudaStream_t s);
+  // one PCG iteration of every instance still running
+  static void iteration(const MultiArgs& m, cudaStream_t s);
+  static void pending(const MultiArgs& m, cudaStream_t s);
+  static int particle_tile();  // particles per tile (one per thread of a block)
+};
+
 template <int D, typename R>
 struct Kernels {
   static void morton_keys(const double* x, int64_t n, const GridGeo& g, uint64_t* keys,

@@ -11,6 +11,7 @@
 #include "osmpm_pcg.cuh"
 #include "osmpm_tile.cuh"
 #include "osmpm_contact.cuh"
+#include "osmpm_multi.cuh"
 
 namespace osmpm {
 
@@ -1283,6 +1284,28 @@ template <int D, typename R>
 void Kernels<D, R>::barrier_timeout_check(unsigned* words, int* err, cudaStream_t s) {
   g_launch_count += 1;
   k_barrier_timeout_check<D, R><<<2, 32, 0, s>>>(words, err);
+}
+
+template <int D>
+void MultiKernels<D>::start(const MultiArgs& m, cudaStream_t s) {
+  g_launch_count += 1;
+  k_m_start<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
+}
+template <int D>
+void MultiKernels<D>::iteration(const MultiArgs& m, cudaStream_t s) {
+  g_launch_count += 3;
+  k_m_hvp<D><<<std::max(1, std::min(m.n_pt, kRedBlocksMax)), TileCap<D>::THREADS, 0, s>>>(m);
+  k_m_alpha<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
+  k_m_beta<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
+}
+template <int D>
+void MultiKernels<D>::pending(const MultiArgs& m, cudaStream_t s) {
+  g_launch_count += 1;
+  k_m_pending<D><<<1, kThreads, 0, s>>>(m);
+}
+template <int D>
+int MultiKernels<D>::particle_tile() {
+  return TileCap<D>::THREADS;
 }
 
 #undef OSMPM_NB

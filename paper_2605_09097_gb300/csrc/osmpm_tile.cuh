@@ -19,7 +19,7 @@ namespace osmpm {
 // Shared tile capacity in nodes, per dimension.
 template <int D>
 struct TileCap {
-  static constexpr int NODES = 1024;
+  static constexpr int NODES = (D == 2) ? 1024 : 768;
   static constexpr int THREADS = (D == 2) ? 256 : 128;  // one particle per thread
 };
 
@@ -252,36 +252,51 @@ __device__ __forceinline__ void group_reduce_scatter(float (&v)[NV], int r) {
   }
 }
 
-// Streaming-PCG Hessian-vector product, mixed precision, block tiles:
-// q = K p on the free DOFs (q = a.w[0], zeroed by the start and beta
-// kernels; p = a.s[0]) and p:Kp = sum_p G:Y into S->pq.  The particle
-// Hessian is recomputed from the Newton iterate a.u (no cached blocks or
-// stencils): per particle it reads x, F^n, V0, mu, lam.  Blocks loop over
-// the particle tiles (grid stride), so the launch may be smaller than the
-// tile count.
+// Shared memory of one block of the tiled Hessian-vector product.
 template <int D>
-__global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<float> a) {
-  if (__ldcg(&a.S->cg_done)) return;
+struct HvpTileShared {
+  static constexpr int CAP = TileCap<D>::NODES;
+  float su[D][CAP];   // Newton iterate u
+  float sd[D][CAP];   // direction p
+  // K p accumulators in FP64: a node sums the contributions of up to 27
+  // cells; for smooth directions they nearly cancel, and an FP32 sum loses
+  // the small remainder (the plate-bending modes of a thin body)
+  double sq[D][CAP];
+  TileBox<D> box;
+};
+
+// The tiled Hessian-vector product of one run of particles [p0, p1)
+// (p1 - p0 <= blockDim.x, one particle per thread; the whole block calls
+// it): q = a.w[0] += K p on the free DOFs with p = a.s[0], the particle
+// Hessian recomputed from the Newton iterate a.u (no cached blocks or
+// stencils: per particle it reads x, F^n, V0, mu, lam); acc += this run's
+// share of p.Kp = sum_p G:Y.  The block stages the node box of the run's
+// stencils in shared memory (gathers from it, scatters into FP64 shared
+// accumulators flushed with one global atomic per tile node and
+// component); a warp of full cells (aligned groups of 2^D particles with one
+// stencil base) first reduce-scatters its contributions over each group.
+// A run whose node box exceeds the tile works on global memory.
+template <int D>
+__device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t p0, int64_t p1,
+                                         HvpTileShared<D>& sh, double& acc) {
   constexpr int DD = D * D;
   constexpr int K = (D == 2) ? 9 : 27;
   constexpr int CAP = TileCap<D>::NODES;
-  __shared__ float su[D][CAP];   // Newton iterate u
-  __shared__ float sd[D][CAP];   // direction p
-  __shared__ float sq[D][CAP];   // K p accumulators
-  __shared__ TileBox<D> box;
   constexpr int GL = 1 << D;                 // particles per full cell (2 per axis)
   constexpr int KC = 9;                      // stencil nodes per scatter chunk
   constexpr int NVP = ((KC * D + GL - 1) / GL) * GL;
+  auto& su = sh.su;
+  auto& sd = sh.sd;
+  auto& sq = sh.sq;
+  auto& box = sh.box;
   const GridGeo& g = a.g;
   const int64_t n = a.P.n;
   const double* pv = a.s[0];
   double* q = a.w[0];
   const int lane = threadIdx.x & 31, gr = lane & (GL - 1);
-  double acc[1] = {0.0};
-  const int64_t tiles = (n + blockDim.x - 1) / blockDim.x;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t pi = t * blockDim.x + threadIdx.x;
-    const bool in = pi < n;
+  {
+    const int64_t pi = p0 + threadIdx.x;
+    const bool in = pi < p1;
     double xp[D];
     int base[D];
     float w[D][3], dw[D][3];
@@ -315,7 +330,7 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<f
         for (int c = 0; c < D; ++c) {
           su[c][l] = (float)__ldg(&a.u[c * g.nn + gi]);
           sd[c][l] = (float)__ldcg(&pv[c * g.nn + gi]);
-          sq[c][l] = 0.0f;
+          sq[c][l] = 0.0;
         }
       }
       __syncthreads();
@@ -377,7 +392,7 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<f
       float Y[DD];
       const float qf = hessian_apply_f32<D>(Gu, Gd, Fn, (float)a.P.mu[pi], (float)a.P.lam[pi],
                                             (float)a.P.vol0[pi], Y);
-      acc[0] += (double)qf;
+      acc += (double)qf;
       if (grouped) {
         // the lanes of one cell share their 3^D target nodes: reduce-scatter
         // each chunk of KC nodes (one stencil layer) over the group, then
@@ -407,7 +422,7 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<f
             if (idx < KC * D) {
               const int kk = idx / D, c = idx - kk * D;
               const int k = (D == 2 ? 0 : 9 * o2c) + kk;
-              atomicAdd(&sq[c][lb + tile_local<D>(box, k % 3, (k / 3) % 3, k / 9)], v[j]);
+              atomicAdd(&sq[c][lb + tile_local<D>(box, k % 3, (k / 3) % 3, k / 9)], (double)v[j]);
             }
           }
           if (D == 2) break;  // one chunk holds the whole 2D stencil
@@ -429,7 +444,7 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<f
         if (tiled) {
           const int l = lb + tile_local<D>(box, o0, o1, o2);
 #pragma unroll
-          for (int c = 0; c < D; ++c) atomicAdd(&sq[c][l], f[c]);
+          for (int c = 0; c < D; ++c) atomicAdd(&sq[c][l], (double)f[c]);
         } else {
           const int64_t gi =
               gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
@@ -450,10 +465,26 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<f
         if (!fm) continue;
 #pragma unroll
         for (int c = 0; c < D; ++c)
-          if (((fm >> c) & 1u) && sq[c][l] != 0.0f) atomicAdd(&q[c * g.nn + gi], (double)sq[c][l]);
+          if (((fm >> c) & 1u) && sq[c][l] != 0.0) atomicAdd(&q[c * g.nn + gi], sq[c][l]);
       }
     }
     __syncthreads();  // the tile arrays are reused by the next tile
+  }
+}
+
+// Streaming-PCG Hessian-vector product, mixed precision, block tiles
+// (hvp_tile over runs of TileCap<D>::THREADS particles, grid stride); p.Kp
+// into S->pq.
+template <int D>
+__global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<float> a) {
+  if (__ldcg(&a.S->cg_done)) return;
+  __shared__ HvpTileShared<D> sh;
+  const int64_t n = a.P.n;
+  double acc[1] = {0.0};
+  const int64_t tiles = (n + blockDim.x - 1) / blockDim.x;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int64_t p0 = t * blockDim.x;
+    hvp_tile<D>(a, p0, p0 + blockDim.x < n ? p0 + blockDim.x : n, sh, acc[0]);
   }
   double tot[1];
   if (grid_sum<1>(acc, a.partials, &a.S->counter, tot) && threadIdx.x == 0) a.S->pq = tot[0];

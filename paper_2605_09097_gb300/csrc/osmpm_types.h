@@ -92,4 +92,30 @@ struct PcgArgsT {
   const double* u;      // the Newton iterate (the tiled product recomputes the Hessian)
 };
 
+// Batched PCG over many domains (osmpm_multi.cuh): items [lo, hi)
+// (particles or DOFs) of instance `inst`.
+struct MultiTile {
+  int inst;
+  int lo, hi;
+};
+
+// Where an instance's tiles sit in the two work lists.
+struct MultiInfo {
+  int pt0, npt;  // particle tiles
+  int dt0, ndt;  // DOF tiles
+};
+
+struct MultiArgs {
+  const PcgArgsT<float>* inst;  // the instances' PCG arguments (domain buffers, scalars)
+  const MultiInfo* info;
+  const MultiTile* pt;
+  int n_pt;
+  const MultiTile* dtl;
+  int n_dt;
+  int n_inst;
+  double* part;   // tile partials, row k at part[k * stride + tile]
+  int stride;
+  int* pending;   // instances whose PCG is still running (written by k_m_pending)
+};
+
 }  // namespace osmpm

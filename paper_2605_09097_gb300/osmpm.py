@@ -113,6 +113,20 @@ class osmpm_plane(Structure):
                 ("cand_hi", c_double), ("spacing", c_double)]
 
 
+class osmpm_multi_desc(Structure):
+    _fields_ = [("n_threads", c_int32), ("dof_tile", c_int32), ("chunk", c_int32),
+                ("reserved", c_int32)]
+
+
+class osmpm_multi_stats(Structure):
+    _fields_ = [("batches", c_int64), ("instances", c_int64), ("chunks", c_int64),
+                ("max_batch", c_int64), ("particles", c_int64), ("dofs", c_int64),
+                ("device_ms", c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class osmpm_noalloc_grid(Structure):
     _fields_ = [("dim", c_int32), ("origin", c_double * 3), ("dx", c_double),
                 ("res", c_int32 * 3), ("mass_eps", c_double), ("gravity", c_double * 3),
@@ -159,6 +173,12 @@ _sig = {
     "osmpm_check_wait_timeout": (c_int32, [c_void_p]),
     "osmpm_record": (c_int32, [c_void_p, c_int32]),
     "osmpm_set_plane": (c_int32, [c_void_p, POINTER(osmpm_plane)]),
+    "osmpm_autotune_multi": (c_int32, [c_void_p, c_void_p, c_int32, c_double, c_void_p,
+                                       POINTER(osmpm_multi_desc), c_int32, POINTER(c_int32),
+                                       POINTER(c_double)]),
+    "osmpm_schwarz_couple_multi": (c_int32, [c_void_p, c_void_p, c_int32, c_double, c_void_p,
+                                             POINTER(osmpm_multi_desc), c_void_p, c_void_p,
+                                             POINTER(osmpm_multi_stats)]),
     "osmpm_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, POINTER(osmpm_adjoint_out),
                                 POINTER(osmpm_stats)]),
     "osmpm_energy_change_noalloc": (c_int32, [POINTER(osmpm_noalloc_grid),
@@ -546,6 +566,45 @@ def osmpm_schwarz_couple_batch(coarse: List[Domain], fine: List[Domain], dT: flo
     _check(_lib.osmpm_schwarz_couple_batch(cs, fs, n, dT, sd, n_threads, st, status),
            "osmpm_schwarz_couple_batch", warn_ok=True)
     return [s.as_dict() for s in st], list(status)
+
+
+def osmpm_schwarz_couple_multi(coarse: List[Domain], fine: List[Domain], dT: float, schs,
+                               n_threads: int = 0, dof_tile: int = 0, chunk: int = 0):
+    """One global step of every pair (mixed precision) with the batched PCG
+    service: host threads drive the pairs, every Newton system is solved in a
+    batched PCG together with the systems of the other pairs.  Returns
+    (stats list, status list, service counters)."""
+    n = len(coarse)
+    cs = (c_void_p * n)(*[d.h.value for d in coarse])
+    fs = (c_void_p * n)(*[d.h.value for d in fine])
+    sd = (osmpm_schwarz_desc * n)(*[make_schwarz_desc(s) for s in schs])
+    st = (osmpm_stats * n)()
+    status = (c_int32 * n)()
+    md = osmpm_multi_desc(int(n_threads), int(dof_tile), int(chunk), 0)
+    ms = osmpm_multi_stats()
+    _check(_lib.osmpm_schwarz_couple_multi(cs, fs, n, dT, sd, ctypes.byref(md), st, status,
+                                           ctypes.byref(ms)),
+           "osmpm_schwarz_couple_multi", warn_ok=True)
+    return [s.as_dict() for s in st], list(status), ms.as_dict()
+
+
+def osmpm_autotune_multi(coarse: List[Domain], fine: List[Domain], dT: float, schs, candidates):
+    """Launch shape of osmpm_schwarz_couple_multi chosen by timing one step
+    per candidate, each a (n_threads, dof_tile, chunk) tuple (the pairs
+    advance by len(candidates) + 1 global steps).  Returns (best candidate,
+    list of wall microseconds per PCG iteration)."""
+    n = len(coarse)
+    cs = (c_void_p * n)(*[d.h.value for d in coarse])
+    fs = (c_void_p * n)(*[d.h.value for d in fine])
+    sd = (osmpm_schwarz_desc * n)(*[make_schwarz_desc(s) for s in schs])
+    cand = (osmpm_multi_desc * len(candidates))(*[osmpm_multi_desc(int(a), int(b), int(c), 0)
+                                                  for a, b, c in candidates])
+    best = c_int32(0)
+    score = np.zeros(len(candidates), dtype=np.float64)
+    _check(_lib.osmpm_autotune_multi(cs, fs, n, dT, sd, cand, len(candidates), ctypes.byref(best),
+                                     score.ctypes.data_as(_DP)),
+           "osmpm_autotune_multi", warn_ok=True)
+    return tuple(candidates[int(best.value)]), [float(v) for v in score]
 
 
 def create_stream() -> int:

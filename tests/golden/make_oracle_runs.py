@@ -31,9 +31,10 @@ OUT = os.path.join(HERE, "oracle_runs")
 
 # name -> (description, workload builder, global steps)
 RUNS = {
-    "inclusion_dxS0.02_M2_100steps": (
-        "2D elastic inclusion OS-MPM (coarse dx 0.05, fine dx 0.02, M = 2), FP64 oracle",
-        lambda: W.inclusion(dx_S=0.02, M=2), 100),
+    "inclusion_dxS0.02_M2_80steps": (
+        "2D elastic inclusion OS-MPM (coarse dx 0.05, fine dx 0.02, M = 2), top edge moved "
+        "1e-3 per step, FP64 oracle",
+        lambda: W.inclusion(dx_S=0.02, M=2), 80),
     "inclusion_dxS0.02_M2_top3e-4_100steps": (
         "2D elastic inclusion OS-MPM (coarse dx 0.05, fine dx 0.02, M = 2), top edge moved "
         "3e-4 per step (3 % compression after 100 steps), FP64 oracle",

@@ -392,9 +392,9 @@ def test_batched_instance_gradient_over_50_checkpointed_steps(osmpm):
     Schwarz iterations each, recorded with a checkpoint every 10 steps;
     J = mean y-displacement of the inclusion's top-cap particles.  dJ/dE
     against the FP64 oracle's adjoint unrolled over the same iterations
-    (stored run, 1e-6), against the full record (1e-8), and against a
-    central difference of the CUDA forward along a random direction of the
-    moduli."""
+    (stored run, 1e-6) and against the full record (1e-8); over the first
+    20 steps also against a central difference of the CUDA forward along a
+    random direction of the moduli (1e-5)."""
     import torch
     mod = _golden_module()
     cB, cS, sch, dT, c = mod.adjoint_case()
@@ -402,12 +402,12 @@ def test_batched_instance_gradient_over_50_checkpointed_steps(osmpm):
     oE, oxB, oxS = _stored_gradient(mod)
     g = torch.from_numpy(np.ascontiguousarray(c)).cuda()
 
-    def forward(specB, specS, every=0):
+    def forward(specB, specS, every=0, steps=mod.ADJ_STEPS):
         B, S = osmpm.Domain(specB), osmpm.Domain(specS)
         if every:
             B.record(True, every=every)
             S.record(True, every=every)
-        for _ in range(mod.ADJ_STEPS):
+        for _ in range(steps):
             st = osmpm.osmpm_schwarz_couple(B, S, dT, sch)
             assert st["schwarz_iters"] == mod.ADJ_ITERS
         return B, S
@@ -424,7 +424,16 @@ def test_batched_instance_gradient_over_50_checkpointed_steps(osmpm):
         S.close()
     assert _rel(res[10], oE) <= 1e-6
     assert _rel(res[10], res[1]) <= 1e-8
-    # directional central difference: E_p (1 + eps w_p), w_p = +-1
+    # directional central difference E_p (1 + eps w_p), w_p = +-1, over the
+    # first 20 steps (checkpoints every 7: segments of 7, 7, 6).  Later in
+    # this run the unrolled map stops being smooth (central differences at
+    # eps 1e-3, 1e-4, 1e-5 disagree after 50 steps while they agree to seven
+    # digits up to 25), as node and receiver sets change along it.
+    n20 = 20
+    B, S = forward(cB, cS, 7, steps=n20)
+    dE20 = osmpm.osmpm_adjoint(B, S, g)[0].cpu().numpy()
+    B.close()
+    S.close()
     rng = np.random.default_rng(50)
     w = rng.choice([-1.0, 1.0], nB + cS.particles.n)
     eps = 1e-4
@@ -435,7 +444,7 @@ def test_batched_instance_gradient_over_50_checkpointed_steps(osmpm):
             q = spec.particles.copy()
             q.E = q.E * (1.0 + sign * eps * ww)
             specs.append(dataclasses.replace(spec, particles=q))
-        B, S = forward(*specs)
+        B, S = forward(*specs, steps=n20)
         val = float(np.sum(c[nB:] * (S.get_particles()[0] - cS.particles.x)))
         B.close()
         S.close()
@@ -443,5 +452,5 @@ def test_batched_instance_gradient_over_50_checkpointed_steps(osmpm):
 
     fd = (J(1.0) - J(-1.0)) / (2 * eps)
     E = np.concatenate([cB.particles.E, cS.particles.E])
-    ad = float(np.sum(res[10] * E * w))
-    np.testing.assert_allclose(ad, fd, rtol=1e-4)
+    ad = float(np.sum(dE20 * E * w))
+    np.testing.assert_allclose(ad, fd, rtol=1e-5)
