@@ -1,20 +1,25 @@
 """Throughput of the OS-MPM hot path on GB300.
 
-One step = one global Schwarz step (Alg. 1) of the 2D elastic-inclusion
-workload in FP64: coarse grid [0,1]^2 at dx 0.05 with the matrix
-[0.1,0.9]^2 minus the disk r < 0.1, fine grid [0.3,0.7]^2 at dx 0.005 with
-the disk r < 0.15 holding the stiff inclusion r < 0.05 (E 1e8 in E 1e6,
-nu 0.3), top edge displaced 1e-3 per step, M = 2 fine sub-steps, 4 particles
-per cell.  Metric: particle-substeps/s (fine particles count M per global
-step, coarse particles 1; Schwarz re-iterations are overhead).
+Default line (no --workload): one step = one global Schwarz step (Alg. 1) of
+every pair of the batched inclusion family (256 instances of uneven size:
+inclusion radius, modulus and fine resolution 0.01 / 0.005 from SplitMix64;
+coarse grid [0,1]^2 at dx 0.05, fine grid [0.3,0.7]^2, M = 2, top edge
+displaced 1e-3 per step) in mixed precision, advanced by
+osmpm_schwarz_couple_multi: host threads drive the pairs and one batched
+PCG service solves every Newton system.  Beside it, ``fp64_single_instance``
+times the FP64 single inclusion (fine dx 0.005, M = 2) with CUDA events.
+Metric: particle-substeps/s (fine particles count M per global step,
+coarse particles 1; Schwarz re-iterations are overhead).
 
-The device number times each step with CUDA events on the domains' stream,
-with the L2 cache flushed (a 256 MiB write) between steps, outside the
-events.  The end-to-end number times, on the host clock, the public-API
-sequence a user runs per step: upload both domains' particle state from
-pinned host memory, the coupled step, download the state.
+The batched line is timed on the host clock around each batched step with
+the device synchronised on both sides (the pairs run on their own streams);
+the single-instance line with CUDA events on its stream, the L2 flushed
+(a 256 MiB write) between steps.  End-to-end numbers time the public-API
+sequence a user runs per step: upload every domain's particle state from
+pinned host memory, the step, download the state.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload default|inclusion|batched|fold3d|fold3d_solve]
 
 ``--impl reference`` times the FP64 CPU oracle (the reference arm of this
 repository: a plain NumPy/SciPy restatement of the method) on the host cores.
@@ -398,11 +403,25 @@ def cpu_baseline(n_iters):
                       "of a global step's units"}
 
 
+# Algorithmic bytes of one PCG iteration per particle in mixed precision
+# (particle state read once: x, F^n, V0, mu, lam and the gathered x_hat, p,
+# scattered Kp per node, plus the Jacobi-PCG vector updates per node at
+# 1/ppc node per particle): 2D 52 + 40/4 B, 3D 78 + 60/8 B.
+MIXED_PCG_BYTES_PER_PARTICLE = {2: 52.0 + 40.0 / 4, 3: 78.0 + 60.0 / 8}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the batched
+# Hessian-vector product (k_m_hvp) on the batched family, from ncu; None
+# until captured for the current kernel
+MULTI_HVP_TRAFFIC_BYTES = None
+
+
 def run_batched(args, rank, local, world):
     """Aggregate throughput of ``--instances`` independent inclusion pairs of
     the batched family (uneven fine resolutions), each on its own stream,
-    advanced together by osmpm_schwarz_couple_batch (host wall clock around
-    each batched step, the device synchronised on both sides)."""
+    advanced together by osmpm_schwarz_couple_multi (mixed precision: one
+    batched PCG service for every pair's Newton systems; ``--batch-mode
+    multi``) or osmpm_schwarz_couple_batch (each pair launching its own PCG;
+    ``--batch-mode threads``).  Host wall clock around each batched step,
+    the device synchronised on both sides (the pairs run on many streams)."""
     import torch
     torch.cuda.set_device(local)
     from paper_2605_09097_gb300 import build
@@ -422,10 +441,12 @@ def run_batched(args, rank, local, world):
     threads, tuned = args.threads, None
     multi = args.batch_mode == "multi"
     shape = None
+    tune_steps = 0
     if multi:
         if args.threads == 0:
             shape, scores = osmpm.osmpm_autotune_multi(B, S, dT, schs, AUTOTUNE_MULTI)
             tuned = {"x".join(map(str, c)): v for c, v in zip(AUTOTUNE_MULTI, scores)}
+            tune_steps = len(AUTOTUNE_MULTI) + 1
         else:
             shape = (args.threads, 0, 0)
         threads = shape[0]
@@ -434,13 +455,14 @@ def run_batched(args, rank, local, world):
             return osmpm.osmpm_schwarz_couple_multi(B, S, dT, schs, *shape)[2]
     else:
         if threads == 0:
-            # the launch-shape autotuner's steps stand in for the warm-up
             threads, tuned = osmpm.osmpm_autotune_batch(B, S, dT, schs, AUTOTUNE_THREADS)
+            tune_steps = len(AUTOTUNE_THREADS) + 1
 
         def batched_step():
             osmpm.osmpm_schwarz_couple_batch(B, S, dT, schs, n_threads=threads)
             return None
-    for _ in range(args.warmup if tuned is None else 0):
+    # the autotuner's steps count as warm-up steps
+    for _ in range(max(args.warmup - tune_steps, 0)):
         batched_step()
     torch.cuda.synchronize()
     barrier(world)
@@ -456,49 +478,180 @@ def run_batched(args, rank, local, world):
     clk = clocks.stop()
     value = sum_over_ranks(units * args.steps, world) / t
     launches = int(osmpm.launch_count() - launches0)
-    for d in B + S:
-        d.close()
+    roofline = None
+    if multi and service:
+        peaks, src = measured_peaks()
+        d = specs[0][0].grid.dim
+        bytes_ = sum(x["particle_iterations"] for x in service) * MIXED_PCG_BYTES_PER_PARTICLE[d]
+        dev_s = sum(x["device_ms"] for x in service) / 1e3
+        nb = sum(x["batches"] for x in service)
+        achieved = bytes_ / dev_s / 1e9 if dev_s > 0 else 0.0
+        roofline = {"kernel": "batched PCG (k_m_hvp + k_m_alpha + k_m_beta per iteration)",
+                    "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": MULTI_HVP_TRAFFIC_BYTES,
+                    "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)" if src == "measured"
+                    else "fallback 6.8 TB/s",
+                    "launches": nb, "avg_launch_us": 1e6 * dev_s / max(nb, 1),
+                    "bytes_per_launch": bytes_ / max(nb, 1),
+                    "bytes_per_particle_iteration": MIXED_PCG_BYTES_PER_PARTICLE[d],
+                    "pcg_iterations": sum(x["iterations"] for x in service),
+                    "systems_per_batch": sum(x["instances"] for x in service) / max(nb, 1)}
+    e2e = None
+    if args.e2e_steps > 0:
+        # end to end through the public API: every pair's particle state
+        # uploaded from pinned host memory, the batched step, the state read
+        # back, per step
+        host = []
+        for dd in B + S:
+            arrs = []
+            for a in dd.get_particles():
+                tp = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+                tp.numpy()[...] = a
+                arrs.append(tp.numpy())
+            host.append(arrs)
+        nbytes = sum(a.nbytes for h in host for a in h)
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for dd, h in zip(B + S, host):
+                dd.set_particles(*h)
+            batched_step()
+            for dd, h in zip(B + S, host):
+                x, v, Bm, F = dd.get_particles()
+                h[0][...] = x
+                h[1][...] = v
+                h[2][...] = Bm
+                h[3][...] = F
+        torch.cuda.synchronize()
+        te = max_over_ranks(time.perf_counter() - te0, world)
+        e2e = {"value": sum_over_ranks(units * args.e2e_steps, world) / te, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "steps": args.e2e_steps}
+    for dd in B + S:
+        dd.close()
     for st in streams:
         osmpm.destroy_stream(st)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup if tuned is None else len(AUTOTUNE_THREADS) + 1,
+            "warmup": max(args.warmup, tune_steps),
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32/f64",
             "data": "synthetic",
-            "config": {"workload": f"batched_inclusion_{args.instances}_literal",
+            "config": {"workload": f"batched_inclusion_{args.instances}_literal_"
+                                   f"{'mixed' if prec else 'fp64'}",
                        "instances": args.instances, "host_threads": threads,
                        "batch_mode": args.batch_mode, "launch_shape": shape,
                        "pcg_service": service if multi else None,
                        "autotune_us_per_cg_iter": tuned,
                        "particles": sum(s[0].particles.n + s[1].particles.n for s in specs),
                        "units_per_step": units, "precision": args.precision,
-                       "timing": "host wall clock around each batched step",
+                       "timing": "host wall clock around each batched step, device synchronised "
+                                 "on both sides (the pairs run on their own streams)",
                        "l2": "not flushed: the instances' resident state (~0.6 KB per particle, "
                              "1.96M particles at 256 instances) is larger than L2",
                        "parallelism": f"replicas{world}"},
-            "gpu_launches": launches, "clocks": clk}
+            "gpu_launches": launches, "roofline": roofline, "clocks": clk, "e2e": e2e}
+
+
+def oracle_instance_sample(i, n_iters=ORACLE_SAMPLE_ITERS):
+    """The FP64 oracle on instance i of the batched family: the first
+    ``n_iters`` Schwarz iterations of global step 1.  Returns (seconds,
+    units), units scaled by n_iters / ORACLE_SCHWARZ_ITERS_PER_STEP of a
+    global step's particle-substeps."""
+    from oracle import osmpm_oracle as O
+    cB, cS, sch, dT = W.inclusion_instance(i)
+    sch = dataclasses.replace(sch, k_max=n_iters - 1)
+    B, S = O.DomainState.create(cB), O.DomainState.create(cS)
+    t0 = time.perf_counter()
+    O.schwarz_step(B, S, dT, sch)
+    t = time.perf_counter() - t0
+    return t, units_per_step(cB, cS, sch.M) * n_iters / ORACLE_SCHWARZ_ITERS_PER_STEP
+
+
+def cpu_baseline_batched():
+    """The oracle on a bounded sample of the batched family: on one core the
+    first Schwarz iterations of instances 0 and 1 (one of each fine
+    resolution) one after the other; on all host cores one such sample per
+    core (instances 0 .. nproc-1) in a spawn-started process pool, counted
+    by wall clock.  Rates in particle-substeps/s, reported only."""
+    import multiprocessing as mp
+    t0, u0 = oracle_instance_sample(0)
+    t1, u1 = oracle_instance_sample(1)
+    one = (u0 + u1) / (t0 + t1)
+    cores = os.cpu_count() or 1
+    out = {"value": one, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"first {ORACLE_SAMPLE_ITERS} Schwarz iterations of global step 1 of batched "
+                     f"instances 0 and 1 (fine dx 0.01 and 0.005; {t0 + t1:.1f} s), units scaled "
+                     f"by {ORACLE_SAMPLE_ITERS}/{ORACLE_SCHWARZ_ITERS_PER_STEP:g} of a global step"}
+    try:
+        ctx = mp.get_context("spawn")
+        tw = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            res = pool.map(oracle_instance_sample, range(cores))
+        wall = time.perf_counter() - tw
+        out["all_cores"] = {"value": sum(u for _, u in res) / wall, "unit": UNIT, "cores": cores,
+                            "sample": f"instances 0..{cores - 1}, one process each, wall clock "
+                                      f"{wall:.1f} s (process start included)"}
+    except Exception as e:  # the one-core figure stands alone
+        out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
+
+
+def run_default(args, rank, local, world):
+    """The headline: the batched inclusion family (BASELINE's batched
+    configuration: 256 instances of uneven size, mixed precision) through the
+    batched PCG service, with the plain FP64 single-instance inclusion
+    (fine dx 0.005, M = 2) beside it as ``fp64_single_instance``."""
+    a = argparse.Namespace(**vars(args))
+    a.precision, a.batch_mode, a.instances = "mixed", "multi", 256
+    main_line = run_batched(a, rank, local, world)
+    b = argparse.Namespace(**vars(args))
+    b.steps, b.warmup, b.no_cpu_baseline = max(args.steps, 10), max(args.warmup, 3), True
+    single = run_ours(b, rank, local, world)
+    main_line["fp64_single_instance"] = {
+        k: single[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config",
+                               "roofline", "e2e", "clocks", "gpu_launches") if k in single}
+    main_line["adjoint"] = single.get("adjoint")
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        main_line["cpu_baseline"] = cpu_baseline_batched()
+    return main_line
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, on the
+    workload of ``--workload`` (default: the batched family; each step one
+    bounded sample, the first Schwarz iteration of global step 1 of the next
+    instance; inclusion: the FP64 single inclusion, same sample)."""
     if rank != 0:
         return None
+    batched = args.workload in ("default", "batched")
+    k = [0]
+
+    def sample():
+        if batched:
+            i = k[0] % 2  # instances 0 and 1: one of each fine resolution
+            k[0] += 1
+            return oracle_instance_sample(i, 1)
+        return oracle_sample(1)
+
     for _ in range(args.warmup):
-        oracle_sample(1)
+        sample()
     tot_t, tot_u = 0.0, 0.0
     for _ in range(args.steps):
-        t, u = oracle_sample(1)
+        t, u = sample()
         tot_t += t
         tot_u += u
     value = tot_u / tot_t
     cores = _threads()
+    workload = "batched_inclusion_256_literal_mixed" if batched else WORKLOAD
+    what = ("batched instances 0, 1, 0, ... (fine dx 0.01, 0.005)" if batched else WORKLOAD)
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "cpu"},
+            "config": {"workload": workload, "parallelism": "cpu"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"each step: the first Schwarz iteration of global step 1 of "
-                                       f"{WORKLOAD}, scaled by 1/{ORACLE_SCHWARZ_ITERS_PER_STEP:g} "
+                                       f"{what}, scaled by 1/{ORACLE_SCHWARZ_ITERS_PER_STEP:g} "
                                        "of a global step's units"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -609,10 +762,13 @@ def main():
                     help="0: each Newton iteration replays a captured CUDA graph; 1: plain launches")
     ap.add_argument("--hvp-mode", type=int, choices=[0, 1, 2], default=0,
                     help="fold3d_solve: Hessian-vector product of the streaming PCG")
-    ap.add_argument("--workload", choices=["inclusion", "batched", "fold3d", "fold3d_solve"],
-                    default="inclusion",
-                    help="inclusion: the headline FP64 configuration; batched: many instances; "
-                         "fold3d: the 3D folding plate (mixed)")
+    ap.add_argument("--workload", choices=["default", "inclusion", "batched", "fold3d",
+                                           "fold3d_solve"],
+                    default="default",
+                    help="default: the batched family in mixed precision with the FP64 single "
+                         "inclusion beside it; inclusion: the FP64 single inclusion alone; batched: "
+                         "many instances; fold3d: the 3D folding plate (mixed); fold3d_solve: the "
+                         "fold's 3.07M-particle band folded on its own")
     ap.add_argument("--scaled", action="store_true", help="fold3d: the 3.07M-particle band")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--threads", type=int, default=0,
@@ -625,6 +781,8 @@ def main():
     rank, local, world = dist_init(args.gpus)
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.workload == "default":
+        out = run_default(args, rank, local, world)
     elif args.workload == "batched":
         out = run_batched(args, rank, local, world)
     elif args.workload == "fold3d":

@@ -323,12 +323,16 @@ typedef struct osmpm_multi_desc {
 } osmpm_multi_desc;
 
 typedef struct osmpm_multi_stats {
-  int64_t batches;     /* batched PCG solves */
-  int64_t instances;   /* Newton systems solved, summed over the batches */
-  int64_t chunks;      /* graph replays (chunks of iterations) */
-  int64_t max_batch;   /* most systems in one batch */
-  int64_t particles;   /* particles of the systems, summed over the batches */
-  int64_t dofs;        /* grid DOFs of the systems, summed over the batches */
+  int64_t batches;     /* compositions of the running set: each time systems
+                          join or leave, its tables are rebuilt */
+  int64_t instances;   /* Newton systems solved */
+  int64_t chunks;      /* chunks of iterations (graph replays) */
+  int64_t max_batch;   /* most systems iterating together */
+  int64_t particles;   /* particles of the systems solved, summed */
+  int64_t dofs;        /* grid DOFs of the systems solved, summed */
+  int64_t iterations;  /* PCG iterations, summed over the systems */
+  int64_t particle_iterations;  /* sum over the systems of iterations x particles */
+  int64_t dof_iterations;       /* sum over the systems of iterations x grid DOFs */
   double device_ms;    /* device time of the batched PCGs (CUDA events) */
 } osmpm_multi_stats;
 

@@ -131,6 +131,7 @@ struct osmpm_domain {
   double *cw1 = nullptr, *cw2 = nullptr, *cpp = nullptr;
   void* L = nullptr;       // per-particle Hessian blocks (particle-state type)
   int* sbase = nullptr;    // stencil cache of the last P2G (base node, grad N)
+  int* slot2p = nullptr;   // mixed precision: cell-aligned slots of the last P2G
   void* sdn = nullptr;
   uint8_t *dofmask = nullptr, *physmask = nullptr, *gam = nullptr, *recv = nullptr;
   double *bc0 = nullptr, *bc1 = nullptr, *bc_prev = nullptr, *bc_applied = nullptr;
@@ -461,6 +462,13 @@ osmpm_status run_p2g(osmpm_domain* d, bool boundary_mass) {
   DISPATCH(d, K::p2g(P_, d->geo, d->m, d->mv, boundary_mass ? d->bm : nullptr, d->err, d->sbase,
                      SDN_, d->stream));
   DISPATCH(d, K::normalize(d->geo, d->m, d->mv, d->vn, d->stream));
+  if (d->slot2p) {
+    // the sort scratch (idle between sorts) holds the slot builder's scans
+    int* rs = (int*)d->keys;
+    int* flag = rs + d->n;
+    DISPATCH(d, K::build_slots(d->sbase, d->n, rs, flag, (int*)d->vals, (int*)d->keys_alt,
+                               d->slot2p, (int64_t)(1 << D) * d->n, &d->S->n_slots, d->stream));
+  }
   return OSMPM_OK;
 }
 
@@ -517,6 +525,10 @@ PcgArgsT<R> pcg_args(osmpm_domain* d, double dt) {
   a.sbase = d->sbase;
   a.sdn = (const R*)d->sdn;
   a.u = d->u;
+  a.slot2p = d->slot2p;
+  a.n_slots = &d->S->n_slots;
+  const int npk = (d->dim * d->dim) * (d->dim * d->dim + 1) / 2;
+  a.fhat = (const R*)d->L + (int64_t)npk * d->n;
   return a;
 }
 
@@ -801,7 +813,8 @@ struct PcgBatcher {
   size_t dev_bytes = 0;
   char* host = nullptr;
   size_t host_bytes = 0;
-  int* pending_host = nullptr;
+  int* pending_host = nullptr;  // pending count, then the instances' iteration counts
+  int pending_cap = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::string error;
   osmpm_multi_stats stats{};
@@ -811,7 +824,8 @@ struct PcgBatcher {
     dof_tile = dof_tile_ > 0 ? dof_tile_ : 2048;
     chunk = chunk_ > 0 ? chunk_ : 16;
     CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-    CUDA_TRY(cudaMallocHost(&pending_host, sizeof(int)));
+    pending_cap = 4096;
+    CUDA_TRY(cudaMallocHost(&pending_host, sizeof(int) * (1 + pending_cap)));
     CUDA_TRY(cudaEventCreate(&ev[0]));
     CUDA_TRY(cudaEventCreate(&ev[1]));
     int dev_id = 0;
@@ -851,25 +865,77 @@ struct PcgBatcher {
     return r.st;
   }
 
+  // The service loop: continuous batching.  The systems in flight ("live")
+  // iterate together in chunks; after each chunk the converged ones leave
+  // (their threads resume at once) and the systems handed in meanwhile join
+  // (their PCG start runs with the next chunk).
   void loop() {
+    std::vector<Req*> live;
+    std::vector<int> fresh_flags;
+    bool dirty = false;
+    MultiArgs m{};
+    cudaGraphExec_t exec = nullptr;
+    long long per_chunk = 0;
     for (;;) {
-      std::vector<Req*> batch;
+      std::vector<Req*> fresh;
       {
         std::unique_lock<std::mutex> lk(mu);
-        cv_work.wait(lk, [&] { return stop || !queue.empty(); });
-        if (queue.empty()) return;
-        batch.swap(queue);
+        if (live.empty()) cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+        if (live.empty() && queue.empty()) break;
+        fresh.swap(queue);
       }
-      const osmpm_status st = run(batch);
+      osmpm_status st = OSMPM_OK;
+      if (!fresh.empty() || dirty) {
+        const size_t old = live.size();
+        live.insert(live.end(), fresh.begin(), fresh.end());
+        fresh_flags.assign(live.size(), 0);
+        for (size_t i = old; i < live.size(); ++i) fresh_flags[i] = 1;
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        st = build(live, fresh_flags, &m);
+        if (st == OSMPM_OK) {
+          stats.batches += 1;
+          stats.instances += (int64_t)fresh.size();
+          if ((int64_t)live.size() > stats.max_batch) stats.max_batch = (int64_t)live.size();
+          if (dim == 2) MultiKernels<2>::start(m, stream);
+          else MultiKernels<3>::start(m, stream);
+          exec = capture(m, &per_chunk);
+        }
+        dirty = false;
+      }
+      if (st == OSMPM_OK) st = run_chunk(m, exec, per_chunk, live.size());
+      // the systems that stopped leave (all of them after a failure)
+      std::vector<Req*> done;
+      std::vector<Req*> keep;
+      for (size_t i = 0; i < live.size(); ++i) {
+        const bool stopped = st != OSMPM_OK || pending_host[1 + 2 * i] != 0 ||
+                             pending_host[2 + 2 * i] >= live[i]->d->desc.cg_max;
+        if (stopped) {
+          done.push_back(live[i]);
+          if (st == OSMPM_OK) {
+            const int it = pending_host[2 + 2 * i];
+            stats.iterations += it;
+            stats.particle_iterations += (int64_t)it * live[i]->d->n;
+            stats.dof_iterations += (int64_t)it * live[i]->d->dim * live[i]->d->geo.nn;
+            stats.particles += live[i]->d->n;
+            stats.dofs += (int64_t)live[i]->d->dim * live[i]->d->geo.nn;
+          }
+        } else {
+          keep.push_back(live[i]);
+        }
+      }
+      live.swap(keep);
+      dirty = !done.empty();
       {
         std::lock_guard<std::mutex> lk(mu);
-        for (Req* r : batch) {
+        for (Req* r : done) {
           r->st = st;
           r->done = true;
         }
       }
-      cv_done.notify_all();
+      if (!done.empty()) cv_done.notify_all();
     }
+    if (exec) cudaGraphExecDestroy(exec);
   }
 
   template <class T>
@@ -877,34 +943,37 @@ struct PcgBatcher {
     return (b + 255) & ~size_t(255);
   }
 
-  osmpm_status run(const std::vector<Req*>& batch) {
-    const int n = (int)batch.size();
+  // Uploads the instance table and work lists of `live` (fresh[i] = 1 for
+  // the systems whose PCG start is still to run).
+  osmpm_status build(const std::vector<Req*>& live, const std::vector<int>& fresh, MultiArgs* out) {
+    const int n = (int)live.size();
     const int TP = dim == 2 ? MultiKernels<2>::particle_tile() : MultiKernels<3>::particle_tile();
     std::vector<PcgArgsT<float>> inst((size_t)n);
     std::vector<MultiInfo> info((size_t)n);
     std::vector<MultiTile> pt, dtl;
-    long long particles = 0, dofs = 0;
     for (int i = 0; i < n; ++i) {
-      osmpm_domain* d = batch[(size_t)i]->d;
-      inst[(size_t)i] = pcg_args<float>(d, batch[(size_t)i]->dt);
+      osmpm_domain* d = live[(size_t)i]->d;
+      inst[(size_t)i] = pcg_args<float>(d, live[(size_t)i]->dt);
       info[(size_t)i].pt0 = (int)pt.size();
-      for (int64_t p0 = 0; p0 < d->n; p0 += TP)
-        pt.push_back(MultiTile{i, (int)p0, (int)std::min<int64_t>(d->n, p0 + TP)});
+      const int64_t ns = d->S_host->n_slots;  // the slots of the last P2G (read back since)
+      for (int64_t s0 = 0; s0 < ns; s0 += TP)
+        pt.push_back(MultiTile{i, (int)s0, (int)std::min<int64_t>(ns, s0 + TP)});
       info[(size_t)i].npt = (int)pt.size() - info[(size_t)i].pt0;
       info[(size_t)i].dt0 = (int)dtl.size();
       const int64_t ndof = (int64_t)d->dim * d->geo.nn;
       for (int64_t q0 = 0; q0 < ndof; q0 += dof_tile)
         dtl.push_back(MultiTile{i, (int)q0, (int)std::min<int64_t>(ndof, q0 + dof_tile)});
       info[(size_t)i].ndt = (int)dtl.size() - info[(size_t)i].dt0;
-      particles += d->n;
-      dofs += ndof;
+      info[(size_t)i].fresh = fresh[(size_t)i];
     }
-    const int stride = (int)std::max(pt.size(), dtl.size());
+    const int stride = (int)std::max<size_t>(std::max(pt.size(), dtl.size()), 1);
     const size_t b_inst = up<char>(sizeof(PcgArgsT<float>) * n), b_info = up<char>(sizeof(MultiInfo) * n);
     const size_t b_pt = up<char>(sizeof(MultiTile) * pt.size()), b_dt = up<char>(sizeof(MultiTile) * dtl.size());
-    const size_t b_part = up<char>(sizeof(double) * 2 * stride), b_pend = 256;
+    const size_t b_part = up<char>(sizeof(double) * 2 * stride);
+    const size_t b_pend = up<char>(sizeof(int) * (1 + 2 * n));
     const size_t in_bytes = b_inst + b_info + b_pt + b_dt;
     const size_t need = in_bytes + b_part + b_pend;
+    CUDA_TRY(cudaStreamSynchronize(stream));  // the previous tables are no longer read
     if (need > dev_bytes) {
       if (dev) cudaFreeAsync(dev, stream);
       dev = nullptr;
@@ -914,24 +983,27 @@ struct PcgBatcher {
       dev_bytes = want;
     }
     if (in_bytes > host_bytes) {
-      if (host) {
-        cudaStreamSynchronize(stream);
-        cudaFreeHost(host);
-      }
+      if (host) cudaFreeHost(host);
       host = nullptr;
       host_bytes = 0;
       const size_t want = in_bytes + in_bytes / 2;
       if (cudaMallocHost(&host, want) != cudaSuccess) return set_error(OSMPM_E_NOMEM, "batched PCG: pinned memory");
       host_bytes = want;
     }
+    if (2 * n > pending_cap) {
+      cudaFreeHost(pending_host);
+      pending_cap = 2 * n;
+      if (cudaMallocHost(&pending_host, sizeof(int) * (1 + pending_cap)) != cudaSuccess)
+        return set_error(OSMPM_E_NOMEM, "batched PCG: pinned memory");
+    }
     memcpy(host, inst.data(), sizeof(PcgArgsT<float>) * n);
     memcpy(host + b_inst, info.data(), sizeof(MultiInfo) * n);
-    memcpy(host + b_inst + b_info, pt.data(), sizeof(MultiTile) * pt.size());
-    memcpy(host + b_inst + b_info + b_pt, dtl.data(), sizeof(MultiTile) * dtl.size());
+    if (!pt.empty()) memcpy(host + b_inst + b_info, pt.data(), sizeof(MultiTile) * pt.size());
+    if (!dtl.empty()) memcpy(host + b_inst + b_info + b_pt, dtl.data(), sizeof(MultiTile) * dtl.size());
     char* dv = (char*)dev;
-    if (cudaMemcpyAsync(dv, host, in_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-      return set_error(OSMPM_E_CUDA, "batched PCG: upload");
-    MultiArgs m{};
+    CUDA_TRY(cudaMemcpyAsync(dv, host, in_bytes, cudaMemcpyHostToDevice, stream));
+    MultiArgs& m = *out;
+    m = MultiArgs{};
     m.inst = (const PcgArgsT<float>*)dv;
     m.info = (const MultiInfo*)(dv + b_inst);
     m.pt = (const MultiTile*)(dv + b_inst + b_info);
@@ -942,62 +1014,55 @@ struct PcgBatcher {
     m.part = (double*)(dv + in_bytes);
     m.stride = stride;
     m.pending = (int*)(dv + in_bytes + b_part);
-    auto launch_chunk = [&] {
-      for (int c = 0; c < chunk; ++c) {
-        if (dim == 2) MultiKernels<2>::iteration(m, stream);
-        else MultiKernels<3>::iteration(m, stream);
-      }
-      if (dim == 2) MultiKernels<2>::pending(m, stream);
-      else MultiKernels<3>::pending(m, stream);
-      cudaMemcpyAsync(pending_host, m.pending, sizeof(int), cudaMemcpyDeviceToHost, stream);
-    };
-    cudaEventRecord(ev[0], stream);
-    if (dim == 2) MultiKernels<2>::start(m, stream);
-    else MultiKernels<3>::start(m, stream);
-    // the chunk as a CUDA graph captured for this batch (its arguments are
-    // fixed for the batch), replayed until every instance stopped
+    return OSMPM_OK;
+  }
+
+  void enqueue_chunk(const MultiArgs& m, int n) {
+    for (int c = 0; c < chunk; ++c) {
+      if (dim == 2) MultiKernels<2>::iteration(m, stream);
+      else MultiKernels<3>::iteration(m, stream);
+    }
+    if (dim == 2) MultiKernels<2>::pending(m, stream);
+    else MultiKernels<3>::pending(m, stream);
+    cudaMemcpyAsync(pending_host, m.pending, sizeof(int) * (1 + 2 * n), cudaMemcpyDeviceToHost, stream);
+  }
+
+  // The chunk as a CUDA graph for this composition of the batch (nullptr:
+  // plain launches).
+  cudaGraphExec_t capture(const MultiArgs& m, long long* per_chunk) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     const long long before = g_launch_count.load();
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      launch_chunk();
+      enqueue_chunk(m, m.n_inst);
       if (cudaStreamEndCapture(stream, &graph) != cudaSuccess || !graph ||
           cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
         exec = nullptr;
     }
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
-    const long long per_chunk = g_launch_count.load() - before;
-    if (exec) g_launch_count -= per_chunk;  // replays count them
-    int chunks = 0;
-    cudaError_t e = cudaSuccess;
-    const int max_chunks = 1 + (int)((int64_t)batch[0]->d->desc.cg_max / chunk) + 1;
-    for (;;) {
-      if (exec) {
-        e = cudaGraphLaunch(exec, stream);
-        g_launch_count += per_chunk;
-      } else {
-        launch_chunk();
-        e = cudaGetLastError();
-      }
-      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-      if (e != cudaSuccess) break;
-      ++chunks;
-      if (*pending_host == 0 || chunks > max_chunks) break;
+    *per_chunk = g_launch_count.load() - before;
+    g_launch_count -= *per_chunk;  // counted when replayed or launched
+    return exec;
+  }
+
+  osmpm_status run_chunk(const MultiArgs& m, cudaGraphExec_t exec, long long per_chunk, size_t n) {
+    cudaEventRecord(ev[0], stream);
+    cudaError_t e;
+    if (exec) {
+      e = cudaGraphLaunch(exec, stream);
+      g_launch_count += per_chunk;
+    } else {
+      enqueue_chunk(m, (int)n);
+      e = cudaGetLastError();
     }
     cudaEventRecord(ev[1], stream);
-    if (exec) cudaGraphExecDestroy(exec);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return set_error(OSMPM_E_CUDA, "batched PCG: %s", cudaGetErrorString(e));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
-    stats.batches += 1;
-    stats.instances += n;
-    stats.chunks += chunks;
+    stats.chunks += 1;
     stats.device_ms += ms;
-    stats.particles += particles;
-    stats.dofs += dofs;
-    if (n > stats.max_batch) stats.max_batch = n;
     return OSMPM_OK;
   }
 };
@@ -1010,9 +1075,9 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check
   const bool timed = d->time_hvp && !d->ev.empty();
   if (d->batcher) {
     // the batched PCG service solves the system with the other pairs' ones
+    // (the scalars read back here carry the slot count of the last P2G)
     enqueue_gradient(d, dt, first, check);
-    CUDA_TRY(cudaStreamSynchronize(d->stream));
-    CUDA_TRY(cudaGetLastError());
+    OSMPM_TRY(sync_scalars(d));
     OSMPM_TRY(d->batcher->solve(d, dt));
     DISPATCH(d, K::maxabs(d->geo, d->dofmask, d->cx, d->S, d->partials, d->stream));
     OSMPM_TRY(sync_scalars(d));
@@ -1474,7 +1539,10 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(dalloc_n(d, D * nn, &d->cpp));
   C_TRY(dalloc_n(d, D * nn, &d->cq));
   const int npk = (D * D) * (D * D + 1) / 2;
-  C_TRY(dalloc(d, d->rsize * npk * n, &d->L));
+  // mixed precision: the Hessian blocks, then each particle's deformation
+  // gradient at the Newton iterate (the tiled product), and its slots
+  C_TRY(dalloc(d, d->rsize * (npk + (d->prec == 1 ? D * D : 0)) * n, &d->L));
+  if (d->prec == 1) C_TRY(dalloc_n(d, (int64_t)(1 << D) * n, &d->slot2p));
   C_TRY(dalloc_n(d, n, &d->sbase));
   C_TRY(dalloc(d, d->rsize * D * (D == 2 ? 9 : 27) * n, &d->sdn));
   C_TRY(dalloc_n(d, nn, &d->dofmask));

@@ -199,6 +199,11 @@ struct Kernels {
                           cudaStream_t s);
   static void set_cg_state(DevScalars* S, int iter, int done, cudaStream_t s);
   static void barrier_timeout_check(unsigned* words, int* err, cudaStream_t s);
+  // cell-aligned slots of the tiled product from the stencil bases of the
+  // last P2G (scratch: rs, flag, gsum n ints each, bsum n/1024 + 1 ints;
+  // slot2p slot_cap = 2^D n ints; the slot count into *n_slots)
+  static void build_slots(const int* sbase, int64_t n, int* rs, int* flag, int* gsum, int* bsum,
+                          int* slot2p, int64_t slot_cap, int* n_slots, cudaStream_t s);
   // rigid-plane contact (2D; osmpm_contact.cuh)
   static void plane_colmin(const PartPtrsT<R>& P, const GridGeo& g, double spacing,
                            unsigned long long* colmin, cudaStream_t s);

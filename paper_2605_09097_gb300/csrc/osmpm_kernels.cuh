@@ -388,6 +388,11 @@ __global__ void __launch_bounds__(kThreads) k_grad(PartPtrsT<R> P, GridGeo g, co
 #pragma unroll
     for (int j = i; j < DD; ++j)
       L[(int64_t)Sym<D>::idx(i, j) * P.n + p] = (R)(0.5 * (Lfull[i * DD + j] + Lfull[j * DD + i]));
+  if constexpr (std::is_same<R, float>::value) {
+    // the deformation gradient at this iterate, for the tiled product
+#pragma unroll
+    for (int e = 0; e < DD; ++e) L[(int64_t)(Sym<D>::packed + e) * P.n + p] = (R)F[e];
+  }
   // scatter gradient and diagonal
 #pragma unroll 3
   for (int k = 0; k < Pow3<D>::K; ++k) {
@@ -1244,7 +1249,8 @@ void Kernels<D, R>::cgs_hvp(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s) 
   bool tiled = false;
   if constexpr (std::is_same<R, float>::value) {
     if (hvp_mode != 1) {
-      const int64_t tiles = (a.P.n + TileCap<D>::THREADS - 1) / TileCap<D>::THREADS;
+      // tiles over the slot capacity; the kernel reads the slot count
+      const int64_t tiles = ((int64_t)(1 << D) * a.P.n + TileCap<D>::THREADS - 1) / TileCap<D>::THREADS;
       const int blocks = (int)std::min<int64_t>(std::max<int64_t>(tiles, 1), kRedBlocksMax);
       g_launch_count += 1;
       k_cgs_hvp_tile<D><<<blocks, TileCap<D>::THREADS, 0, s>>>(a);
@@ -1284,6 +1290,28 @@ template <int D, typename R>
 void Kernels<D, R>::barrier_timeout_check(unsigned* words, int* err, cudaStream_t s) {
   g_launch_count += 1;
   k_barrier_timeout_check<D, R><<<2, 32, 0, s>>>(words, err);
+}
+
+template <int D, typename R>
+void Kernels<D, R>::build_slots(const int* sbase, int64_t n, int* rs, int* flag, int* gsum,
+                                int* bsum, int* slot2p, int64_t slot_cap, int* n_slots,
+                                cudaStream_t s) {
+  constexpr int GL = 1 << D;
+  cudaMemsetAsync(slot2p, 0xFF, sizeof(int) * slot_cap, s);
+  cudaMemsetAsync(n_slots, 0, sizeof(int), s);
+  if (n <= 0) return;
+  const int nb = (int)((n + kScanItems - 1) / kScanItems);
+  const int blocks = blocks_for(n);
+  g_launch_count += 9;
+  k_slot_starts<GL><<<blocks, kThreads, 0, s>>>(sbase, n, rs);
+  k_scan_block<true><<<nb, 256, 0, s>>>(rs, rs, n, bsum);
+  k_scan_top<true><<<1, 256, 0, s>>>(bsum, nb);
+  k_scan_add<true><<<blocks, kThreads, 0, s>>>(rs, n, bsum);
+  k_slot_flags<GL><<<blocks, kThreads, 0, s>>>(rs, n, flag);
+  k_scan_block<false><<<nb, 256, 0, s>>>(flag, gsum, n, bsum);
+  k_scan_top<false><<<1, 256, 0, s>>>(bsum, nb);
+  k_scan_add<false><<<blocks, kThreads, 0, s>>>(gsum, n, bsum);
+  k_slot_fill<GL><<<blocks, kThreads, 0, s>>>(rs, gsum, flag, n, slot2p, n_slots);
 }
 
 template <int D>

@@ -57,6 +57,7 @@ template <int D>
 __global__ void __launch_bounds__(kThreads) k_m_start(MultiArgs m) {
   for (int t = blockIdx.x; t < m.n_dt; t += gridDim.x) {
     const MultiTile T = m.dtl[t];
+    if (!m.info[T.inst].fresh) continue;  // already iterating
     const PcgArgsT<float>& a = m.inst[T.inst];
     const int64_t nn = a.g.nn;
     double acc[1] = {0.0};
@@ -84,14 +85,14 @@ __global__ void __launch_bounds__(kThreads) k_m_start(MultiArgs m) {
 // q = K p over the particle tiles of the running instances (the tiled
 // product), p:Kp into pq.
 template <int D>
-__global__ void __launch_bounds__(TileCap<D>::THREADS) k_m_hvp(MultiArgs m) {
+__global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS) k_m_hvp(MultiArgs m) {
   __shared__ HvpTileShared<D> sh;
   for (int t = blockIdx.x; t < m.n_pt; t += gridDim.x) {
     const MultiTile T = m.pt[t];
     const PcgArgsT<float>& a = m.inst[T.inst];
     if (__ldcg(&a.S->cg_done)) continue;  // the whole instance stopped (set by the alpha kernel)
     double acc[1] = {0.0};
-    hvp_tile<D>(a, T.lo, T.hi, sh, acc[0]);
+    hvp_tile<D>(a, T.lo, T.hi, sh, acc[0]);  // T.lo, T.hi: slots
     const MultiInfo in = m.info[T.inst];
     double tot[1];
     if (inst_sum<1>(acc, m.part, m.stride, t, in.pt0, in.npt, &a.S->counter, tot) &&
@@ -183,14 +184,21 @@ __global__ void __launch_bounds__(kThreads) k_m_beta(MultiArgs m) {
   }
 }
 
-// The number of instances still iterating (one block).
+// The number of systems still iterating into pending[0], every system's
+// stop flag and iteration count into pending[1 + 2i], pending[2 + 2i] (one
+// block).
 template <int D>
 __global__ void k_m_pending(MultiArgs m) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < m.n_inst; i += blockDim.x)
-    if (!__ldcg(&m.inst[i].S->cg_done)) atomicAdd(&cnt, 1);
+  for (int i = threadIdx.x; i < m.n_inst; i += blockDim.x) {
+    const DevScalars* S = m.inst[i].S;
+    const int done = __ldcg(&S->cg_done);
+    if (!done) atomicAdd(&cnt, 1);
+    m.pending[1 + 2 * i] = done;
+    m.pending[2 + 2 * i] = __ldcg(&S->cg_iter);
+  }
   __syncthreads();
   if (threadIdx.x == 0) *m.pending = cnt;
 }

@@ -20,7 +20,8 @@ namespace osmpm {
 template <int D>
 struct TileCap {
   static constexpr int NODES = (D == 2) ? 1024 : 768;
-  static constexpr int THREADS = (D == 2) ? 256 : 128;  // one particle per thread
+  static constexpr int THREADS = (D == 2) ? 256 : 128;  // one slot per thread
+  static constexpr int MIN_BLOCKS = (D == 2) ? 2 : 4;    // resident blocks per SM (registers)
 };
 
 // Geometry of one block's tile: the box [lo, lo + ext) of grid nodes.
@@ -136,32 +137,47 @@ __device__ __forceinline__ void grad_n_f32(const float (&w)[D][3], const float (
   }
 }
 
-// The neo-Hookean Hessian applied to one particle in FP32, recomputed from
-// the current Newton iterate: F_hat = (I + G_u) F^n, dF = G_d F^n and
-// Y = V0 dP[F_hat; dF] F^nT with
+// Reduce-scatter over an aligned group of L lanes (L a power of two, NV a
+// multiple of L): afterwards lane r of the group holds, in v[0 .. NV/L), the
+// group's sums of the values r NV/L .. (r + 1) NV/L - 1.  Recursive halving:
+// at distance h a lane keeps the half of its current segment selected by
+// (r & h), sends the other half to lane r ^ h and adds what it receives.
+template <int L, int NV>
+__device__ __forceinline__ void group_reduce_scatter(float (&v)[NV], int r) {
+  static_assert(NV % L == 0, "NV must be a multiple of L");
+#pragma unroll
+  for (int h = L / 2, seg = NV; h >= 1; h >>= 1, seg >>= 1) {
+    const bool upper = (r & h) != 0;
+#pragma unroll
+    for (int i = 0; i < seg / 2; ++i) {
+      const float send = upper ? v[i] : v[i + seg / 2];
+      const float keep = upper ? v[i + seg / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, h);
+    }
+  }
+}
+
+// The particle Hessian in FP32 at the Newton iterate's deformation
+// gradient F_hat (stored per particle by the gradient kernel, computed there
+// in FP64): dF = G_d F^n and Y = V0 dP[F_hat; dF] F^nT with
 //   dP[dF] = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
-// (the same operator as the cached block L(G) = V0 dP[G F^n] F^nT of the
+// (the operator of the cached block L(G) = V0 dP[G F^n] F^nT of the
 // gradient kernel).  Returns G_d : Y, the particle's share of d.Kd.
 template <int D>
-__device__ __forceinline__ float hessian_apply_f32(const float (&Gu)[D * D], const float (&Gd)[D * D],
-                                                   const float (&Fn)[D * D], float mu, float lam,
-                                                   float V0, float (&Y)[D * D]) {
+__device__ __forceinline__ float hessian_apply_fh(const float (&Fh)[D * D], const float (&Gd)[D * D],
+                                                  const float (&Fn)[D * D], float mu, float lam,
+                                                  float V0, float (&Y)[D * D]) {
   constexpr int DD = D * D;
-  float Fh[DD], dF[DD];
+  float dF[DD];
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-      float t = Fn[a * D + b], s = 0.0f;
+      float t = 0.0f;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        t = fmaf(Gu[a * D + c], Fn[c * D + b], t);
-        s = fmaf(Gd[a * D + c], Fn[c * D + b], s);
-      }
-      Fh[a * D + b] = t;
-      dF[a * D + b] = s;
+      for (int c = 0; c < D; ++c) t = fmaf(Gd[a * D + c], Fn[c * D + b], t);
+      dF[a * D + b] = t;
     }
-  // J - 1 expanded in H = F_hat - I (no cancellation near J = 1), F^-T
   float H[DD];
 #pragma unroll
   for (int i = 0; i < DD; ++i) H[i] = Fh[i] - ((i % (D + 1)) == 0 ? 1.0f : 0.0f);
@@ -197,8 +213,7 @@ __device__ __forceinline__ float hessian_apply_f32(const float (&Gu)[D * D], con
 #pragma unroll
   for (int i = 0; i < DD; ++i) tr = fmaf(A[i], dF[i], tr);
   const float c1 = mu - lam * lnJ, c2 = lam * tr;
-  // B = dF^T A, then (A dF^T A)_ac = sum_e A_ae B_ec
-  float Bm[DD];
+  float Bm[DD];  // dF^T A
 #pragma unroll
   for (int e = 0; e < D; ++e)
 #pragma unroll
@@ -232,32 +247,11 @@ __device__ __forceinline__ float hessian_apply_f32(const float (&Gu)[D * D], con
   return qf;
 }
 
-// Reduce-scatter over an aligned group of L lanes (L a power of two, NV a
-// multiple of L): afterwards lane r of the group holds, in v[0 .. NV/L), the
-// group's sums of the values r NV/L .. (r + 1) NV/L - 1.  Recursive halving:
-// at distance h a lane keeps the half of its current segment selected by
-// (r & h), sends the other half to lane r ^ h and adds what it receives.
-template <int L, int NV>
-__device__ __forceinline__ void group_reduce_scatter(float (&v)[NV], int r) {
-  static_assert(NV % L == 0, "NV must be a multiple of L");
-#pragma unroll
-  for (int h = L / 2, seg = NV; h >= 1; h >>= 1, seg >>= 1) {
-    const bool upper = (r & h) != 0;
-#pragma unroll
-    for (int i = 0; i < seg / 2; ++i) {
-      const float send = upper ? v[i] : v[i + seg / 2];
-      const float keep = upper ? v[i + seg / 2] : v[i];
-      v[i] = keep + __shfl_xor_sync(kFull, send, h);
-    }
-  }
-}
-
 // Shared memory of one block of the tiled Hessian-vector product.
 template <int D>
 struct HvpTileShared {
   static constexpr int CAP = TileCap<D>::NODES;
-  float su[D][CAP];   // Newton iterate u
-  float sd[D][CAP];   // direction p
+  float sd[D][CAP];   // direction p at the tile nodes
   // K p accumulators in FP64: a node sums the contributions of up to 27
   // cells; for smooth directions they nearly cancel, and an FP32 sum loses
   // the small remainder (the plate-bending modes of a thin body)
@@ -265,27 +259,27 @@ struct HvpTileShared {
   TileBox<D> box;
 };
 
-// The tiled Hessian-vector product of one run of particles [p0, p1)
-// (p1 - p0 <= blockDim.x, one particle per thread; the whole block calls
-// it): q = a.w[0] += K p on the free DOFs with p = a.s[0], the particle
-// Hessian recomputed from the Newton iterate a.u (no cached blocks or
-// stencils: per particle it reads x, F^n, V0, mu, lam); acc += this run's
-// share of p.Kp = sum_p G:Y.  The block stages the node box of the run's
-// stencils in shared memory (gathers from it, scatters into FP64 shared
-// accumulators flushed with one global atomic per tile node and
-// component); a warp of full cells (aligned groups of 2^D particles with one
-// stencil base) first reduce-scatters its contributions over each group.
-// A run whose node box exceeds the tile works on global memory.
+// The tiled Hessian-vector product of the particles in slots [s0, s1)
+// (s1 - s0 <= blockDim.x, one slot per thread, s0 a multiple of 2^D; the
+// whole block calls it): q = a.w[0] += K p on the free DOFs with
+// p = a.s[0], and acc += this run's share of p.Kp = sum_p G:Y.  Per particle
+// it reads x, F^n, the Newton iterate's F_hat, V0, mu, lam.  The block
+// stages the node box of its particles' stencils in shared memory, gathers
+// from it, and scatters into FP64 shared accumulators flushed with one
+// global atomic per tile node and component.  The slots come in aligned
+// groups of 2^D whose particles share a stencil base, so each group first
+// reduce-scatters its contributions among its lanes (FP32, 2^D terms) and
+// every lane adds a few group sums to the tile.  A run whose node box
+// exceeds the tile works on global memory (per-lane global atomics).
 template <int D>
-__device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t p0, int64_t p1,
+__device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, int64_t s1,
                                          HvpTileShared<D>& sh, double& acc) {
   constexpr int DD = D * D;
   constexpr int K = (D == 2) ? 9 : 27;
   constexpr int CAP = TileCap<D>::NODES;
-  constexpr int GL = 1 << D;                 // particles per full cell (2 per axis)
+  constexpr int GL = 1 << D;                 // lanes per slot group
   constexpr int KC = 9;                      // stencil nodes per scatter chunk
   constexpr int NVP = ((KC * D + GL - 1) / GL) * GL;
-  auto& su = sh.su;
   auto& sd = sh.sd;
   auto& sq = sh.sq;
   auto& box = sh.box;
@@ -293,198 +287,171 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t p0, i
   const int64_t n = a.P.n;
   const double* pv = a.s[0];
   double* q = a.w[0];
-  const int lane = threadIdx.x & 31, gr = lane & (GL - 1);
-  {
-    const int64_t pi = p0 + threadIdx.x;
-    const bool in = pi < p1;
-    double xp[D];
-    int base[D];
-    float w[D][3], dw[D][3];
-    bool valid = false;
-    if (in) {
+  const int gr = threadIdx.x & (GL - 1);
+  const int64_t slot = s0 + threadIdx.x;
+  const int64_t pi = slot < s1 ? (int64_t)a.slot2p[slot] : -1;
+  double xp[D];
+  int base[D];
+  float w[D][3], dw[D][3];
+  bool valid = false;
+  if (pi >= 0) {
 #pragma unroll
-      for (int c = 0; c < D; ++c) xp[c] = a.P.x[c * n + pi];
-      valid = stencil_f32<D>(xp, g, base, w, dw);
-    } else {
-#pragma unroll
-      for (int c = 0; c < D; ++c) base[c] = 0;
-    }
-    tile_box<D>(base, valid, CAP, box);
-    const bool tiled = box.nodes > 0;
-    // a warp whose lanes form aligned groups of GL = 2^D particles with one
-    // stencil base per group (full cells of 2^D particles, Morton-sorted)
-    // scatters through the group reduce-scatter
-    bool grouped = false;
-    if (tiled) {
-      int key = -1 - lane;
-      if (valid) key = tile_local<D>(box, base[0] - box.lo[0], base[1] - box.lo[1],
-                                     base[D - 1] - box.lo[D - 1]);
-      const unsigned run = __match_any_sync(kFull, key);
-      const unsigned mine = ((1u << GL) - 1u) << (lane & ~(GL - 1));
-      grouped = __all_sync(kFull, valid && run == mine);
-    }
-    if (tiled) {
-      for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
-        const int64_t gi = tile_global<D>(box, g, l);
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          su[c][l] = (float)__ldg(&a.u[c * g.nn + gi]);
-          sd[c][l] = (float)__ldcg(&pv[c * g.nn + gi]);
-          sq[c][l] = 0.0;
-        }
-      }
-      __syncthreads();
-    }
-    if (valid) {
-      // local index of the stencil base inside the tile (when tiled)
-      const int lb = tiled ? tile_local<D>(box, base[0] - box.lo[0], base[1] - box.lo[1],
-                                           base[D - 1] - box.lo[D - 1])
-                           : 0;
-      int64_t gb = base[0];
-      {
-        int64_t stride = g.res[0];
-#pragma unroll
-        for (int c = 1; c < D; ++c) {
-          gb += (int64_t)base[c] * stride;
-          stride *= g.res[c];
-        }
-      }
-      float Gu[DD], Gd[DD];
-#pragma unroll
-      for (int e = 0; e < DD; ++e) {
-        Gu[e] = 0.0f;
-        Gd[e] = 0.0f;
-      }
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
-        float dN[D];
-        grad_n_f32<D>(w, dw, k, dN);
-        float uk[D], dk[D];
-        if (tiled) {
-          const int l = lb + tile_local<D>(box, o0, o1, o2);
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            uk[c] = su[c][l];
-            dk[c] = sd[c][l];
-          }
-        } else {
-          const int64_t gi =
-              gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
-                           : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            uk[c] = (float)__ldg(&a.u[c * g.nn + gi]);
-            dk[c] = (float)__ldcg(&pv[c * g.nn + gi]);
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-#pragma unroll
-          for (int b = 0; b < D; ++b) {
-            Gu[c * D + b] = fmaf(uk[c], dN[b], Gu[c * D + b]);
-            Gd[c * D + b] = fmaf(dk[c], dN[b], Gd[c * D + b]);
-          }
-      }
-      float Fn[DD];
-#pragma unroll
-      for (int e = 0; e < DD; ++e) Fn[e] = a.P.F[e * n + pi];
-      float Y[DD];
-      const float qf = hessian_apply_f32<D>(Gu, Gd, Fn, (float)a.P.mu[pi], (float)a.P.lam[pi],
-                                            (float)a.P.vol0[pi], Y);
-      acc += (double)qf;
-      if (grouped) {
-        // the lanes of one cell share their 3^D target nodes: reduce-scatter
-        // each chunk of KC nodes (one stencil layer) over the group, then
-        // every lane adds its share of the chunk's sums to the tile
-#pragma unroll
-        for (int o2c = 0; o2c < 3; ++o2c) {
-          float v[NVP];
-#pragma unroll
-          for (int j = 0; j < NVP; ++j) v[j] = 0.0f;
-#pragma unroll
-          for (int kk = 0; kk < KC; ++kk) {
-            const int k = (D == 2 ? 0 : 9 * o2c) + kk;
-            float dN[D];
-            grad_n_f32<D>(w, dw, k, dN);
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-              float s = 0.0f;
-#pragma unroll
-              for (int b = 0; b < D; ++b) s = fmaf(Y[c * D + b], dN[b], s);
-              v[kk * D + c] = s;
-            }
-          }
-          group_reduce_scatter<GL, NVP>(v, gr);
-#pragma unroll
-          for (int j = 0; j < NVP / GL; ++j) {
-            const int idx = gr * (NVP / GL) + j;  // value index within the chunk
-            if (idx < KC * D) {
-              const int kk = idx / D, c = idx - kk * D;
-              const int k = (D == 2 ? 0 : 9 * o2c) + kk;
-              atomicAdd(&sq[c][lb + tile_local<D>(box, k % 3, (k / 3) % 3, k / 9)], (double)v[j]);
-            }
-          }
-          if (D == 2) break;  // one chunk holds the whole 2D stencil
-        }
-      } else {
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
-        float dN[D];
-        grad_n_f32<D>(w, dw, k, dN);
-        float f[D];
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          float s = 0.0f;
-#pragma unroll
-          for (int b = 0; b < D; ++b) s = fmaf(Y[c * D + b], dN[b], s);
-          f[c] = s;
-        }
-        if (tiled) {
-          const int l = lb + tile_local<D>(box, o0, o1, o2);
-#pragma unroll
-          for (int c = 0; c < D; ++c) atomicAdd(&sq[c][l], (double)f[c]);
-        } else {
-          const int64_t gi =
-              gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
-                           : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
-          const unsigned fm = a.dofmask[gi];
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            if ((fm >> c) & 1u) atomicAdd(&q[c * g.nn + gi], (double)f[c]);
-        }
-      }
-      }
-    }
-    if (tiled) {
-      __syncthreads();
-      for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
-        const int64_t gi = tile_global<D>(box, g, l);
-        const unsigned fm = a.dofmask[gi];
-        if (!fm) continue;
-#pragma unroll
-        for (int c = 0; c < D; ++c)
-          if (((fm >> c) & 1u) && sq[c][l] != 0.0) atomicAdd(&q[c * g.nn + gi], sq[c][l]);
-      }
-    }
-    __syncthreads();  // the tile arrays are reused by the next tile
+    for (int c = 0; c < D; ++c) xp[c] = a.P.x[c * n + pi];
+    valid = stencil_f32<D>(xp, g, base, w, dw);
   }
+  if (!valid) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) base[c] = 0;
+  }
+  tile_box<D>(base, valid, CAP, box);
+  const bool tiled = box.nodes > 0;
+  if (tiled) {
+    for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
+      const int64_t gi = tile_global<D>(box, g, l);
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        sd[c][l] = (float)__ldcg(&pv[c * g.nn + gi]);
+        sq[c][l] = 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  const int lb = (tiled && valid) ? tile_local<D>(box, base[0] - box.lo[0], base[1] - box.lo[1],
+                                                  base[D - 1] - box.lo[D - 1])
+                                  : 0;
+  int64_t gb = base[0];
+  {
+    int64_t stride = g.res[0];
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+      gb += (int64_t)base[c] * stride;
+      stride *= g.res[c];
+    }
+  }
+  float Y[DD];
+#pragma unroll
+  for (int e = 0; e < DD; ++e) Y[e] = 0.0f;
+  if (valid) {
+    float Gd[DD];
+#pragma unroll
+    for (int e = 0; e < DD; ++e) Gd[e] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+      float dN[D];
+      grad_n_f32<D>(w, dw, k, dN);
+      float dk[D];
+      if (tiled) {
+        const int l = lb + tile_local<D>(box, o0, o1, o2);
+#pragma unroll
+        for (int c = 0; c < D; ++c) dk[c] = sd[c][l];
+      } else {
+        const int64_t gi = gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
+                                        : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
+#pragma unroll
+        for (int c = 0; c < D; ++c) dk[c] = (float)__ldcg(&pv[c * g.nn + gi]);
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int b = 0; b < D; ++b) Gd[c * D + b] = fmaf(dk[c], dN[b], Gd[c * D + b]);
+    }
+    float Fn[DD], Fh[DD];
+#pragma unroll
+    for (int e = 0; e < DD; ++e) {
+      Fn[e] = a.P.F[e * n + pi];
+      Fh[e] = a.fhat[e * n + pi];
+    }
+    acc += (double)hessian_apply_fh<D>(Fh, Gd, Fn, (float)a.P.mu[pi], (float)a.P.lam[pi],
+                                       (float)a.P.vol0[pi], Y);
+  }
+  if (tiled) {
+    // every lane of the warp takes part in its group's reduce-scatter (a
+    // padding slot adds zeros); chunks of KC stencil nodes (one layer)
+#pragma unroll
+    for (int o2c = 0; o2c < 3; ++o2c) {
+      float v[NVP];
+#pragma unroll
+      for (int j = 0; j < NVP; ++j) v[j] = 0.0f;
+      if (valid) {
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+          const int k = (D == 2 ? 0 : 9 * o2c) + kk;
+          float dN[D];
+          grad_n_f32<D>(w, dw, k, dN);
+#pragma unroll
+          for (int c = 0; c < D; ++c) {
+            float t = 0.0f;
+#pragma unroll
+            for (int b = 0; b < D; ++b) t = fmaf(Y[c * D + b], dN[b], t);
+            v[kk * D + c] = t;
+          }
+        }
+      }
+      group_reduce_scatter<GL, NVP>(v, gr);
+      // the group's base: from any valid lane of the group (lane gr holds the
+      // sums of values gr NVP/GL .. (gr + 1) NVP/GL - 1)
+      const unsigned gmask = ((1u << GL) - 1u) << ((threadIdx.x & 31) & ~(GL - 1));
+      // (the shuffle runs in every lane: a group with no particle reads its
+      // own lane, so no lane of a partly filled warp skips it)
+      const unsigned vmask = __ballot_sync(kFull, valid) & gmask;
+      const int glb = __shfl_sync(kFull, lb, vmask ? __ffs(vmask) - 1 : (int)(threadIdx.x & 31));
+      if (vmask) {
+#pragma unroll
+        for (int j = 0; j < NVP / GL; ++j) {
+          const int idx = gr * (NVP / GL) + j;
+          if (idx < KC * D) {
+            const int kk = idx / D, c = idx - kk * D;
+            const int k = (D == 2 ? 0 : 9 * o2c) + kk;
+            atomicAdd(&sq[c][glb + tile_local<D>(box, k % 3, (k / 3) % 3, k / 9)], (double)v[j]);
+          }
+        }
+      }
+      if (D == 2) break;  // one chunk holds the whole 2D stencil
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
+      const int64_t gi = tile_global<D>(box, g, l);
+      const unsigned fm = a.dofmask[gi];
+      if (!fm) continue;
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        if (((fm >> c) & 1u) && sq[c][l] != 0.0) atomicAdd(&q[c * g.nn + gi], sq[c][l]);
+    }
+  } else if (valid) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+      float dN[D];
+      grad_n_f32<D>(w, dw, k, dN);
+      const int64_t gi = gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
+                                      : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
+      const unsigned fm = a.dofmask[gi];
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float t = 0.0f;
+#pragma unroll
+        for (int b = 0; b < D; ++b) t = fmaf(Y[c * D + b], dN[b], t);
+        if ((fm >> c) & 1u) atomicAdd(&q[c * g.nn + gi], (double)t);
+      }
+    }
+  }
+  __syncthreads();  // the tile arrays are reused by the next run
 }
 
-// Streaming-PCG Hessian-vector product, mixed precision, block tiles
-// (hvp_tile over runs of TileCap<D>::THREADS particles, grid stride); p.Kp
-// into S->pq.
+// Streaming-PCG Hessian-vector product, mixed precision, block tiles over
+// the cell-aligned slots (hvp_tile, grid stride); p.Kp into S->pq.
 template <int D>
-__global__ void __launch_bounds__(TileCap<D>::THREADS) k_cgs_hvp_tile(PcgArgsT<float> a) {
+__global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS)
+    k_cgs_hvp_tile(PcgArgsT<float> a) {
   if (__ldcg(&a.S->cg_done)) return;
   __shared__ HvpTileShared<D> sh;
-  const int64_t n = a.P.n;
+  const int64_t ns = __ldcg(a.n_slots);
   double acc[1] = {0.0};
-  const int64_t tiles = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t tiles = (ns + blockDim.x - 1) / blockDim.x;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t p0 = t * blockDim.x;
-    hvp_tile<D>(a, p0, p0 + blockDim.x < n ? p0 + blockDim.x : n, sh, acc[0]);
+    const int64_t s0 = t * blockDim.x;
+    hvp_tile<D>(a, s0, s0 + blockDim.x < ns ? s0 + blockDim.x : ns, sh, acc[0]);
   }
   double tot[1];
   if (grid_sum<1>(acc, a.partials, &a.S->counter, tot) && threadIdx.x == 0) a.S->pq = tot[0];
@@ -650,6 +617,110 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS)
     }
     __syncthreads();  // the tile is reused by the next run of particles
   }
+}
+
+// ---------------------------------------------------------------------------
+// Cell-aligned slots.  The tiled Hessian-vector product works on groups of
+// 2^D lanes whose particles share a stencil base (they scatter to the same
+// 3^D nodes, so a group reduces its contributions among its lanes before
+// touching shared memory).  Runs of equal base in Morton order are not
+// aligned to such groups (a body's boundary cells hold fewer particles), so
+// after each P2G the particles are dealt to slots: every run starts a new
+// group of 2^D slots and longer runs take several groups; unused slots hold
+// -1.  slot2p[slot] = particle.
+// ---------------------------------------------------------------------------
+constexpr int kScanItems = 1024;  // items per block of the device-wide scans
+
+// Inclusive scan (sum or max, non-negative ints) of one block's items; the
+// block's total into bsum.
+template <bool MAX>
+__global__ void __launch_bounds__(256) k_scan_block(const int* in, int* out, int64_t n,
+                                                     int* bsum) {
+  __shared__ int sh[kScanItems];
+  const int64_t base = (int64_t)blockIdx.x * kScanItems;
+  for (int i = threadIdx.x; i < kScanItems; i += blockDim.x)
+    sh[i] = base + i < n ? in[base + i] : 0;
+  __syncthreads();
+  for (int off = 1; off < kScanItems; off <<= 1) {
+    int v[kScanItems / 256];
+#pragma unroll
+    for (int r = 0; r < kScanItems / 256; ++r) {
+      const int i = threadIdx.x + r * 256;
+      v[r] = i >= off ? (MAX ? max(sh[i], sh[i - off]) : sh[i] + sh[i - off]) : sh[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kScanItems / 256; ++r) sh[threadIdx.x + r * 256] = v[r];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < kScanItems; i += blockDim.x)
+    if (base + i < n) out[base + i] = sh[i];
+  if (threadIdx.x == 0) bsum[blockIdx.x] = sh[kScanItems - 1];
+}
+
+// Inclusive scan of the block totals in place (one block, serial chunks).
+template <bool MAX>
+__global__ void k_scan_top(int* bsum, int nb) {
+  __shared__ int carry;
+  __shared__ int sh[256];
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int b0 = 0; b0 < nb; b0 += 256) {
+    const int i = b0 + threadIdx.x;
+    sh[threadIdx.x] = i < nb ? bsum[i] : 0;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+      const int v = threadIdx.x >= off ? (MAX ? max(sh[threadIdx.x], sh[threadIdx.x - off])
+                                              : sh[threadIdx.x] + sh[threadIdx.x - off])
+                                       : sh[threadIdx.x];
+      __syncthreads();
+      sh[threadIdx.x] = v;
+      __syncthreads();
+    }
+    const int c = carry;
+    if (i < nb) bsum[i] = MAX ? max(c, sh[threadIdx.x]) : c + sh[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) carry = MAX ? max(c, sh[255]) : c + sh[255];
+    __syncthreads();
+  }
+}
+
+template <bool MAX>
+__global__ void k_scan_add(int* out, int64_t n, const int* bsum) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = (int)(i / kScanItems);
+  if (b == 0) return;
+  const int c = bsum[b - 1];
+  out[i] = MAX ? max(out[i], c) : out[i] + c;
+}
+
+// rs[p] = p at a run start (p = 0 or a new stencil base), else 0.
+__device__ __forceinline__ bool run_start(const int* sbase, int64_t p) {
+  return p == 0 || sbase[p] != sbase[p - 1];
+}
+template <int GL>
+__global__ void k_slot_starts(const int* sbase, int64_t n, int* rs) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) rs[p] = run_start(sbase, p) ? (int)p : 0;
+}
+// flag[p] = 1 where a group of GL slots starts (rank in the run a multiple of GL)
+template <int GL>
+__global__ void k_slot_flags(const int* rs, int64_t n, int* flag) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) flag[p] = ((p - rs[p]) % GL) == 0 ? 1 : 0;
+}
+// slot2p[GL (groups before p's group) + lane] = p; the slot count into *n_slots
+template <int GL>
+__global__ void k_slot_fill(const int* rs, const int* gsum, const int* flag, int64_t n,
+                            int* slot2p, int* n_slots) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int lane = (int)((p - rs[p]) % GL);
+  const int64_t g0 = p - lane;                      // the group's first particle
+  const int group = gsum[g0] - 1;                   // inclusive sum of flags - 1
+  slot2p[(int64_t)GL * group + lane] = (int)p;
+  if (p == n - 1) *n_slots = GL * gsum[p];
 }
 
 }  // namespace osmpm

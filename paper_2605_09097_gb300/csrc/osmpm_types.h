@@ -60,6 +60,8 @@ struct DevScalars {
   int err;
   unsigned counter;
   unsigned bar_count, bar_spare;  // grid-barrier counter of the persistent PCG kernel
+  int n_slots;                     // cell-aligned slots of the last P2G (tiled product)
+  int pad_;
 };
 
 enum : int {
@@ -89,7 +91,13 @@ struct PcgArgsT {
   int* err;
   const int* sbase;     // per particle: flat index of the stencil's base node
   const R* sdn;         // per particle: grad N of the 3^D stencil nodes, [(c*K + k)*n + p]
-  const double* u;      // the Newton iterate (the tiled product recomputes the Hessian)
+  const double* u;      // the Newton iterate
+  // the tiled product (mixed precision): cell-aligned slots of the last P2G
+  // (slot2p[slot] = particle or -1, *n_slots of them, device) and each
+  // particle's deformation gradient at the Newton iterate, [e*n + p]
+  const int* slot2p;
+  const int* n_slots;
+  const R* fhat;
 };
 
 // Batched PCG over many domains (osmpm_multi.cuh): items [lo, hi)
@@ -101,8 +109,10 @@ struct MultiTile {
 
 // Where an instance's tiles sit in the two work lists.
 struct MultiInfo {
-  int pt0, npt;  // particle tiles
+  int pt0, npt;  // slot tiles
   int dt0, ndt;  // DOF tiles
+  int fresh;     // 1: the system joins with this launch (its PCG start runs)
+  int pad_;
 };
 
 struct MultiArgs {
@@ -115,7 +125,7 @@ struct MultiArgs {
   int n_inst;
   double* part;   // tile partials, row k at part[k * stride + tile]
   int stride;
-  int* pending;   // instances whose PCG is still running (written by k_m_pending)
+  int* pending;   // [0]: systems still iterating; [1 + 2i], [2 + 2i]: stop flag, iterations
 };
 
 }  // namespace osmpm

@@ -121,7 +121,8 @@ class osmpm_multi_desc(Structure):
 class osmpm_multi_stats(Structure):
     _fields_ = [("batches", c_int64), ("instances", c_int64), ("chunks", c_int64),
                 ("max_batch", c_int64), ("particles", c_int64), ("dofs", c_int64),
-                ("device_ms", c_double)]
+                ("iterations", c_int64), ("particle_iterations", c_int64),
+                ("dof_iterations", c_int64), ("device_ms", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -13,6 +13,17 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_json_line():
     out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
                           "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    _check_reference_line(out, "batched_inclusion_256_literal_mixed")
+
+
+def test_reference_arm_json_line_single_inclusion():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                          "inclusion", "--steps", "1", "--warmup", "0"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=300)
+    _check_reference_line(out, "inclusion_osmpm_2d_fp64")
+
+
+def _check_reference_line(out, workload):
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -22,7 +33,7 @@ def test_reference_arm_json_line():
               "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
         assert k in d, k
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
-    assert d["config"]["workload"].startswith("inclusion_osmpm_2d_fp64")
+    assert d["config"]["workload"].startswith(workload)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     e2e = d["e2e"]

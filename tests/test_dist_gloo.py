@@ -53,9 +53,11 @@ def _ref_worker(rank, world, port, out):
     r, local, w = bench.dist_init(world)
     calls = []
     bench.oracle_sample = lambda n: (calls.append(n), (0.5, 10.0))[1]
+    bench.oracle_instance_sample = lambda i, s: (calls.append((i, s)), (0.5, 10.0))[1]
 
     class A:
         steps, warmup = 2, 1
+        workload = "default"
     res = bench.run_reference(A, r, w)
     out[rank] = (res is None, len(calls), None if res is None else res["value"])
     import torch.distributed as dist

@@ -59,7 +59,9 @@ def test_multi_matches_pairs_stepped_alone(env, threads, dof_tile, chunk):
         stats, status, ms = osmpm.osmpm_schwarz_couple_multi(
             B, S, dT, [s[2] for s in specs], n_threads=threads, dof_tile=dof_tile, chunk=chunk)
         assert all(s == osmpm.OSMPM_OK for s in status)
-        assert ms["batches"] > 0 and ms["instances"] >= ms["batches"] and ms["max_batch"] >= 1
+        assert ms["batches"] > 0 and ms["chunks"] >= ms["batches"] and ms["instances"] > 0
+        assert 1 <= ms["max_batch"] <= len(specs)
+        assert ms["iterations"] > 0 and ms["particle_iterations"] >= ms["iterations"]
         for i in range(len(specs)):
             st1 = osmpm.osmpm_schwarz_couple(B1[i], S1[i], dT, specs[i][2])
             assert abs(stats[i]["schwarz_iters"] - st1["schwarz_iters"]) <= 1
