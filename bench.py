@@ -403,11 +403,16 @@ def cpu_baseline(n_iters):
                       "of a global step's units"}
 
 
-# Algorithmic bytes of one PCG iteration per particle in mixed precision
-# (particle state read once: x, F^n, V0, mu, lam and the gathered x_hat, p,
-# scattered Kp per node, plus the Jacobi-PCG vector updates per node at
-# 1/ppc node per particle): 2D 52 + 40/4 B, 3D 78 + 60/8 B.
-MIXED_PCG_BYTES_PER_PARTICLE = {2: 52.0 + 40.0 / 4, 3: 78.0 + 60.0 / 8}
+# Algorithmic bytes of one mixed-precision Hessian-vector product per
+# particle (SURVEY's HVP row: the particle state read once, the gathered
+# x_hat and d and the scattered Hd once per node at 1/ppc node per
+# particle): 2D x 16 + F^n 16 + V0 4 + mu lam 8 + (16 + 8 + 8)/4 = 52 B,
+# 3D x 24 + F^n 36 + V0 4 + mu lam 8 + (24 + 12 + 12)/8 = 78 B
+MIXED_HVP_BYTES_PER_PARTICLE = {2: 52.0, 3: 78.0}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch on the
+# 3.07M-particle fold band (ncu), per kernel; absent until captured for the
+# current kernel
+FOLD_HVP_TRAFFIC_BYTES = {}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the batched
 # Hessian-vector product (k_m_hvp) on the batched family, from ncu; None
 # until captured for the current kernel
@@ -480,22 +485,31 @@ def run_batched(args, rank, local, world):
     launches = int(osmpm.launch_count() - launches0)
     roofline = None
     if multi and service:
+        # the dominant kernel of the PCG service: the batched Hessian-vector
+        # product k_m_hvp, each launch bracketed by CUDA events on the
+        # service's stream; its algorithmic bytes are SURVEY's HVP figure per
+        # particle and iteration over the systems that launch iterated
         peaks, src = measured_peaks()
         d = specs[0][0].grid.dim
-        bytes_ = sum(x["particle_iterations"] for x in service) * MIXED_PCG_BYTES_PER_PARTICLE[d]
-        dev_s = sum(x["device_ms"] for x in service) / 1e3
-        nb = sum(x["batches"] for x in service)
-        achieved = bytes_ / dev_s / 1e9 if dev_s > 0 else 0.0
-        roofline = {"kernel": "batched PCG (k_m_hvp + k_m_alpha + k_m_beta per iteration)",
-                    "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+        pit = sum(x["particle_iterations"] for x in service)
+        bytes_ = pit * MIXED_HVP_BYTES_PER_PARTICLE[d]
+        hvp_s = sum(x["hvp_ms"] for x in service) / 1e3
+        nl = sum(x["hvp_launches"] for x in service)
+        achieved = bytes_ / hvp_s / 1e9 if hvp_s > 0 else 0.0
+        roofline = {"kernel": "k_m_hvp", "bound": "hbm", "achieved": achieved,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": MULTI_HVP_TRAFFIC_BYTES,
                     "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)" if src == "measured"
                     else "fallback 6.8 TB/s",
-                    "launches": nb, "avg_launch_us": 1e6 * dev_s / max(nb, 1),
-                    "bytes_per_launch": bytes_ / max(nb, 1),
-                    "bytes_per_particle_iteration": MIXED_PCG_BYTES_PER_PARTICLE[d],
+                    "launches": nl, "avg_launch_us": 1e6 * hvp_s / max(nl, 1),
+                    "bytes_per_launch": bytes_ / max(nl, 1),
+                    "bytes_per_particle_iteration": MIXED_HVP_BYTES_PER_PARTICLE[d],
+                    "particle_iterations": pit,
                     "pcg_iterations": sum(x["iterations"] for x in service),
-                    "systems_per_batch": sum(x["instances"] for x in service) / max(nb, 1)}
+                    "pcg_device_ms": sum(x["device_ms"] for x in service),
+                    "hvp_device_ms": 1e3 * hvp_s,
+                    "systems_per_composition": sum(x["instances"] for x in service)
+                    / max(sum(x["batches"] for x in service), 1)}
     e2e = None
     if args.e2e_steps > 0:
         # end to end through the public API: every pair's particle state
@@ -739,6 +753,20 @@ def run_fold_solve(args, rank, local, world):
             ms += a.elapsed_time(b)
         c = dom.counters()
     n = spec.particles.n
+    peaks, src = measured_peaks()
+    # the dominant kernel: the streaming PCG's Hessian-vector product (each
+    # launch that iterated bracketed by CUDA events on the domain's stream);
+    # algorithmic bytes per launch = particles x SURVEY's 3D mixed HVP figure
+    nl, hvp_s = c["hvp_launches"], c["hvp_ms"] / 1e3
+    bpl = n * MIXED_HVP_BYTES_PER_PARTICLE[3]
+    achieved = nl * bpl / hvp_s / 1e9 if hvp_s > 0 else 0.0
+    kname = "k_cgs_hvp_tile" if args.hvp_mode != 1 else "k_cgs_hvp"
+    roofline = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "traffic": FOLD_HVP_TRAFFIC_BYTES.get(kname),
+                "peak_source": f"{src} hbm_gbs (MEASURED_PEAKS.json)" if src == "measured"
+                else "fallback 6.8 TB/s",
+                "launches": nl, "avg_launch_us": 1e6 * hvp_s / max(nl, 1), "bytes_per_launch": bpl}
     return {"metric": METRIC, "value": n * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "mixed",
@@ -747,7 +775,8 @@ def run_fold_solve(args, rank, local, world):
                        "hvp_mode": args.hvp_mode, "dt": dt,
                        "newton_iters_per_step": [s["newton_iters"] for s in stats],
                        "cg_iters_per_step": [s["cg_iters"] for s in stats],
-                       "us_per_pcg_iter": 1e3 * c["pcg_ms"] / max(c["pcg_iters"], 1)}}
+                       "us_per_pcg_iter": 1e3 * c["pcg_ms"] / max(c["pcg_iters"], 1)},
+            "roofline": roofline}
 
 
 def main():

@@ -334,6 +334,8 @@ typedef struct osmpm_multi_stats {
   int64_t particle_iterations;  /* sum over the systems of iterations x particles */
   int64_t dof_iterations;       /* sum over the systems of iterations x grid DOFs */
   double device_ms;    /* device time of the batched PCGs (CUDA events) */
+  double hvp_ms;       /* of which the batched Hessian-vector products (k_m_hvp) */
+  int64_t hvp_launches;  /* launches of k_m_hvp */
 } osmpm_multi_stats;
 
 osmpm_status osmpm_schwarz_couple_multi(osmpm_domain* const* coarse, osmpm_domain* const* fine,
@@ -500,6 +502,8 @@ typedef struct osmpm_counters {
   int64_t graph_replays;
   int32_t graphs;
   int32_t graph_error;
+  double hvp_ms;        /* streaming PCG: summed durations of its Hessian-vector */
+  int64_t hvp_launches; /* product launches that iterated (CUDA events) */
 } osmpm_counters;
 
 /* Enables (1) or disables (0) CUDA-event timing of this domain's PCG

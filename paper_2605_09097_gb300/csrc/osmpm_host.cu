@@ -222,6 +222,9 @@ struct osmpm_domain {
 
   // optional CUDA-event timing of the PCG launches (osmpm_set_profiling)
   bool time_hvp = false;
+  std::vector<cudaEvent_t> hev;  // streaming PCG: around each product of a chunk
+  double hvp_ms = 0.0;
+  int64_t hvp_launches = 0;
   std::vector<cudaEvent_t> ev;  // one start/stop pair
   double pcg_ms = 0.0;
   long long pcg_launches = 0, pcg_iters = 0;
@@ -320,6 +323,8 @@ void free_all(osmpm_domain* d) {
   }
   for (cudaEvent_t e : d->ev) cudaEventDestroy(e);
   d->ev.clear();
+  for (cudaEvent_t e : d->hev) cudaEventDestroy(e);
+  d->hev.clear();
   if (d->S_host) cudaFreeHost(d->S_host);
   if (d->err_host) cudaFreeHost(d->err_host);
   d->S_host = nullptr;
@@ -528,7 +533,7 @@ PcgArgsT<R> pcg_args(osmpm_domain* d, double dt) {
   a.slot2p = d->slot2p;
   a.n_slots = &d->S->n_slots;
   const int npk = (d->dim * d->dim) * (d->dim * d->dim + 1) / 2;
-  a.fhat = (const R*)d->L + (int64_t)npk * d->n;
+  a.tx = (const R*)d->L + (int64_t)npk * d->n;
   return a;
 }
 
@@ -567,10 +572,14 @@ cudaError_t launch_pcg(osmpm_domain* d, double dt, int64_t work, bool timed) {
 constexpr int kStreamChunk = 16;
 
 template <class K, class R>
-cudaError_t stream_pcg_chunk(osmpm_domain* d, double dt, bool first) {
+cudaError_t stream_pcg_chunk(osmpm_domain* d, double dt, bool first, bool timed) {
   const PcgArgsT<R> a = pcg_args<R>(d, dt);
   if (first) K::cgs_start(a, d->stream);
-  for (int i = 0; i < kStreamChunk; ++i) K::cgs_iteration(a, d->desc.hvp_mode, d->stream);
+  for (int i = 0; i < kStreamChunk; ++i) {
+    cudaEvent_t e0 = timed ? d->hev[(size_t)2 * i] : nullptr;
+    cudaEvent_t e1 = timed ? d->hev[(size_t)2 * i + 1] : nullptr;
+    K::cgs_iteration(a, d->desc.hvp_mode, d->stream, e0, e1);
+  }
   return cudaGetLastError();
 }
 
@@ -585,6 +594,17 @@ osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st);
 // only to kCheckEta and accepted when max |delta| <= tol / 2.
 constexpr double kCheckRatio = 500.0, kCheckEta = 0.1;
 
+// What the gradient kernel stores for the PCG's products: the packed
+// Hessian blocks (FP64, the persistent PCG, the lane-group product) and/or
+// the tiled product's per-particle data (mixed precision).  A mixed domain
+// on the streaming PCG with the tiled product, or in the batched PCG
+// service, needs only the latter.
+int grad_lmode(const osmpm_domain* d) {
+  if (d->prec != 1) return 1;
+  const bool tiled = d->desc.hvp_mode != 1;
+  return (tiled && (d->desc.pcg_mode == 2 || d->batcher)) ? 2 : 3;
+}
+
 // Gradient, Jacobi diagonal and the PCG start (x = 0, r[0], inverted
 // diagonal, tolerance and controls) of a Newton iteration.
 void enqueue_gradient(osmpm_domain* d, double dt, bool first, bool check) {
@@ -592,7 +612,8 @@ void enqueue_gradient(osmpm_domain* d, double dt, bool first, bool check) {
   const int D = d->dim;
   cudaMemsetAsync(d->grad, 0, sizeof(double) * D * nn, d->stream);
   cudaMemsetAsync(d->diag, 0, sizeof(double) * D * nn, d->stream);
-  DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream));
+  DISPATCH(d, K::grad(P_, d->geo, d->u, d->dofmask, d->grad, d->diag, L_, d->err, d->stream,
+                      grad_lmode(d)));
   const double eta_max = d->desc.cg_eta_max > 0.0 ? d->desc.cg_eta_max : kEtaMax;
   const double rtol = check ? std::max(kCheckEta, d->desc.cg_rtol) : d->desc.cg_rtol;
   DISPATCH(d, K::grad_finish(d->geo, d->m, d->vn, d->u, d->dofmask, d->desc.gravity, dt, rtol,
@@ -816,6 +837,7 @@ struct PcgBatcher {
   int* pending_host = nullptr;  // pending count, then the instances' iteration counts
   int pending_cap = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> hev;  // around each k_m_hvp of a chunk
   std::string error;
   osmpm_multi_stats stats{};
 
@@ -828,6 +850,8 @@ struct PcgBatcher {
     CUDA_TRY(cudaMallocHost(&pending_host, sizeof(int) * (1 + pending_cap)));
     CUDA_TRY(cudaEventCreate(&ev[0]));
     CUDA_TRY(cudaEventCreate(&ev[1]));
+    hev.assign((size_t)2 * chunk, nullptr);
+    for (auto& e : hev) CUDA_TRY(cudaEventCreate(&e));
     int dev_id = 0;
     cudaGetDevice(&dev_id);
     th = std::thread([this, dev_id] {
@@ -850,6 +874,8 @@ struct PcgBatcher {
     if (host) cudaFreeHost(host);
     if (pending_host) cudaFreeHost(pending_host);
     for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto& e : hev)
       if (e) cudaEventDestroy(e);
     if (stream) cudaStreamDestroy(stream);
   }
@@ -1017,10 +1043,11 @@ struct PcgBatcher {
     return OSMPM_OK;
   }
 
-  void enqueue_chunk(const MultiArgs& m, int n) {
+  void enqueue_chunk(const MultiArgs& m, int n, bool capturing) {
     for (int c = 0; c < chunk; ++c) {
-      if (dim == 2) MultiKernels<2>::iteration(m, stream);
-      else MultiKernels<3>::iteration(m, stream);
+      cudaEvent_t e0 = hev[(size_t)2 * c], e1 = hev[(size_t)2 * c + 1];
+      if (dim == 2) MultiKernels<2>::iteration(m, stream, e0, e1, capturing);
+      else MultiKernels<3>::iteration(m, stream, e0, e1, capturing);
     }
     if (dim == 2) MultiKernels<2>::pending(m, stream);
     else MultiKernels<3>::pending(m, stream);
@@ -1034,7 +1061,7 @@ struct PcgBatcher {
     cudaGraphExec_t exec = nullptr;
     const long long before = g_launch_count.load();
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      enqueue_chunk(m, m.n_inst);
+      enqueue_chunk(m, m.n_inst, true);
       if (cudaStreamEndCapture(stream, &graph) != cudaSuccess || !graph ||
           cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
         exec = nullptr;
@@ -1053,7 +1080,7 @@ struct PcgBatcher {
       e = cudaGraphLaunch(exec, stream);
       g_launch_count += per_chunk;
     } else {
-      enqueue_chunk(m, (int)n);
+      enqueue_chunk(m, (int)n, false);
       e = cudaGetLastError();
     }
     cudaEventRecord(ev[1], stream);
@@ -1063,6 +1090,14 @@ struct PcgBatcher {
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
     stats.chunks += 1;
     stats.device_ms += ms;
+    for (int c = 0; c < chunk; ++c) {
+      float h = 0.f;
+      if (cudaEventElapsedTime(&h, hev[(size_t)2 * c], hev[(size_t)2 * c + 1]) == cudaSuccess) {
+        stats.hvp_ms += h;
+        stats.hvp_launches += 1;
+      }
+    }
+    cudaGetLastError();
     return OSMPM_OK;
   }
 };
@@ -1118,10 +1153,23 @@ osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st) {
     if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "cooperative PCG launch: %s", cudaGetErrorString(le));
   } else {
     if (timed) CUDA_TRY(cudaEventRecord(d->ev[0], d->stream));
+    int done_iters = 0;
     for (bool first = true;; first = false) {
-      DISPATCH(d, (le = stream_pcg_chunk<K, R>(d, dt, first)));
+      DISPATCH(d, (le = stream_pcg_chunk<K, R>(d, dt, first, timed)));
       if (le != cudaSuccess) return fail(OSMPM_E_CUDA, "streaming PCG launch: %s", cudaGetErrorString(le));
       OSMPM_TRY(sync_scalars(d));
+      if (timed) {
+        // the products of this chunk's iterations that ran (later ones
+        // returned at once)
+        const int ran = std::min(kStreamChunk, std::max(0, d->S_host->cg_iter - done_iters));
+        for (int i = 0; i < ran; ++i) {
+          float h = 0.f;
+          CUDA_TRY(cudaEventElapsedTime(&h, d->hev[(size_t)2 * i], d->hev[(size_t)2 * i + 1]));
+          d->hvp_ms += h;
+          d->hvp_launches += 1;
+        }
+        done_iters = d->S_host->cg_iter;
+      }
       if (d->S_host->cg_done || d->S_host->err) break;
     }
     if (timed) CUDA_TRY(cudaEventRecord(d->ev[1], d->stream));
@@ -1539,9 +1587,9 @@ osmpm_status osmpm_create_domain(const osmpm_domain_desc* desc, const osmpm_part
   C_TRY(dalloc_n(d, D * nn, &d->cpp));
   C_TRY(dalloc_n(d, D * nn, &d->cq));
   const int npk = (D * D) * (D * D + 1) / 2;
-  // mixed precision: the Hessian blocks, then each particle's deformation
-  // gradient at the Newton iterate (the tiled product), and its slots
-  C_TRY(dalloc(d, d->rsize * (npk + (d->prec == 1 ? D * D : 0)) * n, &d->L));
+  // mixed precision: the Hessian blocks, then the per-particle data of the
+  // tiled product at the Newton iterate, and the particles' slots
+  C_TRY(dalloc(d, d->rsize * (npk + (d->prec == 1 ? tile_x_count(D) : 0)) * n, &d->L));
   if (d->prec == 1) C_TRY(dalloc_n(d, (int64_t)(1 << D) * n, &d->slot2p));
   C_TRY(dalloc_n(d, n, &d->sbase));
   C_TRY(dalloc(d, d->rsize * D * (D == 2 ? 9 : 27) * n, &d->sdn));
@@ -1969,8 +2017,12 @@ osmpm_status osmpm_set_profiling(osmpm_domain* d, int32_t enable) {
   if (enable && d->ev.empty()) {
     d->ev.resize(2);
     for (auto& e : d->ev) CUDA_TRY(cudaEventCreate(&e));
+    d->hev.resize((size_t)2 * kStreamChunk);
+    for (auto& e : d->hev) CUDA_TRY(cudaEventCreate(&e));
   }
   d->time_hvp = enable != 0;
+  d->hvp_ms = 0.0;
+  d->hvp_launches = 0;
   d->pcg_ms = 0.0;
   d->pcg_launches = 0;
   d->pcg_iters = 0;
@@ -1989,6 +2041,8 @@ osmpm_status osmpm_get_counters(const osmpm_domain* d, osmpm_counters* out) {
     out->dofs = d->geo.nn * d->dim;
     out->graph_replays = d->graph_replays;
     out->graph_error = d->graph_error;
+    out->hvp_ms = d->hvp_ms;
+    out->hvp_launches = d->hvp_launches;
     for (const auto& gs : d->ngraph) out->graphs += gs.exec ? 1 : 0;
   }
   return OSMPM_OK;

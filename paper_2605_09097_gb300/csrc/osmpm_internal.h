@@ -91,8 +91,11 @@ struct AdjointKernels {
 template <int D>
 struct MultiKernels {
   static void start(const MultiArgs& m, cudaStream_t s);
-  // one PCG iteration of every instance still running
-  static void iteration(const MultiArgs& m, cudaStream_t s);
+  // one PCG iteration of every instance still running; with e0, e1 the
+  // Hessian-vector product is bracketed by event records (external event
+  // nodes when the stream is being captured)
+  static void iteration(const MultiArgs& m, cudaStream_t s, cudaEvent_t e0 = nullptr,
+                        cudaEvent_t e1 = nullptr, bool capturing = false);
   static void pending(const MultiArgs& m, cudaStream_t s);
   static int particle_tile();  // particles per tile (one per thread of a block)
 };
@@ -117,8 +120,10 @@ struct Kernels {
                         cudaStream_t s);
   static void grid_prep(const GridGeo& g, const double* m, const double* vn, const PrepArgs& a,
                         double dt, uint8_t* dofmask, double* u, cudaStream_t s);
+  // lmode: bit 1 the packed Hessian blocks L, bit 2 the tiled product's
+  // per-particle data (mixed precision); -1: every part the precision uses
   static void grad(const PartPtrsT<R>& P, const GridGeo& g, const double* u, const uint8_t* dofmask,
-                   double* grad, double* diag, R* L, int* err, cudaStream_t s);
+                   double* grad, double* diag, R* L, int* err, cudaStream_t s, int lmode = -1);
   // completes the gradient, inverts the Jacobi diagonal and starts PCG; the
   // PCG tolerance is eta |r0|, eta = |g|/|g_0| clamped to [cg_rtol, eta_max]
   // (g_0: the gradient of the solve's first Newton iteration, `first` = 1)
@@ -149,7 +154,9 @@ struct Kernels {
   static void cgs_start(const PcgArgsT<R>& a, cudaStream_t s);
   // hvp_mode (mixed precision only): 1 lane groups over the cached stencil
   // and Hessian blocks, otherwise block tiles recomputing the Hessian
-  static void cgs_iteration(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s);
+  // with e0, e1 the Hessian-vector product is bracketed by event records
+  static void cgs_iteration(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s,
+                            cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
   // the streaming PCG's particle product alone: a.w[0] += K a.s[0] on the
   // free DOFs, p.Kp into S->pq
   static void cgs_hvp(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s);

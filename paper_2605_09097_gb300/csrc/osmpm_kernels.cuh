@@ -188,61 +188,6 @@ __global__ void k_unpack_in(const double* x, const double* v, const double* B, c
   }
 }
 
-// ---------------------------------------------------------------------------
-// APIC particle-to-grid transfer (Eq. p2g_transfer, Eq. p2g_substep); with
-// bm != nullptr also the boundary-particle mass of Eq. boundary_grid_set.
-// ---------------------------------------------------------------------------
-template <int D, typename R>
-__global__ void __launch_bounds__(kThreads) k_p2g(PartPtrsT<R> P, GridGeo g, double* m, double* mv,
-                                                  double* bm, int* err, int* sbase, R* sdn) {
-  const int64_t p = gtid();
-  if (p >= P.n) return;
-  double xp[D], vp[D], Bp[D * D];
-  load_x<D>(P, p, xp);
-#pragma unroll
-  for (int a = 0; a < D; ++a) vp[a] = P.v[a * P.n + p];
-#pragma unroll
-  for (int e = 0; e < D * D; ++e) Bp[e] = P.B[e * P.n + p];
-  Stencil<D> s;
-  if (!make_stencil<D>(xp, g, s)) {
-    atomicOr(err, kErrOutOfGrid);
-    return;
-  }
-  const double mp = P.mass[p];
-  const double Dinv = 4.0 * g.inv_dx * g.inv_dx;  // D_p^-1 of the quadratic B-spline
-  const bool isb = (bm != nullptr) && (P.flags[p] & 1u);
-  if (sbase) {
-    int64_t b = 0, stride = 1;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      b += (int64_t)s.base[a] * stride;
-      stride *= g.res[a];
-    }
-    sbase[p] = (int)b;
-  }
-#pragma unroll 3
-  for (int k = 0; k < Pow3<D>::K; ++k) {
-    double N, dN[D];
-    const int64_t node = stencil_node<D>(s, g, k, N, dN);
-    if (sdn)
-#pragma unroll
-      for (int a = 0; a < D; ++a) sdn[(int64_t)(a * Pow3<D>::K + k) * P.n + p] = (R)dN[a];
-    double r[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) r[a] = stencil_node_pos<D>(s, g, k, a) - xp[a];
-    const double wm = mp * N;
-    atomicAdd(&m[node], wm);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      double va = 0.0;
-#pragma unroll
-      for (int b = 0; b < D; ++b) va += Bp[a * D + b] * r[b];
-      atomicAdd(&mv[a * g.nn + node], wm * (vp[a] + Dinv * va));
-    }
-    if (isb) atomicAdd(&bm[node], wm);
-  }
-}
-
 template <int D, typename R>
 __global__ void k_normalize(GridGeo g, const double* m, const double* mv, double* vn) {
   for (int64_t i = gtid(); i < g.nn; i += gstride()) {
@@ -329,7 +274,7 @@ __global__ void k_grid_prep(GridGeo g, const double* m, const double* vn, PrepAr
 template <int D, typename R>
 __global__ void __launch_bounds__(kThreads) k_grad(PartPtrsT<R> P, GridGeo g, const double* u,
                                                    const uint8_t* dofmask, double* grad,
-                                                   double* diag, R* L, int* err) {
+                                                   double* diag, R* L, int* err, int lmode) {
   constexpr int DD = D * D;
   const int64_t p = gtid();
   if (p >= P.n) return;
@@ -361,7 +306,8 @@ __global__ void __launch_bounds__(kThreads) k_grad(PartPtrsT<R> P, GridGeo g, co
       for (int b = 0; b < D; ++b) t += Pk[a * D + b] * Fn[c * D + b];
       Y[a * D + c] = V0 * t;
     }
-  // L columns: basis G = e_a e_b^T -> dF = e_a (row b of F^n)
+  // L columns: basis G = e_a e_b^T -> dF = e_a (row b of F^n); its diagonal
+  // blocks give the Jacobi diagonal, the packed blocks are stored when asked
   double Lfull[DD * DD];
 #pragma unroll
   for (int a = 0; a < D; ++a)
@@ -383,15 +329,28 @@ __global__ void __launch_bounds__(kThreads) k_grad(PartPtrsT<R> P, GridGeo g, co
           Lfull[(c * D + e) * DD + (a * D + b)] = V0 * t;
         }
     }
+  if (lmode & 1)
 #pragma unroll
-  for (int i = 0; i < DD; ++i)
+    for (int i = 0; i < DD; ++i)
 #pragma unroll
-    for (int j = i; j < DD; ++j)
-      L[(int64_t)Sym<D>::idx(i, j) * P.n + p] = (R)(0.5 * (Lfull[i * DD + j] + Lfull[j * DD + i]));
+      for (int j = i; j < DD; ++j)
+        L[(int64_t)Sym<D>::idx(i, j) * P.n + p] = (R)(0.5 * (Lfull[i * DD + j] + Lfull[j * DD + i]));
   if constexpr (std::is_same<R, float>::value) {
-    // the deformation gradient at this iterate, for the tiled product
+    if (lmode & 2) {
+      // the tiled product's data at this iterate (TileX): F^-T, the
+      // coefficients of dP with V0 folded in, the offsets from the base
+      R* X = L + (int64_t)Sym<D>::packed * P.n;
 #pragma unroll
-    for (int e = 0; e < DD; ++e) L[(int64_t)(Sym<D>::packed + e) * P.n + p] = (R)F[e];
+      for (int e = 0; e < DD; ++e) X[(int64_t)(TileX<D>::A + e) * P.n + p] = (R)nh.FiT[e];
+      X[(int64_t)TileX<D>::C1 * P.n + p] = (R)(V0 * (mu - lam * nh.lnJ));
+      X[(int64_t)TileX<D>::MU * P.n + p] = (R)(V0 * mu);
+      X[(int64_t)TileX<D>::LAM * P.n + p] = (R)(V0 * lam);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const double t = __dmul_rn(__dsub_rn(xp[a], g.o[a]), g.inv_dx);  // as make_stencil
+        X[(int64_t)(TileX<D>::FX + a) * P.n + p] = (R)(t - (double)s.base[a]);
+      }
+    }
   }
   // scatter gradient and diagonal
 #pragma unroll 3
@@ -1018,8 +977,9 @@ void Kernels<D, R>::grid_prep(const GridGeo& g, const double* m, const double* v
 template <int D, typename R>
 void Kernels<D, R>::grad(const PartPtrsT<R>& P, const GridGeo& g, const double* u,
                       const uint8_t* dofmask, double* grad, double* diag, R* L, int* err,
-                      cudaStream_t s) {
-  k_grad<D, R><<<OSMPM_NB(P.n)>>>(P, g, u, dofmask, grad, diag, L, err);
+                      cudaStream_t s, int lmode) {
+  if (lmode < 0) lmode = std::is_same<R, float>::value ? 3 : 1;
+  k_grad<D, R><<<OSMPM_NB(P.n)>>>(P, g, u, dofmask, grad, diag, L, err, lmode);
 }
 template <int D, typename R>
 void Kernels<D, R>::grad_finish(const GridGeo& g, const double* m, const double* vn,
@@ -1239,8 +1199,11 @@ void Kernels<D, R>::cgs_start(const PcgArgsT<R>& a, cudaStream_t s) {
   k_cgs_start<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
 }
 template <int D, typename R>
-void Kernels<D, R>::cgs_iteration(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s) {
+void Kernels<D, R>::cgs_iteration(const PcgArgsT<R>& a, int hvp_mode, cudaStream_t s,
+                                  cudaEvent_t e0, cudaEvent_t e1) {
+  if (e0) cudaEventRecord(e0, s);
   cgs_hvp(a, hvp_mode, s);
+  if (e1) cudaEventRecord(e1, s);
   k_cgs_alpha<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
   k_cgs_beta<D, R><<<OSMPM_RB(a.g.nn * D)>>>(a);
 }
@@ -1320,9 +1283,13 @@ void MultiKernels<D>::start(const MultiArgs& m, cudaStream_t s) {
   k_m_start<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
 }
 template <int D>
-void MultiKernels<D>::iteration(const MultiArgs& m, cudaStream_t s) {
+void MultiKernels<D>::iteration(const MultiArgs& m, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                                bool capturing) {
   g_launch_count += 3;
+  const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (e0) cudaEventRecordWithFlags(e0, s, flags);
   k_m_hvp<D><<<std::max(1, std::min(m.n_pt, kRedBlocksMax)), TileCap<D>::THREADS, 0, s>>>(m);
+  if (e1) cudaEventRecordWithFlags(e1, s, flags);
   k_m_alpha<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
   k_m_beta<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
 }

@@ -91,8 +91,9 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS) k
     const MultiTile T = m.pt[t];
     const PcgArgsT<float>& a = m.inst[T.inst];
     if (__ldcg(&a.S->cg_done)) continue;  // the whole instance stopped (set by the alpha kernel)
-    double acc[1] = {0.0};
-    hvp_tile<D>(a, T.lo, T.hi, sh, acc[0]);  // T.lo, T.hi: slots
+    float accf = 0.0f;
+    hvp_tile<D>(a, T.lo, T.hi, sh, accf);  // T.lo, T.hi: slots
+    double acc[1] = {(double)accf};
     const MultiInfo in = m.info[T.inst];
     double tot[1];
     if (inst_sum<1>(acc, m.part, m.stride, t, in.pt0, in.npt, &a.S->counter, tot) &&

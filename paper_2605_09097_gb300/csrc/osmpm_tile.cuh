@@ -96,22 +96,63 @@ __device__ __forceinline__ void tile_box(const int (&base)[D], bool valid, int c
   __syncthreads();
 }
 
-// Quadratic B-spline weights of one particle in FP32 (the stencil base in
-// FP64, exactly as make_stencil forms it), and its base node.  Returns false
-// when the support leaves the grid box.
+// Per-particle data of the tiled product, written by the gradient kernel at
+// each Newton iterate (FP32, entry e of particle p at [(off + e) n + p] past
+// the packed Hessian blocks): A = F_hat^-T (D*D), c1 = V0 (mu - lam ln J),
+// V0 mu, V0 lam, and the particle's offset from its stencil base in cells
+// (D values, t - base with t = (x - o)/dx), so that the product reads no
+// FP64 particle data.
 template <int D>
-__device__ __forceinline__ bool stencil_f32(const double* xp, const GridGeo& g, int (&base)[D],
-                                            float (&w)[D][3], float (&dw)[D][3]) {
-  bool ok = true;
-  const float inv_dx = (float)g.inv_dx;
+struct TileX {
+  static constexpr int A = 0;
+  static constexpr int C1 = D * D;
+  static constexpr int MU = D * D + 1;
+  static constexpr int LAM = D * D + 2;
+  static constexpr int FX = D * D + 3;
+  static constexpr int N = D * D + 3 + D;
+  static_assert(N == tile_x_count(D), "TileX layout");
+};
+
+// Conversions between FP32 and FP64 on the integer pipes, from the IEEE-754
+// fields (the GB300's FP64 pipe issues one warp instruction per 16 SM
+// cycles, so a conversion there costs as much as a few dozen integer
+// operations).  float -> double is exact for normal numbers and zero;
+// subnormal floats become signed zero; inf and NaN keep their class.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned m = u & 0x7FFFFFu;
+  const unsigned eh = e == 0u ? 0u : (e == 0xFFu ? 0x7FFu : e + 896u);  // rebias 127 -> 1023
+  const unsigned hi = (u & 0x80000000u) | (eh << 20) | (e == 0u ? 0u : m >> 3);
+  const unsigned lo = e == 0u ? 0u : m << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float rounded to nearest even; magnitudes below the smallest
+// normal float become signed zero, above the largest inf; NaN stays NaN.
+__device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned s = hi & 0x80000000u;
+  const unsigned ef = (hi >> 20) & 0x7FFu;
+  const int e = (int)ef - 896;
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);  // the top 23 mantissa bits
+  const unsigned rest = lo & 0x1FFFFFFFu;                  // the 29 bits rounded off
+  const unsigned up = (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  unsigned r;
+  if (e <= 0) r = s;
+  else if (e >= 0xFF) r = s | ((ef == 0x7FFu && ((hi & 0xFFFFFu) | lo)) ? 0x7FC00000u : 0x7F800000u);
+  else r = s | (((unsigned)e << 23) + m + up);  // a carry out of m rounds into the exponent
+  return __uint_as_float(r);
+}
+
+// Quadratic B-spline weights of one particle in FP32 from its offsets fx
+// (t - base per axis, in [0.5, 1.5)).
+template <int D>
+__device__ __forceinline__ void stencil_fx(const float (&fx)[D], float inv_dx, float (&w)[D][3],
+                                           float (&dw)[D][3]) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    const double t = __dmul_rn(__dsub_rn(xp[a], g.o[a]), g.inv_dx);
-    const double b = floor(__dsub_rn(t, 0.5));
-    ok = ok && (b >= 0.0) && (b + 2.0 < (double)g.res[a]);
-    base[a] = ok ? (int)b : 0;
-    const float fx = (float)(t - b);
-    const float e0 = 1.5f - fx, e1 = fx - 1.0f, e2 = fx - 0.5f;
+    const float e0 = 1.5f - fx[a], e1 = fx[a] - 1.0f, e2 = fx[a] - 0.5f;
     w[a][0] = 0.5f * e0 * e0;
     w[a][1] = 0.75f - e1 * e1;
     w[a][2] = 0.5f * e2 * e2;
@@ -119,7 +160,21 @@ __device__ __forceinline__ bool stencil_f32(const double* xp, const GridGeo& g, 
     dw[a][1] = -2.0f * e1 * inv_dx;
     dw[a][2] = e2 * inv_dx;
   }
-  return ok;
+}
+
+// Per-axis base node from the flat index b0 + res0 (b1 + res1 b2).
+template <int D>
+__device__ __forceinline__ void unflatten_base(int sb, const GridGeo& g, int (&base)[D]) {
+  const unsigned u = (unsigned)sb;
+  if constexpr (D == 2) {
+    base[1] = (int)(u / (unsigned)g.res[0]);
+    base[0] = (int)(u - (unsigned)base[1] * (unsigned)g.res[0]);
+  } else {
+    const unsigned r = u / (unsigned)g.res[0];
+    base[0] = (int)(u - r * (unsigned)g.res[0]);
+    base[2] = (int)(r / (unsigned)g.res[1]);
+    base[1] = (int)(r - (unsigned)base[2] * (unsigned)g.res[1]);
+  }
 }
 
 // grad N of stencil node k (offsets x fastest) from the 1D weights.
@@ -158,15 +213,16 @@ __device__ __forceinline__ void group_reduce_scatter(float (&v)[NV], int r) {
 }
 
 // The particle Hessian in FP32 at the Newton iterate's deformation
-// gradient F_hat (stored per particle by the gradient kernel, computed there
+// gradient F_hat, from the data the gradient kernel stored there (computed
 // in FP64): dF = G_d F^n and Y = V0 dP[F_hat; dF] F^nT with
-//   dP[dF] = mu dF + (mu - lam ln J) F^-T dF^T F^-T + lam tr(F^-1 dF) F^-T
+//   V0 dP[dF] = V0 mu dF + c1 A dF^T A + V0 lam tr(A^T dF) A,
+//   A = F_hat^-T,  c1 = V0 (mu - lam ln J)
 // (the operator of the cached block L(G) = V0 dP[G F^n] F^nT of the
 // gradient kernel).  Returns G_d : Y, the particle's share of d.Kd.
 template <int D>
-__device__ __forceinline__ float hessian_apply_fh(const float (&Fh)[D * D], const float (&Gd)[D * D],
-                                                  const float (&Fn)[D * D], float mu, float lam,
-                                                  float V0, float (&Y)[D * D]) {
+__device__ __forceinline__ float hessian_apply_x(const float (&A)[D * D], float c1, float vmu,
+                                                 float vlam, const float (&Gd)[D * D],
+                                                 const float (&Fn)[D * D], float (&Y)[D * D]) {
   constexpr int DD = D * D;
   float dF[DD];
 #pragma unroll
@@ -178,41 +234,10 @@ __device__ __forceinline__ float hessian_apply_fh(const float (&Fh)[D * D], cons
       for (int c = 0; c < D; ++c) t = fmaf(Gd[a * D + c], Fn[c * D + b], t);
       dF[a * D + b] = t;
     }
-  float H[DD];
-#pragma unroll
-  for (int i = 0; i < DD; ++i) H[i] = Fh[i] - ((i % (D + 1)) == 0 ? 1.0f : 0.0f);
-  float jm1;
-  float A[DD];  // F^-T
-  if constexpr (D == 2) {
-    jm1 = (H[0] + H[3]) + (H[0] * H[3] - H[1] * H[2]);
-    const float rJ = 1.0f / (1.0f + jm1);
-    A[0] = Fh[3] * rJ;
-    A[1] = -Fh[2] * rJ;
-    A[2] = -Fh[1] * rJ;
-    A[3] = Fh[0] * rJ;
-  } else {
-    const float trH = H[0] + H[4] + H[8];
-    const float m2 = (H[0] * H[4] - H[1] * H[3]) + (H[0] * H[8] - H[2] * H[6]) +
-                     (H[4] * H[8] - H[5] * H[7]);
-    const float dH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
-                     H[2] * (H[3] * H[7] - H[4] * H[6]);
-    jm1 = trH + m2 + dH;
-    const float rJ = 1.0f / (1.0f + jm1);
-    A[0] = (Fh[4] * Fh[8] - Fh[5] * Fh[7]) * rJ;
-    A[1] = (Fh[5] * Fh[6] - Fh[3] * Fh[8]) * rJ;
-    A[2] = (Fh[3] * Fh[7] - Fh[4] * Fh[6]) * rJ;
-    A[3] = (Fh[2] * Fh[7] - Fh[1] * Fh[8]) * rJ;
-    A[4] = (Fh[0] * Fh[8] - Fh[2] * Fh[6]) * rJ;
-    A[5] = (Fh[1] * Fh[6] - Fh[0] * Fh[7]) * rJ;
-    A[6] = (Fh[1] * Fh[5] - Fh[2] * Fh[4]) * rJ;
-    A[7] = (Fh[2] * Fh[3] - Fh[0] * Fh[5]) * rJ;
-    A[8] = (Fh[0] * Fh[4] - Fh[1] * Fh[3]) * rJ;
-  }
-  const float lnJ = log1pf(jm1);
   float tr = 0.0f;
 #pragma unroll
   for (int i = 0; i < DD; ++i) tr = fmaf(A[i], dF[i], tr);
-  const float c1 = mu - lam * lnJ, c2 = lam * tr;
+  const float c2 = vlam * tr;
   float Bm[DD];  // dF^T A
 #pragma unroll
   for (int e = 0; e < D; ++e)
@@ -231,7 +256,7 @@ __device__ __forceinline__ float hessian_apply_fh(const float (&Fh)[D * D], cons
       float t = 0.0f;
 #pragma unroll
       for (int e = 0; e < D; ++e) t = fmaf(A[a * D + e], Bm[e * D + c], t);
-      dP[a * D + c] = mu * dF[a * D + c] + c1 * t + c2 * A[a * D + c];
+      dP[a * D + c] = fmaf(vmu, dF[a * D + c], fmaf(c1, t, c2 * A[a * D + c]));
     }
   float qf = 0.0f;
 #pragma unroll
@@ -241,8 +266,8 @@ __device__ __forceinline__ float hessian_apply_fh(const float (&Fh)[D * D], cons
       float t = 0.0f;
 #pragma unroll
       for (int b = 0; b < D; ++b) t = fmaf(dP[a * D + b], Fn[c * D + b], t);
-      Y[a * D + c] = V0 * t;
-      qf = fmaf(Gd[a * D + c], Y[a * D + c], qf);
+      Y[a * D + c] = t;
+      qf = fmaf(Gd[a * D + c], t, qf);
     }
   return qf;
 }
@@ -263,23 +288,25 @@ struct HvpTileShared {
 // (s1 - s0 <= blockDim.x, one slot per thread, s0 a multiple of 2^D; the
 // whole block calls it): q = a.w[0] += K p on the free DOFs with
 // p = a.s[0], and acc += this run's share of p.Kp = sum_p G:Y.  Per particle
-// it reads x, F^n, the Newton iterate's F_hat, V0, mu, lam.  The block
-// stages the node box of its particles' stencils in shared memory, gathers
-// from it, and scatters into FP64 shared accumulators flushed with one
-// global atomic per tile node and component.  The slots come in aligned
-// groups of 2^D whose particles share a stencil base, so each group first
-// reduce-scatters its contributions among its lanes (FP32, 2^D terms) and
-// every lane adds a few group sums to the tile.  A run whose node box
-// exceeds the tile works on global memory (per-lane global atomics).
+// it reads its slot, its stencil base (flat), F^n and the FP32 data of
+// TileX; no FP64 arithmetic runs per particle.  The block stages the node
+// box of its particles' stencils in shared memory, gathers from it, and
+// scatters into FP64 shared accumulators flushed with one global atomic per
+// tile node and component.  The slots come in aligned groups of 2^D whose
+// particles share a stencil base, so each group first reduce-scatters its
+// contributions among its lanes (FP32, 2^D terms) and every lane adds a few
+// group sums to the tile.  A run whose node box exceeds the tile adds the
+// group sums to global memory instead.
 template <int D>
 __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, int64_t s1,
-                                         HvpTileShared<D>& sh, double& acc) {
+                                         HvpTileShared<D>& sh, float& acc) {
   constexpr int DD = D * D;
   constexpr int K = (D == 2) ? 9 : 27;
   constexpr int CAP = TileCap<D>::NODES;
   constexpr int GL = 1 << D;                 // lanes per slot group
   constexpr int KC = 9;                      // stencil nodes per scatter chunk
   constexpr int NVP = ((KC * D + GL - 1) / GL) * GL;
+  using X = TileX<D>;
   auto& sd = sh.sd;
   auto& sq = sh.sq;
   auto& box = sh.box;
@@ -290,16 +317,17 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
   const int gr = threadIdx.x & (GL - 1);
   const int64_t slot = s0 + threadIdx.x;
   const int64_t pi = slot < s1 ? (int64_t)a.slot2p[slot] : -1;
-  double xp[D];
+  const int sb = pi >= 0 ? a.sbase[pi] : -1;  // -1: outside the grid box
+  const bool valid = sb >= 0;
   int base[D];
   float w[D][3], dw[D][3];
-  bool valid = false;
-  if (pi >= 0) {
+  if (valid) {
+    unflatten_base<D>(sb, g, base);
+    float fx[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) xp[c] = a.P.x[c * n + pi];
-    valid = stencil_f32<D>(xp, g, base, w, dw);
-  }
-  if (!valid) {
+    for (int c = 0; c < D; ++c) fx[c] = a.tx[(int64_t)(X::FX + c) * n + pi];
+    stencil_fx<D>(fx, (float)g.inv_dx, w, dw);
+  } else {
 #pragma unroll
     for (int c = 0; c < D; ++c) base[c] = 0;
   }
@@ -310,7 +338,7 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
       const int64_t gi = tile_global<D>(box, g, l);
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        sd[c][l] = (float)__ldcg(&pv[c * g.nn + gi]);
+        sd[c][l] = d2f_bits(__ldcg(&pv[c * g.nn + gi]));
         sq[c][l] = 0.0;
       }
     }
@@ -319,15 +347,6 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
   const int lb = (tiled && valid) ? tile_local<D>(box, base[0] - box.lo[0], base[1] - box.lo[1],
                                                   base[D - 1] - box.lo[D - 1])
                                   : 0;
-  int64_t gb = base[0];
-  {
-    int64_t stride = g.res[0];
-#pragma unroll
-    for (int c = 1; c < D; ++c) {
-      gb += (int64_t)base[c] * stride;
-      stride *= g.res[c];
-    }
-  }
   float Y[DD];
 #pragma unroll
   for (int e = 0; e < DD; ++e) Y[e] = 0.0f;
@@ -346,93 +365,89 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
 #pragma unroll
         for (int c = 0; c < D; ++c) dk[c] = sd[c][l];
       } else {
-        const int64_t gi = gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
-                                        : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
+        const int64_t gi = (int64_t)sb + (D == 2 ? o0 + o1 * g.res[0]
+                                                : o0 + (o1 + o2 * g.res[1]) * g.res[0]);
 #pragma unroll
-        for (int c = 0; c < D; ++c) dk[c] = (float)__ldcg(&pv[c * g.nn + gi]);
+        for (int c = 0; c < D; ++c) dk[c] = d2f_bits(__ldcg(&pv[c * g.nn + gi]));
       }
 #pragma unroll
       for (int c = 0; c < D; ++c)
 #pragma unroll
         for (int b = 0; b < D; ++b) Gd[c * D + b] = fmaf(dk[c], dN[b], Gd[c * D + b]);
     }
-    float Fn[DD], Fh[DD];
+    float Fn[DD], A[DD];
 #pragma unroll
     for (int e = 0; e < DD; ++e) {
       Fn[e] = a.P.F[e * n + pi];
-      Fh[e] = a.fhat[e * n + pi];
+      A[e] = a.tx[(int64_t)(X::A + e) * n + pi];
     }
-    acc += (double)hessian_apply_fh<D>(Fh, Gd, Fn, (float)a.P.mu[pi], (float)a.P.lam[pi],
-                                       (float)a.P.vol0[pi], Y);
+    acc += hessian_apply_x<D>(A, a.tx[(int64_t)X::C1 * n + pi], a.tx[(int64_t)X::MU * n + pi],
+                              a.tx[(int64_t)X::LAM * n + pi], Gd, Fn, Y);
+  }
+  // Scatter: every lane of the warp takes part in its group's
+  // reduce-scatter (a padding slot adds zeros), in chunks of KC stencil
+  // nodes (one layer); each lane then adds its share of the group sums to
+  // the shared tile, or to global memory when the box exceeds the tile.
+#pragma unroll
+  for (int o2c = 0; o2c < 3; ++o2c) {
+    float v[NVP];
+#pragma unroll
+    for (int j = 0; j < NVP; ++j) v[j] = 0.0f;
+    if (valid) {
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) {
+        const int k = (D == 2 ? 0 : 9 * o2c) + kk;
+        float dN[D];
+        grad_n_f32<D>(w, dw, k, dN);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          float t = 0.0f;
+#pragma unroll
+          for (int b = 0; b < D; ++b) t = fmaf(Y[c * D + b], dN[b], t);
+          v[kk * D + c] = t;
+        }
+      }
+    }
+    group_reduce_scatter<GL, NVP>(v, gr);
+    // the group's base from any valid lane of the group (lane gr holds the
+    // sums of values gr NVP/GL .. (gr + 1) NVP/GL - 1).  The shuffle runs in
+    // every lane: a group with no particle reads its own lane, so no lane of
+    // a partly filled warp skips it.
+    const unsigned gmask = ((1u << GL) - 1u) << ((threadIdx.x & 31) & ~(GL - 1));
+    const unsigned vmask = __ballot_sync(kFull, valid) & gmask;
+    const int gbase = __shfl_sync(kFull, tiled ? lb : sb,
+                                  vmask ? __ffs(vmask) - 1 : (int)(threadIdx.x & 31));
+    if (vmask) {
+#pragma unroll
+      for (int j = 0; j < NVP / GL; ++j) {
+        const int idx = gr * (NVP / GL) + j;
+        if (idx < KC * D) {
+          const int kk = idx / D, c = idx - kk * D;
+          const int k = (D == 2 ? 0 : 9 * o2c) + kk;
+          const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+          if (tiled) {
+            atomicAdd(&sq[c][gbase + tile_local<D>(box, o0, o1, o2)], f2d_bits(v[j]));
+          } else {
+            const int64_t gi = (int64_t)gbase + (D == 2 ? o0 + o1 * g.res[0]
+                                                        : o0 + (o1 + o2 * g.res[1]) * g.res[0]);
+            if ((a.dofmask[gi] >> c) & 1u) atomicAdd(&q[c * g.nn + gi], f2d_bits(v[j]));
+          }
+        }
+      }
+    }
+    if (D == 2) break;  // one chunk holds the whole 2D stencil
   }
   if (tiled) {
-    // every lane of the warp takes part in its group's reduce-scatter (a
-    // padding slot adds zeros); chunks of KC stencil nodes (one layer)
-#pragma unroll
-    for (int o2c = 0; o2c < 3; ++o2c) {
-      float v[NVP];
-#pragma unroll
-      for (int j = 0; j < NVP; ++j) v[j] = 0.0f;
-      if (valid) {
-#pragma unroll
-        for (int kk = 0; kk < KC; ++kk) {
-          const int k = (D == 2 ? 0 : 9 * o2c) + kk;
-          float dN[D];
-          grad_n_f32<D>(w, dw, k, dN);
-#pragma unroll
-          for (int c = 0; c < D; ++c) {
-            float t = 0.0f;
-#pragma unroll
-            for (int b = 0; b < D; ++b) t = fmaf(Y[c * D + b], dN[b], t);
-            v[kk * D + c] = t;
-          }
-        }
-      }
-      group_reduce_scatter<GL, NVP>(v, gr);
-      // the group's base: from any valid lane of the group (lane gr holds the
-      // sums of values gr NVP/GL .. (gr + 1) NVP/GL - 1)
-      const unsigned gmask = ((1u << GL) - 1u) << ((threadIdx.x & 31) & ~(GL - 1));
-      // (the shuffle runs in every lane: a group with no particle reads its
-      // own lane, so no lane of a partly filled warp skips it)
-      const unsigned vmask = __ballot_sync(kFull, valid) & gmask;
-      const int glb = __shfl_sync(kFull, lb, vmask ? __ffs(vmask) - 1 : (int)(threadIdx.x & 31));
-      if (vmask) {
-#pragma unroll
-        for (int j = 0; j < NVP / GL; ++j) {
-          const int idx = gr * (NVP / GL) + j;
-          if (idx < KC * D) {
-            const int kk = idx / D, c = idx - kk * D;
-            const int k = (D == 2 ? 0 : 9 * o2c) + kk;
-            atomicAdd(&sq[c][glb + tile_local<D>(box, k % 3, (k / 3) % 3, k / 9)], (double)v[j]);
-          }
-        }
-      }
-      if (D == 2) break;  // one chunk holds the whole 2D stencil
-    }
     __syncthreads();
     for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
       const int64_t gi = tile_global<D>(box, g, l);
       const unsigned fm = a.dofmask[gi];
       if (!fm) continue;
 #pragma unroll
-      for (int c = 0; c < D; ++c)
-        if (((fm >> c) & 1u) && sq[c][l] != 0.0) atomicAdd(&q[c * g.nn + gi], sq[c][l]);
-    }
-  } else if (valid) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
-      float dN[D];
-      grad_n_f32<D>(w, dw, k, dN);
-      const int64_t gi = gb + (D == 2 ? o0 + (int64_t)o1 * g.res[0]
-                                      : o0 + ((int64_t)o1 + (int64_t)o2 * g.res[1]) * g.res[0]);
-      const unsigned fm = a.dofmask[gi];
-#pragma unroll
       for (int c = 0; c < D; ++c) {
-        float t = 0.0f;
-#pragma unroll
-        for (int b = 0; b < D; ++b) t = fmaf(Y[c * D + b], dN[b], t);
-        if ((fm >> c) & 1u) atomicAdd(&q[c * g.nn + gi], (double)t);
+        const double t = sq[c][l];
+        // (a zero test on the bits: no FP64 instruction)
+        if (((fm >> c) & 1u) && (__double_as_longlong(t) << 1) != 0) atomicAdd(&q[c * g.nn + gi], t);
       }
     }
   }
@@ -447,12 +462,13 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS)
   if (__ldcg(&a.S->cg_done)) return;
   __shared__ HvpTileShared<D> sh;
   const int64_t ns = __ldcg(a.n_slots);
-  double acc[1] = {0.0};
+  float accf = 0.0f;  // this thread's particles' share of p.Kp (a few tiles)
   const int64_t tiles = (ns + blockDim.x - 1) / blockDim.x;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int64_t s0 = t * blockDim.x;
-    hvp_tile<D>(a, s0, s0 + blockDim.x < ns ? s0 + blockDim.x : ns, sh, acc[0]);
+    hvp_tile<D>(a, s0, s0 + blockDim.x < ns ? s0 + blockDim.x : ns, sh, accf);
   }
+  double acc[1] = {(double)accf};
   double tot[1];
   if (grid_sum<1>(acc, a.partials, &a.S->counter, tot) && threadIdx.x == 0) a.S->pq = tot[0];
 }
@@ -508,7 +524,10 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS)
 #pragma unroll
       for (int a = 0; a < D; ++a) xp[a] = P.x[a * n + p];
       valid = make_stencil<D>(xp, g, s);
-      if (!valid) atomicOr(err, kErrOutOfGrid);
+      if (!valid) {
+        atomicOr(err, kErrOutOfGrid);
+        if (sbase) sbase[p] = -1;  // no stencil (the slots and the tiled product skip it)
+      }
     } else {
 #pragma unroll
       for (int a = 0; a < D; ++a) s.base[a] = 0;

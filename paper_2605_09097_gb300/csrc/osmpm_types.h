@@ -93,12 +93,18 @@ struct PcgArgsT {
   const R* sdn;         // per particle: grad N of the 3^D stencil nodes, [(c*K + k)*n + p]
   const double* u;      // the Newton iterate
   // the tiled product (mixed precision): cell-aligned slots of the last P2G
-  // (slot2p[slot] = particle or -1, *n_slots of them, device) and each
-  // particle's deformation gradient at the Newton iterate, [e*n + p]
+  // (slot2p[slot] = particle or -1, *n_slots of them, device) and the
+  // per-particle data the gradient kernel stores for it at each Newton
+  // iterate, [e*n + p] (TileX layout)
   const int* slot2p;
   const int* n_slots;
-  const R* fhat;
+  const R* tx;
 };
+
+// FP32 values per particle that the gradient kernel stores for the tiled
+// product (TileX in osmpm_tile.cuh): F_hat^-T, c1, V0 mu, V0 lam, the
+// offsets from the stencil base.
+constexpr int tile_x_count(int D) { return D * D + 3 + D; }
 
 // Batched PCG over many domains (osmpm_multi.cuh): items [lo, hi)
 // (particles or DOFs) of instance `inst`.

@@ -102,7 +102,8 @@ class osmpm_stats(Structure):
 class osmpm_counters(Structure):
     _fields_ = [("launches", c_int64), ("pcg_launches", c_int64), ("pcg_ms", c_double),
                 ("pcg_iters", c_int64), ("particles", c_int64), ("dofs", c_int64),
-                ("graph_replays", c_int64), ("graphs", c_int32), ("graph_error", c_int32)]
+                ("graph_replays", c_int64), ("graphs", c_int32), ("graph_error", c_int32),
+                ("hvp_ms", c_double), ("hvp_launches", c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -122,7 +123,8 @@ class osmpm_multi_stats(Structure):
     _fields_ = [("batches", c_int64), ("instances", c_int64), ("chunks", c_int64),
                 ("max_batch", c_int64), ("particles", c_int64), ("dofs", c_int64),
                 ("iterations", c_int64), ("particle_iterations", c_int64),
-                ("dof_iterations", c_int64), ("device_ms", c_double)]
+                ("dof_iterations", c_int64), ("device_ms", c_double), ("hvp_ms", c_double),
+                ("hvp_launches", c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
