@@ -62,7 +62,7 @@ ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
 AUTOTUNE_THREADS = [8, 12, 16]
 # (host threads, DOFs per DOF tile, PCG iterations per graph replay)
-AUTOTUNE_MULTI = [(32, 2048, 16), (64, 2048, 16), (64, 4096, 8)]
+AUTOTUNE_MULTI = [(64, 2048, 16), (128, 2048, 16), (256, 2048, 16), (128, 2048, 8)]
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
 # launch, from the ncu capture of the current kernel (the k_pcg profile
 # summary of this workload); None whenever the kernel changes
@@ -412,7 +412,7 @@ MIXED_HVP_BYTES_PER_PARTICLE = {2: 52.0, 3: 78.0}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch on the
 # 3.07M-particle fold band (ncu), per kernel; absent until captured for the
 # current kernel
-FOLD_HVP_TRAFFIC_BYTES = {}
+FOLD_HVP_TRAFFIC_BYTES = {"k_cgs_hvp_tile": 347.648e6 + 6.266e6}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the batched
 # Hessian-vector product (k_m_hvp) on the batched family, from ncu; None
 # until captured for the current kernel
@@ -526,10 +526,11 @@ def run_batched(args, rank, local, world):
         nbytes = sum(a.nbytes for h in host for a in h)
         torch.cuda.synchronize()
         te0 = time.perf_counter()
+        service_e2e = []
         for _ in range(args.e2e_steps):
             for dd, h in zip(B + S, host):
                 dd.set_particles(*h)
-            batched_step()
+            service_e2e.append(batched_step())
             for dd, h in zip(B + S, host):
                 x, v, Bm, F = dd.get_particles()
                 h[0][...] = x
@@ -540,7 +541,10 @@ def run_batched(args, rank, local, world):
         te = max_over_ranks(time.perf_counter() - te0, world)
         e2e = {"value": sum_over_ranks(units * args.e2e_steps, world) / te, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "steps": args.e2e_steps}
+               "steps": args.e2e_steps,
+               "note": "the global steps after the timed ones (the state continues from them)"}
+        if multi:
+            e2e["pcg_iterations_per_step"] = [x["iterations"] for x in service_e2e if x]
     for dd in B + S:
         dd.close()
     for st in streams:
@@ -555,6 +559,8 @@ def run_batched(args, rank, local, world):
                        "instances": args.instances, "host_threads": threads,
                        "batch_mode": args.batch_mode, "launch_shape": shape,
                        "pcg_service": service if multi else None,
+                       "pcg_iterations_per_step": [x["iterations"] for x in service] if multi
+                       else None,
                        "autotune_us_per_cg_iter": tuned,
                        "particles": sum(s[0].particles.n + s[1].particles.n for s in specs),
                        "units_per_step": units, "precision": args.precision,

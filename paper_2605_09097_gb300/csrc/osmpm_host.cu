@@ -17,6 +17,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/osmpm.h"
 #include "osmpm_internal.h"
 
@@ -25,6 +27,17 @@ using namespace osmpm;
 std::atomic<long long> osmpm::g_launch_count{0};
 
 namespace {
+
+// An NVTX range over one phase of the method (P2G, Newton, PCG, G2P, a
+// Schwarz iteration, a batched PCG chunk); Nsight tools show them, and
+// without a tool attached a push or pop costs a few nanoseconds.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 thread_local std::string g_last_error = "no error";
 
@@ -458,14 +471,20 @@ osmpm_status upload_rules(osmpm_domain* d, double dt) {
 // ---------------------------------------------------------------------------
 // grid phases
 // ---------------------------------------------------------------------------
+int grad_lmode(osmpm_domain* d);
+
 osmpm_status run_p2g(osmpm_domain* d, bool boundary_mass) {
+  NvtxRange nvtx_("p2g");
   const int64_t nn = d->geo.nn;
   const int D = d->dim;
   CUDA_TRY(cudaMemsetAsync(d->m, 0, sizeof(double) * nn, d->stream));
   CUDA_TRY(cudaMemsetAsync(d->mv, 0, sizeof(double) * D * nn, d->stream));
   if (boundary_mass) CUDA_TRY(cudaMemsetAsync(d->bm, 0, sizeof(double) * nn, d->stream));
+  // the stencil-gradient cache feeds only the lane-group products; a
+  // domain on the tiled product alone skips its write (D x 3^D values per
+  // particle, most of the P2G's traffic)
   DISPATCH(d, K::p2g(P_, d->geo, d->m, d->mv, boundary_mass ? d->bm : nullptr, d->err, d->sbase,
-                     SDN_, d->stream));
+                     grad_lmode(d) == 2 ? nullptr : SDN_, d->stream));
   DISPATCH(d, K::normalize(d->geo, d->m, d->mv, d->vn, d->stream));
   if (d->slot2p) {
     // the sort scratch (idle between sorts) holds the slot builder's scans
@@ -594,17 +613,6 @@ osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st);
 // only to kCheckEta and accepted when max |delta| <= tol / 2.
 constexpr double kCheckRatio = 500.0, kCheckEta = 0.1;
 
-// What the gradient kernel stores for the PCG's products: the packed
-// Hessian blocks (FP64, the persistent PCG, the lane-group product) and/or
-// the tiled product's per-particle data (mixed precision).  A mixed domain
-// on the streaming PCG with the tiled product, or in the batched PCG
-// service, needs only the latter.
-int grad_lmode(const osmpm_domain* d) {
-  if (d->prec != 1) return 1;
-  const bool tiled = d->desc.hvp_mode != 1;
-  return (tiled && (d->desc.pcg_mode == 2 || d->batcher)) ? 2 : 3;
-}
-
 // Gradient, Jacobi diagonal and the PCG start (x = 0, r[0], inverted
 // diagonal, tolerance and controls) of a Newton iteration.
 void enqueue_gradient(osmpm_domain* d, double dt, bool first, bool check) {
@@ -634,6 +642,20 @@ bool pcg_streaming(osmpm_domain* d, double dt, int64_t work) {
   bool streaming = d->desc.pcg_mode == 2;
   if (d->desc.pcg_mode == 0) DISPATCH(d, (streaming = !pcg_persistent_fits<K, R>(d, dt, work)));
   return streaming;
+}
+
+// What the gradient kernel stores for the PCG's products: the packed
+// Hessian blocks (FP64, the persistent PCG, the lane-group product) and/or
+// the tiled product's per-particle data (mixed precision).  A mixed domain
+// whose solves take the streaming PCG with the tiled product, or the
+// batched PCG service, needs only the latter (the P2G then also skips the
+// stencil-gradient cache).
+int grad_lmode(osmpm_domain* d) {
+  if (d->prec != 1) return 1;
+  if (d->desc.hvp_mode == 1) return 3;
+  if (d->batcher || d->desc.pcg_mode == 2) return 2;
+  if (d->desc.pcg_mode == 1) return 3;
+  return pcg_streaming(d, 1.0, pcg_work(d)) ? 2 : 3;  // automatic (independent of dt)
 }
 
 // s[1], w[0..2], p and the barrier counter of the persistent PCG to zero.
@@ -807,16 +829,20 @@ osmpm_status pcg_finish(osmpm_domain* d, bool timed, SolveStats& st) {
 // pairs' host threads run Alg. 1 and Newton as in osmpm_schwarz_couple;
 // when a Newton iteration needs its PCG, the thread enqueues the gradient
 // and PCG start on its stream, waits for it and hands the system to this
-// service.  The service thread takes every system handed in meanwhile and
-// runs one batched streaming PCG over all of them (osmpm_multi.cuh): a work
-// list of (instance, particle tile) and (instance, DOF tile), per-instance
-// scalars and stop flags, iterations replayed in chunks from a CUDA graph
-// captured for the batch; systems handed in during a batch join the next.
+// service.  The service batches continuously: the systems in flight iterate
+// together in chunks over a work list of (instance, slot tile) and
+// (instance, DOF tile) with per-instance scalars and stop flags
+// (osmpm_multi.cuh); after each chunk the converged systems leave and the
+// systems handed in meanwhile join.  The kernels read the work list and
+// their arguments from a device block that is rewritten when the set
+// changes, with fixed grids, so one CUDA graph of a chunk serves every
+// composition (captured again only when the block grows).
 // ---------------------------------------------------------------------------
 struct PcgBatcher {
   int dim = 2;
   int dof_tile = 2048;  // DOFs per DOF tile
   int chunk = 16;       // iterations between looks at the stop flags
+  int grid_pt = 1, grid_dt = 1;  // fixed grids of the product and of the DOF kernels
   cudaStream_t stream = nullptr;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -829,31 +855,55 @@ struct PcgBatcher {
   std::vector<Req*> queue;
   bool stop = false;
   std::thread th;
-  // device and pinned host work areas, grown on demand
-  void* dev = nullptr;
-  size_t dev_bytes = 0;
+  // The device block: MultiArgs, then the instance table, infos, slot tiles,
+  // DOF tiles (capacities cap_*), the tile partials (3 rows) and the
+  // pending words; `host` mirrors it up to the partials (pinned).
+  struct Layout {
+    size_t inst, info, pt, dt, part, pend, bytes;
+    int stride;
+  };
+  int cap_inst = 0, cap_pt = 0, cap_dt = 0;
+  Layout lay{};
+  char* dev = nullptr;
   char* host = nullptr;
-  size_t host_bytes = 0;
-  int* pending_host = nullptr;  // pending count, then the instances' iteration counts
-  int pending_cap = 0;
+  int* pending_host = nullptr;  // pending count, then per system: stop flag, iterations
+  cudaGraphExec_t exec = nullptr;
+  long long per_chunk = 0;  // kernel launches in one replay
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> hev;  // around each k_m_hvp of a chunk
   std::string error;
   osmpm_multi_stats stats{};
 
+  static size_t up(size_t b) { return (b + 255) & ~size_t(255); }
+
+  static Layout layout(int ci, int cp, int cd) {
+    Layout L{};
+    L.inst = up(sizeof(MultiArgs));
+    L.info = L.inst + up(sizeof(PcgArgsT<float>) * (size_t)ci);
+    L.pt = L.info + up(sizeof(MultiInfo) * (size_t)ci);
+    L.dt = L.pt + up(sizeof(MultiTile) * (size_t)cp);
+    L.part = L.dt + up(sizeof(MultiTile) * (size_t)cd);
+    L.stride = std::max(cp, cd);
+    L.pend = L.part + up(sizeof(double) * 3 * (size_t)L.stride);
+    L.bytes = L.pend + up(sizeof(int) * (1 + 2 * (size_t)ci));
+    return L;
+  }
+
   osmpm_status open(int dim_, int dof_tile_, int chunk_) {
     dim = dim_;
     dof_tile = dof_tile_ > 0 ? dof_tile_ : 2048;
     chunk = chunk_ > 0 ? chunk_ : 16;
+    int dev_id = 0, sms = 1;
+    cudaGetDevice(&dev_id);
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
+    const int occ = dim == 2 ? MultiKernels<2>::hvp_blocks_per_sm() : MultiKernels<3>::hvp_blocks_per_sm();
+    grid_pt = sms * std::max(occ, 1);
+    grid_dt = sms * 2;
     CUDA_TRY(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-    pending_cap = 4096;
-    CUDA_TRY(cudaMallocHost(&pending_host, sizeof(int) * (1 + pending_cap)));
     CUDA_TRY(cudaEventCreate(&ev[0]));
     CUDA_TRY(cudaEventCreate(&ev[1]));
     hev.assign((size_t)2 * chunk, nullptr);
     for (auto& e : hev) CUDA_TRY(cudaEventCreate(&e));
-    int dev_id = 0;
-    cudaGetDevice(&dev_id);
     th = std::thread([this, dev_id] {
       cudaSetDevice(dev_id);
       loop();
@@ -868,6 +918,7 @@ struct PcgBatcher {
     }
     cv_work.notify_all();
     if (th.joinable()) th.join();
+    if (exec) cudaGraphExecDestroy(exec);
     if (stream) cudaStreamSynchronize(stream);
     if (dev) cudaFreeAsync(dev, stream);
     if (stream) cudaStreamSynchronize(stream);
@@ -894,14 +945,11 @@ struct PcgBatcher {
   // The service loop: continuous batching.  The systems in flight ("live")
   // iterate together in chunks; after each chunk the converged ones leave
   // (their threads resume at once) and the systems handed in meanwhile join
-  // (their PCG start runs with the next chunk).
+  // (their PCG start runs before the next chunk).
   void loop() {
     std::vector<Req*> live;
     std::vector<int> fresh_flags;
     bool dirty = false;
-    MultiArgs m{};
-    cudaGraphExec_t exec = nullptr;
-    long long per_chunk = 0;
     for (;;) {
       std::vector<Req*> fresh;
       {
@@ -916,20 +964,21 @@ struct PcgBatcher {
         live.insert(live.end(), fresh.begin(), fresh.end());
         fresh_flags.assign(live.size(), 0);
         for (size_t i = old; i < live.size(); ++i) fresh_flags[i] = 1;
-        if (exec) cudaGraphExecDestroy(exec);
-        exec = nullptr;
-        st = build(live, fresh_flags, &m);
+        st = build(live, fresh_flags);
         if (st == OSMPM_OK) {
           stats.batches += 1;
           stats.instances += (int64_t)fresh.size();
           if ((int64_t)live.size() > stats.max_batch) stats.max_batch = (int64_t)live.size();
-          if (dim == 2) MultiKernels<2>::start(m, stream);
-          else MultiKernels<3>::start(m, stream);
-          exec = capture(m, &per_chunk);
+          if (!fresh.empty()) {
+            const MultiArgs* mp = (const MultiArgs*)dev;
+            if (dim == 2) MultiKernels<2>::start(mp, grid_dt, stream);
+            else MultiKernels<3>::start(mp, grid_dt, stream);
+          }
+          if (!exec) exec = capture();
         }
         dirty = false;
       }
-      if (st == OSMPM_OK) st = run_chunk(m, exec, per_chunk, live.size());
+      if (st == OSMPM_OK) st = run_chunk(live.size());
       // the systems that stopped leave (all of them after a failure)
       std::vector<Req*> done;
       std::vector<Req*> keep;
@@ -961,17 +1010,12 @@ struct PcgBatcher {
       }
       if (!done.empty()) cv_done.notify_all();
     }
-    if (exec) cudaGraphExecDestroy(exec);
   }
 
-  template <class T>
-  static size_t up(size_t b) {
-    return (b + 255) & ~size_t(255);
-  }
-
-  // Uploads the instance table and work lists of `live` (fresh[i] = 1 for
-  // the systems whose PCG start is still to run).
-  osmpm_status build(const std::vector<Req*>& live, const std::vector<int>& fresh, MultiArgs* out) {
+  // Writes the argument block for `live` (fresh[i] = 1 for the systems
+  // whose PCG start is still to run), growing it (and dropping the graph)
+  // when a table outgrows its capacity.
+  osmpm_status build(const std::vector<Req*>& live, const std::vector<int>& fresh) {
     const int n = (int)live.size();
     const int TP = dim == 2 ? MultiKernels<2>::particle_tile() : MultiKernels<3>::particle_tile();
     std::vector<PcgArgsT<float>> inst((size_t)n);
@@ -992,95 +1036,89 @@ struct PcgBatcher {
       info[(size_t)i].ndt = (int)dtl.size() - info[(size_t)i].dt0;
       info[(size_t)i].fresh = fresh[(size_t)i];
     }
-    const int stride = (int)std::max<size_t>(std::max(pt.size(), dtl.size()), 1);
-    const size_t b_inst = up<char>(sizeof(PcgArgsT<float>) * n), b_info = up<char>(sizeof(MultiInfo) * n);
-    const size_t b_pt = up<char>(sizeof(MultiTile) * pt.size()), b_dt = up<char>(sizeof(MultiTile) * dtl.size());
-    const size_t b_part = up<char>(sizeof(double) * 2 * stride);
-    const size_t b_pend = up<char>(sizeof(int) * (1 + 2 * n));
-    const size_t in_bytes = b_inst + b_info + b_pt + b_dt;
-    const size_t need = in_bytes + b_part + b_pend;
-    CUDA_TRY(cudaStreamSynchronize(stream));  // the previous tables are no longer read
-    if (need > dev_bytes) {
+    CUDA_TRY(cudaStreamSynchronize(stream));  // the block is no longer read
+    if (n > cap_inst || (int)pt.size() > cap_pt || (int)dtl.size() > cap_dt || !dev) {
+      cap_inst = std::max(cap_inst, n + n / 2 + 8);
+      cap_pt = std::max(cap_pt, (int)pt.size() + (int)pt.size() / 2 + 64);
+      cap_dt = std::max(cap_dt, (int)dtl.size() + (int)dtl.size() / 2 + 64);
+      lay = layout(cap_inst, cap_pt, cap_dt);
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
       if (dev) cudaFreeAsync(dev, stream);
-      dev = nullptr;
-      dev_bytes = 0;
-      const size_t want = need + need / 2;
-      if (cudaMallocAsync(&dev, want, stream) != cudaSuccess) return set_error(OSMPM_E_NOMEM, "batched PCG: device memory");
-      dev_bytes = want;
-    }
-    if (in_bytes > host_bytes) {
       if (host) cudaFreeHost(host);
-      host = nullptr;
-      host_bytes = 0;
-      const size_t want = in_bytes + in_bytes / 2;
-      if (cudaMallocHost(&host, want) != cudaSuccess) return set_error(OSMPM_E_NOMEM, "batched PCG: pinned memory");
-      host_bytes = want;
+      if (pending_host) cudaFreeHost(pending_host);
+      dev = host = nullptr;
+      pending_host = nullptr;
+      if (cudaMallocAsync((void**)&dev, lay.bytes, stream) != cudaSuccess ||
+          cudaMallocHost((void**)&host, lay.part) != cudaSuccess ||
+          cudaMallocHost((void**)&pending_host, sizeof(int) * (1 + 2 * (size_t)cap_inst)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(OSMPM_E_NOMEM, "batched PCG: memory for the work list");
+      }
     }
-    if (2 * n > pending_cap) {
-      cudaFreeHost(pending_host);
-      pending_cap = 2 * n;
-      if (cudaMallocHost(&pending_host, sizeof(int) * (1 + pending_cap)) != cudaSuccess)
-        return set_error(OSMPM_E_NOMEM, "batched PCG: pinned memory");
-    }
-    memcpy(host, inst.data(), sizeof(PcgArgsT<float>) * n);
-    memcpy(host + b_inst, info.data(), sizeof(MultiInfo) * n);
-    if (!pt.empty()) memcpy(host + b_inst + b_info, pt.data(), sizeof(MultiTile) * pt.size());
-    if (!dtl.empty()) memcpy(host + b_inst + b_info + b_pt, dtl.data(), sizeof(MultiTile) * dtl.size());
-    char* dv = (char*)dev;
-    CUDA_TRY(cudaMemcpyAsync(dv, host, in_bytes, cudaMemcpyHostToDevice, stream));
-    MultiArgs& m = *out;
-    m = MultiArgs{};
-    m.inst = (const PcgArgsT<float>*)dv;
-    m.info = (const MultiInfo*)(dv + b_inst);
-    m.pt = (const MultiTile*)(dv + b_inst + b_info);
+    MultiArgs m{};
+    m.inst = (const PcgArgsT<float>*)(dev + lay.inst);
+    m.info = (const MultiInfo*)(dev + lay.info);
+    m.pt = (const MultiTile*)(dev + lay.pt);
     m.n_pt = (int)pt.size();
-    m.dtl = (const MultiTile*)(dv + b_inst + b_info + b_pt);
+    m.dtl = (const MultiTile*)(dev + lay.dt);
     m.n_dt = (int)dtl.size();
     m.n_inst = n;
-    m.part = (double*)(dv + in_bytes);
-    m.stride = stride;
-    m.pending = (int*)(dv + in_bytes + b_part);
+    m.part = (double*)(dev + lay.part);
+    m.stride = lay.stride;
+    m.pending = (int*)(dev + lay.pend);
+    memcpy(host, &m, sizeof(m));
+    memcpy(host + lay.inst, inst.data(), sizeof(PcgArgsT<float>) * n);
+    memcpy(host + lay.info, info.data(), sizeof(MultiInfo) * n);
+    if (!pt.empty()) memcpy(host + lay.pt, pt.data(), sizeof(MultiTile) * pt.size());
+    if (!dtl.empty()) memcpy(host + lay.dt, dtl.data(), sizeof(MultiTile) * dtl.size());
+    const size_t bytes = lay.dt + sizeof(MultiTile) * dtl.size();
+    CUDA_TRY(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, stream));
     return OSMPM_OK;
   }
 
-  void enqueue_chunk(const MultiArgs& m, int n, bool capturing) {
+  void enqueue_chunk(bool capturing) {
+    const MultiArgs* mp = (const MultiArgs*)dev;
     for (int c = 0; c < chunk; ++c) {
       cudaEvent_t e0 = hev[(size_t)2 * c], e1 = hev[(size_t)2 * c + 1];
-      if (dim == 2) MultiKernels<2>::iteration(m, stream, e0, e1, capturing);
-      else MultiKernels<3>::iteration(m, stream, e0, e1, capturing);
+      if (dim == 2) MultiKernels<2>::iteration(mp, grid_pt, grid_dt, stream, e0, e1, capturing);
+      else MultiKernels<3>::iteration(mp, grid_pt, grid_dt, stream, e0, e1, capturing);
     }
-    if (dim == 2) MultiKernels<2>::pending(m, stream);
-    else MultiKernels<3>::pending(m, stream);
-    cudaMemcpyAsync(pending_host, m.pending, sizeof(int) * (1 + 2 * n), cudaMemcpyDeviceToHost, stream);
+    if (dim == 2) MultiKernels<2>::pending(mp, stream);
+    else MultiKernels<3>::pending(mp, stream);
+    cudaMemcpyAsync(pending_host, dev + lay.pend, sizeof(int) * (1 + 2 * (size_t)cap_inst),
+                    cudaMemcpyDeviceToHost, stream);
   }
 
-  // The chunk as a CUDA graph for this composition of the batch (nullptr:
-  // plain launches).
-  cudaGraphExec_t capture(const MultiArgs& m, long long* per_chunk) {
+  // The chunk as a CUDA graph over the current block (nullptr: plain
+  // launches).
+  cudaGraphExec_t capture() {
     cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t ex = nullptr;
     const long long before = g_launch_count.load();
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      enqueue_chunk(m, m.n_inst, true);
+      enqueue_chunk(true);
       if (cudaStreamEndCapture(stream, &graph) != cudaSuccess || !graph ||
-          cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
-        exec = nullptr;
+          cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess)
+        ex = nullptr;
     }
     cudaGetLastError();
     if (graph) cudaGraphDestroy(graph);
-    *per_chunk = g_launch_count.load() - before;
-    g_launch_count -= *per_chunk;  // counted when replayed or launched
-    return exec;
+    per_chunk = g_launch_count.load() - before;
+    g_launch_count -= per_chunk;  // counted when replayed or launched
+    return ex;
   }
 
-  osmpm_status run_chunk(const MultiArgs& m, cudaGraphExec_t exec, long long per_chunk, size_t n) {
+  osmpm_status run_chunk(size_t n) {
+    NvtxRange nvtx_("batched_pcg_chunk");
+    (void)n;
     cudaEventRecord(ev[0], stream);
     cudaError_t e;
     if (exec) {
       e = cudaGraphLaunch(exec, stream);
       g_launch_count += per_chunk;
     } else {
-      enqueue_chunk(m, (int)n, false);
+      enqueue_chunk(false);
       e = cudaGetLastError();
     }
     cudaEventRecord(ev[1], stream);
@@ -1106,6 +1144,7 @@ struct PcgBatcher {
 // max |delta|: a replayed graph where launch_mode 0 allows one, else the
 // same work launched directly; the streaming PCG always launches directly.
 osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check, SolveStats& st) {
+  NvtxRange nvtx_("newton_iteration");
   const int64_t work = pcg_work(d);
   const bool timed = d->time_hvp && !d->ev.empty();
   if (d->batcher) {
@@ -1143,6 +1182,7 @@ osmpm_status gradient_and_pcg(osmpm_domain* d, double dt, bool first, bool check
 // barrier counter start at zero.  With `newton` also reduces max |x| for the
 // Newton stop test.
 osmpm_status run_pcg(osmpm_domain* d, double dt, bool newton, SolveStats& st) {
+  NvtxRange nvtx_("pcg");
   enqueue_pcg_reset(d);
   CUDA_TRY(cudaGetLastError());
   const int64_t work = pcg_work(d);
@@ -1195,6 +1235,7 @@ osmpm_status cold_start(osmpm_domain* d, double dt) {
 }
 
 osmpm_status newton_solve(osmpm_domain* d, double dt, SolveStats& st) {
+  NvtxRange nvtx_("newton");
   st.solves++;
   const double tol = d->desc.newton_tol * dt;
   double prev_dx = INFINITY;
@@ -1703,6 +1744,7 @@ osmpm_status osmpm_set_plane(osmpm_domain* d, const osmpm_plane* plane) {
 }
 
 osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
+  NvtxRange nvtx_("osmpm_step");
   OSMPM_TRY(check_domain(d));
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(OSMPM_E_INVALID, "dt must be > 0");
   SolveStats st;
@@ -1763,7 +1805,10 @@ osmpm_status osmpm_step(osmpm_domain* d, double dt, osmpm_stats* stats) {
   }
   if (slot.mem) T_TRY(tape_end(d, slot, dt));
 #undef T_TRY
-  DISPATCH(d, K::g2p(P_, d->geo, d->u, dt, d->stream));
+  {
+    NvtxRange nvtx_("g2p");
+    DISPATCH(d, K::g2p(P_, d->geo, d->u, dt, d->stream));
+  }
   CUDA_TRY(cudaStreamSynchronize(d->stream));
   CUDA_TRY(cudaGetLastError());
   fill_stats(stats, st, 0, 1, 0.0, 0.0);
@@ -1917,6 +1962,7 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* B, osmpm_domain* S, double dT,
   int k = 0, converged = 0;
   double rB = 0.0, rS = 0.0;
   for (k = 0; k <= sd->k_max; ++k) {
+    NvtxRange nvtx_("schwarz_iteration");
     // 1. coarse solve over dT with Pi data on Gamma_hat_B (Eq. implicit_solve_coarse)
     S_TRY(prep(B, dT, true, B->recv, B->bc0, B->bc0, 1.0, nullptr));
     if (k > 0)
@@ -2352,6 +2398,7 @@ static osmpm_status coupled_adjoint(osmpm_domain* B, osmpm_domain* S, const doub
 
 osmpm_status osmpm_adjoint(osmpm_domain* coarse, osmpm_domain* fine, const double* dJ_dx,
                            const osmpm_adjoint_out* out, osmpm_stats* stats) {
+  NvtxRange nvtx_("osmpm_adjoint");
   OSMPM_TRY(check_domain(coarse));
   if (!dJ_dx || !out || !out->dJ_dE) return fail(OSMPM_E_INVALID, "null dJ_dx or dJ_dE");
   if (fine) return coupled_adjoint(coarse, fine, dJ_dx, out, stats);

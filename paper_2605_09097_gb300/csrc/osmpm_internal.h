@@ -90,14 +90,17 @@ struct AdjointKernels {
 // precision; osmpm_multi.cuh).
 template <int D>
 struct MultiKernels {
-  static void start(const MultiArgs& m, cudaStream_t s);
+  // mp: the device argument block; grids fixed by the caller (grid stride
+  // over the tiles)
+  static void start(const MultiArgs* mp, int grid_dt, cudaStream_t s);
   // one PCG iteration of every instance still running; with e0, e1 the
   // Hessian-vector product is bracketed by event records (external event
   // nodes when the stream is being captured)
-  static void iteration(const MultiArgs& m, cudaStream_t s, cudaEvent_t e0 = nullptr,
-                        cudaEvent_t e1 = nullptr, bool capturing = false);
-  static void pending(const MultiArgs& m, cudaStream_t s);
-  static int particle_tile();  // particles per tile (one per thread of a block)
+  static void iteration(const MultiArgs* mp, int grid_pt, int grid_dt, cudaStream_t s,
+                        cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr, bool capturing = false);
+  static void pending(const MultiArgs* mp, cudaStream_t s);
+  static int particle_tile();      // slots per slot tile (one per thread of a block)
+  static int hvp_blocks_per_sm();  // co-resident blocks of the product per SM
 };
 
 template <int D, typename R>

@@ -1278,29 +1278,38 @@ void Kernels<D, R>::build_slots(const int* sbase, int64_t n, int* rs, int* flag,
 }
 
 template <int D>
-void MultiKernels<D>::start(const MultiArgs& m, cudaStream_t s) {
+void MultiKernels<D>::start(const MultiArgs* mp, int grid_dt, cudaStream_t s) {
   g_launch_count += 1;
-  k_m_start<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
+  k_m_start<D><<<grid_dt, kThreads, 0, s>>>(mp);
 }
 template <int D>
-void MultiKernels<D>::iteration(const MultiArgs& m, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
-                                bool capturing) {
-  g_launch_count += 3;
+void MultiKernels<D>::iteration(const MultiArgs* mp, int grid_pt, int grid_dt, cudaStream_t s,
+                                cudaEvent_t e0, cudaEvent_t e1, bool capturing) {
+  g_launch_count += 2;
   const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
   if (e0) cudaEventRecordWithFlags(e0, s, flags);
-  k_m_hvp<D><<<std::max(1, std::min(m.n_pt, kRedBlocksMax)), TileCap<D>::THREADS, 0, s>>>(m);
+  k_m_hvp<D><<<grid_pt, TileCap<D>::THREADS, 0, s>>>(mp);
   if (e1) cudaEventRecordWithFlags(e1, s, flags);
-  k_m_alpha<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
-  k_m_beta<D><<<std::max(1, std::min(m.n_dt, kRedBlocksMax)), kThreads, 0, s>>>(m);
+  k_m_update<D><<<grid_dt, kThreads, 0, s>>>(mp);
 }
 template <int D>
-void MultiKernels<D>::pending(const MultiArgs& m, cudaStream_t s) {
+void MultiKernels<D>::pending(const MultiArgs* mp, cudaStream_t s) {
   g_launch_count += 1;
-  k_m_pending<D><<<1, kThreads, 0, s>>>(m);
+  k_m_pending<D><<<1, kThreads, 0, s>>>(mp);
 }
 template <int D>
 int MultiKernels<D>::particle_tile() {
   return TileCap<D>::THREADS;
+}
+template <int D>
+int MultiKernels<D>::hvp_blocks_per_sm() {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_m_hvp<D>, TileCap<D>::THREADS, 0) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return TileCap<D>::MIN_BLOCKS;
+  }
+  return b;
 }
 
 #undef OSMPM_NB

@@ -3,8 +3,10 @@
 // k_cgs_start / k_cgs_hvp_tile / k_cgs_alpha / k_cgs_beta run for a set of
 // independent Newton systems at once.  A work list of tiles, (instance,
 // item range) over particles or over DOFs and grouped by instance, is dealt
-// to the blocks of each launch; every instance keeps its own scalars (its
-// domain's DevScalars) and stops on its own.  Per-instance sums use the
+// to the blocks of each launch (fixed grids, grid stride; the kernels read
+// the work list from a device argument block, so a captured graph serves
+// every work list); every instance keeps its own scalars (its domain's
+// DevScalars) and stops on its own.  Per-instance sums use the
 // instance's arrival counter: each tile stores its partial, and the last
 // tile of an instance to arrive adds that instance's partials in tile order
 // (so the sums do not depend on scheduling) and updates the scalars.
@@ -51,10 +53,22 @@ __device__ __forceinline__ bool inst_sum(double (&v)[NV], double* part, int stri
   return true;
 }
 
-// Start: q = 0, the mass part of p.Ap (r, z = D^-1 r, p = z and x = 0 come
-// from each instance's gradient kernel).
+// The batched solver is the Jacobi PCG in Chronopoulos-Gear form: one
+// Hessian-vector product and one vector update per iteration, each ending
+// in one per-instance reduction (the standard form needs a third kernel and
+// reduction for the search direction).  With u = D^-1 r and w = A u:
+//   gamma = r.u, delta = u.Au;  beta = gamma / gamma_prev,
+//   alpha = gamma / (delta - beta gamma / alpha_prev)  (beta = 0 at first);
+//   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
+// the same iterates as the standard form in exact arithmetic.  Vectors:
+// r = a.r[0], u = a.r[1], p = a.s[0], s = a.s[1], w = a.w[0] (K u, the mass
+// part M/dt^2 u added where w is used).
+
+// Start: w = 0, p = s = 0, the mass part of u.Au (r, u = D^-1 r, gamma =
+// r.u and x = 0 come from each instance's gradient kernel).
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_m_start(MultiArgs m) {
+__global__ void __launch_bounds__(kThreads) k_m_start(const MultiArgs* __restrict__ mp) {
+  const MultiArgs m = *mp;
   for (int t = blockIdx.x; t < m.n_dt; t += gridDim.x) {
     const MultiTile T = m.dtl[t];
     if (!m.info[T.inst].fresh) continue;  // already iterating
@@ -65,9 +79,11 @@ __global__ void __launch_bounds__(kThreads) k_m_start(MultiArgs m) {
       const int c = (int)(idx / nn);
       const int64_t i = idx - (int64_t)c * nn;
       a.w[0][idx] = 0.0;
+      a.s[0][idx] = 0.0;
+      a.s[1][idx] = 0.0;
       if ((a.dofmask[i] >> c) & 1u) {
-        const double pi = a.s[0][idx];
-        acc[0] += a.m[i] * a.inv_dt2 * pi * pi;
+        const double ui = a.r[1][idx];
+        acc[0] += a.m[i] * a.inv_dt2 * ui * ui;
       }
     }
     const MultiInfo in = m.info[T.inst];
@@ -77,111 +93,109 @@ __global__ void __launch_bounds__(kThreads) k_m_start(MultiArgs m) {
       a.S->pq_diag = tot[0];
       a.S->cg_iter = 0;
       a.S->cg_neg = 0;
+      a.S->neg0 = 0;
       if (a.S->cg_max <= 0) a.S->cg_done = 1;
     }
   }
 }
 
-// q = K p over the particle tiles of the running instances (the tiled
-// product), p:Kp into pq.
+// w = K u over the particle tiles of the running instances (the tiled
+// product); the instance's last tile forms delta = u.Ku + u.Mu/dt^2 and
+// the step's alpha and beta, or stops the instance on negative curvature.
 template <int D>
-__global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS) k_m_hvp(MultiArgs m) {
+__global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS) k_m_hvp(const MultiArgs* __restrict__ mp) {
+  const MultiArgs m = *mp;
   __shared__ HvpTileShared<D> sh;
   for (int t = blockIdx.x; t < m.n_pt; t += gridDim.x) {
     const MultiTile T = m.pt[t];
     const PcgArgsT<float>& a = m.inst[T.inst];
-    if (__ldcg(&a.S->cg_done)) continue;  // the whole instance stopped (set by the alpha kernel)
+    DevScalars* S = a.S;
+    if (__ldcg(&S->cg_done)) continue;  // the whole instance stopped (set by a last tile)
     float accf = 0.0f;
-    hvp_tile<D>(a, T.lo, T.hi, sh, accf);  // T.lo, T.hi: slots
+    hvp_tile<D>(a, a.r[1], T.lo, T.hi, sh, accf);  // T.lo, T.hi: slots
     double acc[1] = {(double)accf};
     const MultiInfo in = m.info[T.inst];
     double tot[1];
-    if (inst_sum<1>(acc, m.part, m.stride, t, in.pt0, in.npt, &a.S->counter, tot) &&
-        threadIdx.x == 0)
-      a.S->pq = tot[0];
-  }
-}
-
-// alpha = r.z / p.Ap; x += alpha p; r -= alpha (q + M/dt^2 p); z = D^-1 r;
-// the instance's last tile takes r.z, r.r, beta and the stopping tests.  On
-// negative curvature the instance stops (with no direction yet, x = z_0).
-template <int D>
-__global__ void __launch_bounds__(kThreads) k_m_alpha(MultiArgs m) {
-  for (int t = blockIdx.x; t < m.n_dt; t += gridDim.x) {
-    const MultiTile T = m.dtl[t];
-    const PcgArgsT<float>& a = m.inst[T.inst];
-    DevScalars* S = a.S;
-    if (__ldcg(&S->cg_done)) continue;
-    const int64_t nn = a.g.nn;
-    const double pAp = __ldcg(&S->pq) + __ldcg(&S->pq_diag);
-    const double rz = __ldcg(&S->rz);
-    const int it = __ldcg(&S->cg_iter);
-    const bool neg = !(pAp > 0.0);
-    const double alpha = neg ? 0.0 : rz / pAp;
-    double acc[2] = {0.0, 0.0};
-    for (int64_t idx = T.lo + threadIdx.x; idx < T.hi; idx += blockDim.x) {
-      const int c = (int)(idx / nn);
-      const int64_t i = idx - (int64_t)c * nn;
-      if (!((a.dofmask[i] >> c) & 1u)) continue;
-      const double pi = a.s[0][idx];
-      if (neg) {
-        if (it == 0) a.x[idx] = pi;
-        continue;
-      }
-      a.x[idx] += alpha * pi;
-      const double ap = a.w[0][idx] + a.m[i] * a.inv_dt2 * pi;
-      const double ri = a.r[0][idx] - alpha * ap;
-      a.r[0][idx] = ri;
-      const double zi = ri * a.diag[idx];
-      a.r[1][idx] = zi;
-      acc[0] += ri * zi;
-      acc[1] += ri * ri;
-    }
-    const MultiInfo in = m.info[T.inst];
-    double tot[2];
-    if (inst_sum<2>(acc, m.part, m.stride, t, in.dt0, in.ndt, &S->counter, tot) &&
+    if (inst_sum<1>(acc, m.part, m.stride, t, in.pt0, in.npt, &S->counter, tot) &&
         threadIdx.x == 0) {
-      if (neg) {
+      const double delta = tot[0] + S->pq_diag;
+      const double gamma = S->rz;
+      const int it = S->cg_iter;
+      const double beta = it == 0 ? 0.0 : gamma / S->rz_prev;
+      const double den = it == 0 ? delta : delta - beta * gamma / S->alpha_prev;
+      if (!(den > 0.0)) {
+        // negative curvature: stop (with no step yet, x = u_0 = D^-1 r_0)
         S->cg_neg = 1;
         S->cg_done = 1;
+        S->neg0 = it == 0 ? 1 : 0;
       } else {
-        const int itn = it + 1;
-        S->cg_iter = itn;
-        S->beta = tot[0] / rz;
-        S->rz = tot[0];
-        S->rr = tot[1];
-        if (tot[1] <= S->tol2 || itn >= S->cg_max) S->cg_done = 1;
+        S->alpha = gamma / den;
+        S->beta = beta;
       }
     }
   }
 }
 
-// p = z + beta p, q = 0, the mass part of the next p.Ap.
+// p = u + beta p, s = (w + M/dt^2 u) + beta s, x += alpha p, r -= alpha s,
+// u = D^-1 r, w = 0; the instance's last tile takes gamma = r.u, r.r, the
+// mass part of the next delta and the stopping tests.
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_m_beta(MultiArgs m) {
+__global__ void __launch_bounds__(kThreads) k_m_update(const MultiArgs* __restrict__ mp) {
+  const MultiArgs m = *mp;
   for (int t = blockIdx.x; t < m.n_dt; t += gridDim.x) {
     const MultiTile T = m.dtl[t];
     const PcgArgsT<float>& a = m.inst[T.inst];
     DevScalars* S = a.S;
-    if (__ldcg(&S->cg_done)) continue;
     const int64_t nn = a.g.nn;
-    const double beta = __ldcg(&S->beta);
-    double acc[1] = {0.0};
+    if (__ldcg(&S->cg_done)) {
+      if (__ldcg(&S->neg0)) {
+        // the instance stopped before its first step: x = u_0 (every tile
+        // writes its DOFs; the flag is left for the next start to clear)
+        for (int64_t idx = T.lo + threadIdx.x; idx < T.hi; idx += blockDim.x) {
+          const int c = (int)(idx / nn);
+          const int64_t i = idx - (int64_t)c * nn;
+          if ((a.dofmask[i] >> c) & 1u) a.x[idx] = a.r[1][idx];
+        }
+      }
+      continue;
+    }
+    const double alpha = __ldcg(&S->alpha), beta = __ldcg(&S->beta);
+    const int it = __ldcg(&S->cg_iter);
+    double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t idx = T.lo + threadIdx.x; idx < T.hi; idx += blockDim.x) {
       const int c = (int)(idx / nn);
       const int64_t i = idx - (int64_t)c * nn;
+      const double wi = a.w[0][idx];
       a.w[0][idx] = 0.0;
-      if ((a.dofmask[i] >> c) & 1u) {
-        const double pi = a.r[1][idx] + beta * a.s[0][idx];
-        a.s[0][idx] = pi;
-        acc[0] += a.m[i] * a.inv_dt2 * pi * pi;
-      }
+      if (!((a.dofmask[i] >> c) & 1u)) continue;
+      const double mi = a.m[i] * a.inv_dt2;
+      const double ui = a.r[1][idx];
+      const double pi = ui + beta * a.s[0][idx];
+      const double si = (wi + mi * ui) + beta * a.s[1][idx];
+      a.s[0][idx] = pi;
+      a.s[1][idx] = si;
+      a.x[idx] += alpha * pi;
+      const double ri = a.r[0][idx] - alpha * si;
+      a.r[0][idx] = ri;
+      const double un = ri * a.diag[idx];
+      a.r[1][idx] = un;
+      acc[0] += ri * un;
+      acc[1] += ri * ri;
+      acc[2] += mi * un * un;
     }
     const MultiInfo in = m.info[T.inst];
-    double tot[1];
-    if (inst_sum<1>(acc, m.part, m.stride, t, in.dt0, in.ndt, &S->counter, tot) &&
-        threadIdx.x == 0)
-      S->pq_diag = tot[0];
+    double tot[3];
+    if (inst_sum<3>(acc, m.part, m.stride, t, in.dt0, in.ndt, &S->counter, tot) &&
+        threadIdx.x == 0) {
+      const int itn = it + 1;
+      S->cg_iter = itn;
+      S->rz_prev = S->rz;
+      S->alpha_prev = alpha;
+      S->rz = tot[0];
+      S->rr = tot[1];
+      S->pq_diag = tot[2];
+      if (tot[1] <= S->tol2 || itn >= S->cg_max) S->cg_done = 1;
+    }
   }
 }
 
@@ -189,7 +203,8 @@ __global__ void __launch_bounds__(kThreads) k_m_beta(MultiArgs m) {
 // stop flag and iteration count into pending[1 + 2i], pending[2 + 2i] (one
 // block).
 template <int D>
-__global__ void k_m_pending(MultiArgs m) {
+__global__ void k_m_pending(const MultiArgs* __restrict__ mp) {
+  const MultiArgs m = *mp;
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();

@@ -16,12 +16,17 @@
 
 namespace osmpm {
 
-// Shared tile capacity in nodes, per dimension.
+// Tile shape per dimension: threads per block (one slot or particle each),
+// shared tile capacity in nodes, and resident blocks per SM the register
+// budget is set for (2D: 64 registers, 8 blocks of 4 warps; 3D: 96
+// registers, 5 blocks).  Several small tiles per SM keep independent
+// load chains in flight: a tile's particle data depend on its slot map,
+// and its node box on those.
 template <int D>
 struct TileCap {
-  static constexpr int NODES = (D == 2) ? 1024 : 768;
-  static constexpr int THREADS = (D == 2) ? 256 : 128;  // one slot per thread
-  static constexpr int MIN_BLOCKS = (D == 2) ? 2 : 4;    // resident blocks per SM (registers)
+  static constexpr int NODES = (D == 2) ? 512 : 768;
+  static constexpr int THREADS = 128;
+  static constexpr int MIN_BLOCKS = (D == 2) ? 8 : 5;
 };
 
 // Geometry of one block's tile: the box [lo, lo + ext) of grid nodes.
@@ -177,18 +182,33 @@ __device__ __forceinline__ void unflatten_base(int sb, const GridGeo& g, int (&b
   }
 }
 
-// grad N of stencil node k (offsets x fastest) from the 1D weights.
+// The weights of stencil layer o2 (the z offset; 1 and 0 in 2D) by
+// selects, so that a loop over the layers need not index the register
+// arrays with a run-time value.
 template <int D>
-__device__ __forceinline__ void grad_n_f32(const float (&w)[D][3], const float (&dw)[D][3], int k,
-                                           float (&dN)[D]) {
-  const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+__device__ __forceinline__ void layer_weights(const float (&w)[D][3], const float (&dw)[D][3], int o2,
+                                              float& wz, float& dwz) {
+  if constexpr (D == 2) {
+    wz = 1.0f;
+    dwz = 0.0f;
+  } else {
+    wz = o2 == 0 ? w[2][0] : (o2 == 1 ? w[2][1] : w[2][2]);
+    dwz = o2 == 0 ? dw[2][0] : (o2 == 1 ? dw[2][1] : dw[2][2]);
+  }
+}
+
+// grad N of stencil node (o0, o1) of a layer with weights wz, dwz
+// (products left to right: the x factor, the y factor, the layer's).
+template <int D>
+__device__ __forceinline__ void grad_n_layer(const float (&w)[D][3], const float (&dw)[D][3], int o0,
+                                             int o1, float wz, float dwz, float (&dN)[D]) {
   if constexpr (D == 2) {
     dN[0] = dw[0][o0] * w[1][o1];
     dN[1] = w[0][o0] * dw[1][o1];
   } else {
-    dN[0] = dw[0][o0] * w[1][o1] * w[2][o2];
-    dN[1] = w[0][o0] * dw[1][o1] * w[2][o2];
-    dN[2] = w[0][o0] * w[1][o1] * dw[2][o2];
+    dN[0] = dw[0][o0] * w[1][o1] * wz;
+    dN[1] = w[0][o0] * dw[1][o1] * wz;
+    dN[2] = w[0][o0] * w[1][o1] * dwz;
   }
 }
 
@@ -286,8 +306,8 @@ struct HvpTileShared {
 
 // The tiled Hessian-vector product of the particles in slots [s0, s1)
 // (s1 - s0 <= blockDim.x, one slot per thread, s0 a multiple of 2^D; the
-// whole block calls it): q = a.w[0] += K p on the free DOFs with
-// p = a.s[0], and acc += this run's share of p.Kp = sum_p G:Y.  Per particle
+// whole block calls it): q = a.w[0] += K p on the free DOFs with p = pv
+// (a grid vector), and acc += this run's share of p.Kp = sum_p G:Y.  Per particle
 // it reads its slot, its stencil base (flat), F^n and the FP32 data of
 // TileX; no FP64 arithmetic runs per particle.  The block stages the node
 // box of its particles' stencils in shared memory, gathers from it, and
@@ -298,10 +318,9 @@ struct HvpTileShared {
 // group sums to the tile.  A run whose node box exceeds the tile adds the
 // group sums to global memory instead.
 template <int D>
-__device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, int64_t s1,
-                                         HvpTileShared<D>& sh, float& acc) {
+__device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, const double* pv, int64_t s0,
+                                         int64_t s1, HvpTileShared<D>& sh, float& acc) {
   constexpr int DD = D * D;
-  constexpr int K = (D == 2) ? 9 : 27;
   constexpr int CAP = TileCap<D>::NODES;
   constexpr int GL = 1 << D;                 // lanes per slot group
   constexpr int KC = 9;                      // stencil nodes per scatter chunk
@@ -312,7 +331,6 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
   auto& box = sh.box;
   const GridGeo& g = a.g;
   const int64_t n = a.P.n;
-  const double* pv = a.s[0];
   double* q = a.w[0];
   const int gr = threadIdx.x & (GL - 1);
   const int64_t slot = s0 + threadIdx.x;
@@ -354,26 +372,33 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
     float Gd[DD];
 #pragma unroll
     for (int e = 0; e < DD; ++e) Gd[e] = 0.0f;
+    // one layer of 9 stencil nodes per pass (a rolled loop in 3D keeps the
+    // code within the instruction cache)
+#pragma unroll 1
+    for (int o2 = 0; o2 < (D == 3 ? 3 : 1); ++o2) {
+      float wz, dwz;
+      layer_weights<D>(w, dw, o2, wz, dwz);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
-      float dN[D];
-      grad_n_f32<D>(w, dw, k, dN);
-      float dk[D];
-      if (tiled) {
-        const int l = lb + tile_local<D>(box, o0, o1, o2);
+      for (int kk = 0; kk < 9; ++kk) {
+        const int o0 = kk % 3, o1 = kk / 3;
+        float dN[D];
+        grad_n_layer<D>(w, dw, o0, o1, wz, dwz, dN);
+        float dk[D];
+        if (tiled) {
+          const int l = lb + tile_local<D>(box, o0, o1, o2);
 #pragma unroll
-        for (int c = 0; c < D; ++c) dk[c] = sd[c][l];
-      } else {
-        const int64_t gi = (int64_t)sb + (D == 2 ? o0 + o1 * g.res[0]
-                                                : o0 + (o1 + o2 * g.res[1]) * g.res[0]);
+          for (int c = 0; c < D; ++c) dk[c] = sd[c][l];
+        } else {
+          const int64_t gi = (int64_t)sb + (D == 2 ? o0 + o1 * g.res[0]
+                                                  : o0 + (o1 + o2 * g.res[1]) * g.res[0]);
 #pragma unroll
-        for (int c = 0; c < D; ++c) dk[c] = d2f_bits(__ldcg(&pv[c * g.nn + gi]));
+          for (int c = 0; c < D; ++c) dk[c] = d2f_bits(__ldcg(&pv[c * g.nn + gi]));
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int b = 0; b < D; ++b) Gd[c * D + b] = fmaf(dk[c], dN[b], Gd[c * D + b]);
       }
-#pragma unroll
-      for (int c = 0; c < D; ++c)
-#pragma unroll
-        for (int b = 0; b < D; ++b) Gd[c * D + b] = fmaf(dk[c], dN[b], Gd[c * D + b]);
     }
     float Fn[DD], A[DD];
 #pragma unroll
@@ -388,17 +413,18 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
   // reduce-scatter (a padding slot adds zeros), in chunks of KC stencil
   // nodes (one layer); each lane then adds its share of the group sums to
   // the shared tile, or to global memory when the box exceeds the tile.
-#pragma unroll
-  for (int o2c = 0; o2c < 3; ++o2c) {
+#pragma unroll 1
+  for (int o2c = 0; o2c < (D == 3 ? 3 : 1); ++o2c) {
     float v[NVP];
 #pragma unroll
     for (int j = 0; j < NVP; ++j) v[j] = 0.0f;
     if (valid) {
+      float wz, dwz;
+      layer_weights<D>(w, dw, o2c, wz, dwz);
 #pragma unroll
       for (int kk = 0; kk < KC; ++kk) {
-        const int k = (D == 2 ? 0 : 9 * o2c) + kk;
         float dN[D];
-        grad_n_f32<D>(w, dw, k, dN);
+        grad_n_layer<D>(w, dw, kk % 3, kk / 3, wz, dwz, dN);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
           float t = 0.0f;
@@ -423,8 +449,7 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
         const int idx = gr * (NVP / GL) + j;
         if (idx < KC * D) {
           const int kk = idx / D, c = idx - kk * D;
-          const int k = (D == 2 ? 0 : 9 * o2c) + kk;
-          const int o0 = k % 3, o1 = (k / 3) % 3, o2 = k / 9;
+          const int o0 = kk % 3, o1 = kk / 3, o2 = o2c;
           if (tiled) {
             atomicAdd(&sq[c][gbase + tile_local<D>(box, o0, o1, o2)], f2d_bits(v[j]));
           } else {
@@ -435,7 +460,6 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, int64_t s0, i
         }
       }
     }
-    if (D == 2) break;  // one chunk holds the whole 2D stencil
   }
   if (tiled) {
     __syncthreads();
@@ -466,7 +490,7 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS)
   const int64_t tiles = (ns + blockDim.x - 1) / blockDim.x;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int64_t s0 = t * blockDim.x;
-    hvp_tile<D>(a, s0, s0 + blockDim.x < ns ? s0 + blockDim.x : ns, sh, accf);
+    hvp_tile<D>(a, a.s[0], s0, s0 + blockDim.x < ns ? s0 + blockDim.x : ns, sh, accf);
   }
   double acc[1] = {(double)accf};
   double tot[1];
@@ -508,7 +532,7 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS)
                int* sbase, R* sdn) {
   constexpr int K = (D == 2) ? 9 : 27;
   constexpr int NV = D + 2;           // m, mv (D), bm
-  constexpr int CAP = (D == 2) ? 1024 : 768;
+  constexpr int CAP = TileCap<D>::NODES;
   __shared__ double acc[NV][CAP];
   __shared__ TileBox<D> box;
   const int64_t n = P.n;

@@ -61,7 +61,8 @@ struct DevScalars {
   unsigned counter;
   unsigned bar_count, bar_spare;  // grid-barrier counter of the persistent PCG kernel
   int n_slots;                     // cell-aligned slots of the last P2G (tiled product)
-  int pad_;
+  int neg0;                        // batched PCG: negative curvature before the first step
+  double rz_prev, alpha_prev;      // batched PCG (Chronopoulos-Gear): gamma, alpha of the last step
 };
 
 enum : int {

@@ -34,13 +34,15 @@ def rel_disp(x_gpu, x_ref, x0):
 
 
 def two_clusters(dim, gap_cells=40):
-    """Two blocks of material (6^2 cells in 2D, 3^3 in 3D) at opposite
+    """Two blocks of material (6^2 cells in 2D, 4^3 in 3D) at opposite
     corners of a grid whose node box spans gap_cells cells per axis.  In
-    Morton order the block of particles that holds the end of the first
-    cluster and the start of the second has a node box far larger than the
-    tile (the global-memory path); the other blocks are tiled."""
+    Morton order the slot tile that holds the end of the first cluster and
+    the start of the second has a node box far larger than the tile (the
+    global-memory path); the other tiles are staged in shared memory.  In
+    both dimensions the last tile ends inside a warp (a partly filled warp
+    of slots)."""
     dx, ppc = 0.05, 2
-    c = 6 if dim == 2 else 3
+    c = 6 if dim == 2 else 4
     inside = lambda x: np.ones(len(x), dtype=bool)  # noqa: E731
     a = W.sample_lattice((0.0,) * dim, dx, (0,) * dim, (c,) * dim, ppc, inside)
     b = W.sample_lattice((0.0,) * dim, dx, (gap_cells - c,) * dim, (gap_cells,) * dim, ppc, inside)
