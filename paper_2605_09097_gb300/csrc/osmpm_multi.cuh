@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS) k
     DevScalars* S = a.S;
     if (__ldcg(&S->cg_done)) continue;  // the whole instance stopped (set by a last tile)
     float accf = 0.0f;
-    hvp_tile<D>(a, a.r[1], T.lo, T.hi, sh, accf);  // T.lo, T.hi: slots
+    const int64_t slot = T.lo + threadIdx.x;  // T.lo, T.hi: slots
+    hvp_tile<D>(a, a.r[1], slot < T.hi ? (int64_t)a.slot2p[slot] : -1, sh, accf);
     double acc[1] = {(double)accf};
     const MultiInfo in = m.info[T.inst];
     double tot[1];

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "osmpm_device.cuh"
 
@@ -296,7 +297,8 @@ __device__ __forceinline__ float hessian_apply_x(const float (&A)[D * D], float 
 template <int D>
 struct HvpTileShared {
   static constexpr int CAP = TileCap<D>::NODES;
-  float sd[D][CAP];   // direction p at the tile nodes
+  using Vec = typename std::conditional<D == 2, float2, float4>::type;
+  Vec sd[CAP];        // direction p at the tile nodes (one vector load per node)
   // K p accumulators in FP64: a node sums the contributions of up to 27
   // cells; for smooth directions they nearly cancel, and an FP32 sum loses
   // the small remainder (the plate-bending modes of a thin body)
@@ -304,10 +306,11 @@ struct HvpTileShared {
   TileBox<D> box;
 };
 
-// The tiled Hessian-vector product of the particles in slots [s0, s1)
-// (s1 - s0 <= blockDim.x, one slot per thread, s0 a multiple of 2^D; the
-// whole block calls it): q = a.w[0] += K p on the free DOFs with p = pv
-// (a grid vector), and acc += this run's share of p.Kp = sum_p G:Y.  Per particle
+// The tiled Hessian-vector product of one tile of slots (one slot per
+// thread, the tile starting at a multiple of 2^D; the whole block calls it
+// with each thread's particle pi, -1 for a padding slot or a thread past
+// the last slot): q = a.w[0] += K p on the free DOFs with p = pv (a grid
+// vector), and acc += this run's share of p.Kp = sum_p G:Y.  Per particle
 // it reads its slot, its stencil base (flat), F^n and the FP32 data of
 // TileX; no FP64 arithmetic runs per particle.  The block stages the node
 // box of its particles' stencils in shared memory, gathers from it, and
@@ -318,8 +321,8 @@ struct HvpTileShared {
 // group sums to the tile.  A run whose node box exceeds the tile adds the
 // group sums to global memory instead.
 template <int D>
-__device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, const double* pv, int64_t s0,
-                                         int64_t s1, HvpTileShared<D>& sh, float& acc) {
+__device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, const double* pv, int64_t pi,
+                                         HvpTileShared<D>& sh, float& acc) {
   constexpr int DD = D * D;
   constexpr int CAP = TileCap<D>::NODES;
   constexpr int GL = 1 << D;                 // lanes per slot group
@@ -333,8 +336,6 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, const double*
   const int64_t n = a.P.n;
   double* q = a.w[0];
   const int gr = threadIdx.x & (GL - 1);
-  const int64_t slot = s0 + threadIdx.x;
-  const int64_t pi = slot < s1 ? (int64_t)a.slot2p[slot] : -1;
   const int sb = pi >= 0 ? a.sbase[pi] : -1;  // -1: outside the grid box
   const bool valid = sb >= 0;
   int base[D];
@@ -354,11 +355,14 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, const double*
   if (tiled) {
     for (int l = threadIdx.x; l < box.nodes; l += blockDim.x) {
       const int64_t gi = tile_global<D>(box, g, l);
+      float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        sd[c][l] = d2f_bits(__ldcg(&pv[c * g.nn + gi]));
+        t[c] = d2f_bits(__ldcg(&pv[c * g.nn + gi]));
         sq[c][l] = 0.0;
       }
+      if constexpr (D == 2) sd[l] = make_float2(t[0], t[1]);
+      else sd[l] = make_float4(t[0], t[1], t[2], 0.0f);
     }
     __syncthreads();
   }
@@ -386,8 +390,10 @@ __device__ __forceinline__ void hvp_tile(const PcgArgsT<float>& a, const double*
         float dk[D];
         if (tiled) {
           const int l = lb + tile_local<D>(box, o0, o1, o2);
-#pragma unroll
-          for (int c = 0; c < D; ++c) dk[c] = sd[c][l];
+          const auto v = sd[l];
+          dk[0] = v.x;
+          dk[1] = v.y;
+          if constexpr (D == 3) dk[D - 1] = v.z;
         } else {
           const int64_t gi = (int64_t)sb + (D == 2 ? o0 + o1 * g.res[0]
                                                   : o0 + (o1 + o2 * g.res[1]) * g.res[0]);
@@ -488,9 +494,17 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS)
   const int64_t ns = __ldcg(a.n_slots);
   float accf = 0.0f;  // this thread's particles' share of p.Kp (a few tiles)
   const int64_t tiles = (ns + blockDim.x - 1) / blockDim.x;
+  // each thread's slot of the block's next tile is read one tile ahead, so
+  // the slot map's latency overlaps the current tile
+  auto slot_of = [&](int64_t t) -> int64_t {
+    const int64_t sl = t * blockDim.x + threadIdx.x;
+    return (t < tiles && sl < ns) ? (int64_t)a.slot2p[sl] : -1;
+  };
+  int64_t pi_next = slot_of(blockIdx.x);
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t s0 = t * blockDim.x;
-    hvp_tile<D>(a, a.s[0], s0, s0 + blockDim.x < ns ? s0 + blockDim.x : ns, sh, accf);
+    const int64_t pi = pi_next;
+    pi_next = slot_of(t + gridDim.x);
+    hvp_tile<D>(a, a.s[0], pi, sh, accf);
   }
   double acc[1] = {(double)accf};
   double tot[1];
