@@ -62,7 +62,7 @@ ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
 AUTOTUNE_THREADS = [8, 12, 16]
 # (host threads, DOFs per DOF tile, PCG iterations per graph replay)
-AUTOTUNE_MULTI = [(64, 2048, 16), (128, 2048, 16), (256, 2048, 16), (128, 2048, 8)]
+AUTOTUNE_MULTI = [(64, 2048, 16), (128, 2048, 16), (128, 1024, 16), (128, 512, 16)]
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
 # launch, from the ncu capture of the current kernel (the k_pcg profile
 # summary of this workload); None whenever the kernel changes
@@ -412,7 +412,7 @@ MIXED_HVP_BYTES_PER_PARTICLE = {2: 52.0, 3: 78.0}
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch on the
 # 3.07M-particle fold band (ncu), per kernel; absent until captured for the
 # current kernel
-FOLD_HVP_TRAFFIC_BYTES = {"k_cgs_hvp_tile": 347.648e6 + 6.266e6}
+FOLD_HVP_TRAFFIC_BYTES = {"k_cgs_hvp_tile": 347.653e6 + 5.941e6}
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the batched
 # Hessian-vector product (k_m_hvp) on the batched family, from ncu; None
 # until captured for the current kernel
@@ -785,6 +785,74 @@ def run_fold_solve(args, rank, local, world):
             "roofline": roofline}
 
 
+def hertz_profile(p, xc, F, R=0.5, E1=1e7, E2=1e6, nu=0.3):
+    """Contact half-width and peak pressure of a measured pressure profile
+    p(x) (bins centred at xc, contact centre x = 2) by a least-squares fit of
+    the semi-ellipse p0 sqrt(1 - ((x - 2)/b)^2), beside the Hertz closed form
+    for a cylinder on a half-space in plane strain at the measured line load
+    F: E* = 1/((1 - nu^2)/E1 + (1 - nu^2)/E2), b = 2 sqrt(F R/(pi E*)),
+    p_max = 2F/(pi b)."""
+    Es = 1.0 / ((1 - nu ** 2) / E1 + (1 - nu ** 2) / E2)
+    b_h = 2.0 * np.sqrt(F * R / (np.pi * Es))
+    best = (np.inf, 0.0, 0.0)
+    for b in np.linspace(0.3, 3.0, 271) * b_h:
+        shape = np.sqrt(np.clip(1.0 - ((xc - 2.0) / b) ** 2, 0.0, None))
+        den = float(shape @ shape)
+        if den <= 0.0:
+            continue
+        p0 = float(shape @ p) / den
+        res = float(np.sum((p - p0 * shape) ** 2))
+        if res < best[0]:
+            best = (res, b, p0)
+    return {"F_N_per_m": F, "b_fit": best[1], "b_hertz": b_h, "p_max_fit": best[2],
+            "p_max_hertz": 2.0 * F / (np.pi * b_h)}
+
+
+def run_hertz(args, rank, local, world):
+    """The Hertz contact configuration (BASELINE configs[2]: elastic
+    cylinder R 0.5, E 1e7, pressed 0.02 into an elastic block E 1e6 over 100
+    global steps of 2e-4 s, fine box at dx 1/256, M = 4, mixed precision),
+    run whole; every 10 steps the contact pressure on the block's top layer
+    of fine particles (their initial y within one cell below the surface),
+    from the Cauchy stress of each particle's F, binned at the fine spacing,
+    against the Hertz closed form at the measured line load.  A validation
+    study, not a throughput line."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2605_09097_gb300 import build
+    build.build()
+    from paper_2605_09097_gb300 import osmpm
+    cB, cS, sch, dT = W.hertz()
+    B, S = osmpm.Domain(cB), osmpm.Domain(cS)
+    dx = cS.grid.dx
+    x0 = cS.particles.x
+    top = (cS.particles.E < 5e6) & (x0[:, 1] < 2.0) & (x0[:, 1] >= 2.0 - dx)
+    E, nu = cS.particles.E[top], cS.particles.nu[top]
+    mu, lam = E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+    edges = np.arange(1.75, 2.25 + 1e-12, dx)
+    xc = 0.5 * (edges[1:] + edges[:-1])
+    rows, t0 = [], time.perf_counter()
+    for k in range(1, 101):
+        osmpm.osmpm_schwarz_couple(B, S, dT, sch)
+        if k % 10:
+            continue
+        x, _, _, F = S.get_particles()
+        Ft = F[top]
+        J = np.linalg.det(Ft)
+        FFt = np.einsum("pij,pkj->pik", Ft, Ft)
+        sig = (mu[:, None, None] * (FFt - np.eye(2)) +
+               (lam * np.log(J))[:, None, None] * np.eye(2)) / J[:, None, None]
+        idx = np.digitize(x[top, 0], edges) - 1
+        p = np.array([-sig[idx == i, 1, 1].mean() if np.any(idx == i) else 0.0
+                      for i in range(len(xc))])
+        load = float(np.sum(np.clip(p, 0.0, None)) * dx)
+        rows.append({"step": k, **hertz_profile(np.clip(p, 0.0, None), xc, load)})
+    wall = time.perf_counter() - t0
+    return {"workload": "hertz_contact_cylinder_on_block_mixed", "study": "contact pressure vs Hertz",
+            "particles": cB.particles.n + cS.particles.n, "steps": 100, "wall_s": wall,
+            "profiles": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -798,12 +866,13 @@ def main():
     ap.add_argument("--hvp-mode", type=int, choices=[0, 1, 2], default=0,
                     help="fold3d_solve: Hessian-vector product of the streaming PCG")
     ap.add_argument("--workload", choices=["default", "inclusion", "batched", "fold3d",
-                                           "fold3d_solve"],
+                                           "fold3d_solve", "hertz"],
                     default="default",
                     help="default: the batched family in mixed precision with the FP64 single "
                          "inclusion beside it; inclusion: the FP64 single inclusion alone; batched: "
                          "many instances; fold3d: the 3D folding plate (mixed); fold3d_solve: the "
-                         "fold's 3.07M-particle band folded on its own")
+                         "fold's 3.07M-particle band folded on its own; hertz: the contact "
+                         "configuration's pressure against the Hertz closed form (a study)")
     ap.add_argument("--scaled", action="store_true", help="fold3d: the 3.07M-particle band")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--threads", type=int, default=0,
@@ -824,6 +893,8 @@ def main():
         out = run_fold(args, rank, local, world)
     elif args.workload == "fold3d_solve":
         out = run_fold_solve(args, rank, local, world)
+    elif args.workload == "hertz":
+        out = run_hertz(args, rank, local, world)
     else:
         out = run_ours(args, rank, local, world)
     if rank == 0 and out is not None:

@@ -57,3 +57,20 @@ def test_clock_rows_summary():
     hot = bench.parse_clock_rows(["0, 1500, 2070, 1300, 0x48, Active, Not Active, Active, Not Active"])
     assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"] and hot["sm_mhz"] == 1500.0
     assert bench.parse_clock_rows([]) is None
+
+
+def test_hertz_profile_fit_recovers_a_semi_ellipse():
+    """The Hertz study's fit returns the half-width and peak of an exact
+    semi-elliptic profile, and the closed form satisfies F = pi b p_max / 2
+    (the load of a semi-ellipse)."""
+    import numpy as np
+    import bench
+    xc = np.arange(1.75, 2.25, 1 / 256) + 0.5 / 256
+    F = 15000.0
+    h0 = bench.hertz_profile(np.zeros_like(xc), xc, F)
+    b, p0 = h0["b_hertz"], h0["p_max_hertz"]
+    assert abs(np.pi * b * p0 / 2 - F) <= 1e-9 * F
+    p = 0.8 * p0 * np.sqrt(np.clip(1 - ((xc - 2) / (1.2 * b)) ** 2, 0, None))
+    h = bench.hertz_profile(p, xc, F)
+    assert abs(h["b_fit"] / (1.2 * b) - 1) < 0.01
+    assert abs(h["p_max_fit"] / (0.8 * p0) - 1) < 0.01

@@ -3,7 +3,7 @@ block, fine subdomain around the contact, M = 4).  A reduced-resolution
 variant is compared with the FP64 oracle particle by particle, in FP64 and
 in mixed precision; the full-size configuration (dx_c 1/64, ~166k
 particles, mixed) runs two global steps and is checked through properties
-that hold at any size."""
+that hold at any size, and run whole against the Hertz closed form."""
 import dataclasses
 
 import numpy as np
@@ -80,3 +80,22 @@ def test_hertz_full_size_two_steps(osmpm):
     # coupled: fine particles in the contact zone move down with the indenter
     near = (np.abs(cS.particles.x[:, 0] - 2.0) < 0.05) & (cS.particles.x[:, 1] > 2.0)
     assert (xS[near, 1] - cS.particles.x[near, 1]).mean() < 0
+
+
+def test_hertz_full_size_pressure_matches_closed_form(osmpm):
+    """The full contact configuration run whole (100 global steps, the flat
+    face pushed down 0.02): from step 60 on, once the start-up transient of
+    the sudden push has passed, the pressure on the block's top layer, fitted
+    by a semi-ellipse, has its half-width b and peak p_max within 15 % of the
+    Hertz line contact at the measured load (cylinder on a half-space, plane
+    strain).  The configuration bonds the bodies (R22) and loads them
+    dynamically, where Hertz assumes frictionless static contact, so the
+    bound is an engineering one."""
+    import bench
+    out = bench.run_hertz(None, 0, 0, 1)
+    late = [r for r in out["profiles"] if r["step"] >= 60]
+    assert len(late) == 5
+    for r in late:
+        assert r["F_N_per_m"] > 1e4, r
+        assert abs(r["b_fit"] / r["b_hertz"] - 1.0) <= 0.15, r
+        assert abs(r["p_max_fit"] / r["p_max_hertz"] - 1.0) <= 0.15, r
