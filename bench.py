@@ -61,8 +61,10 @@ ORACLE_SCHWARZ_ITERS_PER_STEP = 12.0
 ORACLE_SAMPLE_ITERS = 2
 L2_FLUSH_BYTES = 256 << 20
 AUTOTUNE_THREADS = [8, 12, 16]
-# (host threads, DOFs per DOF tile, PCG iterations per graph replay)
-AUTOTUNE_MULTI = [(64, 2048, 16), (128, 2048, 16), (128, 1024, 16), (128, 512, 16)]
+# (host threads, DOFs per DOF tile, PCG iterations per graph replay, slot
+# tiles per work item of the batched product)
+AUTOTUNE_MULTI = [(128, 2048, 16, 1), (128, 2048, 16, 2), (128, 2048, 16, 4),
+                  (128, 2048, 16, 8)]
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
 # launch, from the ncu capture of the current kernel (the k_pcg profile
 # summary of this workload); None whenever the kernel changes
@@ -453,7 +455,7 @@ def run_batched(args, rank, local, world):
             tuned = {"x".join(map(str, c)): v for c, v in zip(AUTOTUNE_MULTI, scores)}
             tune_steps = len(AUTOTUNE_MULTI) + 1
         else:
-            shape = (args.threads, 0, 0)
+            shape = (args.threads, args.dof_tile, args.chunk, args.slot_tiles)
         threads = shape[0]
 
         def batched_step():
@@ -877,6 +879,12 @@ def main():
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--threads", type=int, default=0,
                     help="host threads of the batched workload; 0: chosen by the autotuner")
+    ap.add_argument("--dof-tile", type=int, default=0,
+                    help="batched multi with --threads > 0: DOFs per DOF tile (0: default)")
+    ap.add_argument("--chunk", type=int, default=0,
+                    help="batched multi with --threads > 0: iterations per graph replay")
+    ap.add_argument("--slot-tiles", type=int, default=0,
+                    help="batched multi with --threads > 0: slot tiles per product work item")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--batch-mode", choices=["threads", "multi"], default="threads",
                     help="batched: per-pair PCG launches from a host thread pool, or the "

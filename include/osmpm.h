@@ -305,12 +305,15 @@ osmpm_status osmpm_autotune_batch(osmpm_domain* const* coarse, osmpm_domain* con
  * batched Jacobi PCG (the streaming PCG with the block-tiled
  * Hessian-vector product) over a work list of (pair's domain, particle
  * tile) and (pair's domain, DOF tile), each system with its own scalars
- * and stopping test; the iterations run in chunks replayed from a CUDA
- * graph captured for the batch, with a look at the stop flags after each.
- * Systems handed in during a batch join the next.  Results per pair are
- * those of osmpm_schwarz_couple within the solver tolerances.
+ * and stopping test; the iterations run in chunks (one CUDA graph reads
+ * the work list from device memory), with a look at the stop flags after
+ * each: converged systems leave and systems handed in meanwhile join
+ * between chunks.  Results per pair are those of osmpm_schwarz_couple
+ * within the solver tolerances.
  *  - desc: n_threads host threads (0: 32), dof_tile DOFs per DOF tile
- *    (0: 2048), chunk iterations per graph replay (0: 16).
+ *    (0: 2048), chunk iterations per graph replay (0: 16), slot_tiles
+ *    slot tiles (128 particle slots each) per work item of the
+ *    Hessian-vector product (0: 1).
  *  - stats / status per pair as for osmpm_schwarz_couple_batch; ms (may be
  *    NULL) receives the service's counters.
  * Errors: OSMPM_E_UNSUPPORTED unless every domain is mixed precision (1)
@@ -319,7 +322,7 @@ typedef struct osmpm_multi_desc {
   int32_t n_threads;
   int32_t dof_tile;
   int32_t chunk;
-  int32_t reserved;
+  int32_t slot_tiles;
 } osmpm_multi_desc;
 
 typedef struct osmpm_multi_stats {
@@ -345,7 +348,8 @@ osmpm_status osmpm_schwarz_couple_multi(osmpm_domain* const* coarse, osmpm_domai
 
 /* Launch-shape autotuner of osmpm_schwarz_couple_multi: runs one untimed
  * and then one timed multi step per candidate descriptor (host threads, DOF
- * tile, iterations per graph replay); these are real global steps, so the
+ * tile, iterations per graph replay, slot tiles per product work item);
+ * these are real global steps, so the
  * pairs advance by n_candidates + 1 steps.  Scored by wall time per PCG
  * iteration summed over the pairs; *best receives the index of the best
  * candidate, us_per_cg_iter (may be NULL) the n_candidates scores. */

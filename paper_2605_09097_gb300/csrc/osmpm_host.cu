@@ -842,6 +842,7 @@ struct PcgBatcher {
   int dim = 2;
   int dof_tile = 2048;  // DOFs per DOF tile
   int chunk = 16;       // iterations between looks at the stop flags
+  int slot_tiles = 1;   // slot tiles per work item of the product
   int grid_pt = 1, grid_dt = 1;  // fixed grids of the product and of the DOF kernels
   cudaStream_t stream = nullptr;
   std::mutex mu;
@@ -889,10 +890,11 @@ struct PcgBatcher {
     return L;
   }
 
-  osmpm_status open(int dim_, int dof_tile_, int chunk_) {
+  osmpm_status open(int dim_, int dof_tile_, int chunk_, int slot_tiles_) {
     dim = dim_;
     dof_tile = dof_tile_ > 0 ? dof_tile_ : 2048;
     chunk = chunk_ > 0 ? chunk_ : 16;
+    slot_tiles = slot_tiles_ > 0 ? slot_tiles_ : 1;
     int dev_id = 0, sms = 1;
     cudaGetDevice(&dev_id);
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id));
@@ -1017,7 +1019,9 @@ struct PcgBatcher {
   // when a table outgrows its capacity.
   osmpm_status build(const std::vector<Req*>& live, const std::vector<int>& fresh) {
     const int n = (int)live.size();
-    const int TP = dim == 2 ? MultiKernels<2>::particle_tile() : MultiKernels<3>::particle_tile();
+    // a product work item covers slot_tiles tiles of TP slots of one instance
+    const int TP = slot_tiles * (dim == 2 ? MultiKernels<2>::particle_tile()
+                                          : MultiKernels<3>::particle_tile());
     std::vector<PcgArgsT<float>> inst((size_t)n);
     std::vector<MultiInfo> info((size_t)n);
     std::vector<MultiTile> pt, dtl;
@@ -2604,8 +2608,8 @@ osmpm_status osmpm_schwarz_couple_multi(osmpm_domain* const* coarse, osmpm_domai
                                         osmpm_status* status, osmpm_multi_stats* ms) {
   if (n < 0 || !coarse || !fine || !sdesc || !desc)
     return fail(OSMPM_E_INVALID, "null argument or n < 0");
-  if (desc->n_threads < 0 || desc->dof_tile < 0 || desc->chunk < 0 || desc->reserved != 0)
-    return fail(OSMPM_E_INVALID, "multi descriptor: counts >= 0, reserved 0");
+  if (desc->n_threads < 0 || desc->dof_tile < 0 || desc->chunk < 0 || desc->slot_tiles < 0)
+    return fail(OSMPM_E_INVALID, "multi descriptor: counts >= 0");
   if (ms) memset(ms, 0, sizeof(*ms));
   if (n == 0) return OSMPM_OK;
   for (int32_t i = 0; i < n; ++i) {
@@ -2619,7 +2623,7 @@ osmpm_status osmpm_schwarz_couple_multi(osmpm_domain* const* coarse, osmpm_domai
         return fail(OSMPM_E_INVALID, "pairs %d and %d share a domain", j, i);
   }
   PcgBatcher b;
-  OSMPM_TRY(b.open(coarse[0]->dim, desc->dof_tile, desc->chunk));
+  OSMPM_TRY(b.open(coarse[0]->dim, desc->dof_tile, desc->chunk, desc->slot_tiles));
   int threads = desc->n_threads > 0 ? desc->n_threads : 32;
   if (threads > n) threads = n;
   std::vector<osmpm_status> st((size_t)n, OSMPM_OK);

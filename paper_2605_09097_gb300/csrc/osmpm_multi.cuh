@@ -26,6 +26,18 @@ __device__ __forceinline__ bool inst_sum(double (&v)[NV], double* part, int stri
   __shared__ bool last;
   __shared__ double tsh[NV];
   block_sum<NV>(v);
+  if (nt == 1) {
+    // the instance's only tile: its block sum is the total (no partials,
+    // fence or arrival count)
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) tsh[k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = tsh[k];
+    __syncthreads();  // tsh is reused by the next call
+    return true;
+  }
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) part[k * stride + tile] = v[k];
@@ -111,9 +123,20 @@ __global__ void __launch_bounds__(TileCap<D>::THREADS, TileCap<D>::MIN_BLOCKS) k
     const PcgArgsT<float>& a = m.inst[T.inst];
     DevScalars* S = a.S;
     if (__ldcg(&S->cg_done)) continue;  // the whole instance stopped (set by a last tile)
+    // T.lo, T.hi: slots, one or more tiles of blockDim.x (a block works
+    // through them with one sum for the item); each thread reads its slot
+    // of the next tile before working on the current one
     float accf = 0.0f;
-    const int64_t slot = T.lo + threadIdx.x;  // T.lo, T.hi: slots
-    hvp_tile<D>(a, a.r[1], slot < T.hi ? (int64_t)a.slot2p[slot] : -1, sh, accf);
+    auto slot_of = [&](int64_t s0) -> int64_t {
+      const int64_t sl = s0 + threadIdx.x;
+      return sl < T.hi ? (int64_t)a.slot2p[sl] : -1;
+    };
+    int64_t pi_next = slot_of(T.lo);
+    for (int64_t s0 = T.lo; s0 < T.hi; s0 += blockDim.x) {
+      const int64_t pi = pi_next;
+      pi_next = slot_of(s0 + blockDim.x);
+      hvp_tile<D>(a, a.r[1], pi, sh, accf);
+    }
     double acc[1] = {(double)accf};
     const MultiInfo in = m.info[T.inst];
     double tot[1];

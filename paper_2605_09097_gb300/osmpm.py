@@ -116,7 +116,7 @@ class osmpm_plane(Structure):
 
 class osmpm_multi_desc(Structure):
     _fields_ = [("n_threads", c_int32), ("dof_tile", c_int32), ("chunk", c_int32),
-                ("reserved", c_int32)]
+                ("slot_tiles", c_int32)]
 
 
 class osmpm_multi_stats(Structure):
@@ -572,7 +572,8 @@ def osmpm_schwarz_couple_batch(coarse: List[Domain], fine: List[Domain], dT: flo
 
 
 def osmpm_schwarz_couple_multi(coarse: List[Domain], fine: List[Domain], dT: float, schs,
-                               n_threads: int = 0, dof_tile: int = 0, chunk: int = 0):
+                               n_threads: int = 0, dof_tile: int = 0, chunk: int = 0,
+                               slot_tiles: int = 0):
     """One global step of every pair (mixed precision) with the batched PCG
     service: host threads drive the pairs, every Newton system is solved in a
     batched PCG together with the systems of the other pairs.  Returns
@@ -583,7 +584,7 @@ def osmpm_schwarz_couple_multi(coarse: List[Domain], fine: List[Domain], dT: flo
     sd = (osmpm_schwarz_desc * n)(*[make_schwarz_desc(s) for s in schs])
     st = (osmpm_stats * n)()
     status = (c_int32 * n)()
-    md = osmpm_multi_desc(int(n_threads), int(dof_tile), int(chunk), 0)
+    md = osmpm_multi_desc(int(n_threads), int(dof_tile), int(chunk), int(slot_tiles))
     ms = osmpm_multi_stats()
     _check(_lib.osmpm_schwarz_couple_multi(cs, fs, n, dT, sd, ctypes.byref(md), st, status,
                                            ctypes.byref(ms)),
@@ -593,15 +594,15 @@ def osmpm_schwarz_couple_multi(coarse: List[Domain], fine: List[Domain], dT: flo
 
 def osmpm_autotune_multi(coarse: List[Domain], fine: List[Domain], dT: float, schs, candidates):
     """Launch shape of osmpm_schwarz_couple_multi chosen by timing one step
-    per candidate, each a (n_threads, dof_tile, chunk) tuple (the pairs
-    advance by len(candidates) + 1 global steps).  Returns (best candidate,
-    list of wall microseconds per PCG iteration)."""
+    per candidate, each a (n_threads, dof_tile, chunk[, slot_tiles]) tuple
+    (the pairs advance by len(candidates) + 1 global steps).  Returns (best
+    candidate, list of wall microseconds per PCG iteration)."""
     n = len(coarse)
     cs = (c_void_p * n)(*[d.h.value for d in coarse])
     fs = (c_void_p * n)(*[d.h.value for d in fine])
     sd = (osmpm_schwarz_desc * n)(*[make_schwarz_desc(s) for s in schs])
-    cand = (osmpm_multi_desc * len(candidates))(*[osmpm_multi_desc(int(a), int(b), int(c), 0)
-                                                  for a, b, c in candidates])
+    cand = (osmpm_multi_desc * len(candidates))(
+        *[osmpm_multi_desc(*[int(v) for v in (tuple(c) + (0,))[:4]]) for c in candidates])
     best = c_int32(0)
     score = np.zeros(len(candidates), dtype=np.float64)
     _check(_lib.osmpm_autotune_multi(cs, fs, n, dT, sd, cand, len(candidates), ctypes.byref(best),

@@ -43,12 +43,16 @@ def rel_disp(x_gpu, x_ref, x0):
     return np.linalg.norm(x_gpu - x_ref) / max(np.linalg.norm(x_ref - x0), 1e-300)
 
 
-@pytest.mark.parametrize("threads,dof_tile,chunk", [(4, 0, 0), (8, 512, 4)])
-def test_multi_matches_pairs_stepped_alone(env, threads, dof_tile, chunk):
+@pytest.mark.parametrize("threads,dof_tile,chunk,slot_tiles",
+                         [(4, 0, 0, 0), (8, 512, 4, 1), (4, 65536, 16, 3)])
+def test_multi_matches_pairs_stepped_alone(env, threads, dof_tile, chunk, slot_tiles):
     """Eight instances of uneven sizes, two global steps: every pair's
     displacement within 1e-6 of the same pair stepped alone (both mixed
-    precision; the batched PCG differs only in the order of its sums), the
-    Schwarz iteration counts within one."""
+    precision; the batched PCG differs in its form and the order of its
+    sums), the Schwarz iteration counts within one.  Launch shapes: the
+    defaults; small DOF tiles and chunks; one DOF tile per system (its sums
+    skip the cross-block arrival count) with product work items of three
+    slot tiles."""
     torch, osmpm = env
     specs = [W.inclusion_instance(i) for i in range(8)]
     assert len({s[1].grid.dx for s in specs}) == 2
@@ -57,7 +61,8 @@ def test_multi_matches_pairs_stepped_alone(env, threads, dof_tile, chunk):
     dT = specs[0][3]
     for _ in range(2):
         stats, status, ms = osmpm.osmpm_schwarz_couple_multi(
-            B, S, dT, [s[2] for s in specs], n_threads=threads, dof_tile=dof_tile, chunk=chunk)
+            B, S, dT, [s[2] for s in specs], n_threads=threads, dof_tile=dof_tile, chunk=chunk,
+            slot_tiles=slot_tiles)
         assert all(s == osmpm.OSMPM_OK for s in status)
         assert ms["batches"] > 0 and ms["chunks"] >= ms["batches"] and ms["instances"] > 0
         assert 1 <= ms["max_batch"] <= len(specs)
