@@ -337,8 +337,9 @@ typedef struct osmpm_multi_stats {
   int64_t particle_iterations;  /* sum over the systems of iterations x particles */
   int64_t dof_iterations;       /* sum over the systems of iterations x grid DOFs */
   double device_ms;    /* device time of the batched PCGs (CUDA events) */
-  double hvp_ms;       /* of which the batched Hessian-vector products (k_m_hvp) */
-  int64_t hvp_launches;  /* launches of k_m_hvp */
+  double hvp_ms;       /* durations of the timed batched Hessian-vector product */
+  int64_t hvp_launches;  /* launches (k_m_hvp; those of every 8th chunk are timed) */
+  int64_t hvp_particle_iterations;  /* particle-iterations of the timed launches */
 } osmpm_multi_stats;
 
 osmpm_status osmpm_schwarz_couple_multi(osmpm_domain* const* coarse, osmpm_domain* const* fine,

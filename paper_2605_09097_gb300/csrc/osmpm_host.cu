@@ -868,8 +868,13 @@ struct PcgBatcher {
   char* dev = nullptr;
   char* host = nullptr;
   int* pending_host = nullptr;  // pending count, then per system: stop flag, iterations
-  cudaGraphExec_t exec = nullptr;
+  // the chunk's graph, and the same chunk with every product launch
+  // bracketed by event records (replayed every kTimedEvery-th chunk: the
+  // records cost ~6 % of the service's device time when in every chunk)
+  static constexpr int kTimedEvery = 8;
+  cudaGraphExec_t exec = nullptr, exec_timed = nullptr;
   long long per_chunk = 0;  // kernel launches in one replay
+  int64_t chunk_no = 0;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> hev;  // around each k_m_hvp of a chunk
   std::string error;
@@ -921,6 +926,7 @@ struct PcgBatcher {
     cv_work.notify_all();
     if (th.joinable()) th.join();
     if (exec) cudaGraphExecDestroy(exec);
+    if (exec_timed) cudaGraphExecDestroy(exec_timed);
     if (stream) cudaStreamSynchronize(stream);
     if (dev) cudaFreeAsync(dev, stream);
     if (stream) cudaStreamSynchronize(stream);
@@ -950,6 +956,7 @@ struct PcgBatcher {
   // (their PCG start runs before the next chunk).
   void loop() {
     std::vector<Req*> live;
+    std::vector<int> iters_before;  // per live system: its iterations before the chunk
     std::vector<int> fresh_flags;
     bool dirty = false;
     for (;;) {
@@ -964,6 +971,7 @@ struct PcgBatcher {
       if (!fresh.empty() || dirty) {
         const size_t old = live.size();
         live.insert(live.end(), fresh.begin(), fresh.end());
+        iters_before.resize(live.size(), 0);
         fresh_flags.assign(live.size(), 0);
         for (size_t i = old; i < live.size(); ++i) fresh_flags[i] = 1;
         st = build(live, fresh_flags);
@@ -976,14 +984,16 @@ struct PcgBatcher {
             if (dim == 2) MultiKernels<2>::start(mp, grid_dt, stream);
             else MultiKernels<3>::start(mp, grid_dt, stream);
           }
-          if (!exec) exec = capture();
+          if (!exec) exec = capture(false);
+          if (!exec_timed) exec_timed = capture(true);
         }
         dirty = false;
       }
-      if (st == OSMPM_OK) st = run_chunk(live.size());
+      if (st == OSMPM_OK) st = run_chunk(live, iters_before);
       // the systems that stopped leave (all of them after a failure)
       std::vector<Req*> done;
       std::vector<Req*> keep;
+      std::vector<int> keep_iters;
       for (size_t i = 0; i < live.size(); ++i) {
         const bool stopped = st != OSMPM_OK || pending_host[1 + 2 * i] != 0 ||
                              pending_host[2 + 2 * i] >= live[i]->d->desc.cg_max;
@@ -999,9 +1009,11 @@ struct PcgBatcher {
           }
         } else {
           keep.push_back(live[i]);
+          keep_iters.push_back(pending_host[2 + 2 * i]);
         }
       }
       live.swap(keep);
+      iters_before.swap(keep_iters);
       dirty = !done.empty();
       {
         std::lock_guard<std::mutex> lk(mu);
@@ -1047,7 +1059,8 @@ struct PcgBatcher {
       cap_dt = std::max(cap_dt, (int)dtl.size() + (int)dtl.size() / 2 + 64);
       lay = layout(cap_inst, cap_pt, cap_dt);
       if (exec) cudaGraphExecDestroy(exec);
-      exec = nullptr;
+      if (exec_timed) cudaGraphExecDestroy(exec_timed);
+      exec = exec_timed = nullptr;
       if (dev) cudaFreeAsync(dev, stream);
       if (host) cudaFreeHost(host);
       if (pending_host) cudaFreeHost(pending_host);
@@ -1081,10 +1094,11 @@ struct PcgBatcher {
     return OSMPM_OK;
   }
 
-  void enqueue_chunk(bool capturing) {
+  void enqueue_chunk(bool capturing, bool timed) {
     const MultiArgs* mp = (const MultiArgs*)dev;
     for (int c = 0; c < chunk; ++c) {
-      cudaEvent_t e0 = hev[(size_t)2 * c], e1 = hev[(size_t)2 * c + 1];
+      cudaEvent_t e0 = timed ? hev[(size_t)2 * c] : nullptr;
+      cudaEvent_t e1 = timed ? hev[(size_t)2 * c + 1] : nullptr;
       if (dim == 2) MultiKernels<2>::iteration(mp, grid_pt, grid_dt, stream, e0, e1, capturing);
       else MultiKernels<3>::iteration(mp, grid_pt, grid_dt, stream, e0, e1, capturing);
     }
@@ -1095,13 +1109,13 @@ struct PcgBatcher {
   }
 
   // The chunk as a CUDA graph over the current block (nullptr: plain
-  // launches).
-  cudaGraphExec_t capture() {
+  // launches); timed: with the product launches bracketed by events.
+  cudaGraphExec_t capture(bool timed) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t ex = nullptr;
     const long long before = g_launch_count.load();
     if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      enqueue_chunk(true);
+      enqueue_chunk(true, timed);
       if (cudaStreamEndCapture(stream, &graph) != cudaSuccess || !graph ||
           cudaGraphInstantiate(&ex, graph, 0) != cudaSuccess)
         ex = nullptr;
@@ -1113,16 +1127,17 @@ struct PcgBatcher {
     return ex;
   }
 
-  osmpm_status run_chunk(size_t n) {
+  osmpm_status run_chunk(const std::vector<Req*>& live, const std::vector<int>& iters_before) {
     NvtxRange nvtx_("batched_pcg_chunk");
-    (void)n;
+    const bool timed = (chunk_no++ % kTimedEvery) == 0;
+    cudaGraphExec_t g = timed ? exec_timed : exec;
     cudaEventRecord(ev[0], stream);
     cudaError_t e;
-    if (exec) {
-      e = cudaGraphLaunch(exec, stream);
+    if (g) {
+      e = cudaGraphLaunch(g, stream);
       g_launch_count += per_chunk;
     } else {
-      enqueue_chunk(false);
+      enqueue_chunk(false, timed);
       e = cudaGetLastError();
     }
     cudaEventRecord(ev[1], stream);
@@ -1132,14 +1147,21 @@ struct PcgBatcher {
     cudaEventElapsedTime(&ms, ev[0], ev[1]);
     stats.chunks += 1;
     stats.device_ms += ms;
-    for (int c = 0; c < chunk; ++c) {
-      float h = 0.f;
-      if (cudaEventElapsedTime(&h, hev[(size_t)2 * c], hev[(size_t)2 * c + 1]) == cudaSuccess) {
-        stats.hvp_ms += h;
-        stats.hvp_launches += 1;
+    if (timed) {
+      for (int c = 0; c < chunk; ++c) {
+        float h = 0.f;
+        if (cudaEventElapsedTime(&h, hev[(size_t)2 * c], hev[(size_t)2 * c + 1]) == cudaSuccess) {
+          stats.hvp_ms += h;
+          stats.hvp_launches += 1;
+        }
       }
+      cudaGetLastError();
+      // the particle-iterations those launches carried: each system's
+      // iterations in this chunk times its particles
+      for (size_t i = 0; i < live.size(); ++i)
+        stats.hvp_particle_iterations +=
+            (int64_t)std::max(0, pending_host[2 + 2 * i] - iters_before[i]) * live[i]->d->n;
     }
-    cudaGetLastError();
     return OSMPM_OK;
   }
 };

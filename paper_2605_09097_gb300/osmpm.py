@@ -124,7 +124,7 @@ class osmpm_multi_stats(Structure):
                 ("max_batch", c_int64), ("particles", c_int64), ("dofs", c_int64),
                 ("iterations", c_int64), ("particle_iterations", c_int64),
                 ("dof_iterations", c_int64), ("device_ms", c_double), ("hvp_ms", c_double),
-                ("hvp_launches", c_int64)]
+                ("hvp_launches", c_int64), ("hvp_particle_iterations", c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

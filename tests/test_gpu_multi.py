@@ -67,6 +67,9 @@ def test_multi_matches_pairs_stepped_alone(env, threads, dof_tile, chunk, slot_t
         assert ms["batches"] > 0 and ms["chunks"] >= ms["batches"] and ms["instances"] > 0
         assert 1 <= ms["max_batch"] <= len(specs)
         assert ms["iterations"] > 0 and ms["particle_iterations"] >= ms["iterations"]
+        # the timed sample of product launches (every 8th chunk)
+        assert ms["hvp_launches"] > 0 and ms["hvp_ms"] > 0.0
+        assert 0 < ms["hvp_particle_iterations"] <= ms["particle_iterations"]
         for i in range(len(specs)):
             st1 = osmpm.osmpm_schwarz_couple(B1[i], S1[i], dT, specs[i][2])
             assert abs(stats[i]["schwarz_iters"] - st1["schwarz_iters"]) <= 1
