@@ -260,7 +260,9 @@ osmpm_status osmpm_schwarz_couple(osmpm_domain* coarse, osmpm_domain* fine, doub
  * the other pairs' ordinary kernels (their grid barriers never wait on a
  * block another grid keeps out).  The worker threads launch directly
  * (launch_mode 0 graphs are built and replayed only by calls made from the
- * caller's thread).  Calls that drive domains concurrently
+ * caller's thread).  A pair whose PCG reports OSMPM_E_TIMEOUT (a grid
+ * barrier gave up waiting) is back at t_n and runs its step once more on
+ * half that grid.  Calls that drive domains concurrently
  * from several host threads must go through this entry point.  stats and
  * status (either may be NULL) receive n entries.  Returns OSMPM_OK, or the
  * status of the first failing pair (message names the pair), or

@@ -2597,6 +2597,16 @@ osmpm_status osmpm_schwarz_couple_batch(osmpm_domain* const* coarse, osmpm_domai
       if (i >= n) break;
       osmpm_stats s;
       st[(size_t)i] = osmpm_schwarz_couple(coarse[i], fine[i], dT, &sdesc[i], &s);
+      if (st[(size_t)i] == OSMPM_E_TIMEOUT) {
+        // a grid barrier of the pair's cooperative PCG gave up waiting (its
+        // blocks could not all become resident beside the other pairs'
+        // work); a failed coupled step leaves the pair at t_n (the fine
+        // particles restored, the coarse ones not yet committed), so it is
+        // run again once on half the grid
+        coarse[i]->pcg_share = fine[i]->pcg_share = 2 * threads;
+        st[(size_t)i] = osmpm_schwarz_couple(coarse[i], fine[i], dT, &sdesc[i], &s);
+        coarse[i]->pcg_share = fine[i]->pcg_share = threads;
+      }
       if (stats) stats[i] = s;
       if (st[(size_t)i] != OSMPM_OK) msg[(size_t)i] = g_last_error;
     }
