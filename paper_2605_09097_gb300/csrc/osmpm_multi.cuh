@@ -87,15 +87,21 @@ __global__ void __launch_bounds__(kThreads) k_m_start(const MultiArgs* __restric
     const PcgArgsT<float>& a = m.inst[T.inst];
     const int64_t nn = a.g.nn;
     double acc[1] = {0.0};
-    for (int64_t idx = T.lo + threadIdx.x; idx < T.hi; idx += blockDim.x) {
-      const int c = (int)(idx / nn);
-      const int64_t i = idx - (int64_t)c * nn;
+    int64_t idx = T.lo + threadIdx.x;
+    int c = (int)(idx / nn);  // component and node of idx, then stepped
+    int64_t i = idx - (int64_t)c * nn;
+    for (; idx < T.hi; idx += blockDim.x) {
       a.w[0][idx] = 0.0;
       a.s[0][idx] = 0.0;
       a.s[1][idx] = 0.0;
       if ((a.dofmask[i] >> c) & 1u) {
         const double ui = a.r[1][idx];
         acc[0] += a.m[i] * a.inv_dt2 * ui * ui;
+      }
+      i += blockDim.x;
+      while (i >= nn) {
+        i -= nn;
+        ++c;
       }
     }
     const MultiInfo in = m.info[T.inst];
@@ -185,27 +191,45 @@ __global__ void __launch_bounds__(kThreads) k_m_update(const MultiArgs* __restri
     }
     const double alpha = __ldcg(&S->alpha), beta = __ldcg(&S->beta);
     const int it = __ldcg(&S->cg_iter);
+    // the instance's vectors, distinct arrays (loads may pass the stores)
+    const double* __restrict__ mass = a.m;
+    const uint8_t* __restrict__ mask = a.dofmask;
+    const double* __restrict__ dg = a.diag;
+    double* __restrict__ w = a.w[0];
+    double* __restrict__ u = a.r[1];
+    double* __restrict__ r = a.r[0];
+    double* __restrict__ p = a.s[0];
+    double* __restrict__ sv = a.s[1];
+    double* __restrict__ x = a.x;
+    const double idt2 = a.inv_dt2;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t idx = T.lo + threadIdx.x; idx < T.hi; idx += blockDim.x) {
-      const int c = (int)(idx / nn);
-      const int64_t i = idx - (int64_t)c * nn;
-      const double wi = a.w[0][idx];
-      a.w[0][idx] = 0.0;
-      if (!((a.dofmask[i] >> c) & 1u)) continue;
-      const double mi = a.m[i] * a.inv_dt2;
-      const double ui = a.r[1][idx];
-      const double pi = ui + beta * a.s[0][idx];
-      const double si = (wi + mi * ui) + beta * a.s[1][idx];
-      a.s[0][idx] = pi;
-      a.s[1][idx] = si;
-      a.x[idx] += alpha * pi;
-      const double ri = a.r[0][idx] - alpha * si;
-      a.r[0][idx] = ri;
-      const double un = ri * a.diag[idx];
-      a.r[1][idx] = un;
-      acc[0] += ri * un;
-      acc[1] += ri * ri;
-      acc[2] += mi * un * un;
+    int64_t idx = T.lo + threadIdx.x;
+    int c = (int)(idx / nn);  // component and node of idx, then stepped
+    int64_t i = idx - (int64_t)c * nn;
+    for (; idx < T.hi; idx += blockDim.x) {
+      const double wi = w[idx];
+      w[idx] = 0.0;
+      if ((mask[i] >> c) & 1u) {
+        const double mi = mass[i] * idt2;
+        const double ui = u[idx];
+        const double pi = ui + beta * p[idx];
+        const double si = (wi + mi * ui) + beta * sv[idx];
+        p[idx] = pi;
+        sv[idx] = si;
+        x[idx] += alpha * pi;
+        const double ri = r[idx] - alpha * si;
+        r[idx] = ri;
+        const double un = ri * dg[idx];
+        u[idx] = un;
+        acc[0] += ri * un;
+        acc[1] += ri * ri;
+        acc[2] += mi * un * un;
+      }
+      i += blockDim.x;
+      while (i >= nn) {
+        i -= nn;
+        ++c;
+      }
     }
     const MultiInfo in = m.info[T.inst];
     double tot[3];

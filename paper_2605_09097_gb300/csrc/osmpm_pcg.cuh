@@ -607,14 +607,24 @@ __global__ void __launch_bounds__(kThreads) k_pcg(PcgArgsT<R> a) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int64_t cgs_tid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t cgs_stride() { return (int64_t)gridDim.x * blockDim.x; }
+// Steps the (component, node) pair of a flat DOF index idx = c nn + i by
+// `step` DOFs without a 64-bit division per DOF.
+__device__ __forceinline__ void dof_step(int& c, int64_t& i, int64_t step, int64_t nn) {
+  i += step;
+  while (i >= nn) {
+    i -= nn;
+    ++c;
+  }
+}
 
 template <int D, typename R>
 __global__ void __launch_bounds__(kThreads) k_cgs_start(PcgArgsT<R> a) {
   const GridGeo& g = a.g;
   double acc[1] = {0.0};
-  for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
-    const int c = (int)(idx / g.nn);
-    const int64_t i = idx - (int64_t)c * g.nn;
+  int64_t idx = cgs_tid();
+  int c = (int)(idx / g.nn);
+  int64_t i = idx - (int64_t)c * g.nn;
+  for (const int64_t step = cgs_stride(); idx < g.nn * D; idx += step, dof_step(c, i, step, g.nn)) {
     a.w[0][idx] = 0.0;
     if ((a.dofmask[i] >> c) & 1u) {
       const double pi = a.s[0][idx];
@@ -661,12 +671,14 @@ __global__ void __launch_bounds__(kThreads) k_cgs_alpha(PcgArgsT<R> a) {
   const int it = __ldcg(&S->cg_iter);
   if (!(pAp > 0.0)) {
     // negative curvature: stop; with no direction yet take z_0 = D^-1 r_0
-    if (it == 0)
-      for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
-        const int c = (int)(idx / g.nn);
-        const int64_t i = idx - (int64_t)c * g.nn;
+    if (it == 0) {
+      int64_t idx = cgs_tid();
+      int c = (int)(idx / g.nn);
+      int64_t i = idx - (int64_t)c * g.nn;
+      for (const int64_t step = cgs_stride(); idx < g.nn * D; idx += step, dof_step(c, i, step, g.nn)) {
         if ((a.dofmask[i] >> c) & 1u) a.x[idx] = a.s[0][idx];
       }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       S->cg_neg = 1;
       S->cg_done = 1;
@@ -677,9 +689,10 @@ __global__ void __launch_bounds__(kThreads) k_cgs_alpha(PcgArgsT<R> a) {
   double* r = a.r[0];
   double* z = a.r[1];
   double acc[2] = {0.0, 0.0};
-  for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
-    const int c = (int)(idx / g.nn);
-    const int64_t i = idx - (int64_t)c * g.nn;
+  int64_t idx = cgs_tid();
+  int c = (int)(idx / g.nn);
+  int64_t i = idx - (int64_t)c * g.nn;
+  for (const int64_t step = cgs_stride(); idx < g.nn * D; idx += step, dof_step(c, i, step, g.nn)) {
     if ((a.dofmask[i] >> c) & 1u) {
       const double pi = a.s[0][idx];
       a.x[idx] += alpha * pi;
@@ -711,9 +724,10 @@ __global__ void __launch_bounds__(kThreads) k_cgs_beta(PcgArgsT<R> a) {
   const double beta = __ldcg(&S->beta);
   const double* z = a.r[1];
   double acc[1] = {0.0};
-  for (int64_t idx = cgs_tid(); idx < g.nn * D; idx += cgs_stride()) {
-    const int c = (int)(idx / g.nn);
-    const int64_t i = idx - (int64_t)c * g.nn;
+  int64_t idx = cgs_tid();
+  int c = (int)(idx / g.nn);
+  int64_t i = idx - (int64_t)c * g.nn;
+  for (const int64_t step = cgs_stride(); idx < g.nn * D; idx += step, dof_step(c, i, step, g.nn)) {
     a.w[0][idx] = 0.0;
     if ((a.dofmask[i] >> c) & 1u) {
       const double pi = z[idx] + beta * a.s[0][idx];
