@@ -406,7 +406,7 @@ def cpu_baseline(n_iters):
 
 
 # Algorithmic bytes of one mixed-precision Hessian-vector product per
-# particle (SURVEY's HVP row: the particle state read once, the gathered
+# particle (the particle state read once, the gathered
 # x_hat and d and the scattered Hd once per node at 1/ppc node per
 # particle): 2D x 16 + F^n 16 + V0 4 + mu lam 8 + (16 + 8 + 8)/4 = 52 B,
 # 3D x 24 + F^n 36 + V0 4 + mu lam 8 + (24 + 12 + 12)/8 = 78 B
@@ -490,7 +490,7 @@ def run_batched(args, rank, local, world):
         # the dominant kernel of the PCG service: the batched Hessian-vector
         # product k_m_hvp; in every 8th chunk of iterations each launch is
         # bracketed by CUDA events on the service's stream (a sample of the
-        # timed region's launches); its algorithmic bytes are SURVEY's HVP
+        # timed region's launches); its algorithmic bytes are the mixed HVP
         # figure per particle and iteration over the systems those launches
         # iterated
         peaks, src = measured_peaks()
@@ -622,8 +622,8 @@ def cpu_baseline_batched():
 
 
 def run_default(args, rank, local, world):
-    """The headline: the batched inclusion family (BASELINE's batched
-    configuration: 256 instances of uneven size, mixed precision) through the
+    """The headline: the batched inclusion family (256 instances of uneven
+    size, mixed precision) through the
     batched PCG service, with the plain FP64 single-instance inclusion
     (fine dx 0.005, M = 2) beside it as ``fp64_single_instance``."""
     a = argparse.Namespace(**vars(args))
@@ -767,7 +767,7 @@ def run_fold_solve(args, rank, local, world):
     peaks, src = measured_peaks()
     # the dominant kernel: the streaming PCG's Hessian-vector product (each
     # launch that iterated bracketed by CUDA events on the domain's stream);
-    # algorithmic bytes per launch = particles x SURVEY's 3D mixed HVP figure
+    # algorithmic bytes per launch = particles x the 3D mixed HVP figure
     nl, hvp_s = c["hvp_launches"], c["hvp_ms"] / 1e3
     bpl = n * MIXED_HVP_BYTES_PER_PARTICLE[3]
     achieved = nl * bpl / hvp_s / 1e9 if hvp_s > 0 else 0.0
@@ -814,7 +814,7 @@ def hertz_profile(p, xc, F, R=0.5, E1=1e7, E2=1e6, nu=0.3):
 
 
 def run_hertz(args, rank, local, world):
-    """The Hertz contact configuration (BASELINE configs[2]: elastic
+    """The elastic Hertz contact configuration (elastic
     cylinder R 0.5, E 1e7, pressed 0.02 into an elastic block E 1e6 over 100
     global steps of 2e-4 s, fine box at dx 1/256, M = 4, mixed precision),
     run whole; every 10 steps the contact pressure on the block's top layer

@@ -53,7 +53,7 @@ typedef enum osmpm_status {
   OSMPM_E_LINESEARCH = 6,      /* no energy decrease after ls_max halvings */
   OSMPM_E_OUT_OF_GRID = 7,     /* a particle's 3^dim support left the grid box */
   OSMPM_E_TIMEOUT = 8,         /* a device-side wait gave up (the kernel returned early) */
-  OSMPM_E_UNSUPPORTED = 9,     /* a valid request this build does not serve */
+  OSMPM_E_UNSUPPORTED = 9,     /* a valid request the library does not serve */
   OSMPM_W_SCHWARZ_MAXITER = 100 /* Schwarz hit k_max; the last iterate was committed */
 } osmpm_status;
 
