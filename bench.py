@@ -63,8 +63,7 @@ L2_FLUSH_BYTES = 256 << 20
 AUTOTUNE_THREADS = [8, 12, 16]
 # (host threads, DOFs per DOF tile, PCG iterations per graph replay, slot
 # tiles per work item of the batched product)
-AUTOTUNE_MULTI = [(128, 2048, 16, 1), (128, 2048, 16, 2), (128, 2048, 16, 4),
-                  (192, 2048, 16, 2)]
+AUTOTUNE_MULTI = [(128, 2048, 16, 1), (128, 2048, 16, 2), (128, 2048, 16, 4)]
 # dram__bytes_read.sum + dram__bytes_write.sum of one fine-domain k_pcg
 # launch, from the ncu capture of the current kernel (the k_pcg profile
 # summary of this workload); None whenever the kernel changes
