@@ -1,7 +1,7 @@
-// Batched streaming PCG over many domains in mixed precision (the batched
-// growth line of the project, not a passage of the paper): the Jacobi PCG of
-// k_cgs_start / k_cgs_hvp_tile / k_cgs_alpha / k_cgs_beta run for a set of
-// independent Newton systems at once.  A work list of tiles, (instance,
+// Batched streaming PCG over many domains in mixed precision (a service for
+// many independent instances, not a passage of the paper): the Jacobi PCG
+// of the streaming kernels, with the tiled Hessian-vector product of
+// k_cgs_hvp_tile, run for a set of independent Newton systems at once.  A work list of tiles, (instance,
 // item range) over particles or over DOFs and grouped by instance, is dealt
 // to the blocks of each launch (fixed grids, grid stride; the kernels read
 // the work list from a device argument block, so a captured graph serves
