@@ -1,12 +1,13 @@
 // Batched streaming PCG over many domains in mixed precision (a service for
 // many independent instances, not a passage of the paper): the Jacobi PCG
 // of the streaming kernels, with the tiled Hessian-vector product of
-// k_cgs_hvp_tile, run for a set of independent Newton systems at once.  A work list of tiles, (instance,
-// item range) over particles or over DOFs and grouped by instance, is dealt
-// to the blocks of each launch (fixed grids, grid stride; the kernels read
-// the work list from a device argument block, so a captured graph serves
-// every work list); every instance keeps its own scalars (its domain's
-// DevScalars) and stops on its own.  Per-instance sums use the
+// k_cgs_hvp_tile, run for a set of independent Newton systems at once.  A
+// work list of tiles, (instance, item range) over particles or over DOFs
+// and grouped by instance, is dealt to the blocks of each launch (fixed
+// grids, grid stride; the kernels read the work list from a device
+// argument block, so a captured graph serves every work list); every
+// instance keeps its own scalars (its domain's DevScalars) and stops on its
+// own.  Per-instance sums use the
 // instance's arrival counter: each tile stores its partial, and the last
 // tile of an instance to arrive adds that instance's partials in tile order
 // (so the sums do not depend on scheduling) and updates the scalars.
