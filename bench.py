@@ -433,7 +433,8 @@ def run_batched(args, rank, local, world):
     from paper_2605_09097_gb300 import build
     build.build()
     from paper_2605_09097_gb300 import osmpm
-    specs = [W.inclusion_instance(i) for i in range(args.instances)]
+    scaled = bool(getattr(args, "scaled", False))
+    specs = [W.inclusion_instance(i, scaled=scaled) for i in range(args.instances)]
     prec = 1 if args.precision == "mixed" else 0
     B, S, streams = [], [], []
     for cB, cS, sch, dT in specs:
@@ -558,7 +559,8 @@ def run_batched(args, rank, local, world):
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32/f64",
             "data": "synthetic",
-            "config": {"workload": f"batched_inclusion_{args.instances}_literal_"
+            "config": {"workload": f"batched_inclusion_{args.instances}_"
+                                   f"{'scaled' if scaled else 'literal'}_"
                                    f"{'mixed' if prec else 'fp64'}",
                        "instances": args.instances, "host_threads": threads,
                        "batch_mode": args.batch_mode, "launch_shape": shape,
@@ -571,7 +573,8 @@ def run_batched(args, rank, local, world):
                        "timing": "host wall clock around each batched step, device synchronised "
                                  "on both sides (the pairs run on their own streams)",
                        "l2": "not flushed: the instances' resident state (~0.6 KB per particle, "
-                             "1.96M particles at 256 instances) is larger than L2",
+                             f"{sum(s[0].particles.n + s[1].particles.n for s in specs):,} "
+                             "particles) is larger than L2",
                        "parallelism": f"replicas{world}"},
             "gpu_launches": launches, "roofline": roofline, "clocks": clk, "e2e": e2e}
 
@@ -877,7 +880,9 @@ def main():
                          "many instances; fold3d: the 3D folding plate (mixed); fold3d_solve: the "
                          "fold's 3.07M-particle band folded on its own; hertz: the contact "
                          "configuration's pressure against the Hertz closed form (a study)")
-    ap.add_argument("--scaled", action="store_true", help="fold3d: the 3.07M-particle band")
+    ap.add_argument("--scaled", action="store_true",
+                    help="fold3d: the 3.07M-particle band; batched: the scaled family (fine dx "
+                         "0.0025 / 0.001, 45k / 283k fine particles per instance)")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--threads", type=int, default=0,
                     help="host threads of the batched workload; 0: chosen by the autotuner")
